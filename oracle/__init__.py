@@ -1,0 +1,234 @@
+"""FP64 CPU oracle of the differentiable XPBD step (ctypes wrapper of ``xpbd_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py``; the product path never imports it.  It shares no code
+with the CUDA library: it takes a ``Scene`` (plain arrays from the seeded generators) and
+computes everything else itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from .build import build as _build, LIB_PATH
+
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class _Model(C.Structure):
+    _fields_ = [("V", C.c_int32), ("rest_x", _dp), ("inv_mass", _dp),
+                ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
+                ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _dp),
+                ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("compliance", _dp),
+                ("f_global", _dp), ("f_vertex", _dp), ("collider_flags", C.c_int32),
+                ("plane_h", C.c_double), ("sphere", C.c_double * 4),
+                ("contact_compliance", C.c_double), ("thickness", C.c_double)]
+
+
+class _Direction(C.Structure):
+    _fields_ = [("d_compliance", _dp), ("d_x0", _dp), ("d_v0", _dp), ("d_f_global", _dp),
+                ("d_f_vertex", _dp), ("d_collider", _dp)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            _build()
+        _lib = C.CDLL(LIB_PATH)
+        _lib.oracle_forward.restype = C.c_int
+        _lib.oracle_adjoint.restype = C.c_int
+        _lib.oracle_tangent.restype = C.c_int
+        _lib.oracle_constraint.restype = C.c_int
+        _lib.oracle_num_threads.restype = C.c_int
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+class _Args:
+    """Keeps the numpy buffers alive while the C structs point into them."""
+
+    def __init__(self, scene, compliance=None, f_global=None, f_vertex=None, plane_h=None,
+                 sphere=None, steps=None):
+        keep = []
+
+        def d(a):
+            arr, p = _d(a)
+            keep.append(arr)
+            return p
+
+        def i(a):
+            arr, p = _i(a)
+            keep.append(arr)
+            return p
+
+        s = scene
+        self.model = _Model(V=s.V, rest_x=d(s.rest_x), inv_mass=d(s.inv_mass),
+                            n_dist=s.n_dist, dist_idx=i(s.dist_idx.reshape(-1)),
+                            n_bend=s.n_bend, bend_idx=i(s.bend_idx.reshape(-1)),
+                            n_tet=s.n_tet, tet_idx=i(s.tet_idx.reshape(-1)),
+                            tet_gamma=d(s.tet_gamma) if s.n_tet else None,
+                            n_colors=s.n_colors, color_offsets=i(s.color_offsets),
+                            color_order=i(s.color_order))
+        comp = s.compliance if compliance is None else compliance
+        fg = s.f_global if f_global is None else f_global
+        fv = s.f_vertex if f_vertex is None else f_vertex
+        if fg is not None and steps is not None:
+            fg = np.asarray(fg, np.float64).reshape(-1, 3)
+            if fg.shape[0] < steps:
+                raise ValueError("f_global has fewer rows than steps")
+        sph = s.sphere if sphere is None else sphere
+        self.params = _Params(dt=s.dt, gravity=(C.c_double * 3)(*s.gravity), compliance=d(comp),
+                              f_global=d(fg), f_vertex=d(fv), collider_flags=s.collider_flags,
+                              plane_h=s.plane_h if plane_h is None else plane_h,
+                              sphere=(C.c_double * 4)(*sph),
+                              contact_compliance=s.contact_compliance, thickness=s.thickness)
+        self.keep = keep
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def forward(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, x0=None, v0=None,
+            compliance=None, f_global=None, f_vertex=None, plane_h=None, sphere=None):
+    """Run the FP64 forward simulation; returns (xs, vs), each [steps+1, V, 3]."""
+    steps = scene.steps if steps is None else steps
+    iters = scene.iters if iters is None else iters
+    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps)
+    x0a, x0p = _d(scene.x0 if x0 is None else x0)
+    v0a, v0p = _d(scene.v0 if v0 is None else v0)
+    xs = np.zeros((steps + 1, scene.V, 3))
+    vs = np.zeros((steps + 1, scene.V, 3))
+    lib().oracle_forward(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p,
+                         xs.ctypes.data_as(_dp), vs.ctypes.data_as(_dp))
+    return xs, vs
+
+
+def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
+            seed_dv_T=None, x0=None, v0=None, compliance=None, f_global=None, f_vertex=None,
+            plane_h=None, sphere=None) -> dict:
+    """Reverse sweep.  ``seeds`` maps step n -> dL/dx_n [V,3].  Returns a dict of FP64
+    gradients: compliance [m], x0 [V,3], v0 [V,3], f_global [steps,3], f_vertex [V,3],
+    collider [5] (plane h, sphere cx, cy, cz, r)."""
+    steps = scene.steps if steps is None else steps
+    iters = scene.iters if iters is None else iters
+    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps)
+    x0a, x0p = _d(scene.x0 if x0 is None else x0)
+    v0a, v0p = _d(scene.v0 if v0 is None else v0)
+    keys = sorted(seeds)
+    ss, ssp = _i(np.asarray(keys, np.int32) if keys else np.zeros(1, np.int32))
+    sd, sdp = _d(np.stack([np.asarray(seeds[k], np.float64).reshape(-1) for k in keys])
+                 if keys else np.zeros(1))
+    dv, dvp = _d(None if seed_dv_T is None else np.asarray(seed_dv_T).reshape(-1))
+    out = dict(compliance=np.zeros(scene.m), x0=np.zeros((scene.V, 3)), v0=np.zeros((scene.V, 3)),
+               f_global=np.zeros((steps, 3)), f_vertex=np.zeros((scene.V, 3)), collider=np.zeros(5))
+    P = lambda k: out[k].ctypes.data_as(_dp)
+    lib().oracle_adjoint(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p, len(keys),
+                         ssp, sdp, dvp, P("compliance"), P("x0"), P("v0"), P("f_global"),
+                         P("f_vertex"), P("collider"))
+    return out
+
+
+def tangent(scene, direction: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
+            x0=None, v0=None, compliance=None, f_global=None, f_vertex=None):
+    """Forward-mode derivative along ``direction`` (keys as in ``adjoint``'s output).
+    Returns (dxs, dvs), each [steps+1, V, 3]."""
+    steps = scene.steps if steps is None else steps
+    iters = scene.iters if iters is None else iters
+    a = _Args(scene, compliance, f_global, f_vertex, None, None, steps)
+    x0a, x0p = _d(scene.x0 if x0 is None else x0)
+    v0a, v0p = _d(scene.v0 if v0 is None else v0)
+    keep = []
+
+    def dd(k):
+        if direction.get(k) is None:
+            return None
+        arr, p = _d(np.asarray(direction[k]).reshape(-1))
+        keep.append(arr)
+        return p
+
+    D = _Direction(d_compliance=dd("compliance"), d_x0=dd("x0"), d_v0=dd("v0"),
+                   d_f_global=dd("f_global"), d_f_vertex=dd("f_vertex"), d_collider=dd("collider"))
+    dxs = np.zeros((steps + 1, scene.V, 3))
+    dvs = np.zeros((steps + 1, scene.V, 3))
+    lib().oracle_tangent(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p, C.byref(D),
+                         dxs.ctypes.data_as(_dp), dvs.ctypes.data_as(_dp))
+    return dxs, dvs
+
+
+def rest_data(scene) -> np.ndarray:
+    """Per constraint id: (L, theta0, B[0..8], vol) as derived by the oracle."""
+    a = _Args(scene)
+    out = np.zeros((scene.m, 12))
+    lib().oracle_rest_data(C.byref(a.model), out.ctypes.data_as(_dp))
+    return out
+
+
+KIND = dict(dist=0, bend=1, tet_h=2, tet_d=3, plane=4, sphere=5)
+N_INPUTS = {0: 6, 1: 12, 2: 12, 3: 12, 4: 4, 5: 7}
+
+
+def constraint(kind, q, rest12=None, u=None):
+    """One constraint in isolation: (C, grad, H u) by automatic differentiation."""
+    k = KIND[kind] if isinstance(kind, str) else int(kind)
+    n = N_INPUTS[k]
+    q, qp = _d(np.asarray(q, np.float64).reshape(-1))
+    r, rp = _d(np.zeros(12) if rest12 is None else np.asarray(rest12, np.float64))
+    Cv = C.c_double(0.0)
+    g = np.zeros(n)
+    hu = np.zeros(n)
+    ua, up = _d(None if u is None else np.asarray(u, np.float64).reshape(-1))
+    lib().oracle_constraint(k, qp, rp, up, C.byref(Cv), g.ctypes.data_as(_dp),
+                            hu.ctypes.data_as(_dp) if u is not None else None)
+    return Cv.value, g, (hu if u is not None else None)
+
+
+def project_one(kind, q, w, rest12, lam, alpha_tilde):
+    """One XPBD update of one constraint; returns (q', lambda')."""
+    k = KIND[kind] if isinstance(kind, str) else int(kind)
+    q = np.array(q, np.float64).reshape(-1)
+    wa, wp = _d(np.asarray(w, np.float64))
+    ra, rp = _d(np.asarray(rest12, np.float64))
+    l = C.c_double(lam)
+    lib().oracle_project_one(k, q.ctypes.data_as(_dp), wp, rp, C.byref(l), C.c_double(alpha_tilde))
+    return q, l.value
+
+
+def vjp_one(kind, q, w, rest12, lam, alpha_tilde, qbar, lambar):
+    """Reverse of ``project_one``: returns (qbar, lambar, alpha_tilde_bar)."""
+    k = KIND[kind] if isinstance(kind, str) else int(kind)
+    qa, qp = _d(np.asarray(q, np.float64).reshape(-1))
+    wa, wp = _d(np.asarray(w, np.float64))
+    ra, rp = _d(np.asarray(rest12, np.float64))
+    qb = np.array(qbar, np.float64).reshape(-1)
+    lb = C.c_double(lambar)
+    ab = C.c_double(0.0)
+    lib().oracle_vjp_one(k, qp, wp, rp, C.c_double(lam), C.c_double(alpha_tilde),
+                         qb.ctypes.data_as(_dp), C.byref(lb), C.byref(ab))
+    return qb, lb.value, ab.value

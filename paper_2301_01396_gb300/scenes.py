@@ -1,0 +1,451 @@
+"""Seeded synthetic scene generators.
+
+This module is the one piece of code shared by the CUDA path (its tests, ``bench.py``)
+and the FP64 oracle's tests.  It builds meshes, constraint topology, graph colorings,
+masses, start states and seeded parameter draws, and nothing else: it evaluates no
+constraint, projects nothing and differentiates nothing.  Rest lengths, rest angles,
+reference shape matrices and rest volumes are computed independently by each side from
+``rest_x``.
+
+Every float this module emits is rounded to a value FP32 represents exactly, so the FP32
+GPU path and the FP64 oracle start from identical inputs.
+
+Constraint id space (used by ``compliance`` and the coloring):
+    [0, nd)                 distance constraints        (``dist_idx`` rows)
+    [nd, nd+nb)             dihedral bending hinges     (``bend_idx`` rows: edge v0-v1, wings v2, v3)
+    [nd+nb, nd+nb+nt)       tet hydrostatic  C_H = det F - gamma
+    [nd+nb+nt, nd+nb+2nt)   tet deviatoric   C_D = ||F||_F
+Compliance units: distance and bending constraints take the constraint compliance alpha
+directly (Sec. 3.1, Eq. xpbdUenergy); tet constraints take the inverse Lame modulus
+alpha_hat, and the constraint compliance is alpha_hat / V_e (V_e the rest volume).
+
+Workload recipes follow the five synthetic configurations: plain pinned cloth (16x16),
+cloth with bending on a ground plane (256x256), a 5-tet-per-cube block falling on a ground
+plane (32^3 cells), a 2950x2950 cloth draped on a sphere with per-frame and per-vertex
+forces, and a mixed serving stream.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+COLLIDE_PLANE = 1
+COLLIDE_SPHERE = 2
+
+
+def f32(a) -> np.ndarray:
+    """Round to FP32-representable values, returned as float64."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@dataclass
+class Scene:
+    """A complete simulation input: topology, coloring, start state and parameters."""
+
+    rest_x: np.ndarray                  # [V,3] rest positions (define L, theta0, Dm^-1, V_e)
+    inv_mass: np.ndarray                # [V] w = 1/m, 0 = pinned
+    dist_idx: np.ndarray                # [nd,2] int32
+    bend_idx: np.ndarray                # [nb,4] int32  (edge v0,v1; wing v2 side A, wing v3 side B)
+    tet_idx: np.ndarray                 # [nt,4] int32  (positively oriented)
+    tet_gamma: np.ndarray               # [nt] hydrostatic rest offset gamma
+    color_offsets: np.ndarray           # [K+1] int32
+    color_order: np.ndarray             # [m] int32 global constraint ids, color by color
+    x0: np.ndarray                      # [V,3]
+    v0: np.ndarray                      # [V,3]
+    compliance: np.ndarray              # [m]
+    dt: float = 1.0 / 60.0
+    gravity: tuple = (0.0, -9.81, 0.0)
+    steps: int = 1
+    iters: int = 1
+    collider_flags: int = 0
+    plane_h: float = 0.0
+    sphere: tuple = (0.0, 0.0, 0.0, 0.0)   # cx, cy, cz, r
+    contact_compliance: float = 1e-8
+    thickness: float = 0.0
+    f_global: Optional[np.ndarray] = None  # [steps,3] force added to every vertex at step n
+    f_vertex: Optional[np.ndarray] = None  # [V,3] time-constant per-vertex force
+    name: str = "scene"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def V(self) -> int:
+        return int(self.rest_x.shape[0])
+
+    @property
+    def n_dist(self) -> int:
+        return int(self.dist_idx.shape[0])
+
+    @property
+    def n_bend(self) -> int:
+        return int(self.bend_idx.shape[0])
+
+    @property
+    def n_tet(self) -> int:
+        return int(self.tet_idx.shape[0])
+
+    @property
+    def m(self) -> int:
+        return self.n_dist + self.n_bend + 2 * self.n_tet
+
+    @property
+    def n_colors(self) -> int:
+        return int(self.color_offsets.shape[0] - 1)
+
+    def with_(self, **kw) -> "Scene":
+        return replace(self, **kw)
+
+
+# ----------------------------------------------------------------------------------------
+# coloring helpers (host logic: graph coloring is an input of the solver, Sec. 3.1)
+# ----------------------------------------------------------------------------------------
+
+def constraint_vertices(scene: Scene, cid: int) -> tuple:
+    nd, nb, nt = scene.n_dist, scene.n_bend, scene.n_tet
+    if cid < nd:
+        return tuple(int(v) for v in scene.dist_idx[cid])
+    cid -= nd
+    if cid < nb:
+        return tuple(int(v) for v in scene.bend_idx[cid])
+    cid -= nb
+    if cid < 2 * nt:
+        return tuple(int(v) for v in scene.tet_idx[cid % nt])
+    raise IndexError("constraint id out of range")
+
+
+def _vertex_table(scene: Scene) -> np.ndarray:
+    """[m, 4] vertex ids of every constraint, -1 padded."""
+    rows = [np.pad(scene.dist_idx, ((0, 0), (0, 2)), constant_values=-1) if scene.n_dist else
+            np.zeros((0, 4), np.int64)]
+    rows.append(scene.bend_idx.astype(np.int64) if scene.n_bend else np.zeros((0, 4), np.int64))
+    rows.append(scene.tet_idx.astype(np.int64) if scene.n_tet else np.zeros((0, 4), np.int64))
+    rows.append(scene.tet_idx.astype(np.int64) if scene.n_tet else np.zeros((0, 4), np.int64))
+    return np.concatenate(rows, axis=0)
+
+
+def validate_coloring(scene: Scene) -> None:
+    """Raise ValueError unless every constraint appears exactly once and no two
+    constraints of one color share a vertex."""
+    order = np.asarray(scene.color_order, np.int64)
+    offs = np.asarray(scene.color_offsets, np.int64)
+    if offs[0] != 0 or offs[-1] != scene.m or np.any(np.diff(offs) < 0):
+        raise ValueError("bad color offsets")
+    if order.shape[0] != scene.m or np.any(np.sort(order) != np.arange(scene.m)):
+        raise ValueError("coloring is not a permutation of the constraints")
+    table = _vertex_table(scene)
+    for c in range(scene.n_colors):
+        ids = order[offs[c]:offs[c + 1]]
+        verts = table[ids].reshape(-1)
+        verts = verts[verts >= 0]
+        if np.unique(verts).shape[0] != verts.shape[0]:
+            raise ValueError(f"color {c} has a vertex shared by two constraints")
+
+
+def greedy_coloring(scene: Scene, groups=None):
+    """First-fit greedy coloring of the constraint graph (constraints adjacent when they
+    share a vertex).  ``groups`` is an optional list of constraint-id arrays colored
+    separately (so every color holds one constraint type).  Returns (offsets, order)."""
+    table = _vertex_table(scene)
+    if groups is None:
+        groups = [np.arange(scene.m)]
+    offsets = [0]
+    order = []
+    for ids in groups:
+        vert_colors = {}
+        buckets: list = []
+        for cid in ids:
+            vs = [int(v) for v in table[cid] if v >= 0]
+            used = set()
+            for v in vs:
+                used |= vert_colors.get(v, set())
+            c = 0
+            while c in used:
+                c += 1
+            if c == len(buckets):
+                buckets.append([])
+            buckets[c].append(int(cid))
+            for v in vs:
+                vert_colors.setdefault(v, set()).add(c)
+        for b in buckets:
+            order.extend(sorted(b, key=lambda j: table[j][0]))
+            offsets.append(len(order))
+    return np.asarray(offsets, np.int32), np.asarray(order, np.int32)
+
+
+# ----------------------------------------------------------------------------------------
+# cloth grid
+# ----------------------------------------------------------------------------------------
+
+def _grid_topology(n: int, diagonals: str, bending: bool):
+    """Edges and hinges of an n x n vertex grid, vertex (i, j) -> j*n + i, grouped into
+    vertex-disjoint color classes (pattern coloring of the regular grid)."""
+    I, J = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")  # I[j, i] = i
+    vid = lambda i, j: (j * n + i)
+    classes = []   # list of (kind, idx array [k, 2|4])
+
+    def add_edges(a, b, key):
+        for par in (0, 1):
+            sel = (key % 2) == par
+            if np.any(sel):
+                classes.append(("dist", np.stack([a[sel], b[sel]], axis=1)))
+
+    # structural: horizontal (i,j)-(i+1,j), colored by i parity
+    i, j = I[:, :-1].ravel(), J[:, :-1].ravel()
+    add_edges(vid(i, j), vid(i + 1, j), i)
+    # structural: vertical (i,j)-(i,j+1), colored by j parity
+    i, j = I[:-1, :].ravel(), J[:-1, :].ravel()
+    add_edges(vid(i, j), vid(i, j + 1), j)
+    if diagonals in ("one", "both"):
+        i, j = I[:-1, :-1].ravel(), J[:-1, :-1].ravel()
+        add_edges(vid(i, j), vid(i + 1, j + 1), i)
+    if diagonals == "both":
+        i, j = I[:-1, :-1].ravel(), J[:-1, :-1].ravel()
+        add_edges(vid(i + 1, j), vid(i, j + 1), i)
+    if bending:
+        # triangulation with diagonal (i,j)-(i+1,j+1): quad (i,j) -> T1=(i,j),(i+1,j),(i+1,j+1)
+        # and T2=(i,j),(i+1,j+1),(i,j+1).  Hinges on interior axis-aligned edges only.
+        # horizontal hinge edge (i,j)-(i+1,j), 1<=j<=n-2: wings (i+1,j+1) [T1 of quad (i,j)]
+        # and (i,j-1) [T2 of quad (i,j-1)]
+        i, j = I[1:-1, :-1].ravel(), J[1:-1, :-1].ravel()
+        h = np.stack([vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j - 1)], axis=1)
+        for pi in (0, 1):
+            for pj in (0, 1):
+                sel = ((i % 2) == pi) & ((j % 2) == pj)
+                if np.any(sel):
+                    classes.append(("bend", h[sel]))
+        # vertical hinge edge (i,j)-(i,j+1), 1<=i<=n-2: wings (i-1,j) [T1 of quad (i-1,j)]
+        # and (i+1,j+1) [T2 of quad (i,j)], ordered so side A/B match the horizontal case
+        i, j = I[:-1, 1:-1].ravel(), J[:-1, 1:-1].ravel()
+        h = np.stack([vid(i, j), vid(i, j + 1), vid(i - 1, j), vid(i + 1, j + 1)], axis=1)
+        for pi in (0, 1):
+            for pj in (0, 1):
+                sel = ((i % 2) == pi) & ((j % 2) == pj)
+                if np.any(sel):
+                    classes.append(("bend", h[sel]))
+    return classes
+
+
+def cloth_grid(n: int, size: float = 1.0, *, vertex_mass: Optional[float] = None,
+               areal_density: float = 2.56, diagonals: str = "both", bending: bool = False,
+               pins=((0, 0), (-1, 0)), y0: float = 0.0, origin=(0.0, 0.0)) -> dict:
+    """An n x n vertex cloth square in the x-z plane at height y0.
+
+    Returns the raw arrays (positions, masses, topology, coloring) of a cloth grid; the
+    ``cloth_*`` config builders below turn them into a Scene."""
+    if n < 2:
+        raise ValueError("grid needs n >= 2")
+    h = size / (n - 1)
+    I, J = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    x = np.stack([origin[0] + I.ravel() * h, np.full(n * n, y0), origin[1] + J.ravel() * h], axis=1)
+    if vertex_mass is None:
+        vertex_mass = areal_density * size * size / (n * n)
+    w = np.full(n * n, 1.0 / vertex_mass)
+    for (pi, pj) in pins:
+        pi = pi % n
+        pj = pj % n
+        w[pj * n + pi] = 0.0
+    classes = _grid_topology(n, diagonals, bending)
+    dist = [c[1] for c in classes if c[0] == "dist"]
+    bend = [c[1] for c in classes if c[0] == "bend"]
+    dist_idx = np.concatenate(dist).astype(np.int32) if dist else np.zeros((0, 2), np.int32)
+    bend_idx = np.concatenate(bend).astype(np.int32) if bend else np.zeros((0, 4), np.int32)
+    nd = dist_idx.shape[0]
+    offsets = [0]
+    order = []
+    d0 = 0
+    b0 = nd
+    for kind, idx in classes:
+        k = idx.shape[0]
+        if kind == "dist":
+            order.append(np.arange(d0, d0 + k))
+            d0 += k
+        else:
+            order.append(np.arange(b0, b0 + k))
+            b0 += k
+        offsets.append(offsets[-1] + k)
+    return dict(rest_x=f32(x), inv_mass=f32(w), dist_idx=dist_idx, bend_idx=bend_idx,
+                color_offsets=np.asarray(offsets, np.int32),
+                color_order=(np.concatenate(order).astype(np.int32) if order else np.zeros(0, np.int32)))
+
+
+def _cloth_scene(g: dict, compliance: np.ndarray, **kw) -> Scene:
+    V = g["rest_x"].shape[0]
+    return Scene(rest_x=g["rest_x"], inv_mass=g["inv_mass"], dist_idx=g["dist_idx"],
+                 bend_idx=g["bend_idx"], tet_idx=np.zeros((0, 4), np.int32),
+                 tet_gamma=np.zeros(0), color_offsets=g["color_offsets"],
+                 color_order=g["color_order"], x0=g["rest_x"].copy(), v0=np.zeros((V, 3)),
+                 compliance=f32(compliance), **kw)
+
+
+def plain_cloth(n: int = 16, *, compliance: float = 1e-7, steps: int = 50, iters: int = 20,
+                seed: int = 1, target: bool = False) -> Scene:
+    """Plain XPBD cloth: 1 m square, 0.01 kg per vertex, two top corners pinned,
+    structural + both shear diagonals, uniform compliance, gravity, dt = 1/60.
+    With ``target``: the per-constraint compliance is multiplied by exp(0.5 z),
+    z ~ N(0, 1) (seeded), as used to produce the target trajectory."""
+    g = cloth_grid(n, 1.0, vertex_mass=0.01, diagonals="both", bending=False)
+    nd = g["dist_idx"].shape[0]
+    alpha = np.full(nd, compliance)
+    if target:
+        rng = np.random.default_rng(seed)
+        alpha = alpha * np.exp(0.5 * rng.standard_normal(nd))
+    return _cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters,
+                        name=f"plain_cloth_{n}")
+
+
+def lognormal_cloth_compliance(rng, nd: int, nb: int, stretch: float = 1e-4,
+                               bend: float = 1e-2) -> np.ndarray:
+    return np.concatenate([stretch * np.exp(0.5 * rng.standard_normal(nd)),
+                           bend * np.exp(0.5 * rng.standard_normal(nb))])
+
+
+def ground_cloth(n: int = 256, *, steps: int = 100, iters: int = 30, seed: int = 2,
+                 plane_h: float = -0.6, pins=((0, 0), (-1, 0))) -> Scene:
+    """Cloth with stretch/shear springs (one diagonal) and dihedral bending, per-constraint
+    lognormal compliance, two corners pinned, ground plane below."""
+    g = cloth_grid(n, 1.0, areal_density=2.56, diagonals="one", bending=True, pins=pins)
+    rng = np.random.default_rng(seed)
+    alpha = lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0])
+    return _cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters,
+                        collider_flags=COLLIDE_PLANE, plane_h=plane_h, contact_compliance=1e-8,
+                        name=f"ground_cloth_{n}")
+
+
+def sphere_cloth(n: int = 2950, *, steps: int = 60, iters: int = 15, seed: int = 4,
+                 radius: float = 0.3, force_scale: float = 0.2) -> Scene:
+    """High-resolution cloth (structural + both diagonals + bending) with no pins, falling
+    on an analytic sphere, driven by a per-frame global force G_n (3 per step) and a
+    time-constant smooth per-vertex wind field W."""
+    g = cloth_grid(n, 1.0, areal_density=2.56, diagonals="both", bending=True, pins=())
+    rng = np.random.default_rng(seed)
+    centre = np.array([0.5, -0.35, 0.5]) + rng.uniform(-0.05, 0.05, 3)
+    alpha = lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0])
+    V = n * n
+    m_i = 2.56 / V
+    amp = force_scale * m_i * 9.81
+    phase = rng.uniform(0, 2 * np.pi, 3)
+    t = np.arange(steps)[:, None]
+    f_global = amp * np.sin(2 * np.pi * t / 60.0 + phase[None, :])
+    # smooth wind: a few low-order Fourier modes over the rest (x, z) coordinates
+    x = g["rest_x"]
+    W = np.zeros((V, 3))
+    for _ in range(3):
+        kx, kz = rng.integers(1, 4, 2)
+        ph = rng.uniform(0, 2 * np.pi)
+        a = rng.normal(0, 0.3, 3)
+        W += amp * a[None, :] * np.sin(2 * np.pi * (kx * x[:, 0:1] + kz * x[:, 2:3]) + ph)
+    return _cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters,
+                        collider_flags=COLLIDE_SPHERE, sphere=tuple(float(v) for v in f32(np.r_[centre, radius])),
+                        contact_compliance=1e-8, f_global=f32(f_global), f_vertex=f32(W),
+                        name=f"sphere_cloth_{n}")
+
+
+# ----------------------------------------------------------------------------------------
+# tetrahedral block
+# ----------------------------------------------------------------------------------------
+
+# 5-tet corner-cut split of a unit cube; corners numbered by bits (x=1, y=2, z=4).
+_EVEN_TETS = ((0, 1, 2, 4), (3, 1, 2, 7), (5, 1, 4, 7), (6, 2, 4, 7), (1, 2, 4, 7))
+_ODD_TETS = ((1, 0, 3, 5), (2, 0, 3, 6), (4, 0, 5, 6), (7, 3, 5, 6), (0, 3, 5, 6))
+
+
+def tet_block(n: int = 32, *, size: float = 1.0, density: float = 1000.0, y0: float = 0.05,
+              steps: int = 120, iters: int = 20, seed: int = 3, plane_h: float = 0.0,
+              alpha_lo: float = 1e-6, alpha_hi: float = 1e-3) -> Scene:
+    """n^3 cube cells split into 5 tets each (mirrored parity so faces conform), falling on
+    a ground plane.  Per-tet hydrostatic and deviatoric inverse moduli drawn log-uniform in
+    [alpha_lo, alpha_hi]; gamma = 1 + alpha_H / alpha_D (rest state in equilibrium)."""
+    h = size / n
+    N1 = n + 1
+    I, J, K = np.meshgrid(np.arange(N1), np.arange(N1), np.arange(N1), indexing="ij")
+    vid = lambda i, j, k: i + N1 * (j + N1 * k)
+    x = np.zeros((N1 ** 3, 3))
+    x[vid(I, J, K).ravel()] = np.stack([I.ravel() * h, y0 + J.ravel() * h, K.ravel() * h], 1)
+    ci, cj, ck = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    corner = np.stack([vid(ci + (b & 1), cj + ((b >> 1) & 1), ck + ((b >> 2) & 1)) for b in range(8)], 1)
+    odd = ((ci + cj + ck) % 2) == 1
+    tets_by_slot = []
+    for s in range(5):
+        t = np.where(odd[:, None], corner[:, list(_ODD_TETS[s])], corner[:, list(_EVEN_TETS[s])])
+        tets_by_slot.append(t)
+    tets = np.stack(tets_by_slot, axis=1)          # [cells, 5, 4]
+    # orient positively (mesh construction: swap two vertices where the signed volume < 0)
+    P = x[tets]
+    vol6 = np.einsum("...i,...i->...", np.cross(P[..., 1, :] - P[..., 0, :], P[..., 2, :] - P[..., 0, :]),
+                     P[..., 3, :] - P[..., 0, :])
+    neg = vol6 < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    vol = np.abs(vol6) / 6.0
+    # lumped mass
+    mass = np.zeros(N1 ** 3)
+    np.add.at(mass, tets.reshape(-1, 4), np.repeat((density * vol.reshape(-1) / 4.0)[:, None], 4, 1))
+    # coloring: cell parity class (8) x tet slot (5); hydrostatic then deviatoric per class
+    cls = (ci % 2) + 2 * (cj % 2) + 4 * (ck % 2)
+    tet_idx = tets.reshape(-1, 4).astype(np.int32)
+    nt = tet_idx.shape[0]
+    tet_id = np.arange(nt).reshape(-1, 5)
+    offsets = [0]
+    order = []
+    for c in range(8):
+        cells = np.nonzero(cls == c)[0]
+        for s in range(5):
+            ids = tet_id[cells, s]
+            order.append(ids)            # hydrostatic constraint ids = tet id
+            offsets.append(offsets[-1] + ids.shape[0])
+            order.append(ids + nt)       # deviatoric constraint ids = nt + tet id
+            offsets.append(offsets[-1] + ids.shape[0])
+    rng = np.random.default_rng(seed)
+    la, lb = np.log(alpha_lo), np.log(alpha_hi)
+    aH = np.exp(rng.uniform(la, lb, nt))
+    aD = np.exp(rng.uniform(la, lb, nt))
+    gamma = 1.0 + aH / aD
+    V = N1 ** 3
+    xr = f32(x)
+    return Scene(rest_x=xr, inv_mass=f32(1.0 / mass), dist_idx=np.zeros((0, 2), np.int32),
+                 bend_idx=np.zeros((0, 4), np.int32), tet_idx=tet_idx, tet_gamma=f32(gamma),
+                 color_offsets=np.asarray(offsets, np.int32),
+                 color_order=np.concatenate(order).astype(np.int32), x0=xr.copy(),
+                 v0=np.zeros((V, 3)), compliance=f32(np.concatenate([aH, aD])),
+                 dt=1.0 / 120.0, steps=steps, iters=iters, collider_flags=COLLIDE_PLANE,
+                 plane_h=plane_h, contact_compliance=1e-8, name=f"tet_block_{n}")
+
+
+# ----------------------------------------------------------------------------------------
+# serving stream
+# ----------------------------------------------------------------------------------------
+
+def serving_requests(n_requests: int = 2000, *, seed: int = 5, side_lo: int = 32,
+                     side_hi: int = 512, steps_lo: int = 20, steps_hi: int = 200,
+                     iters_lo: int = 10, iters_hi: int = 40) -> list:
+    """Parameters of a seeded request trace: per request the cloth side, horizon,
+    iteration count, pins, ground plane and the seed of its compliance draw."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_requests):
+        side = int(rng.integers(side_lo, side_hi + 1))
+        npins = int(rng.integers(0, 5))
+        pins = tuple((int(p), 0) for p in rng.choice(side, size=npins, replace=False))
+        out.append(dict(side=side, steps=int(rng.integers(steps_lo, steps_hi + 1)),
+                        iters=int(rng.integers(iters_lo, iters_hi + 1)), pins=pins,
+                        ground=bool(rng.integers(0, 2)), seed=int(rng.integers(0, 2 ** 31))))
+    return out
+
+
+def request_scene(req: dict) -> Scene:
+    """The cloth scene of one serving request (ground-plane cloth law with its own pins)."""
+    n = req["side"]
+    g = cloth_grid(n, 1.0, areal_density=2.56, diagonals="one", bending=True, pins=req["pins"])
+    rng = np.random.default_rng(req["seed"])
+    alpha = lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0])
+    return _cloth_scene(g, alpha, dt=1.0 / 60.0, steps=req["steps"], iters=req["iters"],
+                        collider_flags=COLLIDE_PLANE if req["ground"] else 0, plane_h=-0.6,
+                        contact_compliance=1e-8, name=f"request_{n}")
+
+
+def perturbed_target_compliance(scene: Scene, seed: int, sigma: float = 0.5) -> np.ndarray:
+    """Per-constraint compliance multiplied by exp(sigma z), z ~ N(0,1): the seeded
+    'ground truth' material used to make target trajectories."""
+    rng = np.random.default_rng(seed)
+    return f32(scene.compliance * np.exp(sigma * rng.standard_normal(scene.m)))

@@ -1,0 +1,79 @@
+"""Small hand-built scenes for the oracle pins and the GPU parity tests."""
+import numpy as np
+
+from paper_2301_01396_gb300 import scenes
+from paper_2301_01396_gb300.scenes import Scene, f32
+
+
+def single_spring(L=0.5, stretch0=0.0, mass=0.01, alpha=1e-3, dt=1.0 / 60.0):
+    """Vertex 0 pinned at the origin, vertex 1 hanging below it on one spring of rest
+    length L (the rest positions define L), both on the y axis."""
+    rest = np.array([[0.0, 0.0, 0.0], [0.0, -L, 0.0]])
+    x0 = np.array([[0.0, 0.0, 0.0], [0.0, -(L + stretch0), 0.0]])
+    return Scene(rest_x=f32(rest), inv_mass=f32([0.0, 1.0 / mass]),
+                 dist_idx=np.array([[0, 1]], np.int32), bend_idx=np.zeros((0, 4), np.int32),
+                 tet_idx=np.zeros((0, 4), np.int32), tet_gamma=np.zeros(0),
+                 color_offsets=np.array([0, 1], np.int32), color_order=np.array([0], np.int32),
+                 x0=f32(x0), v0=np.zeros((2, 3)), compliance=f32([alpha]), dt=dt,
+                 gravity=(0.0, -9.81, 0.0), steps=10, iters=1, name="single_spring")
+
+
+def small_cloth(n=5, *, bending=True, diagonals="both", pins=((0, 0), (-1, 0)), seed=0,
+                plane_h=None, steps=4, iters=3, gravity=(0.0, -9.81, 0.0), jitter=0.0,
+                v_scale=0.0, stretch=1e-3, bend=1e-2):
+    g = scenes.cloth_grid(n, 1.0, areal_density=2.56, diagonals=diagonals, bending=bending, pins=pins)
+    rng = np.random.default_rng(seed)
+    alpha = scenes.lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0],
+                                              stretch=stretch, bend=bend)
+    sc = scenes._cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters, gravity=gravity,
+                             name=f"small_cloth_{n}")
+    if jitter:
+        sc.x0 = f32(sc.x0 + jitter * rng.standard_normal(sc.x0.shape))
+    if v_scale:
+        v = v_scale * rng.standard_normal(sc.x0.shape)
+        v[sc.inv_mass == 0] = 0.0
+        sc.v0 = f32(v)
+    if plane_h is not None:
+        sc.collider_flags = scenes.COLLIDE_PLANE
+        sc.plane_h = plane_h
+    return sc
+
+
+def small_tets(n=2, *, steps=3, iters=3, seed=3, y0=0.02, plane=True, gravity=(0.0, -9.81, 0.0),
+               jitter=0.0, v_scale=0.0):
+    sc = scenes.tet_block(n, size=0.2, y0=y0, steps=steps, iters=iters, seed=seed, alpha_lo=1e-5,
+                          alpha_hi=1e-3)
+    sc.gravity = gravity
+    rng = np.random.default_rng(seed + 100)
+    if jitter:
+        sc.x0 = f32(sc.x0 + jitter * rng.standard_normal(sc.x0.shape))
+    if v_scale:
+        sc.v0 = f32(v_scale * rng.standard_normal(sc.x0.shape))
+    if not plane:
+        sc.collider_flags = 0
+    return sc
+
+
+def small_sphere_cloth(n=6, *, steps=4, iters=3, seed=4):
+    """A small unpinned cloth dropped on a sphere whose top sits just below it, with
+    per-step global forces and a per-vertex force field."""
+    g = scenes.cloth_grid(n, 1.0, areal_density=2.56, diagonals="both", bending=True, pins=())
+    rng = np.random.default_rng(seed)
+    alpha = scenes.lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0],
+                                              stretch=1e-3, bend=1e-2)
+    V = n * n
+    m_i = 2.56 / V
+    sc = scenes._cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters,
+                             collider_flags=scenes.COLLIDE_SPHERE,
+                             sphere=tuple(float(v) for v in f32([0.47, -0.31, 0.52, 0.3])),
+                             contact_compliance=1e-6, name=f"small_sphere_{n}")
+    sc.v0 = f32(np.tile([0.0, -0.6, 0.0], (V, 1)) + 0.05 * rng.standard_normal((V, 3)))
+    sc.f_global = f32(0.3 * m_i * 9.81 * rng.standard_normal((steps, 3)))
+    sc.f_vertex = f32(0.3 * m_i * 9.81 * rng.standard_normal((V, 3)))
+    return sc
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
