@@ -1,0 +1,178 @@
+/*
+ * diffxpbd.h -- C ABI of the GB300 (sm_103a) differentiable XPBD library.
+ *
+ * The library runs the XPBD time step of DiffXPBD (Stuyck & Chen) and its exact discrete
+ * adjoint on one GPU:
+ *   forward  (Sec. 3.1, Eq. xpbdUpdateRule): inertial prediction
+ *            p = x_n + dt v_n + dt^2 M^-1 f_ext, then `iters` Gauss-Seidel iterations
+ *            that visit the constraint colors in order (Sec. 3.1, graph coloring), each
+ *            constraint j taking the single-constraint XPBD update of Eq. xpbd
+ *              dlambda = (-C_j - alpha~_j lambda_j) / (sum_i w_i |grad_i C_j|^2 + alpha~_j),
+ *              alpha~_j = alpha_j / dt^2,   x_i += w_i grad_i C_j dlambda,
+ *            then one collision pass (Sec. 4.6) over the contacts detected at p, and the
+ *            velocity update v_{n+1} = (x_{n+1} - x_n) / dt.
+ *   adjoint  (Sec. 4.2, Eq. rawAdjoint and Eq. gradientRule, in discrete form): the
+ *            reverse-time sweep of the linearised constraint updates, replaying each step
+ *            from its checkpoint, giving dL/d(compliance), dL/dx0, dL/dv0 (Sec. 5.5),
+ *            dL/d(per-step global force) and dL/d(per-vertex force) (Sec. 5.6), and
+ *            dL/d(plane height, sphere centre, sphere radius) (Sec. 4.6).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an xpbd_status and never aborts.  On failure the thread-local
+ *     message of xpbd_last_error() says why.  Errors found by kernels (non-finite state)
+ *     are latched in a device word and reported by xpbd_sync_status().
+ *   - "HOST" pointers are read during the call only.  "DEVICE" pointers are CUDA device
+ *     memory owned by the caller; they must stay valid until the work queued on `stream`
+ *     has finished.  `stream` is a cudaStream_t (NULL = legacy default stream); all GPU
+ *     work of a call is queued on it and the call returns without synchronising unless
+ *     stated otherwise.
+ *   - A handle is not reentrant: calls on one handle must not overlap in time or run on
+ *     two streams at once.  Distinct handles are independent.
+ *   - Layouts: vertex arrays are [V][3] float32 row-major.  Constraint ids are global:
+ *       [0, n_dist) distance, [n_dist, +n_bend) bending, then n_tet hydrostatic and
+ *       n_tet deviatoric tet constraints.
+ *   - Checkpoints (caller-owned DEVICE buffer of xpbd_checkpoint_bytes()): for each step
+ *     n = 0..steps, V float4 positions (x, y, z, inverse mass) followed by V float4
+ *     velocities (vx, vy, vz, 0).
+ */
+#ifndef DIFFXPBD_H
+#define DIFFXPBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XPBD_OK = 0,
+  XPBD_ERR_INVALID = 1,    /* bad argument, index out of range, non-finite rest data   */
+  XPBD_ERR_COLORING = 2,   /* a color has two constraints sharing a vertex, or the
+                              coloring misses / repeats a constraint                    */
+  XPBD_ERR_OOM = 3,        /* device allocation failed                                  */
+  XPBD_ERR_CUDA = 4,       /* a CUDA runtime call failed                                */
+  XPBD_ERR_NONFINITE = 5,  /* a kernel produced a NaN/Inf state (latched device word)   */
+  XPBD_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                             */
+  XPBD_ERR_BOUNDS = 7      /* a size exceeds a fixed limit of the entry point           */
+} xpbd_status;
+
+enum { XPBD_COLLIDE_PLANE = 1, XPBD_COLLIDE_SPHERE = 2 };
+
+typedef struct xpbd_solver* xpbd_handle;
+
+/* Mesh, constraints and coloring.  All HOST pointers, copied by xpbd_create. */
+typedef struct {
+  int32_t n_vertices;
+  const float* rest_x;          /* [V*3] rest positions: define spring rest lengths, hinge
+                                   rest angles, tet reference shapes Dm^-1 and volumes    */
+  const float* inv_mass;        /* [V] w = 1/m; 0 pins the vertex (infinite mass, Sec. 4.2.1) */
+  int32_t n_dist;
+  const int32_t* dist_idx;      /* [n_dist*2]   C = |x_a - x_b| - L                      */
+  int32_t n_bend;
+  const int32_t* bend_idx;      /* [n_bend*4] hinge edge v0-v1, wing v2 (side A), wing v3
+                                   (side B); C = theta - theta0, theta the signed dihedral
+                                   angle between nA = e x (x2-x0) and nB = (x3-x0) x e
+                                   about e = x1 - x0 (Sec. 5.1 discrete bending)           */
+  int32_t n_tet;
+  const int32_t* tet_idx;       /* [n_tet*4] positively oriented; F = Ds Dm^-1,
+                                   C_H = det F - gamma, C_D = sqrt(tr F^T F) (Sec. 5.2)   */
+  const float* tet_gamma;       /* [n_tet] hydrostatic rest offset, or NULL for 1          */
+  int32_t n_colors;
+  const int32_t* color_offsets; /* [n_colors+1]; color c = color_order[offsets[c]..offsets[c+1]) */
+  const int32_t* color_order;   /* [m] every constraint id exactly once                    */
+} xpbd_model;
+
+/* Per-call parameters.  The float fields are HOST values; the pointers are DEVICE. */
+typedef struct {
+  float dt;
+  float gravity[3];             /* acceleration applied to free vertices                  */
+  const float* compliance;      /* DEVICE [m] alpha_j for distance and bending constraints;
+                                   for tet constraints the inverse modulus alpha_hat_j with
+                                   alpha_j = alpha_hat_j / V_e (V_e the rest volume)      */
+  const float* f_global;        /* DEVICE [steps*3] force added to every vertex at step n,
+                                   or NULL                                                 */
+  const float* f_vertex;        /* DEVICE [V*3] time-constant per-vertex force, or NULL   */
+  int32_t collider_flags;       /* XPBD_COLLIDE_PLANE | XPBD_COLLIDE_SPHERE               */
+  float plane_h;                /* plane y = plane_h, normal +y:  C = y - h - thickness    */
+  float sphere[4];              /* centre cx, cy, cz and radius r:  C = |x - c| - r - thickness */
+  float contact_compliance;     /* compliance of every contact spring                     */
+  float thickness;              /* separation kept from the colliders                     */
+} xpbd_params;
+
+/* Gradient outputs.  DEVICE float64 buffers owned by the caller; each non-NULL buffer is
+   overwritten (not accumulated into).  NULL skips that gradient. */
+typedef struct {
+  double* d_compliance;         /* [m] dL/d compliance (the xpbd_params.compliance entries) */
+  double* d_x0;                 /* [V*3] dL/dx_0                                          */
+  double* d_v0;                 /* [V*3] dL/dv_0                                          */
+  double* d_f_global;           /* [steps*3] dL/dG_n                                      */
+  double* d_f_vertex;           /* [V*3] dL/dW_i                                          */
+  double* d_collider;           /* [5] dL/d(plane_h, cx, cy, cz, r)                        */
+} xpbd_grads;
+
+/* Build a solver.  Validates indices (XPBD_ERR_INVALID), the coloring
+   (XPBD_ERR_COLORING: every constraint once; no vertex twice within a color) and the rest
+   data; computes rest lengths, hinge angles, Dm^-1 and rest volumes from rest_x; sorts
+   each color's constraints by type and first vertex and uploads them.  The order inside
+   a color does not change results (its constraints are vertex-disjoint).  Synchronous. */
+xpbd_status xpbd_create(const xpbd_model* model, xpbd_handle* out);
+
+/* Release every device buffer the handle owns.  Synchronises the device first. */
+xpbd_status xpbd_destroy(xpbd_handle h);
+
+/* Sizes: number of vertices / constraints / colors of a handle. */
+xpbd_status xpbd_sizes(xpbd_handle h, int32_t* n_vertices, int32_t* n_constraints, int32_t* n_colors);
+
+/* Bytes of the checkpoint buffer for `steps` steps: (steps+1) * V * 32. */
+size_t xpbd_checkpoint_bytes(xpbd_handle h, int32_t steps);
+
+/* Device bytes the handle allocates for a forward or adjoint call with `iters`
+   iterations (working state, multiplier and position tapes, gradient scratch); the
+   library allocates them on first use and keeps them until xpbd_destroy. */
+size_t xpbd_workspace_bytes(xpbd_handle h, int32_t iters);
+
+/* Forward simulation of `steps` steps (Sec. 3.1).  x0, v0: DEVICE [V*3].  Writes
+   checkpoints 0..steps (checkpoint 0 = x0, v0).  Pinned vertices should start with
+   v0 = 0. */
+xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                         const float* x0, const float* v0, float* checkpoints, void* stream);
+
+/* Copy positions and velocities of checkpoint `step` into DEVICE [V*3] buffers (either
+   may be NULL). */
+xpbd_status xpbd_read_state(xpbd_handle h, const float* checkpoints, int32_t step, float* x_out,
+                            float* v_out, void* stream);
+
+/* Goal function of Sec. 4.1 with W = I, beta = 0 over keyframes:
+     L = 1/2 sum_k |x_{n_k} - x*_k|^2
+   key_steps HOST [n_keys]; targets DEVICE [n_keys*V*3].  Writes L (float64, reduced in a
+   fixed order) to DEVICE loss_out[0] and dL/dx_{n_k} = x_{n_k} - x*_k (float32) to
+   DEVICE seeds_out [n_keys*V*3] (either output may be NULL). */
+xpbd_status xpbd_loss(xpbd_handle h, const float* checkpoints, int32_t n_keys,
+                      const int32_t* key_steps, const float* targets, double* loss_out,
+                      float* seeds_out, void* stream);
+
+/* Reverse sweep (discrete adjoint).  checkpoints: as written by xpbd_forward with the same
+   params/steps/iters.  Seeds dL/dx_n for n = seed_steps[s] (HOST [n_seeds], each in
+   0..steps) in seed_dx (DEVICE [n_seeds*V*3]); seed_dv_T DEVICE [V*3] dL/dv_steps or NULL.
+   Recomputes each step's in-step positions and multipliers from its checkpoint; keeps
+   positions, multipliers and adjoint states in float32 and reduces parameter gradients
+   across constraints and steps in float64 in a fixed order (deterministic). */
+xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                         const float* checkpoints, int32_t n_seeds, const int32_t* seed_steps,
+                         const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
+                         void* stream);
+
+/* Synchronise `stream` and report (then clear) the device error word of the handle:
+   XPBD_ERR_NONFINITE if, since the last check, a call was given a negative or non-finite
+   compliance or a step produced a non-finite state. */
+xpbd_status xpbd_sync_status(xpbd_handle h, void* stream);
+
+/* Thread-local description of the last failure (empty string if none). */
+const char* xpbd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFXPBD_H */

@@ -1,0 +1,300 @@
+"""Python binding of the C ABI in ``include/diffxpbd.h`` (ctypes; argument marshalling only).
+
+Every step of the simulation and of its adjoint runs in the CUDA library
+``_lib/libdiffxpbd.so``; this module only passes device pointers, sizes and the current
+torch stream.  Importing it does not load the library; the first call does, and raises
+``RuntimeError`` if the library is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from .build import LIB_PATH
+
+XPBD_OK = 0
+STATUS = {0: "XPBD_OK", 1: "XPBD_ERR_INVALID", 2: "XPBD_ERR_COLORING", 3: "XPBD_ERR_OOM",
+          4: "XPBD_ERR_CUDA", 5: "XPBD_ERR_NONFINITE", 6: "XPBD_ERR_TIMEOUT", 7: "XPBD_ERR_BOUNDS"}
+COLLIDE_PLANE = 1
+COLLIDE_SPHERE = 2
+
+_fp = C.POINTER(C.c_float)
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class XpbdModel(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("rest_x", _fp), ("inv_mass", _fp),
+                ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
+                ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _fp),
+                ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip)]
+
+
+class XpbdParams(C.Structure):
+    _fields_ = [("dt", C.c_float), ("gravity", C.c_float * 3), ("compliance", C.c_void_p),
+                ("f_global", C.c_void_p), ("f_vertex", C.c_void_p), ("collider_flags", C.c_int32),
+                ("plane_h", C.c_float), ("sphere", C.c_float * 4),
+                ("contact_compliance", C.c_float), ("thickness", C.c_float)]
+
+
+class XpbdGrads(C.Structure):
+    _fields_ = [("d_compliance", C.c_void_p), ("d_x0", C.c_void_p), ("d_v0", C.c_void_p),
+                ("d_f_global", C.c_void_p), ("d_f_vertex", C.c_void_p), ("d_collider", C.c_void_p)]
+
+
+class XpbdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build()); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name in ("xpbd_create", "xpbd_destroy", "xpbd_sizes", "xpbd_forward", "xpbd_read_state",
+                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status"):
+            getattr(L, name).restype = C.c_int
+        L.xpbd_checkpoint_bytes.restype = C.c_size_t
+        L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
+        L.xpbd_workspace_bytes.restype = C.c_size_t
+        L.xpbd_workspace_bytes.argtypes = [C.c_void_p, C.c_int32]
+        L.xpbd_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != XPBD_OK:
+        raise XpbdError(st, lib().xpbd_last_error().decode())
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Params:
+    """Per-call parameters (xpbd_params): device tensors plus host scalars."""
+    dt: float
+    compliance: torch.Tensor                  # [m] float32 cuda
+    gravity: Sequence[float] = (0.0, -9.81, 0.0)
+    f_global: Optional[torch.Tensor] = None   # [steps,3] float32 cuda
+    f_vertex: Optional[torch.Tensor] = None   # [V,3] float32 cuda
+    collider_flags: int = 0
+    plane_h: float = 0.0
+    sphere: Sequence[float] = (0.0, 0.0, 0.0, 0.0)
+    contact_compliance: float = 1e-8
+    thickness: float = 0.0
+
+    def c_struct(self) -> XpbdParams:
+        for t in (self.compliance, self.f_global, self.f_vertex):
+            if t is not None and t.dtype != torch.float32:
+                raise ValueError("params tensors must be float32")
+        return XpbdParams(dt=self.dt, gravity=(C.c_float * 3)(*self.gravity),
+                          compliance=_ptr(self.compliance), f_global=_ptr(self.f_global),
+                          f_vertex=_ptr(self.f_vertex), collider_flags=int(self.collider_flags),
+                          plane_h=float(self.plane_h), sphere=(C.c_float * 4)(*[float(v) for v in self.sphere]),
+                          contact_compliance=float(self.contact_compliance), thickness=float(self.thickness))
+
+
+class Solver:
+    """One xpbd_handle: a mesh, its constraints and its coloring, resident on the GPU."""
+
+    def __init__(self, rest_x, inv_mass, dist_idx=None, bend_idx=None, tet_idx=None, tet_gamma=None,
+                 color_offsets=None, color_order=None):
+        L = lib()
+        keep = []
+
+        def f(a):
+            a = np.ascontiguousarray(a, np.float32).reshape(-1)
+            keep.append(a)
+            return a.ctypes.data_as(_fp)
+
+        def i(a):
+            a = np.ascontiguousarray(a, np.int32).reshape(-1)
+            keep.append(a)
+            return a.ctypes.data_as(_ip)
+
+        z2 = np.zeros((0, 2), np.int32)
+        z4 = np.zeros((0, 4), np.int32)
+        dist_idx = z2 if dist_idx is None else np.asarray(dist_idx)
+        bend_idx = z4 if bend_idx is None else np.asarray(bend_idx)
+        tet_idx = z4 if tet_idx is None else np.asarray(tet_idx)
+        md = XpbdModel(n_vertices=int(np.asarray(rest_x).shape[0]), rest_x=f(rest_x), inv_mass=f(inv_mass),
+                       n_dist=int(dist_idx.shape[0]), dist_idx=i(dist_idx),
+                       n_bend=int(bend_idx.shape[0]), bend_idx=i(bend_idx),
+                       n_tet=int(tet_idx.shape[0]), tet_idx=i(tet_idx),
+                       tet_gamma=f(tet_gamma) if (tet_gamma is not None and len(tet_gamma)) else None,
+                       n_colors=int(len(color_offsets) - 1), color_offsets=i(color_offsets),
+                       color_order=i(color_order))
+        h = C.c_void_p()
+        _check(L.xpbd_create(C.byref(md), C.byref(h)))
+        self._h = h
+        nv, nc, ncol = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(L.xpbd_sizes(h, C.byref(nv), C.byref(nc), C.byref(ncol)))
+        self.V, self.m, self.n_colors = nv.value, nc.value, ncol.value
+
+    @classmethod
+    def from_scene(cls, sc) -> "Solver":
+        return cls(sc.rest_x, sc.inv_mass, sc.dist_idx, sc.bend_idx, sc.tet_idx, sc.tet_gamma,
+                   sc.color_offsets, sc.color_order)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.xpbd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- sizes
+    def checkpoint_bytes(self, steps: int) -> int:
+        return int(lib().xpbd_checkpoint_bytes(self._h, steps))
+
+    def workspace_bytes(self, iters: int) -> int:
+        return int(lib().xpbd_workspace_bytes(self._h, iters))
+
+    def new_checkpoints(self, steps: int, device="cuda") -> torch.Tensor:
+        """[(steps+1), 2, V, 4] float32: per step (x,y,z,w) positions then velocities."""
+        return torch.empty((steps + 1, 2, self.V, 4), dtype=torch.float32, device=device)
+
+    # -- calls
+    def forward(self, params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
+                checkpoints: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        ck = self.new_checkpoints(steps, x0.device) if checkpoints is None else checkpoints
+        p = params.c_struct()
+        _check(lib().xpbd_forward(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
+                                  _ptr(ck), _stream(stream)))
+        return ck
+
+    def read_state(self, checkpoints: torch.Tensor, step: int, stream=None):
+        x = torch.empty((self.V, 3), dtype=torch.float32, device=checkpoints.device)
+        v = torch.empty_like(x)
+        _check(lib().xpbd_read_state(self._h, _ptr(checkpoints), int(step), _ptr(x), _ptr(v), _stream(stream)))
+        return x, v
+
+    def loss(self, checkpoints: torch.Tensor, targets: dict, stream=None):
+        """targets: {step: [V,3] float32 cuda}.  Returns (loss [1] float64, seeds [k,V,3])."""
+        keys = sorted(targets)
+        tg = torch.stack([targets[k] for k in keys]).contiguous()
+        seeds = torch.empty_like(tg)
+        out = torch.empty(1, dtype=torch.float64, device=checkpoints.device)
+        ks = (C.c_int32 * len(keys))(*keys)
+        _check(lib().xpbd_loss(self._h, _ptr(checkpoints), len(keys), ks, _ptr(tg), _ptr(out),
+                               _ptr(seeds), _stream(stream)))
+        return out, seeds
+
+    def adjoint(self, params: Params, steps: int, iters: int, checkpoints: torch.Tensor, seeds: dict,
+                seed_dv_T: Optional[torch.Tensor] = None, want=("compliance", "x0", "v0", "f_global",
+                                                                 "f_vertex", "collider"),
+                out: Optional[dict] = None, stream=None) -> dict:
+        """seeds: {step: dL/dx_step [V,3] float32 cuda}.  Returns float64 gradients."""
+        dev = checkpoints.device
+        keys = sorted(seeds)
+        sd = torch.stack([seeds[k] for k in keys]).contiguous() if keys else None
+        shapes = dict(compliance=(self.m,), x0=(self.V, 3), v0=(self.V, 3), f_global=(max(steps, 1), 3),
+                      f_vertex=(self.V, 3), collider=(5,))
+        if out is None:
+            out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
+        g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
+                      d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
+                      d_f_vertex=_ptr(out.get("f_vertex")), d_collider=_ptr(out.get("collider")))
+        p = params.c_struct()
+        ks = (C.c_int32 * max(len(keys), 1))(*keys)
+        _check(lib().xpbd_adjoint(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
+                                  len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), _stream(stream)))
+        return out
+
+    def sync_status(self, stream=None):
+        _check(lib().xpbd_sync_status(self._h, _stream(stream)))
+
+
+def params_from_scene(sc, device="cuda", compliance=None) -> Params:
+    """Device params of a scenes.Scene (uploads compliance and forces as float32)."""
+    t = lambda a: None if a is None else torch.as_tensor(np.asarray(a, np.float32), device=device).contiguous()
+    return Params(dt=float(sc.dt), compliance=t(sc.compliance if compliance is None else compliance),
+                  gravity=tuple(float(g) for g in sc.gravity), f_global=t(sc.f_global), f_vertex=t(sc.f_vertex),
+                  collider_flags=int(sc.collider_flags), plane_h=float(sc.plane_h),
+                  sphere=tuple(float(v) for v in sc.sphere), contact_compliance=float(sc.contact_compliance),
+                  thickness=float(sc.thickness))
+
+
+class XPBDSolve(torch.autograd.Function):
+    """Differentiable XPBD rollout: positions at the key steps as a function of
+    (compliance, x0, v0, f_global, f_vertex, collider = [plane_h, cx, cy, cz, r]).
+    backward runs the library's reverse sweep; float64 gradients are cast to each input's
+    dtype."""
+
+    @staticmethod
+    def forward(ctx, solver: Solver, cfg: dict, key_steps: tuple, compliance, x0, v0, f_global,
+                f_vertex, collider):
+        steps, iters = cfg["steps"], cfg["iters"]
+        col = [float(v) for v in collider.detach().cpu().tolist()] if collider is not None else [0.0] * 5
+        p = Params(dt=cfg["dt"], compliance=compliance.detach().contiguous(), gravity=cfg.get("gravity", (0, -9.81, 0)),
+                   f_global=None if f_global is None else f_global.detach().contiguous(),
+                   f_vertex=None if f_vertex is None else f_vertex.detach().contiguous(),
+                   collider_flags=cfg.get("collider_flags", 0), plane_h=col[0], sphere=col[1:5],
+                   contact_compliance=cfg.get("contact_compliance", 1e-8), thickness=cfg.get("thickness", 0.0))
+        ck = solver.forward(p, steps, iters, x0.detach().contiguous(), v0.detach().contiguous())
+        outs = [solver.read_state(ck, k)[0] for k in key_steps]
+        ctx.save_for_backward(ck)
+        ctx.solver, ctx.params, ctx.cfg, ctx.key_steps = solver, p, cfg, key_steps
+        ctx.dtypes = [None if t is None else t.dtype for t in (compliance, x0, v0, f_global, f_vertex, collider)]
+        ctx.devices = [None if t is None else t.device for t in (compliance, x0, v0, f_global, f_vertex, collider)]
+        return tuple(outs)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        (ck,) = ctx.saved_tensors
+        seeds = {}
+        for k, g in zip(ctx.key_steps, grads):
+            if g is None:
+                continue
+            g = g.to(torch.float32).contiguous()
+            seeds[k] = seeds[k] + g if k in seeds else g
+        want = [n for n, t in zip(("compliance", "x0", "v0", "f_global", "f_vertex", "collider"), ctx.dtypes)
+                if t is not None]
+        gr = ctx.solver.adjoint(ctx.params, ctx.cfg["steps"], ctx.cfg["iters"], ck, seeds, want=tuple(want))
+        res = []
+        for name, dt, dev in zip(("compliance", "x0", "v0", "f_global", "f_vertex", "collider"), ctx.dtypes,
+                                 ctx.devices):
+            res.append(None if dt is None else gr[name].to(device=dev, dtype=dt))
+        return (None, None, None, *res)
+
+
+def simulate(solver: Solver, cfg: dict, compliance, x0, v0, f_global=None, f_vertex=None, collider=None,
+             key_steps=None):
+    """Autograd entry point: returns the positions [V,3] at each key step (default: the last)."""
+    ks = (cfg["steps"],) if key_steps is None else tuple(key_steps)
+    return XPBDSolve.apply(solver, cfg, ks, compliance, x0, v0, f_global, f_vertex, collider)

@@ -1,0 +1,617 @@
+// Host runtime of the C ABI declared in include/diffxpbd.h.
+//
+// xpbd_create validates the model, derives rest data (spring lengths, hinge angles,
+// Dm^-1, tet volumes) from the rest positions, regroups every color by constraint type and
+// first vertex and uploads the records.  xpbd_forward / xpbd_adjoint queue the per-color
+// kernels of xpbd_kernels.cu on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/diffxpbd.h"
+#include "xpbd_kernels.cuh"
+
+using namespace xpbd;
+
+namespace {
+
+thread_local std::string g_err;
+
+xpbd_status fail(xpbd_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CU_TRY(expr)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? XPBD_ERR_OOM : XPBD_ERR_CUDA,       \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+#define LAUNCH_CHECK()                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(XPBD_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Seg {
+  SegType type;
+  int begin;   // first record of the type array
+  int count;
+};
+
+// Device buffer that grows on demand and is freed with the handle.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need ? need : 16);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+}  // namespace
+
+struct xpbd_solver {
+  int V = 0, nd = 0, nb = 0, nt = 0, m = 0, K = 0;
+  std::vector<std::vector<Seg>> colors;
+  // type arrays in record order; rec_off[t] = offset of type t in the m-long record space
+  int n_rec[4] = {0, 0, 0, 0};
+  int rec_off[4] = {0, 0, 0, 0};
+  void* d_rec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* d_perm = nullptr;        // [m] record index -> global constraint id
+  float* d_w = nullptr;         // [V] inverse masses
+  int* d_err = nullptr;
+  // workspace
+  DevBuf P, lam, cflags, lamc;                       // forward
+  DevBuf tape, lam_tape, tape_c, lamc_tape;          // replay tapes
+  DevBuf xbar, vbar, lb, acc, lbc, cgrad, partials;  // reverse
+  int ws_iters = 0;
+  size_t tape_per_iter() const {  // float4 entries per iteration
+    return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
+  }
+};
+
+namespace {
+
+size_t tape_offset(const xpbd_solver* h, SegType t) {   // float4 offset of type t in one iteration
+  size_t o = 0;
+  for (int k = 0; k < (int)t; ++k) o += (size_t)h->n_rec[k] * kVerts[k];
+  return o;
+}
+
+void* rec_ptr(const xpbd_solver* h, SegType t, int begin) {
+  static const size_t sz[4] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec)};
+  return (char*)h->d_rec[t] + sz[t] * (size_t)begin;
+}
+
+Collide make_collide(const xpbd_params* p) {
+  Collide c;
+  c.flags = p->collider_flags & 3;
+  c.h = p->plane_h;
+  c.cx = p->sphere[0];
+  c.cy = p->sphere[1];
+  c.cz = p->sphere[2];
+  c.r = p->sphere[3];
+  c.at = p->contact_compliance / (p->dt * p->dt);
+  c.thick = p->thickness;
+  return c;
+}
+
+xpbd_status check_params(const xpbd_solver* h, const xpbd_params* p, int steps, int iters) {
+  if (!h || !p) return fail(XPBD_ERR_INVALID, "null handle or params");
+  if (steps < 0 || iters < 1) return fail(XPBD_ERR_INVALID, "steps must be >= 0 and iters >= 1");
+  if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(XPBD_ERR_INVALID, "dt must be positive");
+  if (h->m > 0 && !p->compliance) return fail(XPBD_ERR_INVALID, "compliance is NULL");
+  if (p->collider_flags & ~3) return fail(XPBD_ERR_INVALID, "unknown collider flag");
+  if ((p->collider_flags & XPBD_COLLIDE_SPHERE) && !(p->sphere[3] > 0.f))
+    return fail(XPBD_ERR_INVALID, "sphere radius must be positive");
+  if (p->collider_flags && !(p->contact_compliance >= 0.f))
+    return fail(XPBD_ERR_INVALID, "contact compliance must be >= 0");
+  return XPBD_OK;
+}
+
+// Forward workspace (no tapes).
+xpbd_status ensure_forward_ws(xpbd_solver* h) {
+  CU_TRY(h->P.ensure(sizeof(float4) * (size_t)h->V));
+  CU_TRY(h->lam.ensure(sizeof(float) * (size_t)std::max(h->m, 1)));
+  CU_TRY(h->cflags.ensure((size_t)std::max(h->V, 1)));
+  CU_TRY(h->lamc.ensure(sizeof(float2) * (size_t)std::max(h->V, 1)));
+  return XPBD_OK;
+}
+
+xpbd_status ensure_adjoint_ws(xpbd_solver* h, int iters, bool contacts) {
+  xpbd_status st = ensure_forward_ws(h);
+  if (st != XPBD_OK) return st;
+  size_t V = (size_t)h->V, m = (size_t)std::max(h->m, 1);
+  CU_TRY(h->tape.ensure(sizeof(float4) * h->tape_per_iter() * iters));
+  CU_TRY(h->lam_tape.ensure(sizeof(float) * m * iters));
+  if (contacts) {
+    CU_TRY(h->tape_c.ensure(sizeof(float4) * V * iters));
+    CU_TRY(h->lamc_tape.ensure(sizeof(float2) * V * iters));
+    CU_TRY(h->lbc.ensure(sizeof(float2) * V));
+    CU_TRY(h->cgrad.ensure(sizeof(float) * 5 * V));
+  }
+  CU_TRY(h->xbar.ensure(sizeof(float4) * V));
+  CU_TRY(h->vbar.ensure(sizeof(float4) * V));
+  CU_TRY(h->lb.ensure(sizeof(float2) * m));
+  CU_TRY(h->acc.ensure(sizeof(double) * m));
+  CU_TRY(h->partials.ensure(sizeof(double) * 5 * (size_t)partial_blocks(std::max(h->V, 1))));
+  return XPBD_OK;
+}
+
+xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s) {
+  float inv_dt2 = 1.f / (p->dt * p->dt);
+  for (int t = 0; t < 4; ++t)
+    launch_set_alpha((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t], p->compliance,
+                     inv_dt2, h->d_err, s);
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+// One step: prediction from checkpoint n, `iters` colored iterations, collision passes.
+// With `record`, the multipliers of iteration k go to lam_tape[k] and the pre-projection
+// positions to tape[k] (replay for the reverse sweep); otherwise lambda is updated in place.
+xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, const float4* ckx_n,
+                     const float4* ckv_n, bool record, cudaStream_t s) {
+  Collide c = make_collide(p);
+  float4* P = h->P.as<float4>();
+  uint8_t* cf = h->cflags.as<uint8_t>();
+  launch_predict(ckx_n, ckv_n, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex,
+                 p->dt, p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
+  LAUNCH_CHECK();
+  const size_t tpi = h->tape_per_iter();
+  for (int k = 0; k < iters; ++k) {
+    float* lam_in;
+    float* lam_out;
+    float4* tape_k = nullptr;
+    if (record) {
+      lam_in = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->m;
+      lam_out = h->lam_tape.as<float>() + (size_t)k * h->m;
+      tape_k = h->tape.as<float4>() + (size_t)k * tpi;
+    } else {
+      lam_in = k == 0 ? nullptr : h->lam.as<float>();
+      lam_out = h->lam.as<float>();
+    }
+    for (int col = 0; col < h->K; ++col) {
+      for (const Seg& g : h->colors[col]) {
+        size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+        float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
+        launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
+                       lam_out + ro, tp, s);
+      }
+    }
+    if (c.flags) {
+      float2* li;
+      float2* lo;
+      float4* tc = nullptr;
+      if (record) {
+        li = k == 0 ? nullptr : h->lamc_tape.as<float2>() + (size_t)(k - 1) * h->V;
+        lo = h->lamc_tape.as<float2>() + (size_t)k * h->V;
+        tc = h->tape_c.as<float4>() + (size_t)k * h->V;
+      } else {
+        li = k == 0 ? nullptr : h->lamc.as<float2>();
+        lo = h->lamc.as<float2>();
+      }
+      launch_contact(P, cf, h->V, li, lo, tc, c, s);
+    }
+    LAUNCH_CHECK();
+  }
+  return XPBD_OK;
+}
+
+const float4* ck_x(const float* ck, int V, int n) { return reinterpret_cast<const float4*>(ck) + (size_t)2 * V * n; }
+const float4* ck_v(const float* ck, int V, int n) { return ck_x(ck, V, n) + V; }
+
+double rest_angle(const double* x0, const double* x1, const double* x2, const double* x3) {
+  double e[3], a[3], b[3];
+  for (int c = 0; c < 3; ++c) {
+    e[c] = x1[c] - x0[c];
+    a[c] = x2[c] - x0[c];
+    b[c] = x3[c] - x0[c];
+  }
+  auto cr = [](const double* u, const double* v, double* o) {
+    o[0] = u[1] * v[2] - u[2] * v[1];
+    o[1] = u[2] * v[0] - u[0] * v[2];
+    o[2] = u[0] * v[1] - u[1] * v[0];
+  };
+  double nA[3], nB[3], nn[3];
+  cr(e, a, nA);
+  cr(b, e, nB);
+  cr(nA, nB, nn);
+  double le = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  double sn = (nn[0] * e[0] + nn[1] * e[1] + nn[2] * e[2]) / le;
+  double cs = nA[0] * nB[0] + nA[1] * nB[1] + nA[2] * nB[2];
+  return std::atan2(sn, cs);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xpbd_last_error(void) { return g_err.c_str(); }
+
+xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
+  g_err.clear();
+  if (!md || !out) return fail(XPBD_ERR_INVALID, "null argument");
+  *out = nullptr;
+  const int V = md->n_vertices, nd = md->n_dist, nb = md->n_bend, nt = md->n_tet, K = md->n_colors;
+  if (V < 0 || nd < 0 || nb < 0 || nt < 0 || K < 0) return fail(XPBD_ERR_INVALID, "negative size");
+  const long long mll = (long long)nd + nb + 2LL * nt;
+  if (mll > 0x7fffffffLL) return fail(XPBD_ERR_INVALID, "too many constraints");
+  const int m = (int)mll;
+  if (V > 0 && (!md->rest_x || !md->inv_mass)) return fail(XPBD_ERR_INVALID, "rest_x/inv_mass NULL");
+  if ((nd && !md->dist_idx) || (nb && !md->bend_idx) || (nt && !md->tet_idx))
+    return fail(XPBD_ERR_INVALID, "index array NULL");
+  if (!md->color_offsets || (m > 0 && !md->color_order)) return fail(XPBD_ERR_INVALID, "coloring NULL");
+  for (int i = 0; i < 3 * V; ++i)
+    if (!std::isfinite(md->rest_x[i])) return fail(XPBD_ERR_INVALID, "non-finite rest position");
+  for (int i = 0; i < V; ++i)
+    if (!(md->inv_mass[i] >= 0.f) || !std::isfinite(md->inv_mass[i]))
+      return fail(XPBD_ERR_INVALID, "inverse mass must be finite and >= 0");
+  auto verts_of = [&](int j, int* vs) -> int {
+    if (j < nd) { vs[0] = md->dist_idx[2 * (size_t)j]; vs[1] = md->dist_idx[2 * (size_t)j + 1]; return 2; }
+    j -= nd;
+    if (j < nb) { for (int k = 0; k < 4; ++k) vs[k] = md->bend_idx[4 * (size_t)j + k]; return 4; }
+    j -= nb;
+    int t = j % nt;
+    for (int k = 0; k < 4; ++k) vs[k] = md->tet_idx[4 * (size_t)t + k];
+    return 4;
+  };
+  for (int j = 0; j < m; ++j) {
+    int vs[4];
+    int nv = verts_of(j, vs);
+    for (int k = 0; k < nv; ++k) {
+      if (vs[k] < 0 || vs[k] >= V) return fail(XPBD_ERR_INVALID, "vertex index out of range in constraint " + std::to_string(j));
+      for (int q = 0; q < k; ++q)
+        if (vs[q] == vs[k]) return fail(XPBD_ERR_INVALID, "constraint " + std::to_string(j) + " repeats a vertex");
+    }
+  }
+  // coloring: offsets monotone, a permutation of [0, m), vertex-disjoint colors
+  if (md->color_offsets[0] != 0 || md->color_offsets[K] != m)
+    return fail(XPBD_ERR_COLORING, "color offsets must start at 0 and end at m");
+  std::vector<char> seen(m, 0);
+  std::vector<int> stamp(V, -1);
+  for (int c = 0; c < K; ++c) {
+    int b = md->color_offsets[c], e = md->color_offsets[c + 1];
+    if (e < b) return fail(XPBD_ERR_COLORING, "color offsets decrease");
+    for (int t = b; t < e; ++t) {
+      int j = md->color_order[t];
+      if (j < 0 || j >= m) return fail(XPBD_ERR_COLORING, "constraint id out of range in coloring");
+      if (seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " appears twice");
+      seen[j] = 1;
+      int vs[4];
+      int nv = verts_of(j, vs);
+      for (int k = 0; k < nv; ++k) {
+        if (stamp[vs[k]] == c)
+          return fail(XPBD_ERR_COLORING, "color " + std::to_string(c) + " has two constraints on vertex " + std::to_string(vs[k]));
+        stamp[vs[k]] = c;
+      }
+    }
+  }
+  for (int j = 0; j < m; ++j)
+    if (!seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " has no color");
+
+  // records, grouped by color, then type, then first vertex
+  xpbd_solver* h = new xpbd_solver();
+  h->V = V; h->nd = nd; h->nb = nb; h->nt = nt; h->m = m; h->K = K;
+  h->n_rec[0] = nd; h->n_rec[1] = nb; h->n_rec[2] = nt; h->n_rec[3] = nt;
+  h->rec_off[0] = 0; h->rec_off[1] = nd; h->rec_off[2] = nd + nb; h->rec_off[3] = nd + nb + nt;
+  std::vector<DistRec> rd; rd.reserve(nd);
+  std::vector<BendRec> rb; rb.reserve(nb);
+  std::vector<TetRec> rh, rdv; rh.reserve(nt); rdv.reserve(nt);
+  std::vector<int> perm(m);
+  auto X = [&](int v, double* o) { for (int c = 0; c < 3; ++c) o[c] = md->rest_x[3 * (size_t)v + c]; };
+  h->colors.resize(K);
+  for (int c = 0; c < K; ++c) {
+    int b = md->color_offsets[c], e = md->color_offsets[c + 1];
+    std::vector<int> ids[4];
+    for (int t = b; t < e; ++t) {
+      int j = md->color_order[t];
+      int type = j < nd ? 0 : (j < nd + nb ? 1 : (j < nd + nb + nt ? 2 : 3));
+      ids[type].push_back(j);
+    }
+    for (int type = 0; type < 4; ++type) {
+      if (ids[type].empty()) continue;
+      std::stable_sort(ids[type].begin(), ids[type].end(), [&](int a, int bb) {
+        int va[4], vb[4];
+        verts_of(a, va);
+        verts_of(bb, vb);
+        return va[0] < vb[0];
+      });
+      Seg sg;
+      sg.type = (SegType)type;
+      sg.count = (int)ids[type].size();
+      sg.begin = type == 0 ? (int)rd.size() : type == 1 ? (int)rb.size() : type == 2 ? (int)rh.size() : (int)rdv.size();
+      for (int j : ids[type]) {
+        int vs[4];
+        verts_of(j, vs);
+        if (type == 0) {
+          double a[3], bb[3];
+          X(vs[0], a);
+          X(vs[1], bb);
+          DistRec r;
+          r.a = vs[0];
+          r.b = vs[1];
+          r.L = (float)std::sqrt((a[0] - bb[0]) * (a[0] - bb[0]) + (a[1] - bb[1]) * (a[1] - bb[1]) + (a[2] - bb[2]) * (a[2] - bb[2]));
+          r.at = 0.f;
+          perm[h->rec_off[0] + rd.size()] = j;
+          rd.push_back(r);
+        } else if (type == 1) {
+          double x[4][3];
+          for (int k = 0; k < 4; ++k) X(vs[k], x[k]);
+          BendRec r;
+          for (int k = 0; k < 4; ++k) r.v[k] = vs[k];
+          r.theta0 = (float)rest_angle(x[0], x[1], x[2], x[3]);
+          r.at = 0.f;
+          r.pad0 = r.pad1 = 0.f;
+          perm[h->rec_off[1] + rb.size()] = j;
+          rb.push_back(r);
+        } else {
+          double x[4][3];
+          for (int k = 0; k < 4; ++k) X(vs[k], x[k]);
+          double Dm[9];
+          for (int col = 0; col < 3; ++col)
+            for (int row = 0; row < 3; ++row) Dm[row * 3 + col] = x[col + 1][row] - x[0][row];
+          double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+                       Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+          if (!(std::fabs(det) > 1e-30) || !std::isfinite(det)) {
+            delete h;
+            return fail(XPBD_ERR_INVALID, "degenerate rest tetrahedron " + std::to_string(j));
+          }
+          double inv[9] = {Dm[4] * Dm[8] - Dm[5] * Dm[7], Dm[2] * Dm[7] - Dm[1] * Dm[8], Dm[1] * Dm[5] - Dm[2] * Dm[4],
+                           Dm[5] * Dm[6] - Dm[3] * Dm[8], Dm[0] * Dm[8] - Dm[2] * Dm[6], Dm[2] * Dm[3] - Dm[0] * Dm[5],
+                           Dm[3] * Dm[7] - Dm[4] * Dm[6], Dm[1] * Dm[6] - Dm[0] * Dm[7], Dm[0] * Dm[4] - Dm[1] * Dm[3]};
+          TetRec r;
+          for (int k = 0; k < 4; ++k) r.v[k] = vs[k];
+          for (int k = 0; k < 9; ++k) r.B[k] = (float)(inv[k] / det);
+          r.at = 0.f;
+          int t = (j - nd - nb) % nt;
+          r.gamma = md->tet_gamma ? md->tet_gamma[t] : 1.f;
+          r.vol = (float)(std::fabs(det) / 6.0);
+          if (type == 2) {
+            perm[h->rec_off[2] + rh.size()] = j;
+            rh.push_back(r);
+          } else {
+            perm[h->rec_off[3] + rdv.size()] = j;
+            rdv.push_back(r);
+          }
+        }
+      }
+      h->colors[c].push_back(sg);
+    }
+  }
+  // upload
+  auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    *dst = nullptr;
+    if (!bytes) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = up(&h->d_rec[0], rd.data(), rd.size() * sizeof(DistRec));
+  if (e == cudaSuccess) e = up(&h->d_rec[1], rb.data(), rb.size() * sizeof(BendRec));
+  if (e == cudaSuccess) e = up(&h->d_rec[2], rh.data(), rh.size() * sizeof(TetRec));
+  if (e == cudaSuccess) e = up(&h->d_rec[3], rdv.data(), rdv.size() * sizeof(TetRec));
+  if (e == cudaSuccess) e = up((void**)&h->d_perm, perm.data(), perm.size() * sizeof(int));
+  if (e == cudaSuccess) e = up((void**)&h->d_w, md->inv_mass, (size_t)V * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    xpbd_destroy(h);
+    return fail(e == cudaErrorMemoryAllocation ? XPBD_ERR_OOM : XPBD_ERR_CUDA,
+                std::string("xpbd_create upload: ") + cudaGetErrorString(e));
+  }
+  *out = h;
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_destroy(xpbd_handle h) {
+  if (!h) return XPBD_OK;
+  cudaDeviceSynchronize();
+  for (int t = 0; t < 4; ++t)
+    if (h->d_rec[t]) cudaFree(h->d_rec[t]);
+  if (h->d_perm) cudaFree(h->d_perm);
+  if (h->d_w) cudaFree(h->d_w);
+  if (h->d_err) cudaFree(h->d_err);
+  DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
+                    &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
+                    &h->partials};
+  for (DevBuf* b : bufs) b->release();
+  delete h;
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_sizes(xpbd_handle h, int32_t* nv, int32_t* nc, int32_t* ncol) {
+  if (!h) return fail(XPBD_ERR_INVALID, "null handle");
+  if (nv) *nv = h->V;
+  if (nc) *nc = h->m;
+  if (ncol) *ncol = h->K;
+  return XPBD_OK;
+}
+
+size_t xpbd_checkpoint_bytes(xpbd_handle h, int32_t steps) {
+  if (!h || steps < 0) return 0;
+  return (size_t)(steps + 1) * (size_t)h->V * 2 * sizeof(float4);
+}
+
+size_t xpbd_workspace_bytes(xpbd_handle h, int32_t iters) {
+  if (!h || iters < 1) return 0;
+  size_t V = h->V, m = std::max(h->m, 1);
+  size_t b = 16 * V + 4 * m + V + 8 * V;                          // forward
+  b += 16 * h->tape_per_iter() * iters + 4 * m * iters;            // replay tapes
+  b += (16 + 8) * V * iters + 8 * V + 20 * V;                      // contact tapes and scratch
+  b += 32 * V + 8 * m + 8 * m + 40 * (size_t)partial_blocks(std::max(h->V, 1));
+  return b;
+}
+
+xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                         const float* x0, const float* v0, float* ck, void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (h->V > 0 && (!x0 || !v0 || !ck)) return fail(XPBD_ERR_INVALID, "x0/v0/checkpoints NULL");
+  if (h->V == 0) return XPBD_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_forward_ws(h);
+  if (st != XPBD_OK) return st;
+  st = set_alpha(h, p, s);
+  if (st != XPBD_OK) return st;
+  float4* ck4 = reinterpret_cast<float4*>(ck);
+  launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + h->V, h->V, s);
+  LAUNCH_CHECK();
+  const float inv_dt = 1.f / p->dt;
+  for (int n = 0; n < steps; ++n) {
+    st = run_step(h, p, n, iters, ck_x(ck, h->V, n), ck_v(ck, h->V, n), false, s);
+    if (st != XPBD_OK) return st;
+    float4* nx = ck4 + (size_t)2 * h->V * (n + 1);
+    launch_velocity(h->P.as<float4>(), ck_x(ck, h->V, n), nx, nx + h->V, inv_dt, h->V, h->d_err, s);
+    LAUNCH_CHECK();
+  }
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_read_state(xpbd_handle h, const float* ck, int32_t step, float* x_out, float* v_out,
+                            void* stream) {
+  if (!h || !ck || step < 0) return fail(XPBD_ERR_INVALID, "bad argument");
+  launch_read_state(ck_x(ck, h->V, step), ck_v(ck, h->V, step), x_out, v_out, h->V, (cudaStream_t)stream);
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_loss(xpbd_handle h, const float* ck, int32_t n_keys, const int32_t* key_steps,
+                      const float* targets, double* loss_out, float* seeds_out, void* stream) {
+  g_err.clear();
+  if (!h || !ck || n_keys < 0 || (n_keys > 0 && (!key_steps || !targets)))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int pb = partial_blocks(std::max(h->V, 1));
+  CU_TRY(h->partials.ensure(sizeof(double) * 5 * (size_t)pb));
+  if (loss_out) CU_TRY(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
+  for (int k = 0; k < n_keys; ++k) {
+    if (key_steps[k] < 0) return fail(XPBD_ERR_INVALID, "negative key step");
+    launch_loss(ck_x(ck, h->V, key_steps[k]), targets + 3 * (size_t)h->V * k,
+                seeds_out ? seeds_out + 3 * (size_t)h->V * k : nullptr, h->partials.as<double>(), h->V, s);
+    if (loss_out) launch_reduce_partials(h->partials.as<double>(), pb, 1, loss_out, true, s);
+    LAUNCH_CHECK();
+  }
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                         const float* ck, int32_t n_seeds, const int32_t* seed_steps,
+                         const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
+                         void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (!ck || !out || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  std::vector<int> seed_of(steps + 1, -1);
+  for (int k = 0; k < n_seeds; ++k) {
+    int n = seed_steps[k];
+    if (n < 0 || n > steps) return fail(XPBD_ERR_INVALID, "seed step out of range");
+    if (seed_of[n] >= 0) return fail(XPBD_ERR_INVALID, "two seeds for one step");
+    seed_of[n] = k;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int V = h->V;
+  const bool contacts = (p->collider_flags & 3) != 0;
+  st = ensure_adjoint_ws(h, iters, contacts);
+  if (st != XPBD_OK) return st;
+  st = set_alpha(h, p, s);
+  if (st != XPBD_OK) return st;
+  const int pb = partial_blocks(std::max(V, 1));
+  double* partials = h->partials.as<double>();
+  CU_TRY(cudaMemsetAsync(h->acc.p, 0, sizeof(double) * (size_t)std::max(h->m, 1), s));
+  if (out->d_f_vertex) CU_TRY(cudaMemsetAsync(out->d_f_vertex, 0, sizeof(double) * 3 * (size_t)V, s));
+  if (out->d_collider) CU_TRY(cudaMemsetAsync(out->d_collider, 0, sizeof(double) * 5, s));
+  if (out->d_f_global && steps > 0) CU_TRY(cudaMemsetAsync(out->d_f_global, 0, sizeof(double) * 3 * (size_t)steps, s));
+  float4* xbar = h->xbar.as<float4>();
+  float4* vbar = h->vbar.as<float4>();
+  launch_seed_adjoint(seed_of[steps] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[steps] : nullptr, seed_dv_T,
+                      xbar, vbar, V, s);
+  LAUNCH_CHECK();
+  const float inv_dt = 1.f / p->dt;
+  const size_t tpi = h->tape_per_iter();
+  Collide c = make_collide(p);
+  for (int n = steps - 1; n >= 0; --n) {
+    launch_adj_begin(xbar, vbar, inv_dt, V, s);
+    st = run_step(h, p, n, iters, ck_x(ck, V, n), ck_v(ck, V, n), true, s);
+    if (st != XPBD_OK) return st;
+    for (int k = iters - 1; k >= 0; --k) {
+      const bool first = k == iters - 1, last = k == 0;
+      if (contacts) {
+        launch_vjp_contact(h->tape_c.as<float4>() + (size_t)k * V, h->cflags.as<uint8_t>(), V,
+                           k == 0 ? nullptr : h->lamc_tape.as<float2>() + (size_t)(k - 1) * V, xbar,
+                           h->lbc.as<float2>(), out->d_collider ? h->cgrad.as<float>() : nullptr, first, c, s);
+      }
+      const float4* tape_k = h->tape.as<float4>() + (size_t)k * tpi;
+      const float* lam_pre = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->m;
+      for (int col = h->K - 1; col >= 0; --col) {
+        const std::vector<Seg>& segs = h->colors[col];
+        for (int q = (int)segs.size() - 1; q >= 0; --q) {
+          const Seg& g = segs[q];
+          size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+          launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count,
+                     tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type],
+                     lam_pre ? lam_pre + ro : nullptr, xbar, h->lb.as<float2>() + ro,
+                     h->acc.as<double>() + ro, first, last, s);
+        }
+      }
+      LAUNCH_CHECK();
+    }
+    if (contacts && out->d_collider) {
+      launch_collider_partials(h->cgrad.as<float>(), h->cflags.as<uint8_t>(), V, partials, s);
+      launch_reduce_partials(partials, pb, 5, out->d_collider, true, s);
+    }
+    const float* seed = seed_of[n] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[n] : nullptr;
+    launch_adj_predict(xbar, vbar, ck_x(ck, V, n), seed, p->dt, out->d_f_vertex,
+                       out->d_f_global ? partials : nullptr, V, s);
+    if (out->d_f_global) launch_reduce_partials(partials, pb, 3, out->d_f_global + 3 * (size_t)n, false, s);
+    LAUNCH_CHECK();
+  }
+  if (out->d_x0) launch_to_double(xbar, out->d_x0, V, s);
+  if (out->d_v0) launch_to_double(vbar, out->d_v0, V, s);
+  if (out->d_compliance) {
+    float inv_dt2 = 1.f / (p->dt * p->dt);
+    for (int t = 0; t < 4; ++t)
+      launch_finalize_compliance((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t],
+                                 h->acc.as<double>() + h->rec_off[t], inv_dt2, out->d_compliance, s);
+  }
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_sync_status(xpbd_handle h, void* stream) {
+  if (!h) return fail(XPBD_ERR_INVALID, "null handle");
+  CU_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int err = 0;
+  CU_TRY(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CU_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+  if (err & 2) return fail(XPBD_ERR_NONFINITE, "a compliance value is negative or not finite");
+  if (err & 1) return fail(XPBD_ERR_NONFINITE, "a step produced a non-finite position or velocity");
+  return XPBD_OK;
+}
+
+}  // extern "C"

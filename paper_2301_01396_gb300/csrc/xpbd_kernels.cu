@@ -1,0 +1,723 @@
+// sm_103a kernels of the XPBD step (Sec. 3.1 of DiffXPBD) and of its discrete adjoint.
+//
+// Layout in HBM: vertices as float4 (x, y, z, inverse mass); constraint records of one
+// color contiguous and sorted by first vertex (coalesced gathers along grid rows);
+// multipliers lambda as float in record order; the adjoint's per-iteration tape holds the
+// pre-projection float4 of every vertex of every constraint, in record order.
+//
+// One thread updates one constraint of the current color: the color's constraints are
+// vertex-disjoint (Sec. 3.1, graph coloring), so the Jacobi update inside a color equals
+// the sequential Gauss-Seidel order.  The path is gather/scatter bound (no dense
+// contraction), so the kernels are written for HBM traffic: 128-bit vertex and record
+// accesses, streaming (evict-first) hints on single-use tape/multiplier data.
+#include "xpbd_kernels.cuh"
+
+namespace xpbd {
+
+namespace {
+
+__device__ __forceinline__ f3 xyz(float4 a) { return mk3(a.x, a.y, a.z); }
+__device__ __forceinline__ float4 with_w(f3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
+
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+
+inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
+
+// ------------------------------------------------------------------ deterministic reductions
+// Block-wide sum of NC doubles; thread 0 writes the block's partial sums.  The order of
+// additions depends only on the launch shape, so results are bitwise reproducible.
+template <int NC>
+__device__ void block_sum_store(double v[NC], double* out) {
+  __shared__ double sh[NC][kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double x = v[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[c][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double t = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) t += sh[c][w];
+      out[c] = t;
+    }
+  }
+}
+
+constexpr int kMaxPartialBlocks = 1024;
+
+}  // namespace
+
+int partial_blocks(int V) {
+  int b = grid_for(V);
+  return b < 1 ? 1 : (b > kMaxPartialBlocks ? kMaxPartialBlocks : b);
+}
+
+// ======================================================================== forward
+
+__global__ void k_init_ckpt(const float* __restrict__ x0, const float* __restrict__ v0,
+                            const float* __restrict__ w, float4* __restrict__ ckx,
+                            float4* __restrict__ ckv, int V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  ckx[i] = make_float4(x0[3 * i], x0[3 * i + 1], x0[3 * i + 2], w[i]);
+  ckv[i] = make_float4(v0[3 * i], v0[3 * i + 1], v0[3 * i + 2], 0.f);
+}
+
+void launch_init_ckpt(const float* x0, const float* v0, const float* w, float4* ckx, float4* ckv,
+                      int V, cudaStream_t s) {
+  if (V > 0) k_init_ckpt<<<grid_for(V), kBlock, 0, s>>>(x0, v0, w, ckx, ckv, V);
+}
+
+// alpha~ of every record from the caller's per-constraint compliance (caller order).  A
+// compliance that is negative or not finite sets bit 1 of the error word.
+template <class Rec, bool VOL>
+__global__ void k_set_alpha(Rec* __restrict__ rec, const int* __restrict__ perm, int n,
+                            const float* __restrict__ compliance, float inv_dt2, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float c = compliance[perm[i]];
+  if (!(c >= 0.f) || isinf(c)) atomicOr(err, 2);
+  float a = c * inv_dt2;
+  if constexpr (VOL) a = a / rec[i].vol;
+  rec[i].at = a;
+}
+
+void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float* compliance,
+                      float inv_dt2, int* err, cudaStream_t s) {
+  if (n <= 0) return;
+  switch (t) {
+    case SEG_DIST:
+      k_set_alpha<DistRec, false><<<grid_for(n), kBlock, 0, s>>>((DistRec*)rec, perm, n, compliance, inv_dt2, err);
+      break;
+    case SEG_BEND:
+      k_set_alpha<BendRec, false><<<grid_for(n), kBlock, 0, s>>>((BendRec*)rec, perm, n, compliance, inv_dt2, err);
+      break;
+    default:
+      k_set_alpha<TetRec, true><<<grid_for(n), kBlock, 0, s>>>((TetRec*)rec, perm, n, compliance, inv_dt2, err);
+  }
+}
+
+// Inertial prediction (Eq. xpbdUpdateRule): p = x + dt v + dt^2 (w (G_n + W_i) + [w > 0] g),
+// and contact detection at p: a contact is active for the whole step when C(p) < 0.
+__global__ void k_predict(const float4* __restrict__ ckx, const float4* __restrict__ ckv,
+                          float4* __restrict__ P, const float* __restrict__ fg_n,
+                          const float* __restrict__ fv, float dt, float gx, float gy, float gz,
+                          Collide c, uint8_t* __restrict__ cflags, int V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  float4 x = ckx[i];
+  float4 v = ckv[i];
+  float w = x.w;
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  if (fg_n) { fx = fg_n[0]; fy = fg_n[1]; fz = fg_n[2]; }
+  if (fv) { fx += fv[3 * i]; fy += fv[3 * i + 1]; fz += fv[3 * i + 2]; }
+  float free_ = w > 0.f ? 1.f : 0.f;
+  float dt2 = dt * dt;
+  float4 p;
+  p.x = x.x + dt * v.x + dt2 * (w * fx + free_ * gx);
+  p.y = x.y + dt * v.y + dt2 * (w * fy + free_ * gy);
+  p.z = x.z + dt * v.z + dt2 * (w * fz + free_ * gz);
+  p.w = w;
+  P[i] = p;
+  if (c.flags) {
+    uint8_t f = 0;
+    if ((c.flags & 1) && (p.y - c.h - c.thick < 0.f)) f |= 1;
+    if (c.flags & 2) {
+      float dx = p.x - c.cx, dy = p.y - c.cy, dz = p.z - c.cz;
+      if (sqrtf(dx * dx + dy * dy + dz * dz) - c.r - c.thick < 0.f) f |= 2;
+    }
+    cflags[i] = f;
+  }
+}
+
+void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float* fg_n,
+                    const float* fv, float dt, float gx, float gy, float gz, Collide c,
+                    uint8_t* cflags, int V, cudaStream_t s) {
+  if (V > 0)
+    k_predict<<<grid_for(V), kBlock, 0, s>>>(ckx, ckv, P, fg_n, fv, dt, gx, gy, gz, c, cflags, V);
+}
+
+// ---- distance: C = |x_a - x_b| - L, grad_a = n = (x_a - x_b)/l, grad_b = -n
+// lam_in and lam_out may alias (in-place forward), so they are not __restrict__.
+__global__ void k_proj_dist(const DistRec* __restrict__ rec, int n, float4* __restrict__ P,
+                            const float* lam_in, float* lam_out, float4* __restrict__ tape) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const DistRec r = rec[i];
+  float4 pa = P[r.a];
+  float4 pb = P[r.b];
+  if (tape) {
+    __stcs(tape + 2 * i, pa);
+    __stcs(tape + 2 * i + 1, pb);
+  }
+  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
+  f3 d = xyz(pa) - xyz(pb);
+  float l2 = dot(d, d);
+  float D = pa.w + pb.w + r.at;
+  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
+    float il = rsqrtf(l2);
+    float l = l2 * il;
+    f3 nrm = d * il;
+    float dl = (-(l - r.L) - r.at * lam) / D;
+    lam += dl;
+    f3 a = xyz(pa) + nrm * (pa.w * dl);
+    f3 b = xyz(pb) - nrm * (pb.w * dl);
+    P[r.a] = with_w(a, pa.w);
+    P[r.b] = with_w(b, pb.w);
+  }
+  __stcs(lam_out + i, lam);
+}
+
+// ---- 4-vertex constraints (bending, tet C_H, tet C_D)
+template <int KIND>   // 1 bending, 2 hydrostatic, 3 deviatoric
+struct Quad;
+
+template <>
+struct Quad<1> {
+  typedef BendRec Rec;
+  __device__ static bool eval(const Rec& r, const f3 x[4], f3 g[4], float& C) {
+    if (bend_degenerate(x)) return false;
+    bend_grad<float>(x, g);
+    C = bend_C(x, r.theta0);
+    return true;
+  }
+  __device__ static void hvp(const Rec& r, const f3 x[4], const f3 u[4], f3 hu[4]) {
+    d3 xd[4], gd[4];
+    for (int k = 0; k < 4; ++k) xd[k] = mkd3(x[k], u[k]);
+    bend_grad<df>(xd, gd);
+    for (int k = 0; k < 4; ++k) hu[k] = dpart(gd[k]);
+  }
+};
+
+template <bool HYDRO>
+struct TetQuad {
+  typedef TetRec Rec;
+  __device__ static bool eval(const Rec& r, const f3 x[4], f3 g[4], float& C) {
+    tet_grad<HYDRO, float>(x, r.B, g, &C, r.gamma);
+    if (!HYDRO && C * C < XPBD_DEGEN2) return false;
+    return true;
+  }
+  __device__ static void hvp(const Rec& r, const f3 x[4], const f3 u[4], f3 hu[4]) {
+    d3 xd[4], gd[4];
+    for (int k = 0; k < 4; ++k) xd[k] = mkd3(x[k], u[k]);
+    df C;
+    tet_grad<HYDRO, df>(xd, r.B, gd, &C, r.gamma);
+    for (int k = 0; k < 4; ++k) hu[k] = dpart(gd[k]);
+  }
+};
+template <> struct Quad<2> : TetQuad<true> {};
+template <> struct Quad<3> : TetQuad<false> {};
+
+template <int KIND>
+__global__ void k_proj_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
+                            float4* __restrict__ P, const float* lam_in, float* lam_out,
+                            float4* __restrict__ tape) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const typename Quad<KIND>::Rec r = rec[i];
+  float4 p[4];
+  f3 x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    p[k] = P[r.v[k]];
+    x[k] = xyz(p[k]);
+  }
+  if (tape) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) __stcs(tape + 4 * i + k, p[k]);
+  }
+  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
+  f3 g[4];
+  float C;
+  if (Quad<KIND>::eval(r, x, g, C)) {
+    float D = r.at;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D += p[k].w * dot(g[k], g[k]);
+    if (D > 0.f) {
+      float dl = (-C - r.at * lam) / D;
+      lam += dl;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) P[r.v[k]] = with_w(x[k] + g[k] * (p[k].w * dl), p[k].w);
+    }
+  }
+  __stcs(lam_out + i, lam);
+}
+
+void launch_project(SegType t, const void* rec, int n, float4* P, const float* lam_in,
+                    float* lam_out, float4* tape, cudaStream_t s) {
+  if (n <= 0) return;
+  switch (t) {
+    case SEG_DIST:
+      k_proj_dist<<<grid_for(n), kBlock, 0, s>>>((const DistRec*)rec, n, P, lam_in, lam_out, tape);
+      break;
+    case SEG_BEND:
+      k_proj_quad<1><<<grid_for(n), kBlock, 0, s>>>((const BendRec*)rec, n, P, lam_in, lam_out, tape);
+      break;
+    case SEG_TETH:
+      k_proj_quad<2><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, P, lam_in, lam_out, tape);
+      break;
+    case SEG_TETD:
+      k_proj_quad<3><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, P, lam_in, lam_out, tape);
+      break;
+  }
+}
+
+// ---- contacts (Sec. 4.6): plane then sphere on the same vertex, equality springs for the
+// step in which they were detected
+__device__ __forceinline__ void plane_project(f3& p, float w, float& lam, const Collide& c) {
+  float C = p.y - c.h - c.thick;
+  float D = w + c.at;
+  if (D > 0.f) {
+    float dl = (-C - c.at * lam) / D;
+    lam += dl;
+    p.y += w * dl;
+  }
+}
+
+__device__ __forceinline__ void sphere_project(f3& p, float w, float& lam, const Collide& c) {
+  f3 d = p - mk3(c.cx, c.cy, c.cz);
+  float l2 = dot(d, d);
+  float D = w + c.at;
+  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
+    float il = rsqrtf(l2);
+    float l = l2 * il;
+    f3 nrm = d * il;
+    float dl = (-(l - c.r - c.thick) - c.at * lam) / D;
+    lam += dl;
+    p = p + nrm * (w * dl);
+  }
+}
+
+__global__ void k_contact(float4* __restrict__ P, const uint8_t* __restrict__ cflags, int V,
+                          const float2* lam_in, float2* lam_out, float4* __restrict__ tape,
+                          Collide c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  uint8_t f = cflags[i];
+  if (!f) return;
+  float4 p4 = P[i];
+  if (tape) __stcs(tape + i, p4);
+  float2 lam = lam_in ? lam_in[i] : make_float2(0.f, 0.f);
+  f3 p = xyz(p4);
+  if (f & 1) plane_project(p, p4.w, lam.x, c);
+  if (f & 2) sphere_project(p, p4.w, lam.y, c);
+  P[i] = with_w(p, p4.w);
+  lam_out[i] = lam;
+}
+
+void launch_contact(float4* P, const uint8_t* cflags, int V, const float2* lam_in,
+                    float2* lam_out, float4* tape, Collide c, cudaStream_t s) {
+  if (V > 0 && c.flags) k_contact<<<grid_for(V), kBlock, 0, s>>>(P, cflags, V, lam_in, lam_out, tape, c);
+}
+
+// Velocity update (Eq. xpbdUpdateRule): v_{n+1} = (x_{n+1} - x_n)/dt; flags non-finite state.
+__global__ void k_velocity(const float4* __restrict__ P, const float4* __restrict__ ckx_n,
+                           float4* __restrict__ ckx_next, float4* __restrict__ ckv_next,
+                           float inv_dt, int V, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  float4 p = P[i];
+  float4 x = ckx_n[i];
+  float4 v = make_float4((p.x - x.x) * inv_dt, (p.y - x.y) * inv_dt, (p.z - x.z) * inv_dt, 0.f);
+  ckx_next[i] = p;
+  ckv_next[i] = v;
+  if (!isfinite(p.x + p.y + p.z + v.x + v.y + v.z)) atomicOr(err, 1);
+}
+
+void launch_velocity(const float4* P, const float4* ckx_n, float4* ckx_next, float4* ckv_next,
+                     float inv_dt, int V, int* err, cudaStream_t s) {
+  if (V > 0) k_velocity<<<grid_for(V), kBlock, 0, s>>>(P, ckx_n, ckx_next, ckv_next, inv_dt, V, err);
+}
+
+// ======================================================================== reverse
+
+__global__ void k_seed_adjoint(const float* __restrict__ sx, const float* __restrict__ sv,
+                               float4* __restrict__ xbar, float4* __restrict__ vbar, int V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  xbar[i] = sx ? make_float4(sx[3 * i], sx[3 * i + 1], sx[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  vbar[i] = sv ? make_float4(sv[3 * i], sv[3 * i + 1], sv[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+void launch_seed_adjoint(const float* seed_x, const float* seed_v, float4* xbar, float4* vbar,
+                         int V, cudaStream_t s) {
+  if (V > 0) k_seed_adjoint<<<grid_for(V), kBlock, 0, s>>>(seed_x, seed_v, xbar, vbar, V);
+}
+
+// Adjoint of v_{n+1} = (p - x_n)/dt, x_{n+1} = p:  pbar = xbar + vbar/dt, xbar_n = -vbar/dt.
+// In place: xbar <- pbar, vbar <- the partial xbar_n.
+__global__ void k_adj_begin(float4* __restrict__ xbar, float4* __restrict__ vbar, float inv_dt, int V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  float4 xb = xbar[i], vb = vbar[i];
+  xbar[i] = make_float4(xb.x + vb.x * inv_dt, xb.y + vb.y * inv_dt, xb.z + vb.z * inv_dt, 0.f);
+  vbar[i] = make_float4(-vb.x * inv_dt, -vb.y * inv_dt, -vb.z * inv_dt, 0.f);
+}
+
+void launch_adj_begin(float4* xbar, float4* vbar, float inv_dt, int V, cudaStream_t s) {
+  if (V > 0) k_adj_begin<<<grid_for(V), kBlock, 0, s>>>(xbar, vbar, inv_dt, V);
+}
+
+// Reverse of one XPBD update.  With the pre-projection state from the tape, g = grad C,
+// D = sum w|g|^2 + alpha~, dlambda = (-C - alpha~ lambda)/D recomputed, and the adjoints
+// xbar', lambar' of the updated values:
+//   s = lambar' + sum_i w_i g_i . xbar'_i                 (adjoint of dlambda)
+//   u_i = dlambda w_i xbar'_i - 2 (s dlambda / D) w_i g_i (adjoint of g_i)
+//   xbar_i = xbar'_i - (s/D) g_i + (H u)_i,  lambar = lambar' - (alpha~/D) s,
+//   alphabar~ += -s (lambda + dlambda) / D.
+// These are the terms of Sec. 4.4 (J = D, dJ/dx dlambda, db/dx = -grad C - alpha~ ...)
+// applied in reverse mode to the sequence of single-constraint updates.
+__device__ __forceinline__ void lb_finish(int i, float lambar, float abar, float2* lb, double* acc,
+                                          bool last) {
+  if (last)
+    acc[i] += (double)abar;
+  else
+    lb[i] = make_float2(lambar, abar);
+}
+
+__global__ void k_vjp_dist(const DistRec* __restrict__ rec, int n, const float4* __restrict__ tape,
+                           const float* __restrict__ lam_pre, float4* __restrict__ xbar,
+                           float2* __restrict__ lb, double* __restrict__ acc, bool first, bool last) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const DistRec r = rec[i];
+  float4 pa = ld_stream(tape + 2 * i), pb = ld_stream(tape + 2 * i + 1);
+  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  f3 d = xyz(pa) - xyz(pb);
+  float l2 = dot(d, d);
+  float D = pa.w + pb.w + r.at;
+  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
+    float il = rsqrtf(l2);
+    float len = l2 * il;
+    f3 nrm = d * il;
+    float dl = (-(len - r.L) - r.at * lam) / D;
+    float4 xa4 = xbar[r.a], xb4 = xbar[r.b];
+    f3 xa = xyz(xa4), xb = xyz(xb4);
+    float s = l.x + pa.w * dot(nrm, xa) - pb.w * dot(nrm, xb);
+    // H u for the distance constraint: (P (u_a - u_b))/l on a, the negative on b, with
+    // P = I - n n^T; the n-parallel part of u drops out.
+    f3 t = (xa * pa.w - xb * pb.w) * dl;
+    f3 hv = (t - nrm * dot(nrm, t)) * il;
+    float sD = s / D;
+    xa = xa - nrm * sD + hv;
+    xb = xb + nrm * sD - hv;
+    xbar[r.a] = with_w(xa, 0.f);
+    xbar[r.b] = with_w(xb, 0.f);
+    l.y += -sD * (lam + dl);
+    l.x -= r.at * sD;
+  }
+  lb_finish(i, l.x, l.y, lb, acc, last);
+}
+
+template <int KIND>
+__global__ void k_vjp_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
+                           const float4* __restrict__ tape, const float* __restrict__ lam_pre,
+                           float4* __restrict__ xbar, float2* __restrict__ lb,
+                           double* __restrict__ acc, bool first, bool last) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const typename Quad<KIND>::Rec r = rec[i];
+  float4 p[4];
+  f3 x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    p[k] = ld_stream(tape + 4 * i + k);
+    x[k] = xyz(p[k]);
+  }
+  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  f3 g[4];
+  float C;
+  if (Quad<KIND>::eval(r, x, g, C)) {
+    float D = r.at;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D += p[k].w * dot(g[k], g[k]);
+    if (D > 0.f) {
+      float dl = (-C - r.at * lam) / D;
+      f3 xb[4];
+      float s = l.x;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        xb[k] = xyz(xbar[r.v[k]]);
+        s += p[k].w * dot(g[k], xb[k]);
+      }
+      float sD = s / D;
+      float c2 = 2.f * sD * dl;
+      f3 u[4], hu[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) u[k] = (xb[k] * dl - g[k] * c2) * p[k].w;
+      Quad<KIND>::hvp(r, x, u, hu);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xbar[r.v[k]] = with_w(xb[k] - g[k] * sD + hu[k], 0.f);
+      l.y += -sD * (lam + dl);
+      l.x -= r.at * sD;
+    }
+  }
+  lb_finish(i, l.x, l.y, lb, acc, last);
+}
+
+void launch_vjp(SegType t, const void* rec, int n, const float4* tape, const float* lam_pre,
+                float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s) {
+  if (n <= 0) return;
+  switch (t) {
+    case SEG_DIST:
+      k_vjp_dist<<<grid_for(n), kBlock, 0, s>>>((const DistRec*)rec, n, tape, lam_pre, xbar, lb, acc, first, last);
+      break;
+    case SEG_BEND:
+      k_vjp_quad<1><<<grid_for(n), kBlock, 0, s>>>((const BendRec*)rec, n, tape, lam_pre, xbar, lb, acc, first, last);
+      break;
+    case SEG_TETH:
+      k_vjp_quad<2><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, tape, lam_pre, xbar, lb, acc, first, last);
+      break;
+    case SEG_TETD:
+      k_vjp_quad<3><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, tape, lam_pre, xbar, lb, acc, first, last);
+      break;
+  }
+}
+
+// Reverse of the collision pass.  Plane (inputs p, h; grad_p = e_y, grad_h = -1, H = 0) and
+// sphere (inputs p, c, r; grad_p = n, grad_c = -n, grad_r = -1, H_pp = P/l, H_pc = -P/l;
+// the centre and radius are not moved, so u_c = 0).  Collider adjoints accumulate in the
+// per-vertex float32 scratch cgrad = (hbar, cbar_x, cbar_y, cbar_z, rbar) over the step.
+__global__ void k_vjp_contact(const float4* __restrict__ tape, const uint8_t* __restrict__ cflags,
+                              int V, const float2* __restrict__ lam_pre, float4* __restrict__ xbar,
+                              float2* __restrict__ lbc, float* __restrict__ cgrad, bool first,
+                              Collide c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  uint8_t f = cflags[i];
+  if (!f) return;
+  float4 p4 = tape[i];
+  float w = p4.w;
+  float2 lam = lam_pre ? lam_pre[i] : make_float2(0.f, 0.f);
+  float2 lb = first ? make_float2(0.f, 0.f) : lbc[i];
+  float cg[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (cgrad && !first)
+    for (int k = 0; k < 5; ++k) cg[k] = cgrad[5 * i + k];
+  f3 xb = xyz(xbar[i]);
+  f3 pre = xyz(p4);
+  f3 mid = pre;
+  if ((f & 1) && (f & 2)) {
+    float lp = lam.x;
+    plane_project(mid, w, lp, c);
+  }
+  float D = w + c.at;
+  if ((f & 2) && D > 0.f) {
+    f3 d = mid - mk3(c.cx, c.cy, c.cz);
+    float l2 = dot(d, d);
+    if (l2 >= XPBD_DEGEN2) {
+      float il = rsqrtf(l2);
+      float len = l2 * il;
+      f3 nrm = d * il;
+      float dl = (-(len - c.r - c.thick) - c.at * lam.y) / D;
+      float s = lb.y + w * dot(nrm, xb);
+      float sD = s / D;
+      f3 t = xb * (w * dl);
+      f3 hv = (t - nrm * dot(nrm, t)) * il;
+      xb = xb - nrm * sD + hv;
+      // centre: -(s/D) grad_c + (H u)_c = (s/D) n - hv ; radius: -(s/D) grad_r = s/D
+      cg[1] += nrm.x * sD - hv.x;
+      cg[2] += nrm.y * sD - hv.y;
+      cg[3] += nrm.z * sD - hv.z;
+      cg[4] += sD;
+      lb.y -= c.at * sD;
+    }
+  }
+  if ((f & 1) && D > 0.f) {
+    float s = lb.x + w * xb.y;
+    float sD = s / D;
+    xb.y -= sD;
+    cg[0] += sD;
+    lb.x -= c.at * sD;
+  }
+  xbar[i] = with_w(xb, 0.f);
+  lbc[i] = lb;
+  if (cgrad)
+    for (int k = 0; k < 5; ++k) cgrad[5 * i + k] = cg[k];
+}
+
+void launch_vjp_contact(const float4* tape, const uint8_t* cflags, int V, const float2* lam_pre,
+                        float4* xbar, float2* lbc, float* cgrad, bool first, Collide c,
+                        cudaStream_t s) {
+  if (V > 0 && c.flags)
+    k_vjp_contact<<<grid_for(V), kBlock, 0, s>>>(tape, cflags, V, lam_pre, xbar, lbc, cgrad, first, c);
+}
+
+// Per-block float64 sums of the per-vertex collider adjoints of this step (contact vertices
+// only: cgrad of other vertices is stale).
+__global__ void k_collider_partials(const float* __restrict__ cgrad, const uint8_t* __restrict__ cflags,
+                                    int V, double* __restrict__ partials) {
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    if (cflags[i])
+      for (int k = 0; k < 5; ++k) v[k] += (double)cgrad[5 * i + k];
+  }
+  block_sum_store<5>(v, partials + 5 * blockIdx.x);
+}
+
+void launch_collider_partials(const float* cgrad, const uint8_t* cflags, int V, double* partials,
+                              cudaStream_t s) {
+  k_collider_partials<<<partial_blocks(V), kBlock, 0, s>>>(cgrad, cflags, V, partials);
+}
+
+// Adjoint of the prediction p = x_n + dt v_n + dt^2 (w (G_n + W_i) + [w>0] g):
+//   xbar_n = xbar_partial + pbar (+ dL/dx_n seed),  vbar_n = dt pbar,
+//   fbar_i = dt^2 w_i pbar_i  (Sec. 5.6: force gradients from the adjoint velocities),
+//   dL/dW_i += fbar_i (float64),  dL/dG_n = sum_i fbar_i (float64, fixed-order partials).
+__global__ void k_adj_predict(float4* __restrict__ xbar, float4* __restrict__ vbar,
+                              const float4* __restrict__ ckx_n, const float* __restrict__ seed,
+                              float dt, double* __restrict__ fv_acc, double* __restrict__ fg_partials,
+                              int V) {
+  double fs[3] = {0, 0, 0};
+  float dt2 = dt * dt;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    float4 pb = xbar[i];
+    float4 xp = vbar[i];
+    float w = ckx_n[i].w;
+    float4 xn = make_float4(xp.x + pb.x, xp.y + pb.y, xp.z + pb.z, 0.f);
+    if (seed) {
+      xn.x += seed[3 * i];
+      xn.y += seed[3 * i + 1];
+      xn.z += seed[3 * i + 2];
+    }
+    xbar[i] = xn;
+    vbar[i] = make_float4(dt * pb.x, dt * pb.y, dt * pb.z, 0.f);
+    double fx = (double)(dt2 * w) * (double)pb.x;
+    double fy = (double)(dt2 * w) * (double)pb.y;
+    double fz = (double)(dt2 * w) * (double)pb.z;
+    if (fv_acc) {
+      fv_acc[3 * i] += fx;
+      fv_acc[3 * i + 1] += fy;
+      fv_acc[3 * i + 2] += fz;
+    }
+    fs[0] += fx;
+    fs[1] += fy;
+    fs[2] += fz;
+  }
+  if (fg_partials) block_sum_store<3>(fs, fg_partials + 3 * blockIdx.x);
+}
+
+void launch_adj_predict(float4* xbar, float4* vbar, const float4* ckx_n, const float* seed,
+                        float dt, double* fv_acc, double* fg_partials, int V, cudaStream_t s) {
+  k_adj_predict<<<partial_blocks(V), kBlock, 0, s>>>(xbar, vbar, ckx_n, seed, dt, fv_acc, fg_partials, V);
+}
+
+// Sum of per-block partials in a fixed order (one block).
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, int ncomp,
+                                  double* __restrict__ out, bool accumulate) {
+  __shared__ double sh[kBlock];
+  for (int c = 0; c < ncomp; ++c) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) t += partials[ncomp * b + c];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = accumulate ? out[c] + sh[0] : sh[0];
+    __syncthreads();
+  }
+}
+
+void launch_reduce_partials(const double* partials, int nblocks, int ncomp, double* out,
+                            bool accumulate, cudaStream_t s) {
+  k_reduce_partials<<<1, kBlock, 0, s>>>(partials, nblocks, ncomp, out, accumulate);
+}
+
+// dL/d compliance in the caller's constraint order: alpha~ = compliance / dt^2 (tets:
+// / (V_e dt^2)), so dL/dcompliance = alphabar~ / dt^2 (/ V_e).
+template <class Rec, bool VOL>
+__global__ void k_finalize_compliance(const Rec* __restrict__ rec, const int* __restrict__ perm,
+                                      int n, const double* __restrict__ acc, float inv_dt2,
+                                      double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = acc[i] * (double)inv_dt2;
+  if constexpr (VOL) a = a / (double)rec[i].vol;
+  out[perm[i]] = a;
+}
+
+void launch_finalize_compliance(SegType t, const void* rec, const int* perm, int n,
+                                const double* acc, float inv_dt2, double* out, cudaStream_t s) {
+  if (n <= 0) return;
+  switch (t) {
+    case SEG_DIST:
+      k_finalize_compliance<DistRec, false><<<grid_for(n), kBlock, 0, s>>>((const DistRec*)rec, perm, n, acc, inv_dt2, out);
+      break;
+    case SEG_BEND:
+      k_finalize_compliance<BendRec, false><<<grid_for(n), kBlock, 0, s>>>((const BendRec*)rec, perm, n, acc, inv_dt2, out);
+      break;
+    default:
+      k_finalize_compliance<TetRec, true><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, perm, n, acc, inv_dt2, out);
+  }
+}
+
+__global__ void k_to_double(const float4* __restrict__ a, double* __restrict__ out, int V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  float4 v = a[i];
+  out[3 * i] = v.x;
+  out[3 * i + 1] = v.y;
+  out[3 * i + 2] = v.z;
+}
+
+void launch_to_double(const float4* a, double* out, int V, cudaStream_t s) {
+  if (V > 0) k_to_double<<<grid_for(V), kBlock, 0, s>>>(a, out, V);
+}
+
+// ======================================================================== utilities
+
+// Goal function of Sec. 4.1 on one keyframe: seed = x - x*, partial sums of |x - x*|^2 / 2.
+__global__ void k_loss(const float4* __restrict__ ckx, const float* __restrict__ target,
+                       float* __restrict__ seed_out, double* __restrict__ partials, int V) {
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    float4 x = ckx[i];
+    float dx = x.x - target[3 * i], dy = x.y - target[3 * i + 1], dz = x.z - target[3 * i + 2];
+    if (seed_out) {
+      seed_out[3 * i] = dx;
+      seed_out[3 * i + 1] = dy;
+      seed_out[3 * i + 2] = dz;
+    }
+    acc[0] += 0.5 * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
+  }
+  block_sum_store<1>(acc, partials + blockIdx.x);
+}
+
+void launch_loss(const float4* ckx, const float* target, float* seed_out, double* partials,
+                 int V, cudaStream_t s) {
+  k_loss<<<partial_blocks(V), kBlock, 0, s>>>(ckx, target, seed_out, partials, V);
+}
+
+__global__ void k_read_state(const float4* __restrict__ ckx, const float4* __restrict__ ckv,
+                             float* __restrict__ x_out, float* __restrict__ v_out, int V) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  if (x_out) {
+    float4 x = ckx[i];
+    x_out[3 * i] = x.x;
+    x_out[3 * i + 1] = x.y;
+    x_out[3 * i + 2] = x.z;
+  }
+  if (v_out) {
+    float4 v = ckv[i];
+    v_out[3 * i] = v.x;
+    v_out[3 * i + 1] = v.y;
+    v_out[3 * i + 2] = v.z;
+  }
+}
+
+void launch_read_state(const float4* ckx, const float4* ckv, float* x_out, float* v_out, int V,
+                       cudaStream_t s) {
+  if (V > 0) k_read_state<<<grid_for(V), kBlock, 0, s>>>(ckx, ckv, x_out, v_out, V);
+}
+
+}  // namespace xpbd
