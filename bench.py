@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable XPBD step on one GB300 (or N independent replicas).
+
+One bench step = the whole hot path over the 2950 x 2950 cloth draped on a sphere
+(8,702,500 vertices, 34,792,302 distance + 17,387,304 bending constraints, 60 steps of
+15 colored Gauss-Seidel iterations): forward simulation with per-step checkpoints, the
+keyframe loss at steps 20/40/60 with its seeds, and the full reverse sweep giving float64
+gradients for every compliance, x0, v0, the 60x3 per-step global force, the per-vertex
+force field and the sphere parameters.
+
+metric: fwd+adjoint constraint-updates/s = 2 * m * iters * steps / time per bench step
+(each constraint update of the forward and each reverse (VJP) update of the adjoint counts
+once; the in-adjoint replay is part of the adjoint's cost, not counted as extra units).
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2301_01396_gb300 import scenes  # noqa: E402
+
+METRIC = "fwd+adjoint constraint-updates/s"
+UNIT = "constraint-updates/s"
+KEYFRAMES = (20, 40, 60)
+GRID = 2950
+
+# Algorithmic bytes per unit of each kernel class (steady-state iteration; float4 vertices):
+#   fwd   distance: record 16 + lambda r/w 8 + 2 vertices gathered and scattered 64 = 88
+#         bending / tet: record 32 / 64 + lambda 8 + 4 vertices r/w 128 = 168 / 200
+#   replay: forward + pre-projection tape write (16 B per vertex): 120 / 232 / 264
+#   vjp   distance: record 16 + tape 32 + lambda 4 + vertex adjoints r/w 64 + (lambar,
+#         alphabar) r/w 16 = 132;  bending: 32 + 64 + 4 + 128 + 16 = 244;  tets: 276
+BYTES_PER_UNIT = {
+    "fwd_dist": 88, "fwd_bend": 168, "fwd_tet_h": 200, "fwd_tet_d": 200,
+    "replay_dist": 120, "replay_bend": 232, "replay_tet_h": 264, "replay_tet_d": 264,
+    "vjp_dist": 132, "vjp_bend": 244, "vjp_tet_h": 276, "vjp_tet_d": 276,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--grid", type=int, default=GRID, help="cloth side (default: the 2950^2 workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-window", type=int, default=160)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--forward-only-steps", type=int, default=0,
+                    help="profiling aid: run only this many forward steps and exit (no JSON line)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws):
+    if ws > 1:
+        import torch.distributed as td
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        td.init_process_group(backend=backend)
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        sel = []
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(self.dev), "uuid", None)
+            if u is not None:
+                sel = ["-i", "GPU-" + str(u)]
+        except Exception:
+            sel = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", *sel], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def workload(grid: int):
+    t0 = time.time()
+    sc = scenes.sphere_cloth(grid)
+    return sc, time.time() - t0
+
+
+def cpu_window_scene(nw: int, steps: int, grid: int = GRID):
+    """A nw x nw window of the grid x grid cloth: same spacing, vertex mass, constraint
+    types and compliance law, centred over the sphere; the oracle's bounded sample."""
+    size = (nw - 1) / (grid - 1)
+    g = scenes.cloth_grid(nw, size, vertex_mass=2.56 / grid ** 2, diagonals="both", bending=True, pins=(),
+                          origin=(0.5 - size / 2, 0.5 - size / 2))
+    rng = np.random.default_rng(4)
+    alpha = scenes.lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0])
+    return scenes._cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=15,
+                               collider_flags=scenes.COLLIDE_SPHERE, sphere=(0.5, -0.35, 0.5, 0.3),
+                               contact_compliance=1e-8, name=f"window_{nw}")
+
+
+def run_cpu_oracle(nw: int, steps: int) -> dict:
+    """Time the FP64 oracle (as it stands) on a window of the workload: forward + reverse."""
+    import oracle
+    sc = cpu_window_scene(nw, steps)
+    t0 = time.perf_counter()
+    xs, _ = oracle.forward(sc)
+    t1 = time.perf_counter()
+    oracle.adjoint(sc, {steps: xs[-1] - sc.x0})
+    t2 = time.perf_counter()
+    units = 2 * sc.m * sc.iters * steps
+    return {"value": units / (t2 - t0), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nw}x{nw} window of the {GRID}x{GRID} cloth (same spacing, masses, constraint types "
+                      f"and compliance law; {sc.m} constraints), {steps} steps x 15 iterations, forward + "
+                      f"reverse sweep, FP64; forward {t1 - t0:.2f} s, reverse {t2 - t1:.2f} s"}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_for(cls: str, units_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the kernel
+    source that is built now; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2301_01396_gb300", "csrc", "xpbd_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get("classes", {}).get(cls)
+    if not e or d.get("kernel_source_sha256_16") != h:
+        return None
+    return float(e["dram_bytes_per_unit"]) * units_per_launch
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2301_01396_gb300 import binding
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, t_gen = workload(args.grid)
+    N, I = sc.steps, sc.iters
+    t0 = time.time()
+    solver = binding.Solver.from_scene(sc)
+    t_create = time.time() - t0
+    x0 = torch.as_tensor(sc.x0.astype(np.float32), device=dev)
+    v0 = torch.as_tensor(sc.v0.astype(np.float32), device=dev)
+    p_true = binding.params_from_scene(sc, device=dev)
+    ck = solver.new_checkpoints(N, dev)
+
+    if args.forward_only_steps:
+        solver.forward(p_true, args.forward_only_steps, I, x0, v0)
+        torch.cuda.synchronize()
+        solver.sync_status()
+        print(json.dumps({"forward_only_steps": args.forward_only_steps, "V": sc.V, "m": sc.m}))
+        return None
+
+    # keyframe targets from the driven simulation; the optimisation starts from zero forces
+    solver.forward(p_true, N, I, x0, v0, checkpoints=ck)
+    targets = {k: solver.read_state(ck, k)[0].clone() for k in KEYFRAMES}
+    params = binding.Params(dt=p_true.dt, compliance=p_true.compliance, gravity=p_true.gravity,
+                            f_global=torch.zeros((N, 3), dtype=torch.float32, device=dev),
+                            f_vertex=torch.zeros((sc.V, 3), dtype=torch.float32, device=dev),
+                            collider_flags=p_true.collider_flags, plane_h=p_true.plane_h, sphere=p_true.sphere,
+                            contact_compliance=p_true.contact_compliance, thickness=p_true.thickness)
+    grads = {k: torch.empty(s, dtype=torch.float64, device=dev)
+             for k, s in dict(compliance=(sc.m,), x0=(sc.V, 3), v0=(sc.V, 3), f_global=(N, 3),
+                              f_vertex=(sc.V, 3), collider=(5,)).items()}
+    loss_box = {}
+
+    def step():
+        solver.forward(params, N, I, x0, v0, checkpoints=ck)
+        loss, seeds = solver.loss(ck, targets)
+        solver.adjoint(params, N, I, ck, {k: seeds[i] for i, k in enumerate(KEYFRAMES)}, out=grads)
+        loss_box["loss"] = loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    solver.sync_status()
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    solver.profile(True)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    stats = solver.profile_read()
+    solver.profile(False)
+    solver.sync_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ws, ms)
+    units = 2 * sc.m * I * N
+    value = ws * units / (ms_max / 1e3)
+
+    # dominant kernel class and its roofline
+    timed = {k: v for k, v in stats.items() if v["timed_launches"] > 0}
+    dom = max((k for k in timed if k in BYTES_PER_UNIT), key=lambda k: timed[k]["ms"])
+    d = timed[dom]
+    avg_ms = d["ms"] / d["timed_launches"]
+    upl = d["units"] / d["launches"]
+    achieved = upl * BYTES_PER_UNIT[dom] / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    tr = traffic_for(dom, upl)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr),
+                "kernel": dom, "launch_avg_ms": round(avg_ms, 4), "units_per_launch": round(upl),
+                "bytes_per_unit": BYTES_PER_UNIT[dom], "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": round(upl * BYTES_PER_UNIT[dom])}
+    launches = int(sum(v["launches"] for v in stats.values()))
+    breakdown = {k: round(v["ms"] / args.steps, 2) for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])
+                 if v["ms"] > 0}
+    fwd_ms = sum(v["ms"] for k, v in stats.items() if k.startswith("fwd_") or k in ("predict", "velocity")) / args.steps
+    all_bytes = sum(stats[k]["units"] * b for k, b in BYTES_PER_UNIT.items()) / args.steps
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (f64 gradient reductions)", "data": "synthetic",
+        "config": {"workload": f"sphere_cloth_{args.grid}x{args.grid}: {sc.V} vertices, {sc.n_dist} distance + "
+                               f"{sc.n_bend} bending constraints, {N} steps x {I} iterations, dt=1/60, sphere "
+                               f"collider, keyframe loss at {list(KEYFRAMES)}, gradients for compliance/x0/v0/"
+                               f"f_global/f_vertex/sphere",
+                   "V": sc.V, "m": sc.m, "sim_steps": N, "iters": I, "colors": sc.n_colors,
+                   "l2": "inputs larger than L2 (vertex state 139 MB, records 1.1 GB, tapes 36 GB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "breakdown_ms_per_step": breakdown,
+        "forward_ms_per_step": round(fwd_ms, 2),
+        "adjoint_ms_per_step": round(ms - fwd_ms, 2),
+        "algorithmic_gb_per_step": round(all_bytes / 1e9, 1),
+        "loss": float(loss_box["loss"].item()),
+        "setup_s": {"scene": round(t_gen, 1), "create": round(t_create, 1)},
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, sc, solver, params, targets, dev, ws)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = run_cpu_oracle(args.cpu_window, args.cpu_steps)
+    return result
+
+
+def run_e2e(args, sc, solver, params, targets, dev, ws):
+    """Same metric through the public API with host buffers: every step copies its inputs
+    host->device from pinned memory and the gradients and loss device->host."""
+    import torch
+    from paper_2301_01396_gb300 import binding
+    N, I = sc.steps, sc.iters
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory()
+    h_x0, h_v0 = pin(sc.x0), pin(sc.v0)
+    h_comp = pin(sc.compliance)
+    h_fg, h_fv = pin(np.zeros((N, 3))), pin(np.zeros((sc.V, 3)))
+    h_tg = pin(np.stack([targets[k].cpu().numpy() for k in KEYFRAMES]))
+    shapes = dict(compliance=(sc.m,), x0=(sc.V, 3), v0=(sc.V, 3), f_global=(N, 3), f_vertex=(sc.V, 3), collider=(5,))
+    h_out = {k: torch.empty(s, dtype=torch.float64).pin_memory() for k, s in shapes.items()}
+    h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    ck = solver.new_checkpoints(N, dev)
+    d_out = {k: torch.empty(s, dtype=torch.float64, device=dev) for k, s in shapes.items()}
+    h2d = sum(t.numel() * t.element_size() for t in (h_x0, h_v0, h_comp, h_fg, h_fv, h_tg))
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values()) + 8
+
+    def step():
+        x0 = h_x0.to(dev, non_blocking=True)
+        v0 = h_v0.to(dev, non_blocking=True)
+        p = binding.Params(dt=params.dt, compliance=h_comp.to(dev, non_blocking=True), gravity=params.gravity,
+                           f_global=h_fg.to(dev, non_blocking=True), f_vertex=h_fv.to(dev, non_blocking=True),
+                           collider_flags=params.collider_flags, plane_h=params.plane_h, sphere=params.sphere,
+                           contact_compliance=params.contact_compliance, thickness=params.thickness)
+        tg = h_tg.to(dev, non_blocking=True)
+        solver.forward(p, N, I, x0, v0, checkpoints=ck)
+        loss, seeds = solver.loss(ck, {k: tg[i] for i, k in enumerate(KEYFRAMES)})
+        solver.adjoint(p, N, I, ck, {k: seeds[i] for i, k in enumerate(KEYFRAMES)}, out=d_out)
+        for k in h_out:
+            h_out[k].copy_(d_out[k], non_blocking=True)
+        h_loss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    step()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t = (time.perf_counter() - t0) / args.steps
+    t = max_over_ranks(ws, t)
+    del ck, d_out
+    return {"value": ws * 2 * sc.m * I * N / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t * 1e3, 2)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, ws, rank):
+    """The FP64 oracle as the reference arm, on the host cores: each step is a bounded
+    window sample of the workload (forward + reverse sweep)."""
+    if rank != 0:
+        return None
+    import oracle
+    nw, st = args.cpu_window, 1
+    for _ in range(args.warmup):
+        run_cpu_oracle(nw, st)
+    t_units, t_time = 0, 0.0
+    for _ in range(args.steps):
+        sc = cpu_window_scene(nw, st)
+        t0 = time.perf_counter()
+        xs, _ = oracle.forward(sc)
+        oracle.adjoint(sc, {st: xs[-1] - sc.x0})
+        t_time += time.perf_counter() - t0
+        t_units += 2 * sc.m * sc.iters * st
+    value = t_units / t_time
+    sample = (f"{nw}x{nw} window of the {GRID}x{GRID} cloth, 1 step x 15 iterations forward + reverse sweep "
+              f"per bench step, FP64")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_time / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"sphere_cloth_{GRID}x{GRID} (bounded window sample)", "window": nw},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks exit without work
+        res = run_reference(args, ws, rank)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    dist_init(ws)
+    res = run_ours(args, ws, rank, local)
+    if res is not None and rank == 0:
+        print(json.dumps(res))
+    if ws > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -168,6 +168,36 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
    compliance or a step produced a non-finite state. */
 xpbd_status xpbd_sync_status(xpbd_handle h, void* stream);
 
+/* Kernel launch statistics.  Every kernel launch of a handle is counted per class; while
+   profiling is enabled each launch is also bracketed by two CUDA events recorded on the
+   stream it is launched on, so `ms` is the summed device time of that class.  `units` is
+   the number of constraints (projection and reverse classes) or vertices (per-vertex
+   classes) the launches processed. */
+enum {
+  XPBD_K_FWD_DIST = 0, XPBD_K_FWD_BEND, XPBD_K_FWD_TETH, XPBD_K_FWD_TETD, XPBD_K_FWD_CONTACT,
+  XPBD_K_REPLAY_DIST, XPBD_K_REPLAY_BEND, XPBD_K_REPLAY_TETH, XPBD_K_REPLAY_TETD, XPBD_K_REPLAY_CONTACT,
+  XPBD_K_VJP_DIST, XPBD_K_VJP_BEND, XPBD_K_VJP_TETH, XPBD_K_VJP_TETD, XPBD_K_VJP_CONTACT,
+  XPBD_K_PREDICT, XPBD_K_VELOCITY, XPBD_K_ADJ_OTHER, XPBD_K_OTHER,
+  XPBD_KERNEL_CLASSES
+};
+
+typedef struct {
+  int64_t launches;        /* launches counted since the last xpbd_profile() call          */
+  int64_t units;           /* constraints or vertices processed by them                    */
+  double ms;               /* summed event time of the timed launches                      */
+  int64_t timed_launches;  /* launches bracketed by events (0 while profiling is off)      */
+} xpbd_kernel_stat;
+
+/* Synchronise the device, reset the counters and turn event timing on (enable != 0) or
+   off.  Timing adds two event records per launch on the launching stream. */
+xpbd_status xpbd_profile(xpbd_handle h, int32_t enable);
+
+/* Synchronise the device and fill out[XPBD_KERNEL_CLASSES]. */
+xpbd_status xpbd_profile_read(xpbd_handle h, xpbd_kernel_stat* out);
+
+/* Name of a kernel class ("fwd_dist", "vjp_bend", ...), or "" if out of range. */
+const char* xpbd_kernel_class_name(int32_t cls);
+
 /* Thread-local description of the last failure (empty string if none). */
 const char* xpbd_last_error(void);
 

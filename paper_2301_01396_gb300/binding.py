@@ -47,6 +47,17 @@ class XpbdGrads(C.Structure):
                 ("d_f_global", C.c_void_p), ("d_f_vertex", C.c_void_p), ("d_collider", C.c_void_p)]
 
 
+KERNEL_CLASSES = ("fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
+                  "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
+                  "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
+                  "predict", "velocity", "adjoint_other", "other")
+
+
+class XpbdKernelStat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("units", C.c_int64), ("ms", C.c_double),
+                ("timed_launches", C.c_int64)]
+
+
 class XpbdError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -65,7 +76,7 @@ def lib():
                                "(run __graft_entry__.build()); there is no CPU fallback")
         L = C.CDLL(LIB_PATH)
         for name in ("xpbd_create", "xpbd_destroy", "xpbd_sizes", "xpbd_forward", "xpbd_read_state",
-                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status"):
+                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -238,6 +249,17 @@ class Solver:
 
     def sync_status(self, stream=None):
         _check(lib().xpbd_sync_status(self._h, _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        """Reset the launch counters; time every launch with CUDA events while enabled."""
+        _check(lib().xpbd_profile(self._h, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """{class: {launches, units, ms, timed_launches}} since the last profile() call."""
+        arr = (XpbdKernelStat * len(KERNEL_CLASSES))()
+        _check(lib().xpbd_profile_read(self._h, arr))
+        return {n: dict(launches=a.launches, units=a.units, ms=a.ms, timed_launches=a.timed_launches)
+                for n, a in zip(KERNEL_CLASSES, arr)}
 
 
 def params_from_scene(sc, device="cuda", compliance=None) -> Params:

@@ -85,13 +85,50 @@ struct xpbd_solver {
   DevBuf P, lam, cflags, lamc;                       // forward
   DevBuf tape, lam_tape, tape_c, lamc_tape;          // replay tapes
   DevBuf xbar, vbar, lb, acc, lbc, cgrad, partials;  // reverse
-  int ws_iters = 0;
+  // launch statistics per kernel class (always counted; timed with CUDA events on the
+  // launching stream while profiling is enabled)
+  bool prof_on = false;
+  int64_t launches[XPBD_KERNEL_CLASSES] = {0};
+  int64_t units[XPBD_KERNEL_CLASSES] = {0};
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Timed { int cls; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
   size_t tape_per_iter() const {  // float4 entries per iteration
     return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
   }
 };
 
 namespace {
+
+cudaEvent_t next_event(xpbd_solver* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Counts (and, while profiling, times) one kernel launch of class `cls` covering `units`
+// constraints or vertices.  Launches with no work are skipped by the launchers and not counted.
+template <class F>
+void launch(xpbd_solver* h, int cls, int64_t units, cudaStream_t s, F&& f) {
+  if (units <= 0) return;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->prof_on) {
+    a = next_event(h);
+    b = next_event(h);
+    if (a) cudaEventRecord(a, s);
+  }
+  f();
+  h->launches[cls] += 1;
+  h->units[cls] += units;
+  if (h->prof_on && a && b) {
+    cudaEventRecord(b, s);
+    h->timed.push_back({cls, a, b});
+  }
+}
 
 size_t tape_offset(const xpbd_solver* h, SegType t) {   // float4 offset of type t in one iteration
   size_t o = 0;
@@ -162,8 +199,10 @@ xpbd_status ensure_adjoint_ws(xpbd_solver* h, int iters, bool contacts) {
 xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s) {
   float inv_dt2 = 1.f / (p->dt * p->dt);
   for (int t = 0; t < 4; ++t)
-    launch_set_alpha((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t], p->compliance,
-                     inv_dt2, h->d_err, s);
+    launch(h, XPBD_K_OTHER, h->n_rec[t], s, [&] {
+      launch_set_alpha((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t], p->compliance,
+                       inv_dt2, h->d_err, s);
+    });
   LAUNCH_CHECK();
   return XPBD_OK;
 }
@@ -176,8 +215,10 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
   Collide c = make_collide(p);
   float4* P = h->P.as<float4>();
   uint8_t* cf = h->cflags.as<uint8_t>();
-  launch_predict(ckx_n, ckv_n, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex,
-                 p->dt, p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
+  launch(h, XPBD_K_PREDICT, h->V, s, [&] {
+    launch_predict(ckx_n, ckv_n, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex,
+                   p->dt, p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
+  });
   LAUNCH_CHECK();
   const size_t tpi = h->tape_per_iter();
   for (int k = 0; k < iters; ++k) {
@@ -196,8 +237,10 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
       for (const Seg& g : h->colors[col]) {
         size_t ro = (size_t)h->rec_off[g.type] + g.begin;
         float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
-        launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
-                       lam_out + ro, tp, s);
+        launch(h, (record ? XPBD_K_REPLAY_DIST : XPBD_K_FWD_DIST) + (int)g.type, g.count, s, [&] {
+          launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
+                         lam_out + ro, tp, s);
+        });
       }
     }
     if (c.flags) {
@@ -212,7 +255,8 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
         li = k == 0 ? nullptr : h->lamc.as<float2>();
         lo = h->lamc.as<float2>();
       }
-      launch_contact(P, cf, h->V, li, lo, tc, c, s);
+      launch(h, record ? XPBD_K_REPLAY_CONTACT : XPBD_K_FWD_CONTACT, h->V, s,
+             [&] { launch_contact(P, cf, h->V, li, lo, tc, c, s); });
     }
     LAUNCH_CHECK();
   }
@@ -332,12 +376,14 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     }
     for (int type = 0; type < 4; ++type) {
       if (ids[type].empty()) continue;
-      std::stable_sort(ids[type].begin(), ids[type].end(), [&](int a, int bb) {
+      auto by_first_vertex = [&](int a, int bb) {
         int va[4], vb[4];
         verts_of(a, va);
         verts_of(bb, vb);
         return va[0] < vb[0];
-      });
+      };
+      if (!std::is_sorted(ids[type].begin(), ids[type].end(), by_first_vertex))
+        std::stable_sort(ids[type].begin(), ids[type].end(), by_first_vertex);
       Seg sg;
       sg.type = (SegType)type;
       sg.count = (int)ids[type].size();
@@ -438,6 +484,7 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
                     &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
                     &h->partials};
   for (DevBuf* b : bufs) b->release();
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return XPBD_OK;
 }
@@ -478,14 +525,16 @@ xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   st = set_alpha(h, p, s);
   if (st != XPBD_OK) return st;
   float4* ck4 = reinterpret_cast<float4*>(ck);
-  launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + h->V, h->V, s);
+  launch(h, XPBD_K_OTHER, h->V, s, [&] { launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + h->V, h->V, s); });
   LAUNCH_CHECK();
   const float inv_dt = 1.f / p->dt;
   for (int n = 0; n < steps; ++n) {
     st = run_step(h, p, n, iters, ck_x(ck, h->V, n), ck_v(ck, h->V, n), false, s);
     if (st != XPBD_OK) return st;
     float4* nx = ck4 + (size_t)2 * h->V * (n + 1);
-    launch_velocity(h->P.as<float4>(), ck_x(ck, h->V, n), nx, nx + h->V, inv_dt, h->V, h->d_err, s);
+    launch(h, XPBD_K_VELOCITY, h->V, s, [&] {
+      launch_velocity(h->P.as<float4>(), ck_x(ck, h->V, n), nx, nx + h->V, inv_dt, h->V, h->d_err, s);
+    });
     LAUNCH_CHECK();
   }
   return XPBD_OK;
@@ -494,7 +543,9 @@ xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int
 xpbd_status xpbd_read_state(xpbd_handle h, const float* ck, int32_t step, float* x_out, float* v_out,
                             void* stream) {
   if (!h || !ck || step < 0) return fail(XPBD_ERR_INVALID, "bad argument");
-  launch_read_state(ck_x(ck, h->V, step), ck_v(ck, h->V, step), x_out, v_out, h->V, (cudaStream_t)stream);
+  launch(h, XPBD_K_OTHER, h->V, (cudaStream_t)stream, [&] {
+    launch_read_state(ck_x(ck, h->V, step), ck_v(ck, h->V, step), x_out, v_out, h->V, (cudaStream_t)stream);
+  });
   LAUNCH_CHECK();
   return XPBD_OK;
 }
@@ -510,9 +561,12 @@ xpbd_status xpbd_loss(xpbd_handle h, const float* ck, int32_t n_keys, const int3
   if (loss_out) CU_TRY(cudaMemsetAsync(loss_out, 0, sizeof(double), s));
   for (int k = 0; k < n_keys; ++k) {
     if (key_steps[k] < 0) return fail(XPBD_ERR_INVALID, "negative key step");
-    launch_loss(ck_x(ck, h->V, key_steps[k]), targets + 3 * (size_t)h->V * k,
-                seeds_out ? seeds_out + 3 * (size_t)h->V * k : nullptr, h->partials.as<double>(), h->V, s);
-    if (loss_out) launch_reduce_partials(h->partials.as<double>(), pb, 1, loss_out, true, s);
+    launch(h, XPBD_K_OTHER, h->V, s, [&] {
+      launch_loss(ck_x(ck, h->V, key_steps[k]), targets + 3 * (size_t)h->V * k,
+                  seeds_out ? seeds_out + 3 * (size_t)h->V * k : nullptr, h->partials.as<double>(), h->V, s);
+    });
+    if (loss_out)
+      launch(h, XPBD_K_OTHER, 1, s, [&] { launch_reduce_partials(h->partials.as<double>(), pb, 1, loss_out, true, s); });
     LAUNCH_CHECK();
   }
   return XPBD_OK;
@@ -549,22 +603,26 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   if (out->d_f_global && steps > 0) CU_TRY(cudaMemsetAsync(out->d_f_global, 0, sizeof(double) * 3 * (size_t)steps, s));
   float4* xbar = h->xbar.as<float4>();
   float4* vbar = h->vbar.as<float4>();
-  launch_seed_adjoint(seed_of[steps] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[steps] : nullptr, seed_dv_T,
-                      xbar, vbar, V, s);
+  launch(h, XPBD_K_ADJ_OTHER, V, s, [&] {
+    launch_seed_adjoint(seed_of[steps] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[steps] : nullptr, seed_dv_T,
+                        xbar, vbar, V, s);
+  });
   LAUNCH_CHECK();
   const float inv_dt = 1.f / p->dt;
   const size_t tpi = h->tape_per_iter();
   Collide c = make_collide(p);
   for (int n = steps - 1; n >= 0; --n) {
-    launch_adj_begin(xbar, vbar, inv_dt, V, s);
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_adj_begin(xbar, vbar, inv_dt, V, s); });
     st = run_step(h, p, n, iters, ck_x(ck, V, n), ck_v(ck, V, n), true, s);
     if (st != XPBD_OK) return st;
     for (int k = iters - 1; k >= 0; --k) {
       const bool first = k == iters - 1, last = k == 0;
       if (contacts) {
-        launch_vjp_contact(h->tape_c.as<float4>() + (size_t)k * V, h->cflags.as<uint8_t>(), V,
-                           k == 0 ? nullptr : h->lamc_tape.as<float2>() + (size_t)(k - 1) * V, xbar,
-                           h->lbc.as<float2>(), out->d_collider ? h->cgrad.as<float>() : nullptr, first, c, s);
+        launch(h, XPBD_K_VJP_CONTACT, V, s, [&] {
+          launch_vjp_contact(h->tape_c.as<float4>() + (size_t)k * V, h->cflags.as<uint8_t>(), V,
+                             k == 0 ? nullptr : h->lamc_tape.as<float2>() + (size_t)(k - 1) * V, xbar,
+                             h->lbc.as<float2>(), out->d_collider ? h->cgrad.as<float>() : nullptr, first, c, s);
+        });
       }
       const float4* tape_k = h->tape.as<float4>() + (size_t)k * tpi;
       const float* lam_pre = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->m;
@@ -573,33 +631,81 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
         for (int q = (int)segs.size() - 1; q >= 0; --q) {
           const Seg& g = segs[q];
           size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-          launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count,
-                     tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type],
-                     lam_pre ? lam_pre + ro : nullptr, xbar, h->lb.as<float2>() + ro,
-                     h->acc.as<double>() + ro, first, last, s);
+          launch(h, XPBD_K_VJP_DIST + (int)g.type, g.count, s, [&] {
+            launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count,
+                       tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type],
+                       lam_pre ? lam_pre + ro : nullptr, xbar, h->lb.as<float2>() + ro,
+                       h->acc.as<double>() + ro, first, last, s);
+          });
         }
       }
       LAUNCH_CHECK();
     }
     if (contacts && out->d_collider) {
-      launch_collider_partials(h->cgrad.as<float>(), h->cflags.as<uint8_t>(), V, partials, s);
-      launch_reduce_partials(partials, pb, 5, out->d_collider, true, s);
+      launch(h, XPBD_K_ADJ_OTHER, V, s,
+             [&] { launch_collider_partials(h->cgrad.as<float>(), h->cflags.as<uint8_t>(), V, partials, s); });
+      launch(h, XPBD_K_ADJ_OTHER, 1, s, [&] { launch_reduce_partials(partials, pb, 5, out->d_collider, true, s); });
     }
     const float* seed = seed_of[n] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[n] : nullptr;
-    launch_adj_predict(xbar, vbar, ck_x(ck, V, n), seed, p->dt, out->d_f_vertex,
-                       out->d_f_global ? partials : nullptr, V, s);
-    if (out->d_f_global) launch_reduce_partials(partials, pb, 3, out->d_f_global + 3 * (size_t)n, false, s);
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] {
+      launch_adj_predict(xbar, vbar, ck_x(ck, V, n), seed, p->dt, out->d_f_vertex,
+                         out->d_f_global ? partials : nullptr, V, s);
+    });
+    if (out->d_f_global)
+      launch(h, XPBD_K_ADJ_OTHER, 1, s,
+             [&] { launch_reduce_partials(partials, pb, 3, out->d_f_global + 3 * (size_t)n, false, s); });
     LAUNCH_CHECK();
   }
-  if (out->d_x0) launch_to_double(xbar, out->d_x0, V, s);
-  if (out->d_v0) launch_to_double(vbar, out->d_v0, V, s);
+  if (out->d_x0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(xbar, out->d_x0, V, s); });
+  if (out->d_v0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(vbar, out->d_v0, V, s); });
   if (out->d_compliance) {
     float inv_dt2 = 1.f / (p->dt * p->dt);
     for (int t = 0; t < 4; ++t)
-      launch_finalize_compliance((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t],
-                                 h->acc.as<double>() + h->rec_off[t], inv_dt2, out->d_compliance, s);
+      launch(h, XPBD_K_ADJ_OTHER, h->n_rec[t], s, [&] {
+        launch_finalize_compliance((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t],
+                                   h->acc.as<double>() + h->rec_off[t], inv_dt2, out->d_compliance, s);
+      });
   }
   LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+static const char* kClassNames[XPBD_KERNEL_CLASSES] = {
+    "fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
+    "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
+    "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
+    "predict", "velocity", "adjoint_other", "other"};
+
+const char* xpbd_kernel_class_name(int32_t cls) {
+  return (cls >= 0 && cls < XPBD_KERNEL_CLASSES) ? kClassNames[cls] : "";
+}
+
+xpbd_status xpbd_profile(xpbd_handle h, int32_t enable) {
+  if (!h) return fail(XPBD_ERR_INVALID, "null handle");
+  CU_TRY(cudaDeviceSynchronize());
+  h->prof_on = enable != 0;
+  h->timed.clear();
+  h->ev_used = 0;
+  for (int c = 0; c < XPBD_KERNEL_CLASSES; ++c) h->launches[c] = h->units[c] = 0;
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_profile_read(xpbd_handle h, xpbd_kernel_stat* out) {
+  if (!h || !out) return fail(XPBD_ERR_INVALID, "null argument");
+  CU_TRY(cudaDeviceSynchronize());
+  for (int c = 0; c < XPBD_KERNEL_CLASSES; ++c) {
+    out[c].launches = h->launches[c];
+    out[c].units = h->units[c];
+    out[c].ms = 0.0;
+    out[c].timed_launches = 0;
+  }
+  for (const auto& t : h->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      out[t.cls].ms += ms;
+      out[t.cls].timed_launches += 1;
+    }
+  }
   return XPBD_OK;
 }
 
