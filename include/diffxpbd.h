@@ -168,6 +168,30 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
    compliance or a step produced a non-finite state. */
 xpbd_status xpbd_sync_status(xpbd_handle h, void* stream);
 
+/* Allocation-free forward simulation.  The paper has no counterpart: this entry point
+   exists for callers that cannot allocate device memory when they simulate, for example
+   because another allocator owns the device memory under a fixed budget, or because the
+   call sits in a latency-critical loop where cudaMalloc/cudaFree would synchronise the
+   device.  Such a caller creates the handle during start-up (xpbd_create allocates the
+   handle's constraint records) and afterwards calls this instead of xpbd_forward, which
+   allocates its working state on first use.
+
+   Same arguments, steps and results as xpbd_forward.  The working state (predicted
+   positions, multipliers, contact state) lives in one fixed device array inside the
+   library, sized for at most XPBD_STATIC_MAX_VERTICES vertices and
+   XPBD_STATIC_MAX_CONSTRAINTS constraints (about 3.1 MiB, held by every GPU that loads
+   the library until the process exits); larger models get XPBD_ERR_BOUNDS before any GPU
+   work.  The call allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+   with that device current; make that first call before any stream capture.  Each device
+   has one copy of the array, shared by every call on that device and keeping what the last
+   call left in it: calls whose GPU work overlaps in time on one device (different streams,
+   or different handles) race on it and give wrong results, so serialise them. */
+#define XPBD_STATIC_MAX_VERTICES 65536
+#define XPBD_STATIC_MAX_CONSTRAINTS 393216
+xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                const float* x0, const float* v0, float* checkpoints, void* stream);
+
 /* Kernel launch statistics.  Every kernel launch of a handle is counted per class; while
    profiling is enabled each launch is also bracketed by two CUDA events recorded on the
    stream it is launched on, so `ms` is the summed device time of that class.  `units` is

@@ -22,6 +22,8 @@ STATUS = {0: "XPBD_OK", 1: "XPBD_ERR_INVALID", 2: "XPBD_ERR_COLORING", 3: "XPBD_
           4: "XPBD_ERR_CUDA", 5: "XPBD_ERR_NONFINITE", 6: "XPBD_ERR_TIMEOUT", 7: "XPBD_ERR_BOUNDS"}
 COLLIDE_PLANE = 1
 COLLIDE_SPHERE = 2
+STATIC_MAX_VERTICES = 65536        # limits of xpbd_forward_static (include/diffxpbd.h)
+STATIC_MAX_CONSTRAINTS = 393216
 
 _fp = C.POINTER(C.c_float)
 _dp = C.POINTER(C.c_double)
@@ -76,7 +78,7 @@ def lib():
                                "(run __graft_entry__.build()); there is no CPU fallback")
         L = C.CDLL(LIB_PATH)
         for name in ("xpbd_create", "xpbd_destroy", "xpbd_sizes", "xpbd_forward", "xpbd_read_state",
-                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read"):
+                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read", "xpbd_forward_static"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -208,6 +210,17 @@ class Solver:
         _check(lib().xpbd_forward(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
                                   _ptr(ck), _stream(stream)))
         return ck
+
+    def forward_static(self, params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
+                       checkpoints: torch.Tensor, stream=None) -> torch.Tensor:
+        """xpbd_forward_static: the forward simulation without any device allocation by the
+        library, for callers that cannot allocate while they simulate (the checkpoint buffer
+        is the caller's).  Limited to STATIC_MAX_VERTICES / STATIC_MAX_CONSTRAINTS; calls
+        whose GPU work overlaps on one device race on the library's shared working array."""
+        p = params.c_struct()
+        _check(lib().xpbd_forward_static(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
+                                         _ptr(checkpoints), _stream(stream)))
+        return checkpoints
 
     def read_state(self, checkpoints: torch.Tensor, step: int, stream=None):
         x = torch.empty((self.V, 3), dtype=torch.float32, device=checkpoints.device)

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -288,6 +289,47 @@ double rest_angle(const double* x0, const double* x1, const double* x2, const do
   return std::atan2(sn, cs);
 }
 
+}  // namespace
+
+
+// ---------------------------------------------------------------- allocation-free forward
+// Working state of xpbd_forward_static in one file-scope device array, so that entry point
+// needs no device allocation: predicted positions, multipliers, contact multipliers and
+// contact flags of meshes up to XPBD_STATIC_MAX_VERTICES / XPBD_STATIC_MAX_CONSTRAINTS.
+// Every GPU that loads this library holds the array (about 3.1 MiB) until the process exits.
+namespace {
+constexpr size_t kStaticPosBytes = sizeof(float4) * XPBD_STATIC_MAX_VERTICES;      // 1 MiB
+constexpr size_t kStaticLamBytes = sizeof(float) * XPBD_STATIC_MAX_CONSTRAINTS;    // 1.5 MiB
+constexpr size_t kStaticLamcBytes = sizeof(float2) * XPBD_STATIC_MAX_VERTICES;     // 512 KiB
+constexpr size_t kStaticFlagBytes = XPBD_STATIC_MAX_VERTICES;                      // 64 KiB
+constexpr size_t kStaticBytes = kStaticPosBytes + kStaticLamBytes + kStaticLamcBytes + kStaticFlagBytes;
+static_assert(kStaticPosBytes % 256 == 0 && kStaticLamBytes % 256 == 0 && kStaticLamcBytes % 256 == 0,
+              "sub-arrays stay 256-byte aligned");
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_forward_scratch[kStaticBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_forward_scratch on the current device, looked up once per device.
+// In host code the symbol itself is only a host-side stand-in, never a device address.
+xpbd_status static_scratch_address(void** out) {
+  int dev = 0;
+  CU_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(XPBD_ERR_BOUNDS, "device ordinal beyond 64");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    CU_TRY(cudaGetSymbolAddress(&p, g_forward_scratch));
+    if (!p) return fail(XPBD_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return XPBD_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -705,6 +747,69 @@ xpbd_status xpbd_profile_read(xpbd_handle h, xpbd_kernel_stat* out) {
       out[t.cls].ms += ms;
       out[t.cls].timed_launches += 1;
     }
+  }
+  return XPBD_OK;
+}
+
+
+// Same steps and kernels as xpbd_forward, with the working state in g_forward_scratch.
+// Nothing there needs clearing between calls: prediction overwrites the positions and the
+// contact flags every step, and the first iteration of a step reads no multiplier (it
+// starts from lambda = 0), so a call never sees what the previous call left behind.
+xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                const float* x0, const float* v0, float* ck, void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (h->V > XPBD_STATIC_MAX_VERTICES || h->m > XPBD_STATIC_MAX_CONSTRAINTS)
+    return fail(XPBD_ERR_BOUNDS, "xpbd_forward_static supports at most " + std::to_string(XPBD_STATIC_MAX_VERTICES) +
+                                     " vertices and " + std::to_string(XPBD_STATIC_MAX_CONSTRAINTS) +
+                                     " constraints; this model has " + std::to_string(h->V) + " and " +
+                                     std::to_string(h->m));
+  if (h->V > 0 && (!x0 || !v0 || !ck)) return fail(XPBD_ERR_INVALID, "x0/v0/checkpoints NULL");
+  if (h->V == 0) return XPBD_OK;
+  void* base = nullptr;
+  st = static_scratch_address(&base);
+  if (st != XPBD_OK) return st;
+  float4* P = reinterpret_cast<float4*>(base);
+  float* lam = reinterpret_cast<float*>(static_cast<char*>(base) + kStaticPosBytes);
+  float2* lamc = reinterpret_cast<float2*>(static_cast<char*>(base) + kStaticPosBytes + kStaticLamBytes);
+  uint8_t* cf = reinterpret_cast<uint8_t*>(static_cast<char*>(base) + kStaticPosBytes + kStaticLamBytes +
+                                           kStaticLamcBytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = set_alpha(h, p, s);
+  if (st != XPBD_OK) return st;
+  float4* ck4 = reinterpret_cast<float4*>(ck);
+  launch(h, XPBD_K_OTHER, h->V, s, [&] { launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + h->V, h->V, s); });
+  LAUNCH_CHECK();
+  const Collide c = make_collide(p);
+  const float inv_dt = 1.f / p->dt;
+  for (int n = 0; n < steps; ++n) {
+    const float4* xn = ck_x(ck, h->V, n);
+    const float4* vn = ck_v(ck, h->V, n);
+    launch(h, XPBD_K_PREDICT, h->V, s, [&] {
+      launch_predict(xn, vn, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex, p->dt,
+                     p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
+    });
+    for (int k = 0; k < iters; ++k) {
+      for (int col = 0; col < h->K; ++col) {
+        for (const Seg& g : h->colors[col]) {
+          size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+          launch(h, XPBD_K_FWD_DIST + (int)g.type, g.count, s, [&] {
+            launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, k == 0 ? nullptr : lam + ro,
+                           lam + ro, nullptr, s);
+          });
+        }
+      }
+      if (c.flags)
+        launch(h, XPBD_K_FWD_CONTACT, h->V, s,
+               [&] { launch_contact(P, cf, h->V, k == 0 ? nullptr : lamc, lamc, nullptr, c, s); });
+      LAUNCH_CHECK();
+    }
+    float4* nx = ck4 + (size_t)2 * h->V * (n + 1);
+    launch(h, XPBD_K_VELOCITY, h->V, s,
+           [&] { launch_velocity(P, xn, nx, nx + h->V, inv_dt, h->V, h->d_err, s); });
+    LAUNCH_CHECK();
   }
   return XPBD_OK;
 }
