@@ -62,8 +62,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=160)
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--forward-only-steps", type=int, default=0,
-                    help="profiling aid: run only this many forward steps and exit (no JSON line)")
+    ap.add_argument("--sim-steps", type=int, default=0,
+                    help="profiling aid: shorter horizon (same per-step kernel mix); not a bench value")
+    ap.add_argument("--iters", type=int, default=0, help="profiling aid: fewer iterations; not a bench value")
     return ap.parse_args()
 
 
@@ -229,7 +230,13 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc, t_gen = workload(args.grid)
+    if args.sim_steps:
+        sc.steps = args.sim_steps
+        sc.f_global = sc.f_global[:args.sim_steps]
+    if args.iters:
+        sc.iters = args.iters
     N, I = sc.steps, sc.iters
+    keys = tuple(k for k in KEYFRAMES if k <= N) or (N,)
     t0 = time.time()
     solver = binding.Solver.from_scene(sc)
     t_create = time.time() - t0
@@ -238,16 +245,9 @@ def run_ours(args, ws, rank, local):
     p_true = binding.params_from_scene(sc, device=dev)
     ck = solver.new_checkpoints(N, dev)
 
-    if args.forward_only_steps:
-        solver.forward(p_true, args.forward_only_steps, I, x0, v0)
-        torch.cuda.synchronize()
-        solver.sync_status()
-        print(json.dumps({"forward_only_steps": args.forward_only_steps, "V": sc.V, "m": sc.m}))
-        return None
-
     # keyframe targets from the driven simulation; the optimisation starts from zero forces
     solver.forward(p_true, N, I, x0, v0, checkpoints=ck)
-    targets = {k: solver.read_state(ck, k)[0].clone() for k in KEYFRAMES}
+    targets = {k: solver.read_state(ck, k)[0].clone() for k in keys}
     params = binding.Params(dt=p_true.dt, compliance=p_true.compliance, gravity=p_true.gravity,
                             f_global=torch.zeros((N, 3), dtype=torch.float32, device=dev),
                             f_vertex=torch.zeros((sc.V, 3), dtype=torch.float32, device=dev),
@@ -261,7 +261,7 @@ def run_ours(args, ws, rank, local):
     def step():
         solver.forward(params, N, I, x0, v0, checkpoints=ck)
         loss, seeds = solver.loss(ck, targets)
-        solver.adjoint(params, N, I, ck, {k: seeds[i] for i, k in enumerate(KEYFRAMES)}, out=grads)
+        solver.adjoint(params, N, I, ck, {k: seeds[i] for i, k in enumerate(keys)}, out=grads)
         loss_box["loss"] = loss
 
     for _ in range(args.warmup):
@@ -317,11 +317,13 @@ def run_ours(args, ws, rank, local):
         "dtype": "f32 (f64 gradient reductions)", "data": "synthetic",
         "config": {"workload": f"sphere_cloth_{args.grid}x{args.grid}: {sc.V} vertices, {sc.n_dist} distance + "
                                f"{sc.n_bend} bending constraints, {N} steps x {I} iterations, dt=1/60, sphere "
-                               f"collider, keyframe loss at {list(KEYFRAMES)}, gradients for compliance/x0/v0/"
+                               f"collider, keyframe loss at {list(keys)}, gradients for compliance/x0/v0/"
                                f"f_global/f_vertex/sphere",
                    "V": sc.V, "m": sc.m, "sim_steps": N, "iters": I, "colors": sc.n_colors,
                    "l2": "inputs larger than L2 (vertex state 139 MB, records 1.1 GB, tapes 36 GB)",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}",
+                   **({"profiling_override": f"sim_steps={N} iters={I} (not a bench value)"}
+                      if (args.sim_steps or args.iters) else {})},
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": launches,
@@ -334,13 +336,13 @@ def run_ours(args, ws, rank, local):
     }
 
     if not args.no_e2e:
-        result["e2e"] = run_e2e(args, sc, solver, params, targets, dev, ws)
+        result["e2e"] = run_e2e(args, sc, solver, params, targets, keys, dev, ws)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = run_cpu_oracle(args.cpu_window, args.cpu_steps)
     return result
 
 
-def run_e2e(args, sc, solver, params, targets, dev, ws):
+def run_e2e(args, sc, solver, params, targets, keys, dev, ws):
     """Same metric through the public API with host buffers: every step copies its inputs
     host->device from pinned memory and the gradients and loss device->host."""
     import torch
@@ -350,7 +352,7 @@ def run_e2e(args, sc, solver, params, targets, dev, ws):
     h_x0, h_v0 = pin(sc.x0), pin(sc.v0)
     h_comp = pin(sc.compliance)
     h_fg, h_fv = pin(np.zeros((N, 3))), pin(np.zeros((sc.V, 3)))
-    h_tg = pin(np.stack([targets[k].cpu().numpy() for k in KEYFRAMES]))
+    h_tg = pin(np.stack([targets[k].cpu().numpy() for k in keys]))
     shapes = dict(compliance=(sc.m,), x0=(sc.V, 3), v0=(sc.V, 3), f_global=(N, 3), f_vertex=(sc.V, 3), collider=(5,))
     h_out = {k: torch.empty(s, dtype=torch.float64).pin_memory() for k, s in shapes.items()}
     h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -368,8 +370,8 @@ def run_e2e(args, sc, solver, params, targets, dev, ws):
                            contact_compliance=params.contact_compliance, thickness=params.thickness)
         tg = h_tg.to(dev, non_blocking=True)
         solver.forward(p, N, I, x0, v0, checkpoints=ck)
-        loss, seeds = solver.loss(ck, {k: tg[i] for i, k in enumerate(KEYFRAMES)})
-        solver.adjoint(p, N, I, ck, {k: seeds[i] for i, k in enumerate(KEYFRAMES)}, out=d_out)
+        loss, seeds = solver.loss(ck, {k: tg[i] for i, k in enumerate(keys)})
+        solver.adjoint(p, N, I, ck, {k: seeds[i] for i, k in enumerate(keys)}, out=d_out)
         for k in h_out:
             h_out[k].copy_(d_out[k], non_blocking=True)
         h_loss.copy_(loss, non_blocking=True)
