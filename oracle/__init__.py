@@ -111,6 +111,24 @@ def set_threads(n: int) -> None:
     lib().oracle_set_threads(int(n))
 
 
+def set_fp32_rounding(on: bool) -> None:
+    """Round every state value the forward program produces to float32 (attainable-floor
+    measurement); off by default."""
+    lib().oracle_set_fp32_rounding(int(bool(on)))
+
+
+class fp32_rounding:
+    """Context manager: run oracle calls with the FP32-rounding emulation on."""
+
+    def __enter__(self):
+        set_fp32_rounding(True)
+        return self
+
+    def __exit__(self, *exc):
+        set_fp32_rounding(False)
+        return False
+
+
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
 

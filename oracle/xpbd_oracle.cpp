@@ -36,6 +36,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #ifdef _OPENMP
@@ -95,6 +96,20 @@ template <class S> V3<S> cross(const V3<S>& a, const V3<S>& b) {
 template <class S> V3<S> load3(const S* p) { return {p[0], p[1], p[2]}; }
 
 const double kPi = 3.14159265358979323846;
+
+// FP32-rounding emulation (off by default): when on, every position, velocity and
+// multiplier the FP64 forward program produces is rounded to the nearest float, as the
+// float32 GPU state is.  Comparing the two FP64 runs measures how far float32 state
+// rounding alone moves a result: the attainable agreement between a float32 and a
+// float64 implementation.  It changes nothing when off.
+bool g_round32 = false;
+
+template <class T>
+inline void round32(T& v) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (g_round32) v = (double)(float)v;
+  }
+}
 
 // ------------------------------------------------------------------ constraint definitions
 enum Kind { K_DIST = 0, K_BEND = 1, K_TETH = 2, K_TETD = 3, K_PLANE = 4, K_SPHERE = 5 };
@@ -373,8 +388,12 @@ void project_one(int kind, T* q, const double* wv, const Rest& r, T& lam, const 
   if (!(val(D) > 0.0)) return;
   T dl = (-C - at * lam) / D;
   lam = lam + dl;
+  round32(lam);
   for (int a = 0; a < n_verts(kind); ++a)
-    for (int c = 0; c < 3; ++c) q[3 * a + c] = q[3 * a + c] + wv[a] * g[3 * a + c] * dl;
+    for (int c = 0; c < 3; ++c) {
+      q[3 * a + c] = q[3 * a + c] + wv[a] * g[3 * a + c] * dl;
+      round32(q[3 * a + c]);
+    }
 }
 
 template <class T>
@@ -435,6 +454,7 @@ void predict(const Model& M, const Params<T>& P, int n, const std::vector<T>& x,
       if (!P.f_vertex.empty()) f = f + P.f_vertex[3 * i + c];
       T acc = w * f + (w > 0.0 ? P.g[c] : 0.0);
       p[3 * i + c] = x[3 * i + c] + dt * v[3 * i + c] + dt * dt * acc;
+      round32(p[3 * i + c]);
     }
   }
 }
@@ -482,6 +502,7 @@ void forward(const Model& M, const Params<T>& P, int steps, int iters, const std
     for (size_t i = 0; i < V3n; ++i) {
       xs[V3n * (n + 1) + i] = W.p[i];
       vs[V3n * (n + 1) + i] = (W.p[i] - x[i]) / P.dt;
+      round32(vs[V3n * (n + 1) + i]);
     }
   }
 }
@@ -766,6 +787,9 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+// Turn the FP32-rounding emulation on (1) or off (0); see g_round32.
+void oracle_set_fp32_rounding(int on) { g_round32 = on != 0; }
 
 void oracle_set_threads(int n) {
 #ifdef _OPENMP

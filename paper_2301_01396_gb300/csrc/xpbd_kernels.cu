@@ -25,6 +25,77 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p);
 
 inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
 
+// ------------------------------------------------------------------ cache policy
+// Vertex positions and vertex adjoints are re-read by every color pass of an iteration;
+// records, multipliers and tapes are streamed once per pass.  XPBD_L2_VERTEX_HINT marks
+// vertex traffic L2 evict-last (a fraction XPBD_L2_VERTEX_FRACTION of the lines) so the
+// streams evict it last; XPBD_REC_STREAM loads records with the streaming (evict-first)
+// hint.  Both are on by default: on the 2950^2 cloth they cut the forward and replay
+// passes by 7-13% (measured with CUDA events per kernel class).
+#ifndef XPBD_L2_VERTEX_HINT
+#define XPBD_L2_VERTEX_HINT 1
+#endif
+#ifndef XPBD_L2_VERTEX_FRACTION
+#define XPBD_L2_VERTEX_FRACTION 1.0
+#endif
+#ifndef XPBD_REC_STREAM
+#define XPBD_REC_STREAM 1
+#endif
+#define XPBD_STR2(x) #x
+#define XPBD_STR(x) XPBD_STR2(x)
+
+__device__ __forceinline__ uint64_t vtx_policy() {
+#if XPBD_L2_VERTEX_HINT
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, " XPBD_STR(XPBD_L2_VERTEX_FRACTION) ";" : "=l"(p));
+  return p;
+#else
+  return 0;
+#endif
+}
+
+__device__ __forceinline__ float4 ld_vtx(const float4* a, uint64_t pol) {
+#if XPBD_L2_VERTEX_HINT
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return *a;
+#endif
+}
+
+__device__ __forceinline__ void st_vtx(float4* a, float4 v, uint64_t pol) {
+#if XPBD_L2_VERTEX_HINT
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+#else
+  (void)pol;
+  *a = v;
+#endif
+}
+
+// A record of 16, 32 or 64 bytes as 128-bit loads (streaming hint when XPBD_REC_STREAM).
+template <class Rec>
+__device__ __forceinline__ Rec ld_rec(const Rec* p) {
+#if XPBD_REC_STREAM
+  static_assert(sizeof(Rec) % 16 == 0, "records are 16-byte multiples");
+  union {
+    int4 v[sizeof(Rec) / 16];
+    Rec r;
+  } u;
+  const int4* q = reinterpret_cast<const int4*>(p);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(Rec) / 16); ++k) u.v[k] = __ldcs(q + k);
+  return u.r;
+#else
+  return *p;
+#endif
+}
+
 // ------------------------------------------------------------------ deterministic reductions
 // Block-wide sum of NC doubles; thread 0 writes the block's partial sums.  The order of
 // additions depends only on the launch shape, so results are bitwise reproducible.
@@ -149,9 +220,10 @@ __global__ void k_proj_dist(const DistRec* __restrict__ rec, int n, float4* __re
                             const float* lam_in, float* lam_out, float4* __restrict__ tape) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const DistRec r = rec[i];
-  float4 pa = P[r.a];
-  float4 pb = P[r.b];
+  const DistRec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
+  float4 pa = ld_vtx(P + r.a, pol);
+  float4 pb = ld_vtx(P + r.b, pol);
   if (tape) {
     __stcs(tape + 2 * i, pa);
     __stcs(tape + 2 * i + 1, pb);
@@ -168,82 +240,89 @@ __global__ void k_proj_dist(const DistRec* __restrict__ rec, int n, float4* __re
     lam += dl;
     f3 a = xyz(pa) + nrm * (pa.w * dl);
     f3 b = xyz(pb) - nrm * (pb.w * dl);
-    P[r.a] = with_w(a, pa.w);
-    P[r.b] = with_w(b, pb.w);
+    st_vtx(P + r.a, with_w(a, pa.w), pol);
+    st_vtx(P + r.b, with_w(b, pb.w), pol);
   }
   __stcs(lam_out + i, lam);
 }
 
-// ---- 4-vertex constraints (bending, tet C_H, tet C_D)
+// ---- 4-vertex constraints (bending, tet C_H, tet C_D), in relative coordinates
+// e1 = x1 - x0, e2 = x2 - x0, e3 = x3 - x0 (all three constraints are translation
+// invariant): grad_0 = -(grad_1 + grad_2 + grad_3) and (H u)_0 = -sum_k (H u)_k.
 template <int KIND>   // 1 bending, 2 hydrostatic, 3 deviatoric
 struct Quad;
 
 template <>
 struct Quad<1> {
   typedef BendRec Rec;
-  __device__ static bool eval(const Rec& r, const f3 x[4], f3 g[4], float& C) {
-    if (bend_degenerate(x)) return false;
-    bend_grad<float>(x, g);
-    C = bend_C(x, r.theta0);
+  // value and gradient (g1..g3); false if degenerate
+  __device__ static bool eval(const Rec& r, const f3& e1, const f3& e2, const f3& e3, f3& g1, f3& g2,
+                              f3& g3, float& C) {
+    if (bend_degenerate_rel(e1, e2, e3)) return false;
+    bend_grad_rel<float>(e1, e2, e3, g1, g2, g3);
+    C = bend_C_rel(e1, e2, e3, r.theta0);
     return true;
   }
-  __device__ static void hvp(const Rec& r, const f3 x[4], const f3 u[4], f3 hu[4]) {
-    d3 xd[4], gd[4];
-    for (int k = 0; k < 4; ++k) xd[k] = mkd3(x[k], u[k]);
-    bend_grad<df>(xd, gd);
-    for (int k = 0; k < 4; ++k) hu[k] = dpart(gd[k]);
+  // gradient (value parts) and H u (derivative parts) for relative directions du1..du3
+  __device__ static void hvp(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
+                             const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
+    bend_grad_rel<df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), g1, g2, g3);
   }
 };
 
 template <bool HYDRO>
 struct TetQuad {
   typedef TetRec Rec;
-  __device__ static bool eval(const Rec& r, const f3 x[4], f3 g[4], float& C) {
-    tet_grad<HYDRO, float>(x, r.B, g, &C, r.gamma);
+  __device__ static bool eval(const Rec& r, const f3& e1, const f3& e2, const f3& e3, f3& g1, f3& g2,
+                              f3& g3, float& C) {
+    tet_grad_rel<HYDRO, float>(e1, e2, e3, r.B, g1, g2, g3, &C, r.gamma);
     if (!HYDRO && C * C < XPBD_DEGEN2) return false;
     return true;
   }
-  __device__ static void hvp(const Rec& r, const f3 x[4], const f3 u[4], f3 hu[4]) {
-    d3 xd[4], gd[4];
-    for (int k = 0; k < 4; ++k) xd[k] = mkd3(x[k], u[k]);
-    df C;
-    tet_grad<HYDRO, df>(xd, r.B, gd, &C, r.gamma);
-    for (int k = 0; k < 4; ++k) hu[k] = dpart(gd[k]);
+  __device__ static void hvp(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
+                             const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
+    tet_grad_rel<HYDRO, df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), r.B, g1, g2, g3, nullptr,
+                            r.gamma);
   }
 };
 template <> struct Quad<2> : TetQuad<true> {};
 template <> struct Quad<3> : TetQuad<false> {};
 
+#ifndef XPBD_PROJ_QUAD_MIN_BLOCKS
+#define XPBD_PROJ_QUAD_MIN_BLOCKS 1
+#endif
 template <int KIND>
-__global__ void k_proj_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
+__global__ void __launch_bounds__(kBlock, XPBD_PROJ_QUAD_MIN_BLOCKS)
+k_proj_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
                             float4* __restrict__ P, const float* lam_in, float* lam_out,
                             float4* __restrict__ tape) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const typename Quad<KIND>::Rec r = rec[i];
+  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
   float4 p[4];
-  f3 x[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    p[k] = P[r.v[k]];
-    x[k] = xyz(p[k]);
-  }
+  for (int k = 0; k < 4; ++k) p[k] = ld_vtx(P + r.v[k], pol);
   if (tape) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) __stcs(tape + 4 * i + k, p[k]);
   }
   float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
-  f3 g[4];
+  const f3 x0 = xyz(p[0]);
+  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
+  f3 g1, g2, g3;
   float C;
-  if (Quad<KIND>::eval(r, x, g, C)) {
-    float D = r.at;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) D += p[k].w * dot(g[k], g[k]);
+  if (Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
+    const f3 g0 = -(g1 + g2 + g3);
+    float D = r.at + p[0].w * dot(g0, g0) + p[1].w * dot(g1, g1) + p[2].w * dot(g2, g2) +
+              p[3].w * dot(g3, g3);
     if (D > 0.f) {
       float dl = (-C - r.at * lam) / D;
       lam += dl;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) P[r.v[k]] = with_w(x[k] + g[k] * (p[k].w * dl), p[k].w);
+      st_vtx(P + r.v[0], with_w(x0 + g0 * (p[0].w * dl), p[0].w), pol);
+      st_vtx(P + r.v[1], with_w(xyz(p[1]) + g1 * (p[1].w * dl), p[1].w), pol);
+      st_vtx(P + r.v[2], with_w(xyz(p[2]) + g2 * (p[2].w * dl), p[2].w), pol);
+      st_vtx(P + r.v[3], with_w(xyz(p[3]) + g3 * (p[3].w * dl), p[3].w), pol);
     }
   }
   __stcs(lam_out + i, lam);
@@ -386,7 +465,8 @@ __global__ void k_vjp_dist(const DistRec* __restrict__ rec, int n, const float4*
                            float2* __restrict__ lb, double* __restrict__ acc, bool first, bool last) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const DistRec r = rec[i];
+  const DistRec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
   float4 pa = ld_stream(tape + 2 * i), pb = ld_stream(tape + 2 * i + 1);
   float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
   float2 l = first ? make_float2(0.f, 0.f) : lb[i];
@@ -398,7 +478,7 @@ __global__ void k_vjp_dist(const DistRec* __restrict__ rec, int n, const float4*
     float len = l2 * il;
     f3 nrm = d * il;
     float dl = (-(len - r.L) - r.at * lam) / D;
-    float4 xa4 = xbar[r.a], xb4 = xbar[r.b];
+    float4 xa4 = ld_vtx(xbar + r.a, pol), xb4 = ld_vtx(xbar + r.b, pol);
     f3 xa = xyz(xa4), xb = xyz(xb4);
     float s = l.x + pa.w * dot(nrm, xa) - pb.w * dot(nrm, xb);
     // H u for the distance constraint: (P (u_a - u_b))/l on a, the negative on b, with
@@ -408,54 +488,64 @@ __global__ void k_vjp_dist(const DistRec* __restrict__ rec, int n, const float4*
     float sD = s / D;
     xa = xa - nrm * sD + hv;
     xb = xb + nrm * sD - hv;
-    xbar[r.a] = with_w(xa, 0.f);
-    xbar[r.b] = with_w(xb, 0.f);
+    st_vtx(xbar + r.a, with_w(xa, 0.f), pol);
+    st_vtx(xbar + r.b, with_w(xb, 0.f), pol);
     l.y += -sD * (lam + dl);
     l.x -= r.at * sD;
   }
   lb_finish(i, l.x, l.y, lb, acc, last);
 }
 
+// 3 resident blocks of 256 threads for the 4-vertex reverse passes (<= 85 registers; the
+// compiler spills 32-48 bytes): 11% faster than 2 blocks at 96-107 registers on the
+// bending reverse pass.
+#ifndef XPBD_VJP_QUAD_MIN_BLOCKS
+#define XPBD_VJP_QUAD_MIN_BLOCKS 3
+#endif
 template <int KIND>
-__global__ void k_vjp_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
+__global__ void __launch_bounds__(kBlock, XPBD_VJP_QUAD_MIN_BLOCKS)
+k_vjp_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
                            const float4* __restrict__ tape, const float* __restrict__ lam_pre,
                            float4* __restrict__ xbar, float2* __restrict__ lb,
                            double* __restrict__ acc, bool first, bool last) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const typename Quad<KIND>::Rec r = rec[i];
-  float4 p[4];
-  f3 x[4];
+  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
+  // every global read is independent of the arithmetic: issue them all first
+  float4 p[4], xb4[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    p[k] = ld_stream(tape + 4 * i + k);
-    x[k] = xyz(p[k]);
-  }
+  for (int k = 0; k < 4; ++k) p[k] = ld_stream(tape + 4 * i + k);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) xb4[k] = ld_vtx(xbar + r.v[k], pol);
   float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
   float2 l = first ? make_float2(0.f, 0.f) : lb[i];
-  f3 g[4];
+  const f3 x0 = xyz(p[0]);
+  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
+  f3 g1, g2, g3;
   float C;
-  if (Quad<KIND>::eval(r, x, g, C)) {
-    float D = r.at;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) D += p[k].w * dot(g[k], g[k]);
+  if (Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
+    const f3 g0 = -(g1 + g2 + g3);
+    const float w0 = p[0].w, w1 = p[1].w, w2 = p[2].w, w3 = p[3].w;
+    float D = r.at + w0 * dot(g0, g0) + w1 * dot(g1, g1) + w2 * dot(g2, g2) + w3 * dot(g3, g3);
     if (D > 0.f) {
       float dl = (-C - r.at * lam) / D;
-      f3 xb[4];
-      float s = l.x;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        xb[k] = xyz(xbar[r.v[k]]);
-        s += p[k].w * dot(g[k], xb[k]);
-      }
+      const f3 xb0 = xyz(xb4[0]), xb1 = xyz(xb4[1]), xb2 = xyz(xb4[2]), xb3 = xyz(xb4[3]);
+      float s = l.x + w0 * dot(g0, xb0) + w1 * dot(g1, xb1) + w2 * dot(g2, xb2) + w3 * dot(g3, xb3);
       float sD = s / D;
       float c2 = 2.f * sD * dl;
-      f3 u[4], hu[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) u[k] = (xb[k] * dl - g[k] * c2) * p[k].w;
-      Quad<KIND>::hvp(r, x, u, hu);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) xbar[r.v[k]] = with_w(xb[k] - g[k] * sD + hu[k], 0.f);
+      const f3 u0 = (xb0 * dl - g0 * c2) * w0;
+      const f3 du1 = (xb1 * dl - g1 * c2) * w1 - u0;
+      const f3 du2 = (xb2 * dl - g2 * c2) * w2 - u0;
+      const f3 du3 = (xb3 * dl - g3 * c2) * w3 - u0;
+      d3 h1, h2, h3;
+      Quad<KIND>::hvp(r, e1, e2, e3, du1, du2, du3, h1, h2, h3);
+      const f3 hu1 = dpart(h1), hu2 = dpart(h2), hu3 = dpart(h3);
+      const f3 hu0 = -(hu1 + hu2 + hu3);
+      st_vtx(xbar + r.v[0], with_w(xb0 - g0 * sD + hu0, 0.f), pol);
+      st_vtx(xbar + r.v[1], with_w(xb1 - g1 * sD + hu1, 0.f), pol);
+      st_vtx(xbar + r.v[2], with_w(xb2 - g2 * sD + hu2, 0.f), pol);
+      st_vtx(xbar + r.v[3], with_w(xb3 - g3 * sD + hu3, 0.f), pol);
       l.y += -sD * (lam + dl);
       l.x -= r.at * sD;
     }

@@ -126,6 +126,41 @@ XHD void bend_grad(const v3<S> x[4], v3<S> g[4]) {
   g[1] = tA0 * qA + tB0 * qB;
 }
 
+// The same gradient in relative coordinates e = x1 - x0, a = x2 - x0, b = x3 - x0 (the
+// constraint is translation invariant): returns g1, g2, g3; g0 = -(g1 + g2 + g3).  With
+// dual inputs whose derivative parts are u_k - u_0, the derivative parts of the result are
+// (H u)_1..3, and (H u)_0 = -((H u)_1 + (H u)_2 + (H u)_3) (rows of H sum to zero).
+template <class S>
+XHD void bend_grad_rel(const v3<S>& e, const v3<S>& a, const v3<S>& b, v3<S>& g1, v3<S>& g2,
+                       v3<S>& g3) {
+  v3<S> nA = cross(e, a);
+  v3<S> nB = cross(b, e);
+  S le = sqrt_(dot(e, e));
+  S ile = inv_(le);
+  v3<S> qA = nA * inv_(dot(nA, nA));
+  v3<S> qB = nB * inv_(dot(nB, nB));
+  g2 = -(le * qA);
+  g3 = -(le * qB);
+  g1 = (dot(a, e) * ile) * qA + (dot(b, e) * ile) * qB;
+}
+
+XHD bool bend_degenerate_rel(const f3& e, const f3& a, const f3& b) {
+  f3 nA = cross(e, a);
+  f3 nB = cross(b, e);
+  return dot(e, e) < XPBD_DEGEN2 || dot(nA, nA) < XPBD_DEGEN2 || dot(nB, nB) < XPBD_DEGEN2;
+}
+
+XHD float bend_C_rel(const f3& e, const f3& a, const f3& b, float theta0) {
+  f3 nA = cross(e, a);
+  f3 nB = cross(b, e);
+  float sn = dot(cross(nA, nB), e) * (1.f / sqrtf(dot(e, e)));
+  float cs = dot(nA, nB);
+  float c = atan2f(sn, cs) - theta0;
+  if (c > kPi) c -= 2.f * kPi;
+  if (c <= -kPi) c += 2.f * kPi;
+  return c;
+}
+
 XHD bool bend_degenerate(const f3 x[4]) {
   f3 e = x[1] - x[0];
   f3 nA = cross(e, x[2] - x[0]);
@@ -154,6 +189,31 @@ template <class S>
 XHD void tet_F(const v3<S> x[4], const float* B, v3<S> f[3]) {
   v3<S> d1 = x[1] - x[0], d2 = x[2] - x[0], d3 = x[3] - x[0];
   for (int j = 0; j < 3; ++j) f[j] = d1 * S(B[0 * 3 + j]) + d2 * S(B[1 * 3 + j]) + d3 * S(B[2 * 3 + j]);
+}
+
+// Relative form: Ds columns d1, d2, d3 in, g1..g3 out (g0 = -(g1 + g2 + g3)).
+template <bool HYDRO, class S>
+XHD void tet_grad_rel(const v3<S>& d1, const v3<S>& d2, const v3<S>& d3, const float* B, v3<S>& g1,
+                      v3<S>& g2, v3<S>& g3, S* C_out, float gamma) {
+  v3<S> f[3];
+  for (int j = 0; j < 3; ++j) f[j] = d1 * S(B[0 * 3 + j]) + d2 * S(B[1 * 3 + j]) + d3 * S(B[2 * 3 + j]);
+  v3<S> p[3];
+  if (HYDRO) {
+    p[0] = cross(f[1], f[2]);
+    p[1] = cross(f[2], f[0]);
+    p[2] = cross(f[0], f[1]);
+    if (C_out) *C_out = dot(f[0], p[0]) - gamma;
+  } else {
+    S nrm = sqrt_(dot(f[0], f[0]) + dot(f[1], f[1]) + dot(f[2], f[2]));
+    S in = inv_(nrm);
+    p[0] = f[0] * in;
+    p[1] = f[1] * in;
+    p[2] = f[2] * in;
+    if (C_out) *C_out = nrm;
+  }
+  g1 = p[0] * S(B[0]) + p[1] * S(B[1]) + p[2] * S(B[2]);
+  g2 = p[0] * S(B[3]) + p[1] * S(B[4]) + p[2] * S(B[5]);
+  g3 = p[0] * S(B[6]) + p[1] * S(B[7]) + p[2] * S(B[8]);
 }
 
 template <bool HYDRO, class S>

@@ -301,10 +301,18 @@ def lognormal_cloth_compliance(rng, nd: int, nb: int, stretch: float = 1e-4,
 
 
 def ground_cloth(n: int = 256, *, steps: int = 100, iters: int = 30, seed: int = 2,
-                 plane_h: float = -0.6, pins=((0, 0), (-1, 0))) -> Scene:
+                 plane_h: float = -0.6, pins=(), tilt: float = 0.3) -> Scene:
     """Cloth with stretch/shear springs (one diagonal) and dihedral bending, per-constraint
-    lognormal compliance, two corners pinned, ground plane below."""
+    lognormal compliance, falling onto a ground plane.  No vertex is pinned; the sheet
+    starts flat and at rest, tilted by `tilt` radians about the x axis (through its centre
+    line z = 0.5), so it reaches the ground progressively."""
     g = cloth_grid(n, 1.0, areal_density=2.56, diagonals="one", bending=True, pins=pins)
+    if tilt:
+        x = g["rest_x"].copy()
+        z = x[:, 2] - 0.5
+        x[:, 1] = x[:, 1] + np.sin(tilt) * z
+        x[:, 2] = 0.5 + np.cos(tilt) * z
+        g["rest_x"] = f32(x)
     rng = np.random.default_rng(seed)
     alpha = lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0])
     return _cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters,
@@ -354,8 +362,10 @@ def tet_block(n: int = 32, *, size: float = 1.0, density: float = 1000.0, y0: fl
               steps: int = 120, iters: int = 20, seed: int = 3, plane_h: float = 0.0,
               alpha_lo: float = 1e-6, alpha_hi: float = 1e-3) -> Scene:
     """n^3 cube cells split into 5 tets each (mirrored parity so faces conform), falling on
-    a ground plane.  Per-tet hydrostatic and deviatoric inverse moduli drawn log-uniform in
-    [alpha_lo, alpha_hi]; gamma = 1 + alpha_H / alpha_D (rest state in equilibrium)."""
+    a ground plane.  Per tet, two inverse moduli are drawn log-uniform in [alpha_lo,
+    alpha_hi]; the smaller is the hydrostatic one (1/lambda) and the larger the deviatoric
+    one (1/mu), so lambda >= mu (Poisson ratio >= 1/4), and gamma = 1 + alpha_H / alpha_D
+    in (1, 2] makes the rest state an equilibrium."""
     h = size / n
     N1 = n + 1
     I, J, K = np.meshgrid(np.arange(N1), np.arange(N1), np.arange(N1), indexing="ij")
@@ -398,8 +408,9 @@ def tet_block(n: int = 32, *, size: float = 1.0, density: float = 1000.0, y0: fl
             offsets.append(offsets[-1] + ids.shape[0])
     rng = np.random.default_rng(seed)
     la, lb = np.log(alpha_lo), np.log(alpha_hi)
-    aH = np.exp(rng.uniform(la, lb, nt))
-    aD = np.exp(rng.uniform(la, lb, nt))
+    a1 = np.exp(rng.uniform(la, lb, nt))
+    a2 = np.exp(rng.uniform(la, lb, nt))
+    aH, aD = np.minimum(a1, a2), np.maximum(a1, a2)
     gamma = 1.0 + aH / aD
     V = N1 ** 3
     xr = f32(x)

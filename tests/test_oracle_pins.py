@@ -409,3 +409,17 @@ def test_initial_velocity_gradient_is_adjoint_state(oracle_mod):
     seed[1] = [0.3, -0.7, 0.2]
     gr = oracle_mod.adjoint(sc, {1: seed}, 1, 1)
     assert rel(gr["v0"], sc.dt * gr["x0"]) < 1e-13
+
+
+def test_fp32_rounding_emulation_is_off_by_default(oracle_mod):
+    """The FP32-rounding emulation (used to measure attainable float32 agreement) changes
+    nothing unless switched on, and when on every state value is float-representable."""
+    sc = small_cloth(6, steps=3, iters=2, plane_h=-0.02, v_scale=0.2)
+    a, _ = oracle_mod.forward(sc)
+    with oracle_mod.fp32_rounding():
+        b, vb = oracle_mod.forward(sc)
+    c, _ = oracle_mod.forward(sc)
+    assert np.array_equal(a, c)
+    assert np.array_equal(b, b.astype(np.float32).astype(np.float64))
+    assert np.array_equal(vb, vb.astype(np.float32).astype(np.float64))
+    assert 0 < np.abs(a - b).max() < 1e-5
