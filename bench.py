@@ -65,6 +65,13 @@ def parse():
     ap.add_argument("--sim-steps", type=int, default=0,
                     help="profiling aid: shorter horizon (same per-step kernel mix); not a bench value")
     ap.add_argument("--iters", type=int, default=0, help="profiling aid: fewer iterations; not a bench value")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving stream instead of the default workload: p50/p99 latency and steps/s, "
+                         "continuous batching vs one request at a time")
+    ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--serving-load", type=float, default=1.0,
+                    help="arrival rate as a multiple of the one-at-a-time service rate")
+    ap.add_argument("--serving-slots", type=int, default=64)
     return ap.parse_args()
 
 
@@ -389,6 +396,120 @@ def run_e2e(args, sc, solver, params, targets, keys, dev, ws):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t * 1e3, 2)}
 
 
+# ----------------------------------------------------------------------------- serving
+
+def run_serving(args):
+    """Serving stream: seeded cloth requests (side U{32..512}, horizon U{20..200} steps,
+    U{10..40} iterations, 0-4 pins on the top row, ground plane with probability 1/2), each
+    a forward solve + keyframe loss at the last step + full reverse sweep.  Poisson arrivals
+    at `serving-load` x the one-at-a-time service rate (measured on the first requests).
+    The same trace is served (a) one request at a time, FIFO, through the one-request API,
+    (b) by the continuous-batching server; every request's gradients from (b) are checked
+    against (a)."""
+    import torch
+    from paper_2301_01396_gb300 import binding
+    dev = torch.device("cuda")
+    trace = scenes.serving_requests(args.serving_requests, seed=5)
+    items = []
+    for k, rq in enumerate(trace):
+        sc = scenes.request_scene(rq)
+        solver = binding.Solver.from_scene(sc)
+        p = binding.params_from_scene(sc, device=dev)
+        rng = np.random.default_rng(1000 + k)
+        target = sc.x0 + 0.05 * rng.standard_normal(sc.x0.shape)
+        items.append(dict(sc=sc, solver=solver, p=p, x0=torch.as_tensor(sc.x0.astype(np.float32), device=dev),
+                          v0=torch.as_tensor(sc.v0.astype(np.float32), device=dev),
+                          target=torch.as_tensor(target.astype(np.float32), device=dev)))
+    want = ("compliance", "x0", "v0")
+
+    def serve_one(it):
+        sc, solver, p = it["sc"], it["solver"], it["p"]
+        ck = solver.forward(p, sc.steps, sc.iters, it["x0"], it["v0"])
+        loss, seeds = solver.loss(ck, {sc.steps: it["target"]})
+        g = solver.adjoint(p, sc.steps, sc.iters, ck, {sc.steps: seeds[0]}, want=want)
+        torch.cuda.synchronize()
+        return g
+
+    n_cal = min(6, len(items))
+    t0 = time.perf_counter()
+    for it in items[:n_cal]:
+        serve_one(it)
+    mean_service = (time.perf_counter() - t0) / n_cal
+    rng = np.random.default_rng(55)
+    gaps = rng.exponential(mean_service / args.serving_load, len(items))
+    arrivals = np.cumsum(gaps) - gaps[0]
+
+    # (a) one request at a time, FIFO, one-request API
+    lat_a, ref = [], []
+    t0 = time.perf_counter()
+    for k, it in enumerate(items):
+        now = time.perf_counter() - t0
+        if now < arrivals[k]:
+            time.sleep(arrivals[k] - now)
+        g = serve_one(it)
+        lat_a.append(time.perf_counter() - t0 - arrivals[k])
+        ref.append({kk: v.cpu() for kk, v in g.items()})
+    span_a = time.perf_counter() - t0
+
+    # (b) continuous batching: arrivals are admitted while earlier requests run
+    srv = binding.Server(max_slots=args.serving_slots)
+    lat_b = [0.0] * len(items)
+    tickets = [None] * len(items)
+    live = {}
+    nxt = 0
+    max_active = 0
+    t0 = time.perf_counter()
+    while nxt < len(items) or live:
+        now = time.perf_counter() - t0
+        while nxt < len(items) and arrivals[nxt] <= now:
+            it = items[nxt]
+            sc = it["sc"]
+            t = srv.submit(it["solver"], it["p"], sc.steps, sc.iters, it["x0"], it["v0"], it["target"], want=want)
+            tickets[nxt] = t
+            live[t] = nxt
+            nxt += 1
+        if not live:
+            time.sleep(min(max(arrivals[nxt] - now, 0.0), 0.002))
+            continue
+        max_active = max(max_active, srv.run(32))
+        for t in list(live):
+            if srv.poll(t):
+                k = live.pop(t)
+                lat_b[k] = time.perf_counter() - t0 - arrivals[k]
+    span_b = time.perf_counter() - t0
+    st = srv.stats()
+    worst = 0.0
+    for k, t in enumerate(tickets):
+        res = srv.result(t)
+        for kk in want:
+            a, b = res[kk].cpu(), ref[k][kk]
+            d = float((a - b).norm() / max(float(b.norm()), 1e-300))
+            worst = max(worst, d)
+    srv.close()
+
+    def pct(lat):
+        return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+    sim_steps = sum(it["sc"].steps for it in items)
+    updates = sum(2 * it["sc"].m * it["sc"].iters * it["sc"].steps for it in items)
+    pa, pb = pct(lat_a), pct(lat_b)
+    return {
+        "metric": "serving p50/p99 latency (s) and simulated steps/s", "impl": "ours", "mode": "serving",
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": f"serving stream: {len(items)} seeded cloth requests (side 32-512, 20-200 steps, "
+                               f"10-40 iterations, forward + loss + full reverse sweep), Poisson arrivals at "
+                               f"{args.serving_load} x the one-at-a-time service rate",
+                   "requests": len(items), "slots": args.serving_slots, "mean_service_s": round(mean_service, 4)},
+        "batched": {"p50_s": round(pb[0], 4), "p99_s": round(pb[1], 4), "makespan_s": round(span_b, 3),
+                    "steps_per_s": round(sim_steps / span_b, 1), "updates_per_s": updates / span_b,
+                    "max_resident": max_active, "dispatch_launches": st["ticks"], "passes": st["items"]},
+        "one_at_a_time": {"p50_s": round(pa[0], 4), "p99_s": round(pa[1], 4), "makespan_s": round(span_a, 3),
+                          "steps_per_s": round(sim_steps / span_a, 1), "updates_per_s": updates / span_a},
+        "speedup_steps_per_s": round(span_a / span_b, 3),
+        "max_rel_grad_diff_batched_vs_single": worst,
+    }
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, ws, rank):
@@ -430,6 +551,10 @@ def main():
             print(json.dumps(res))
         return
     dist_init(ws)
+    if args.serving:
+        if rank == 0:
+            print(json.dumps(run_serving(args)))
+        return
     res = run_ours(args, ws, rank, local)
     if res is not None and rank == 0:
         print(json.dumps(res))

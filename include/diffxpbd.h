@@ -192,6 +192,75 @@ xpbd_status xpbd_sync_status(xpbd_handle h, void* stream);
 xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
                                 const float* x0, const float* v0, float* checkpoints, void* stream);
 
+/* ---------------------------------------------------------------- serving
+   Continuous batching of forward + gradient requests (one GPU).  A request is one solve:
+   `steps` steps of `iters` iterations from (x0, v0), the loss L = 1/2 |x_steps - target|^2
+   (Sec. 4.1 with one keyframe at the last step), and the full reverse sweep.  The server
+   keeps every admitted request's state, checkpoints and tapes resident and advances all
+   of them together: each launch of its dispatch kernel runs the next pass (a color of a
+   forward or reverse iteration, a contact pass, a prediction, ...) of every resident
+   request, reading a concatenated table of those passes.  Requests submitted while others
+   run are admitted at the next xpbd_server_run call, in submission order, as soon as a
+   slot is free and their workspace fits in the memory budget; their passes then share the
+   GPU with the requests already running.  Every request computes exactly the values it
+   would compute alone on the server: its passes run the same per-element code in the same
+   order, whatever else shares the launch.
+
+   Ownership: the request's handle (one handle per in-flight request: the server writes the
+   handle's per-call parameters into its records), params pointers, x0, v0, target and the
+   output buffers belong to the caller and must stay valid until xpbd_server_poll reports
+   the request done.  The server allocates each request's workspace (stream-ordered, on the
+   server's stream) at admission and frees it when the request completes. */
+typedef struct xpbd_server_t* xpbd_server;
+
+typedef struct {
+  xpbd_handle handle;       /* model of the request                                       */
+  xpbd_params params;       /* as for xpbd_forward (device pointers stay caller-owned)     */
+  int32_t steps, iters;
+  const float* x0;          /* DEVICE [V*3]                                                */
+  const float* v0;          /* DEVICE [V*3]                                                */
+  const float* target;      /* DEVICE [V*3] target positions at the last step              */
+  double* loss_out;         /* DEVICE [1] L (float64), or NULL                             */
+  xpbd_grads grads;         /* DEVICE outputs as for xpbd_adjoint (NULL entries skipped)   */
+} xpbd_request;
+
+typedef struct {
+  int64_t submitted, admitted, completed;
+  int32_t pending, active;  /* waiting for admission / resident on the GPU                 */
+  size_t bytes_in_use, budget;
+  int64_t ticks;            /* dispatch-kernel launches so far                             */
+  int64_t items;            /* passes executed by them                                     */
+} xpbd_server_stats;
+
+/* Device bytes a request allocates at admission (checkpoints, tapes, gradient state). */
+size_t xpbd_request_bytes(xpbd_handle h, int32_t steps, int32_t iters, int32_t collider_flags);
+
+/* Create a server on `stream` (cudaStream_t) that keeps at most `max_slots` requests
+   resident and at most `hbm_budget` bytes of request workspace (0: 90% of the device
+   memory free now).  Allocates its dispatch tables (device and pinned host memory). */
+xpbd_status xpbd_server_create(size_t hbm_budget, int32_t max_slots, void* stream, xpbd_server* out);
+
+/* Wait for the server's work, free everything it owns (requests not yet polled are
+   dropped). */
+xpbd_status xpbd_server_destroy(xpbd_server s);
+
+/* Queue a request (HOST struct, copied).  XPBD_ERR_OOM if its workspace alone exceeds the
+   budget; XPBD_ERR_INVALID for bad arguments.  Returns a ticket. */
+xpbd_status xpbd_server_submit(xpbd_server s, const xpbd_request* r, uint64_t* ticket);
+
+/* Retire finished requests, admit queued ones that fit, and queue up to `max_ticks`
+   dispatch launches on the server's stream (fewer if every resident request finishes).
+   Returns without waiting for the GPU; at most two batches of launches are in flight.
+   *active_out (may be NULL) receives the number of resident requests afterwards. */
+xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_out);
+
+/* *done = 1 once every pass of the request has finished on the GPU (its outputs are then
+   valid and its workspace freed), else 0.  Non-blocking.  Polling a completed ticket
+   again returns XPBD_ERR_INVALID. */
+xpbd_status xpbd_server_poll(xpbd_server s, uint64_t ticket, int32_t* done);
+
+xpbd_status xpbd_server_get_stats(xpbd_server s, xpbd_server_stats* out);
+
 /* Kernel launch statistics.  Every kernel launch of a handle is counted per class; while
    profiling is enabled each launch is also bracketed by two CUDA events recorded on the
    stream it is launched on, so `ms` is the summed device time of that class.  `units` is

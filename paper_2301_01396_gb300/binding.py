@@ -60,6 +60,18 @@ class XpbdKernelStat(C.Structure):
                 ("timed_launches", C.c_int64)]
 
 
+class XpbdRequest(C.Structure):
+    _fields_ = [("handle", C.c_void_p), ("params", XpbdParams), ("steps", C.c_int32), ("iters", C.c_int32),
+                ("x0", C.c_void_p), ("v0", C.c_void_p), ("target", C.c_void_p), ("loss_out", C.c_void_p),
+                ("grads", XpbdGrads)]
+
+
+class XpbdServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("pending", C.c_int32), ("active", C.c_int32), ("bytes_in_use", C.c_size_t),
+                ("budget", C.c_size_t), ("ticks", C.c_int64), ("items", C.c_int64)]
+
+
 class XpbdError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -78,13 +90,17 @@ def lib():
                                "(run __graft_entry__.build()); there is no CPU fallback")
         L = C.CDLL(LIB_PATH)
         for name in ("xpbd_create", "xpbd_destroy", "xpbd_sizes", "xpbd_forward", "xpbd_read_state",
-                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read", "xpbd_forward_static"):
+                     "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read", "xpbd_forward_static",
+                     "xpbd_server_create", "xpbd_server_destroy", "xpbd_server_submit", "xpbd_server_run",
+                     "xpbd_server_poll", "xpbd_server_get_stats"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
         L.xpbd_workspace_bytes.restype = C.c_size_t
         L.xpbd_workspace_bytes.argtypes = [C.c_void_p, C.c_int32]
         L.xpbd_last_error.restype = C.c_char_p
+        L.xpbd_request_bytes.restype = C.c_size_t
+        L.xpbd_request_bytes.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]
         _lib = L
     return _lib
 
@@ -333,3 +349,81 @@ def simulate(solver: Solver, cfg: dict, compliance, x0, v0, f_global=None, f_ver
     """Autograd entry point: returns the positions [V,3] at each key step (default: the last)."""
     ks = (cfg["steps"],) if key_steps is None else tuple(key_steps)
     return XPBDSolve.apply(solver, cfg, ks, compliance, x0, v0, f_global, f_vertex, collider)
+
+
+class Server:
+    """Continuous-batching server (xpbd_server_*): forward + loss + full reverse sweep per
+    request, with every resident request advanced by each launch of the dispatch kernel.
+
+    submit() keeps references to the request's tensors (and allocates its float64 outputs)
+    until poll() reports it done; result() then returns {"loss": [1], <gradient groups>}."""
+
+    def __init__(self, budget: int = 0, max_slots: int = 64, stream=None):
+        self._stream = torch.cuda.current_stream() if stream is None else stream
+        s = C.c_void_p()
+        _check(lib().xpbd_server_create(C.c_size_t(int(budget)), int(max_slots), C.c_void_p(self._stream.cuda_stream),
+                                        C.byref(s)))
+        self._s = s
+        self._live = {}
+        self._done = {}
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and _lib is not None:
+            _lib.xpbd_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def request_bytes(solver: "Solver", steps: int, iters: int, collider_flags: int = 0) -> int:
+        return int(lib().xpbd_request_bytes(solver.handle, int(steps), int(iters), int(collider_flags)))
+
+    def submit(self, solver: "Solver", params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
+               target: torch.Tensor, want=("compliance", "x0", "v0")) -> int:
+        dev = x0.device
+        shapes = dict(compliance=(solver.m,), x0=(solver.V, 3), v0=(solver.V, 3), f_global=(max(steps, 1), 3),
+                      f_vertex=(solver.V, 3), collider=(5,))
+        out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
+        out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+        g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")), d_v0=_ptr(out.get("v0")),
+                      d_f_global=_ptr(out.get("f_global")), d_f_vertex=_ptr(out.get("f_vertex")),
+                      d_collider=_ptr(out.get("collider")))
+        req = XpbdRequest(handle=solver.handle, params=params.c_struct(), steps=int(steps), iters=int(iters),
+                          x0=_ptr(x0), v0=_ptr(v0), target=_ptr(target), loss_out=_ptr(out["loss"]), grads=g)
+        t = C.c_uint64()
+        _check(lib().xpbd_server_submit(self._s, C.byref(req), C.byref(t)))
+        self._live[t.value] = (solver, params, x0, v0, target, out)
+        return t.value
+
+    def run(self, max_ticks: int = 64) -> int:
+        active = C.c_int32()
+        _check(lib().xpbd_server_run(self._s, int(max_ticks), C.byref(active)))
+        return active.value
+
+    def poll(self, ticket: int) -> bool:
+        if ticket in self._done:
+            return True
+        d = C.c_int32()
+        _check(lib().xpbd_server_poll(self._s, C.c_uint64(ticket), C.byref(d)))
+        if d.value:
+            self._done[ticket] = self._live.pop(ticket)[-1]
+        return bool(d.value)
+
+    def result(self, ticket: int) -> dict:
+        return self._done[ticket]
+
+    def drain(self, tickets, max_ticks: int = 64):
+        """Run until every ticket in `tickets` is done."""
+        pending = [t for t in tickets if t not in self._done]
+        while pending:
+            self.run(max_ticks)
+            pending = [t for t in pending if not self.poll(t)]
+
+    def stats(self) -> dict:
+        st = XpbdServerStats()
+        _check(lib().xpbd_server_get_stats(self._s, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in XpbdServerStats._fields_}

@@ -1,0 +1,621 @@
+// Per-element device functions of the XPBD step and of its discrete adjoint.
+//
+// Every kernel of the library is one of these functions applied to an index range: the
+// one-request kernels (xpbd_kernels.cu) launch them over a whole color or vertex array,
+// and the batched serving kernel (xpbd_serve.cu) dispatches them from a work table.  Both
+// call exactly this code, so a request computes the same values in either path.
+//
+// Layout in HBM: vertices as float4 (x, y, z, inverse mass); constraint records of one
+// color contiguous and sorted by first vertex (coalesced gathers along grid rows);
+// multipliers lambda as float in record order; the reverse sweep's per-iteration tape
+// holds the pre-projection float4 of every vertex of every constraint, in record order.
+//
+// One thread updates one constraint of the current color: a color's constraints are
+// vertex-disjoint (Sec. 3.1, graph coloring), so the Jacobi update inside a color equals
+// the sequential Gauss-Seidel order.  The path is gather/scatter bound (no dense
+// contraction): 128-bit vertex and record accesses, streaming (evict-first) hints on
+// single-use data, evict-last on the vertex arrays that every color pass re-reads.
+#pragma once
+
+#include "xpbd_kernels.cuh"
+
+namespace xpbd {
+
+__device__ __forceinline__ f3 xyz(float4 a) { return mk3(a.x, a.y, a.z); }
+__device__ __forceinline__ float4 with_w(f3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
+
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+
+// ------------------------------------------------------------------ cache policy
+// XPBD_L2_VERTEX_HINT marks vertex traffic L2 evict-last (a fraction
+// XPBD_L2_VERTEX_FRACTION of the lines) so the streams evict it last; XPBD_REC_STREAM
+// loads records with the streaming (evict-first) hint.  Both are on by default: on the
+// 2950^2 cloth they cut the forward and replay passes by 7-13% (CUDA events per class).
+#ifndef XPBD_L2_VERTEX_HINT
+#define XPBD_L2_VERTEX_HINT 1
+#endif
+#ifndef XPBD_L2_VERTEX_FRACTION
+#define XPBD_L2_VERTEX_FRACTION 1.0
+#endif
+#ifndef XPBD_REC_STREAM
+#define XPBD_REC_STREAM 1
+#endif
+#define XPBD_STR2(x) #x
+#define XPBD_STR(x) XPBD_STR2(x)
+
+__device__ __forceinline__ uint64_t vtx_policy() {
+#if XPBD_L2_VERTEX_HINT
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, " XPBD_STR(XPBD_L2_VERTEX_FRACTION) ";" : "=l"(p));
+  return p;
+#else
+  return 0;
+#endif
+}
+
+__device__ __forceinline__ float4 ld_vtx(const float4* a, uint64_t pol) {
+#if XPBD_L2_VERTEX_HINT
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return *a;
+#endif
+}
+
+__device__ __forceinline__ void st_vtx(float4* a, float4 v, uint64_t pol) {
+#if XPBD_L2_VERTEX_HINT
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+#else
+  (void)pol;
+  *a = v;
+#endif
+}
+
+// A record of 16, 32 or 64 bytes as 128-bit loads (streaming hint when XPBD_REC_STREAM).
+template <class Rec>
+__device__ __forceinline__ Rec ld_rec(const Rec* p) {
+#if XPBD_REC_STREAM
+  static_assert(sizeof(Rec) % 16 == 0, "records are 16-byte multiples");
+  union {
+    int4 v[sizeof(Rec) / 16];
+    Rec r;
+  } u;
+  const int4* q = reinterpret_cast<const int4*>(p);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(Rec) / 16); ++k) u.v[k] = __ldcs(q + k);
+  return u.r;
+#else
+  return *p;
+#endif
+}
+
+// ------------------------------------------------------------------ deterministic reductions
+// Block-wide sum of NC doubles; thread 0 writes the block's partial sums.  The order of
+// additions depends only on the launch shape, so results are bitwise reproducible.  Every
+// thread of the block must call it.
+template <int NC>
+__device__ __forceinline__ void block_sum_store(double v[NC], double* out) {
+  __shared__ double sh[NC][kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double x = v[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[c][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double t = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) t += sh[c][w];
+      out[c] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// One block sums nblocks x ncomp partials (row-major) in a fixed order into out[0..ncomp).
+__device__ __forceinline__ void reduce_partials_block(const double* __restrict__ partials, int nblocks,
+                                                      int ncomp, double* __restrict__ out, bool accumulate) {
+  __shared__ double sh[kBlock];
+  for (int c = 0; c < ncomp; ++c) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) t += partials[ncomp * b + c];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = accumulate ? out[c] + sh[0] : sh[0];
+    __syncthreads();
+  }
+}
+
+// ======================================================================== forward
+
+__device__ __forceinline__ void init_ckpt_elem(int i, const float* __restrict__ x0, const float* __restrict__ v0,
+                                               const float* __restrict__ w, float4* __restrict__ ckx,
+                                               float4* __restrict__ ckv) {
+  ckx[i] = make_float4(x0[3 * i], x0[3 * i + 1], x0[3 * i + 2], w[i]);
+  ckv[i] = make_float4(v0[3 * i], v0[3 * i + 1], v0[3 * i + 2], 0.f);
+}
+
+// alpha~ of record i from the caller's per-constraint compliance (caller order).  A
+// compliance that is negative or not finite sets bit 1 of the error word.
+template <class Rec, bool VOL>
+__device__ __forceinline__ void set_alpha_elem(int i, Rec* __restrict__ rec, const int* __restrict__ perm,
+                                               const float* __restrict__ compliance, float inv_dt2,
+                                               int* __restrict__ err) {
+  float c = compliance[perm[i]];
+  if (!(c >= 0.f) || isinf(c)) atomicOr(err, 2);
+  float a = c * inv_dt2;
+  if constexpr (VOL) a = a / rec[i].vol;
+  rec[i].at = a;
+}
+
+// Inertial prediction (Eq. xpbdUpdateRule): p = x + dt v + dt^2 (w (G_n + W_i) + [w > 0] g),
+// and contact detection at p: a contact is active for the whole step when C(p) < 0.
+__device__ __forceinline__ void predict_elem(int i, const float4* __restrict__ ckx, const float4* __restrict__ ckv,
+                                             float4* __restrict__ P, const float* __restrict__ fg_n,
+                                             const float* __restrict__ fv, float dt, float gx, float gy,
+                                             float gz, const Collide& c, uint8_t* __restrict__ cflags) {
+  float4 x = ckx[i];
+  float4 v = ckv[i];
+  float w = x.w;
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  if (fg_n) { fx = fg_n[0]; fy = fg_n[1]; fz = fg_n[2]; }
+  if (fv) { fx += fv[3 * i]; fy += fv[3 * i + 1]; fz += fv[3 * i + 2]; }
+  float free_ = w > 0.f ? 1.f : 0.f;
+  float dt2 = dt * dt;
+  float4 p;
+  p.x = x.x + dt * v.x + dt2 * (w * fx + free_ * gx);
+  p.y = x.y + dt * v.y + dt2 * (w * fy + free_ * gy);
+  p.z = x.z + dt * v.z + dt2 * (w * fz + free_ * gz);
+  p.w = w;
+  P[i] = p;
+  if (c.flags) {
+    uint8_t f = 0;
+    if ((c.flags & 1) && (p.y - c.h - c.thick < 0.f)) f |= 1;
+    if (c.flags & 2) {
+      float dx = p.x - c.cx, dy = p.y - c.cy, dz = p.z - c.cz;
+      if (sqrtf(dx * dx + dy * dy + dz * dz) - c.r - c.thick < 0.f) f |= 2;
+    }
+    cflags[i] = f;
+  }
+}
+
+// ---- distance: C = |x_a - x_b| - L, grad_a = n = (x_a - x_b)/l, grad_b = -n.
+// lam_in and lam_out may alias (in-place forward), so they are not __restrict__.
+__device__ __forceinline__ void proj_dist_elem(int i, const DistRec* __restrict__ rec, float4* __restrict__ P,
+                                               const float* lam_in, float* lam_out, float4* __restrict__ tape) {
+  const DistRec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
+  float4 pa = ld_vtx(P + r.a, pol);
+  float4 pb = ld_vtx(P + r.b, pol);
+  if (tape) {
+    __stcs(tape + 2 * i, pa);
+    __stcs(tape + 2 * i + 1, pb);
+  }
+  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
+  f3 d = xyz(pa) - xyz(pb);
+  float l2 = dot(d, d);
+  float D = pa.w + pb.w + r.at;
+  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
+    float il = rsqrtf(l2);
+    float l = l2 * il;
+    f3 nrm = d * il;
+    float dl = (-(l - r.L) - r.at * lam) / D;
+    lam += dl;
+    f3 a = xyz(pa) + nrm * (pa.w * dl);
+    f3 b = xyz(pb) - nrm * (pb.w * dl);
+    st_vtx(P + r.a, with_w(a, pa.w), pol);
+    st_vtx(P + r.b, with_w(b, pb.w), pol);
+  }
+  __stcs(lam_out + i, lam);
+}
+
+// ---- 4-vertex constraints (bending, tet C_H, tet C_D), in relative coordinates
+// e1 = x1 - x0, e2 = x2 - x0, e3 = x3 - x0 (all three constraints are translation
+// invariant): grad_0 = -(grad_1 + grad_2 + grad_3) and (H u)_0 = -sum_k (H u)_k.
+template <int KIND>   // 1 bending, 2 hydrostatic, 3 deviatoric
+struct Quad;
+
+template <>
+struct Quad<1> {
+  typedef BendRec Rec;
+  // value and gradient (g1..g3); false if degenerate
+  __device__ static bool eval(const Rec& r, const f3& e1, const f3& e2, const f3& e3, f3& g1, f3& g2,
+                              f3& g3, float& C) {
+    if (bend_degenerate_rel(e1, e2, e3)) return false;
+    bend_grad_rel<float>(e1, e2, e3, g1, g2, g3);
+    C = bend_C_rel(e1, e2, e3, r.theta0);
+    return true;
+  }
+  // gradient (value parts) and H u (derivative parts) for relative directions du1..du3
+  __device__ static void hvp(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
+                             const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
+    bend_grad_rel<df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), g1, g2, g3);
+  }
+};
+
+template <bool HYDRO>
+struct TetQuad {
+  typedef TetRec Rec;
+  __device__ static bool eval(const Rec& r, const f3& e1, const f3& e2, const f3& e3, f3& g1, f3& g2,
+                              f3& g3, float& C) {
+    tet_grad_rel<HYDRO, float>(e1, e2, e3, r.B, g1, g2, g3, &C, r.gamma);
+    if (!HYDRO && C * C < XPBD_DEGEN2) return false;
+    return true;
+  }
+  __device__ static void hvp(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
+                             const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
+    tet_grad_rel<HYDRO, df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), r.B, g1, g2, g3, nullptr,
+                            r.gamma);
+  }
+};
+template <> struct Quad<2> : TetQuad<true> {};
+template <> struct Quad<3> : TetQuad<false> {};
+
+template <int KIND>
+__device__ __forceinline__ void proj_quad_elem(int i, const typename Quad<KIND>::Rec* __restrict__ rec,
+                                               float4* __restrict__ P, const float* lam_in, float* lam_out,
+                                               float4* __restrict__ tape) {
+  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
+  float4 p[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p[k] = ld_vtx(P + r.v[k], pol);
+  if (tape) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) __stcs(tape + 4 * i + k, p[k]);
+  }
+  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
+  const f3 x0 = xyz(p[0]);
+  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
+  f3 g1, g2, g3;
+  float C;
+  if (Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
+    const f3 g0 = -(g1 + g2 + g3);
+    float D = r.at + p[0].w * dot(g0, g0) + p[1].w * dot(g1, g1) + p[2].w * dot(g2, g2) +
+              p[3].w * dot(g3, g3);
+    if (D > 0.f) {
+      float dl = (-C - r.at * lam) / D;
+      lam += dl;
+      st_vtx(P + r.v[0], with_w(x0 + g0 * (p[0].w * dl), p[0].w), pol);
+      st_vtx(P + r.v[1], with_w(xyz(p[1]) + g1 * (p[1].w * dl), p[1].w), pol);
+      st_vtx(P + r.v[2], with_w(xyz(p[2]) + g2 * (p[2].w * dl), p[2].w), pol);
+      st_vtx(P + r.v[3], with_w(xyz(p[3]) + g3 * (p[3].w * dl), p[3].w), pol);
+    }
+  }
+  __stcs(lam_out + i, lam);
+}
+
+// ---- contacts (Sec. 4.6): plane then sphere on the same vertex, equality springs for the
+// step in which they were detected
+__device__ __forceinline__ void plane_project(f3& p, float w, float& lam, const Collide& c) {
+  float C = p.y - c.h - c.thick;
+  float D = w + c.at;
+  if (D > 0.f) {
+    float dl = (-C - c.at * lam) / D;
+    lam += dl;
+    p.y += w * dl;
+  }
+}
+
+__device__ __forceinline__ void sphere_project(f3& p, float w, float& lam, const Collide& c) {
+  f3 d = p - mk3(c.cx, c.cy, c.cz);
+  float l2 = dot(d, d);
+  float D = w + c.at;
+  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
+    float il = rsqrtf(l2);
+    float l = l2 * il;
+    f3 nrm = d * il;
+    float dl = (-(l - c.r - c.thick) - c.at * lam) / D;
+    lam += dl;
+    p = p + nrm * (w * dl);
+  }
+}
+
+__device__ __forceinline__ void contact_elem(int i, float4* __restrict__ P, const uint8_t* __restrict__ cflags,
+                                             const float2* lam_in, float2* lam_out, float4* __restrict__ tape,
+                                             const Collide& c) {
+  uint8_t f = cflags[i];
+  if (!f) return;
+  float4 p4 = P[i];
+  if (tape) __stcs(tape + i, p4);
+  float2 lam = lam_in ? lam_in[i] : make_float2(0.f, 0.f);
+  f3 p = xyz(p4);
+  if (f & 1) plane_project(p, p4.w, lam.x, c);
+  if (f & 2) sphere_project(p, p4.w, lam.y, c);
+  P[i] = with_w(p, p4.w);
+  lam_out[i] = lam;
+}
+
+// Velocity update (Eq. xpbdUpdateRule): v_{n+1} = (x_{n+1} - x_n)/dt; flags non-finite state.
+__device__ __forceinline__ void velocity_elem(int i, const float4* __restrict__ P, const float4* __restrict__ ckx_n,
+                                              float4* __restrict__ ckx_next, float4* __restrict__ ckv_next,
+                                              float inv_dt, int* __restrict__ err) {
+  float4 p = P[i];
+  float4 x = ckx_n[i];
+  float4 v = make_float4((p.x - x.x) * inv_dt, (p.y - x.y) * inv_dt, (p.z - x.z) * inv_dt, 0.f);
+  ckx_next[i] = p;
+  ckv_next[i] = v;
+  if (!isfinite(p.x + p.y + p.z + v.x + v.y + v.z)) atomicOr(err, 1);
+}
+
+// ======================================================================== reverse
+
+__device__ __forceinline__ void seed_adjoint_elem(int i, const float* __restrict__ sx, const float* __restrict__ sv,
+                                                  float4* __restrict__ xbar, float4* __restrict__ vbar) {
+  xbar[i] = sx ? make_float4(sx[3 * i], sx[3 * i + 1], sx[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  vbar[i] = sv ? make_float4(sv[3 * i], sv[3 * i + 1], sv[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Adjoint of v_{n+1} = (p - x_n)/dt, x_{n+1} = p:  pbar = xbar + vbar/dt, xbar_n = -vbar/dt.
+// In place: xbar <- pbar, vbar <- the partial xbar_n.
+__device__ __forceinline__ void adj_begin_elem(int i, float4* __restrict__ xbar, float4* __restrict__ vbar,
+                                               float inv_dt) {
+  float4 xb = xbar[i], vb = vbar[i];
+  xbar[i] = make_float4(xb.x + vb.x * inv_dt, xb.y + vb.y * inv_dt, xb.z + vb.z * inv_dt, 0.f);
+  vbar[i] = make_float4(-vb.x * inv_dt, -vb.y * inv_dt, -vb.z * inv_dt, 0.f);
+}
+
+// Reverse of one XPBD update.  With the pre-projection state from the tape, g = grad C,
+// D = sum w|g|^2 + alpha~, dlambda = (-C - alpha~ lambda)/D recomputed, and the adjoints
+// xbar', lambar' of the updated values:
+//   s = lambar' + sum_i w_i g_i . xbar'_i                 (adjoint of dlambda)
+//   u_i = dlambda w_i xbar'_i - 2 (s dlambda / D) w_i g_i (adjoint of g_i)
+//   xbar_i = xbar'_i - (s/D) g_i + (H u)_i,  lambar = lambar' - (alpha~/D) s,
+//   alphabar~ += -s (lambda + dlambda) / D.
+// These are the terms of Sec. 4.4 (J = D, dJ/dx dlambda, db/dx = -grad C - alpha~ ...)
+// applied in reverse mode to the sequence of single-constraint updates.  `first`: the
+// first reverse iteration of a step (lambar', alphabar' start at 0); `last`: fold the step's
+// alphabar into the float64 accumulator.
+__device__ __forceinline__ void lb_finish(int i, float lambar, float abar, float2* __restrict__ lb,
+                                          double* __restrict__ acc, bool last) {
+  if (last)
+    acc[i] += (double)abar;
+  else
+    lb[i] = make_float2(lambar, abar);
+}
+
+__device__ __forceinline__ void vjp_dist_elem(int i, const DistRec* __restrict__ rec, const float4* __restrict__ tape,
+                                              const float* __restrict__ lam_pre, float4* __restrict__ xbar,
+                                              float2* __restrict__ lb, double* __restrict__ acc, bool first,
+                                              bool last) {
+  const DistRec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
+  float4 pa = ld_stream(tape + 2 * i), pb = ld_stream(tape + 2 * i + 1);
+  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  f3 d = xyz(pa) - xyz(pb);
+  float l2 = dot(d, d);
+  float D = pa.w + pb.w + r.at;
+  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
+    float il = rsqrtf(l2);
+    float len = l2 * il;
+    f3 nrm = d * il;
+    float dl = (-(len - r.L) - r.at * lam) / D;
+    float4 xa4 = ld_vtx(xbar + r.a, pol), xb4 = ld_vtx(xbar + r.b, pol);
+    f3 xa = xyz(xa4), xb = xyz(xb4);
+    float s = l.x + pa.w * dot(nrm, xa) - pb.w * dot(nrm, xb);
+    // H u for the distance constraint: (P (u_a - u_b))/l on a, the negative on b, with
+    // P = I - n n^T; the n-parallel part of u drops out.
+    f3 t = (xa * pa.w - xb * pb.w) * dl;
+    f3 hv = (t - nrm * dot(nrm, t)) * il;
+    float sD = s / D;
+    xa = xa - nrm * sD + hv;
+    xb = xb + nrm * sD - hv;
+    st_vtx(xbar + r.a, with_w(xa, 0.f), pol);
+    st_vtx(xbar + r.b, with_w(xb, 0.f), pol);
+    l.y += -sD * (lam + dl);
+    l.x -= r.at * sD;
+  }
+  lb_finish(i, l.x, l.y, lb, acc, last);
+}
+
+template <int KIND>
+__device__ __forceinline__ void vjp_quad_elem(int i, const typename Quad<KIND>::Rec* __restrict__ rec,
+                                              const float4* __restrict__ tape, const float* __restrict__ lam_pre,
+                                              float4* __restrict__ xbar, float2* __restrict__ lb,
+                                              double* __restrict__ acc, bool first, bool last) {
+  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
+  const uint64_t pol = vtx_policy();
+  // every global read is independent of the arithmetic: issue them all first
+  float4 p[4], xb4[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p[k] = ld_stream(tape + 4 * i + k);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) xb4[k] = ld_vtx(xbar + r.v[k], pol);
+  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  const f3 x0 = xyz(p[0]);
+  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
+  f3 g1, g2, g3;
+  float C;
+  if (Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
+    const f3 g0 = -(g1 + g2 + g3);
+    const float w0 = p[0].w, w1 = p[1].w, w2 = p[2].w, w3 = p[3].w;
+    float D = r.at + w0 * dot(g0, g0) + w1 * dot(g1, g1) + w2 * dot(g2, g2) + w3 * dot(g3, g3);
+    if (D > 0.f) {
+      float dl = (-C - r.at * lam) / D;
+      const f3 xb0 = xyz(xb4[0]), xb1 = xyz(xb4[1]), xb2 = xyz(xb4[2]), xb3 = xyz(xb4[3]);
+      float s = l.x + w0 * dot(g0, xb0) + w1 * dot(g1, xb1) + w2 * dot(g2, xb2) + w3 * dot(g3, xb3);
+      float sD = s / D;
+      float c2 = 2.f * sD * dl;
+      const f3 u0 = (xb0 * dl - g0 * c2) * w0;
+      const f3 du1 = (xb1 * dl - g1 * c2) * w1 - u0;
+      const f3 du2 = (xb2 * dl - g2 * c2) * w2 - u0;
+      const f3 du3 = (xb3 * dl - g3 * c2) * w3 - u0;
+      d3 h1, h2, h3;
+      Quad<KIND>::hvp(r, e1, e2, e3, du1, du2, du3, h1, h2, h3);
+      const f3 hu1 = dpart(h1), hu2 = dpart(h2), hu3 = dpart(h3);
+      const f3 hu0 = -(hu1 + hu2 + hu3);
+      st_vtx(xbar + r.v[0], with_w(xb0 - g0 * sD + hu0, 0.f), pol);
+      st_vtx(xbar + r.v[1], with_w(xb1 - g1 * sD + hu1, 0.f), pol);
+      st_vtx(xbar + r.v[2], with_w(xb2 - g2 * sD + hu2, 0.f), pol);
+      st_vtx(xbar + r.v[3], with_w(xb3 - g3 * sD + hu3, 0.f), pol);
+      l.y += -sD * (lam + dl);
+      l.x -= r.at * sD;
+    }
+  }
+  lb_finish(i, l.x, l.y, lb, acc, last);
+}
+
+// Reverse of the collision pass.  Plane (inputs p, h; grad_p = e_y, grad_h = -1, H = 0) and
+// sphere (inputs p, c, r; grad_p = n, grad_c = -n, grad_r = -1, H_pp = P/l, H_pc = -P/l;
+// the centre and radius are not moved, so u_c = 0).  Collider adjoints accumulate in the
+// per-vertex float32 scratch cgrad = (hbar, cbar_x, cbar_y, cbar_z, rbar) over the step.
+__device__ __forceinline__ void vjp_contact_elem(int i, const float4* __restrict__ tape,
+                                                 const uint8_t* __restrict__ cflags, const float2* __restrict__ lam_pre,
+                                                 float4* __restrict__ xbar, float2* __restrict__ lbc,
+                                                 float* __restrict__ cgrad, bool first, const Collide& c) {
+  uint8_t f = cflags[i];
+  if (!f) return;
+  float4 p4 = tape[i];
+  float w = p4.w;
+  float2 lam = lam_pre ? lam_pre[i] : make_float2(0.f, 0.f);
+  float2 lb = first ? make_float2(0.f, 0.f) : lbc[i];
+  float cg[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (cgrad && !first)
+    for (int k = 0; k < 5; ++k) cg[k] = cgrad[5 * i + k];
+  f3 xb = xyz(xbar[i]);
+  f3 pre = xyz(p4);
+  f3 mid = pre;
+  if ((f & 1) && (f & 2)) {
+    float lp = lam.x;
+    plane_project(mid, w, lp, c);
+  }
+  float D = w + c.at;
+  if ((f & 2) && D > 0.f) {
+    f3 d = mid - mk3(c.cx, c.cy, c.cz);
+    float l2 = dot(d, d);
+    if (l2 >= XPBD_DEGEN2) {
+      float il = rsqrtf(l2);
+      float len = l2 * il;
+      f3 nrm = d * il;
+      float dl = (-(len - c.r - c.thick) - c.at * lam.y) / D;
+      float s = lb.y + w * dot(nrm, xb);
+      float sD = s / D;
+      f3 t = xb * (w * dl);
+      f3 hv = (t - nrm * dot(nrm, t)) * il;
+      xb = xb - nrm * sD + hv;
+      // centre: -(s/D) grad_c + (H u)_c = (s/D) n - hv ; radius: -(s/D) grad_r = s/D
+      cg[1] += nrm.x * sD - hv.x;
+      cg[2] += nrm.y * sD - hv.y;
+      cg[3] += nrm.z * sD - hv.z;
+      cg[4] += sD;
+      lb.y -= c.at * sD;
+    }
+  }
+  if ((f & 1) && D > 0.f) {
+    float s = lb.x + w * xb.y;
+    float sD = s / D;
+    xb.y -= sD;
+    cg[0] += sD;
+    lb.x -= c.at * sD;
+  }
+  xbar[i] = with_w(xb, 0.f);
+  lbc[i] = lb;
+  if (cgrad)
+    for (int k = 0; k < 5; ++k) cgrad[5 * i + k] = cg[k];
+}
+
+// Per-vertex collider adjoints of this step (contact vertices only: cgrad of the other
+// vertices is stale), added to v.
+__device__ __forceinline__ void collider_contrib(int i, const float* __restrict__ cgrad,
+                                                 const uint8_t* __restrict__ cflags, double v[5]) {
+  if (cflags[i])
+    for (int k = 0; k < 5; ++k) v[k] += (double)cgrad[5 * i + k];
+}
+
+// Adjoint of the prediction p = x_n + dt v_n + dt^2 (w (G_n + W_i) + [w>0] g):
+//   xbar_n = xbar_partial + pbar (+ dL/dx_n seed),  vbar_n = dt pbar,
+//   fbar_i = dt^2 w_i pbar_i  (Sec. 5.6: force gradients from the adjoint velocities),
+//   dL/dW_i += fbar_i (float64); fbar_i is added to fs for dL/dG_n.
+__device__ __forceinline__ void adj_predict_elem(int i, float4* __restrict__ xbar, float4* __restrict__ vbar,
+                                                 const float4* __restrict__ ckx_n, const float* __restrict__ seed,
+                                                 float dt, double* __restrict__ fv_acc, double fs[3]) {
+  float dt2 = dt * dt;
+  float4 pb = xbar[i];
+  float4 xp = vbar[i];
+  float w = ckx_n[i].w;
+  float4 xn = make_float4(xp.x + pb.x, xp.y + pb.y, xp.z + pb.z, 0.f);
+  if (seed) {
+    xn.x += seed[3 * i];
+    xn.y += seed[3 * i + 1];
+    xn.z += seed[3 * i + 2];
+  }
+  xbar[i] = xn;
+  vbar[i] = make_float4(dt * pb.x, dt * pb.y, dt * pb.z, 0.f);
+  double fx = (double)(dt2 * w) * (double)pb.x;
+  double fy = (double)(dt2 * w) * (double)pb.y;
+  double fz = (double)(dt2 * w) * (double)pb.z;
+  if (fv_acc) {
+    fv_acc[3 * i] += fx;
+    fv_acc[3 * i + 1] += fy;
+    fv_acc[3 * i + 2] += fz;
+  }
+  fs[0] += fx;
+  fs[1] += fy;
+  fs[2] += fz;
+}
+
+// dL/d compliance in the caller's constraint order: alpha~ = compliance / dt^2 (tets:
+// / (V_e dt^2)), so dL/dcompliance = alphabar~ / dt^2 (/ V_e).
+template <class Rec, bool VOL>
+__device__ __forceinline__ void finalize_elem(int i, const Rec* __restrict__ rec, const int* __restrict__ perm,
+                                              const double* __restrict__ acc, float inv_dt2,
+                                              double* __restrict__ out) {
+  double a = acc[i] * (double)inv_dt2;
+  if constexpr (VOL) a = a / (double)rec[i].vol;
+  out[perm[i]] = a;
+}
+
+__device__ __forceinline__ void to_double_elem(int i, const float4* __restrict__ a, double* __restrict__ out) {
+  float4 v = a[i];
+  out[3 * i] = v.x;
+  out[3 * i + 1] = v.y;
+  out[3 * i + 2] = v.z;
+}
+
+// Goal function of Sec. 4.1 on one keyframe: seed = x - x*, accumulates |x - x*|^2 / 2.
+__device__ __forceinline__ void loss_elem(int i, const float4* __restrict__ ckx, const float* __restrict__ target,
+                                          float* __restrict__ seed_out, double& acc) {
+  float4 x = ckx[i];
+  float dx = x.x - target[3 * i], dy = x.y - target[3 * i + 1], dz = x.z - target[3 * i + 2];
+  if (seed_out) {
+    seed_out[3 * i] = dx;
+    seed_out[3 * i + 1] = dy;
+    seed_out[3 * i + 2] = dz;
+  }
+  acc += 0.5 * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
+}
+
+__device__ __forceinline__ void read_state_elem(int i, const float4* __restrict__ ckx, const float4* __restrict__ ckv,
+                                                float* __restrict__ x_out, float* __restrict__ v_out) {
+  if (x_out) {
+    float4 x = ckx[i];
+    x_out[3 * i] = x.x;
+    x_out[3 * i + 1] = x.y;
+    x_out[3 * i + 2] = x.z;
+  }
+  if (v_out) {
+    float4 v = ckv[i];
+    v_out[3 * i] = v.x;
+    v_out[3 * i + 1] = v.y;
+    v_out[3 * i + 2] = v.z;
+  }
+}
+
+}  // namespace xpbd

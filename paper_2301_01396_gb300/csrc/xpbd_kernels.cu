@@ -1,126 +1,19 @@
-// sm_103a kernels of the XPBD step (Sec. 3.1 of DiffXPBD) and of its discrete adjoint.
-//
-// Layout in HBM: vertices as float4 (x, y, z, inverse mass); constraint records of one
-// color contiguous and sorted by first vertex (coalesced gathers along grid rows);
-// multipliers lambda as float in record order; the adjoint's per-iteration tape holds the
-// pre-projection float4 of every vertex of every constraint, in record order.
-//
-// One thread updates one constraint of the current color: the color's constraints are
-// vertex-disjoint (Sec. 3.1, graph coloring), so the Jacobi update inside a color equals
-// the sequential Gauss-Seidel order.  The path is gather/scatter bound (no dense
-// contraction), so the kernels are written for HBM traffic: 128-bit vertex and record
-// accesses, streaming (evict-first) hints on single-use tape/multiplier data.
-#include "xpbd_kernels.cuh"
+// sm_103a kernels of the XPBD step (Sec. 3.1 of DiffXPBD) and of its discrete adjoint for
+// one request: each kernel applies one element function of xpbd_elems.cuh to a whole
+// color (one thread per constraint) or to every vertex.
+#include "xpbd_elems.cuh"
 
 namespace xpbd {
 
 namespace {
 
-__device__ __forceinline__ f3 xyz(float4 a) { return mk3(a.x, a.y, a.z); }
-__device__ __forceinline__ float4 with_w(f3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
-
-__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
-__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
-__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
-
 inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
 
-// ------------------------------------------------------------------ cache policy
-// Vertex positions and vertex adjoints are re-read by every color pass of an iteration;
-// records, multipliers and tapes are streamed once per pass.  XPBD_L2_VERTEX_HINT marks
-// vertex traffic L2 evict-last (a fraction XPBD_L2_VERTEX_FRACTION of the lines) so the
-// streams evict it last; XPBD_REC_STREAM loads records with the streaming (evict-first)
-// hint.  Both are on by default: on the 2950^2 cloth they cut the forward and replay
-// passes by 7-13% (measured with CUDA events per kernel class).
-#ifndef XPBD_L2_VERTEX_HINT
-#define XPBD_L2_VERTEX_HINT 1
-#endif
-#ifndef XPBD_L2_VERTEX_FRACTION
-#define XPBD_L2_VERTEX_FRACTION 1.0
-#endif
-#ifndef XPBD_REC_STREAM
-#define XPBD_REC_STREAM 1
-#endif
-#define XPBD_STR2(x) #x
-#define XPBD_STR(x) XPBD_STR2(x)
-
-__device__ __forceinline__ uint64_t vtx_policy() {
-#if XPBD_L2_VERTEX_HINT
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, " XPBD_STR(XPBD_L2_VERTEX_FRACTION) ";" : "=l"(p));
-  return p;
-#else
-  return 0;
-#endif
-}
-
-__device__ __forceinline__ float4 ld_vtx(const float4* a, uint64_t pol) {
-#if XPBD_L2_VERTEX_HINT
-  float4 v;
-  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(a), "l"(pol));
-  return v;
-#else
-  (void)pol;
-  return *a;
-#endif
-}
-
-__device__ __forceinline__ void st_vtx(float4* a, float4 v, uint64_t pol) {
-#if XPBD_L2_VERTEX_HINT
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w), "l"(pol)
-               : "memory");
-#else
-  (void)pol;
-  *a = v;
-#endif
-}
-
-// A record of 16, 32 or 64 bytes as 128-bit loads (streaming hint when XPBD_REC_STREAM).
-template <class Rec>
-__device__ __forceinline__ Rec ld_rec(const Rec* p) {
-#if XPBD_REC_STREAM
-  static_assert(sizeof(Rec) % 16 == 0, "records are 16-byte multiples");
-  union {
-    int4 v[sizeof(Rec) / 16];
-    Rec r;
-  } u;
-  const int4* q = reinterpret_cast<const int4*>(p);
-#pragma unroll
-  for (int k = 0; k < (int)(sizeof(Rec) / 16); ++k) u.v[k] = __ldcs(q + k);
-  return u.r;
-#else
-  return *p;
-#endif
-}
-
-// ------------------------------------------------------------------ deterministic reductions
-// Block-wide sum of NC doubles; thread 0 writes the block's partial sums.  The order of
-// additions depends only on the launch shape, so results are bitwise reproducible.
-template <int NC>
-__device__ void block_sum_store(double v[NC], double* out) {
-  __shared__ double sh[NC][kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    double x = v[c];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[c][warp] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      double t = 0.0;
-      for (int w = 0; w < kBlock / 32; ++w) t += sh[c][w];
-      out[c] = t;
-    }
-  }
-}
-
 constexpr int kMaxPartialBlocks = 1024;
+
+#define XPBD_TID_OR_RETURN(n)                          \
+  const int i = blockIdx.x * blockDim.x + threadIdx.x; \
+  if (i >= (n)) return
 
 }  // namespace
 
@@ -134,10 +27,8 @@ int partial_blocks(int V) {
 __global__ void k_init_ckpt(const float* __restrict__ x0, const float* __restrict__ v0,
                             const float* __restrict__ w, float4* __restrict__ ckx,
                             float4* __restrict__ ckv, int V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  ckx[i] = make_float4(x0[3 * i], x0[3 * i + 1], x0[3 * i + 2], w[i]);
-  ckv[i] = make_float4(v0[3 * i], v0[3 * i + 1], v0[3 * i + 2], 0.f);
+  XPBD_TID_OR_RETURN(V);
+  init_ckpt_elem(i, x0, v0, w, ckx, ckv);
 }
 
 void launch_init_ckpt(const float* x0, const float* v0, const float* w, float4* ckx, float4* ckv,
@@ -145,18 +36,11 @@ void launch_init_ckpt(const float* x0, const float* v0, const float* w, float4* 
   if (V > 0) k_init_ckpt<<<grid_for(V), kBlock, 0, s>>>(x0, v0, w, ckx, ckv, V);
 }
 
-// alpha~ of every record from the caller's per-constraint compliance (caller order).  A
-// compliance that is negative or not finite sets bit 1 of the error word.
 template <class Rec, bool VOL>
 __global__ void k_set_alpha(Rec* __restrict__ rec, const int* __restrict__ perm, int n,
                             const float* __restrict__ compliance, float inv_dt2, int* __restrict__ err) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float c = compliance[perm[i]];
-  if (!(c >= 0.f) || isinf(c)) atomicOr(err, 2);
-  float a = c * inv_dt2;
-  if constexpr (VOL) a = a / rec[i].vol;
-  rec[i].at = a;
+  XPBD_TID_OR_RETURN(n);
+  set_alpha_elem<Rec, VOL>(i, rec, perm, compliance, inv_dt2, err);
 }
 
 void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float* compliance,
@@ -174,37 +58,12 @@ void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float*
   }
 }
 
-// Inertial prediction (Eq. xpbdUpdateRule): p = x + dt v + dt^2 (w (G_n + W_i) + [w > 0] g),
-// and contact detection at p: a contact is active for the whole step when C(p) < 0.
 __global__ void k_predict(const float4* __restrict__ ckx, const float4* __restrict__ ckv,
                           float4* __restrict__ P, const float* __restrict__ fg_n,
                           const float* __restrict__ fv, float dt, float gx, float gy, float gz,
                           Collide c, uint8_t* __restrict__ cflags, int V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  float4 x = ckx[i];
-  float4 v = ckv[i];
-  float w = x.w;
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  if (fg_n) { fx = fg_n[0]; fy = fg_n[1]; fz = fg_n[2]; }
-  if (fv) { fx += fv[3 * i]; fy += fv[3 * i + 1]; fz += fv[3 * i + 2]; }
-  float free_ = w > 0.f ? 1.f : 0.f;
-  float dt2 = dt * dt;
-  float4 p;
-  p.x = x.x + dt * v.x + dt2 * (w * fx + free_ * gx);
-  p.y = x.y + dt * v.y + dt2 * (w * fy + free_ * gy);
-  p.z = x.z + dt * v.z + dt2 * (w * fz + free_ * gz);
-  p.w = w;
-  P[i] = p;
-  if (c.flags) {
-    uint8_t f = 0;
-    if ((c.flags & 1) && (p.y - c.h - c.thick < 0.f)) f |= 1;
-    if (c.flags & 2) {
-      float dx = p.x - c.cx, dy = p.y - c.cy, dz = p.z - c.cz;
-      if (sqrtf(dx * dx + dy * dy + dz * dz) - c.r - c.thick < 0.f) f |= 2;
-    }
-    cflags[i] = f;
-  }
+  XPBD_TID_OR_RETURN(V);
+  predict_elem(i, ckx, ckv, P, fg_n, fv, dt, gx, gy, gz, c, cflags);
 }
 
 void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float* fg_n,
@@ -214,118 +73,21 @@ void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float
     k_predict<<<grid_for(V), kBlock, 0, s>>>(ckx, ckv, P, fg_n, fv, dt, gx, gy, gz, c, cflags, V);
 }
 
-// ---- distance: C = |x_a - x_b| - L, grad_a = n = (x_a - x_b)/l, grad_b = -n
-// lam_in and lam_out may alias (in-place forward), so they are not __restrict__.
 __global__ void k_proj_dist(const DistRec* __restrict__ rec, int n, float4* __restrict__ P,
                             const float* lam_in, float* lam_out, float4* __restrict__ tape) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const DistRec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  float4 pa = ld_vtx(P + r.a, pol);
-  float4 pb = ld_vtx(P + r.b, pol);
-  if (tape) {
-    __stcs(tape + 2 * i, pa);
-    __stcs(tape + 2 * i + 1, pb);
-  }
-  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
-  f3 d = xyz(pa) - xyz(pb);
-  float l2 = dot(d, d);
-  float D = pa.w + pb.w + r.at;
-  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
-    float il = rsqrtf(l2);
-    float l = l2 * il;
-    f3 nrm = d * il;
-    float dl = (-(l - r.L) - r.at * lam) / D;
-    lam += dl;
-    f3 a = xyz(pa) + nrm * (pa.w * dl);
-    f3 b = xyz(pb) - nrm * (pb.w * dl);
-    st_vtx(P + r.a, with_w(a, pa.w), pol);
-    st_vtx(P + r.b, with_w(b, pb.w), pol);
-  }
-  __stcs(lam_out + i, lam);
+  XPBD_TID_OR_RETURN(n);
+  proj_dist_elem(i, rec, P, lam_in, lam_out, tape);
 }
-
-// ---- 4-vertex constraints (bending, tet C_H, tet C_D), in relative coordinates
-// e1 = x1 - x0, e2 = x2 - x0, e3 = x3 - x0 (all three constraints are translation
-// invariant): grad_0 = -(grad_1 + grad_2 + grad_3) and (H u)_0 = -sum_k (H u)_k.
-template <int KIND>   // 1 bending, 2 hydrostatic, 3 deviatoric
-struct Quad;
-
-template <>
-struct Quad<1> {
-  typedef BendRec Rec;
-  // value and gradient (g1..g3); false if degenerate
-  __device__ static bool eval(const Rec& r, const f3& e1, const f3& e2, const f3& e3, f3& g1, f3& g2,
-                              f3& g3, float& C) {
-    if (bend_degenerate_rel(e1, e2, e3)) return false;
-    bend_grad_rel<float>(e1, e2, e3, g1, g2, g3);
-    C = bend_C_rel(e1, e2, e3, r.theta0);
-    return true;
-  }
-  // gradient (value parts) and H u (derivative parts) for relative directions du1..du3
-  __device__ static void hvp(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
-                             const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
-    bend_grad_rel<df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), g1, g2, g3);
-  }
-};
-
-template <bool HYDRO>
-struct TetQuad {
-  typedef TetRec Rec;
-  __device__ static bool eval(const Rec& r, const f3& e1, const f3& e2, const f3& e3, f3& g1, f3& g2,
-                              f3& g3, float& C) {
-    tet_grad_rel<HYDRO, float>(e1, e2, e3, r.B, g1, g2, g3, &C, r.gamma);
-    if (!HYDRO && C * C < XPBD_DEGEN2) return false;
-    return true;
-  }
-  __device__ static void hvp(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
-                             const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
-    tet_grad_rel<HYDRO, df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), r.B, g1, g2, g3, nullptr,
-                            r.gamma);
-  }
-};
-template <> struct Quad<2> : TetQuad<true> {};
-template <> struct Quad<3> : TetQuad<false> {};
 
 #ifndef XPBD_PROJ_QUAD_MIN_BLOCKS
 #define XPBD_PROJ_QUAD_MIN_BLOCKS 1
 #endif
 template <int KIND>
 __global__ void __launch_bounds__(kBlock, XPBD_PROJ_QUAD_MIN_BLOCKS)
-k_proj_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
-                            float4* __restrict__ P, const float* lam_in, float* lam_out,
-                            float4* __restrict__ tape) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  float4 p[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) p[k] = ld_vtx(P + r.v[k], pol);
-  if (tape) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) __stcs(tape + 4 * i + k, p[k]);
-  }
-  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
-  const f3 x0 = xyz(p[0]);
-  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
-  f3 g1, g2, g3;
-  float C;
-  if (Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
-    const f3 g0 = -(g1 + g2 + g3);
-    float D = r.at + p[0].w * dot(g0, g0) + p[1].w * dot(g1, g1) + p[2].w * dot(g2, g2) +
-              p[3].w * dot(g3, g3);
-    if (D > 0.f) {
-      float dl = (-C - r.at * lam) / D;
-      lam += dl;
-      st_vtx(P + r.v[0], with_w(x0 + g0 * (p[0].w * dl), p[0].w), pol);
-      st_vtx(P + r.v[1], with_w(xyz(p[1]) + g1 * (p[1].w * dl), p[1].w), pol);
-      st_vtx(P + r.v[2], with_w(xyz(p[2]) + g2 * (p[2].w * dl), p[2].w), pol);
-      st_vtx(P + r.v[3], with_w(xyz(p[3]) + g3 * (p[3].w * dl), p[3].w), pol);
-    }
-  }
-  __stcs(lam_out + i, lam);
+k_proj_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n, float4* __restrict__ P,
+            const float* lam_in, float* lam_out, float4* __restrict__ tape) {
+  XPBD_TID_OR_RETURN(n);
+  proj_quad_elem<KIND>(i, rec, P, lam_in, lam_out, tape);
 }
 
 void launch_project(SegType t, const void* rec, int n, float4* P, const float* lam_in,
@@ -347,47 +109,10 @@ void launch_project(SegType t, const void* rec, int n, float4* P, const float* l
   }
 }
 
-// ---- contacts (Sec. 4.6): plane then sphere on the same vertex, equality springs for the
-// step in which they were detected
-__device__ __forceinline__ void plane_project(f3& p, float w, float& lam, const Collide& c) {
-  float C = p.y - c.h - c.thick;
-  float D = w + c.at;
-  if (D > 0.f) {
-    float dl = (-C - c.at * lam) / D;
-    lam += dl;
-    p.y += w * dl;
-  }
-}
-
-__device__ __forceinline__ void sphere_project(f3& p, float w, float& lam, const Collide& c) {
-  f3 d = p - mk3(c.cx, c.cy, c.cz);
-  float l2 = dot(d, d);
-  float D = w + c.at;
-  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
-    float il = rsqrtf(l2);
-    float l = l2 * il;
-    f3 nrm = d * il;
-    float dl = (-(l - c.r - c.thick) - c.at * lam) / D;
-    lam += dl;
-    p = p + nrm * (w * dl);
-  }
-}
-
 __global__ void k_contact(float4* __restrict__ P, const uint8_t* __restrict__ cflags, int V,
-                          const float2* lam_in, float2* lam_out, float4* __restrict__ tape,
-                          Collide c) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  uint8_t f = cflags[i];
-  if (!f) return;
-  float4 p4 = P[i];
-  if (tape) __stcs(tape + i, p4);
-  float2 lam = lam_in ? lam_in[i] : make_float2(0.f, 0.f);
-  f3 p = xyz(p4);
-  if (f & 1) plane_project(p, p4.w, lam.x, c);
-  if (f & 2) sphere_project(p, p4.w, lam.y, c);
-  P[i] = with_w(p, p4.w);
-  lam_out[i] = lam;
+                          const float2* lam_in, float2* lam_out, float4* __restrict__ tape, Collide c) {
+  XPBD_TID_OR_RETURN(V);
+  contact_elem(i, P, cflags, lam_in, lam_out, tape, c);
 }
 
 void launch_contact(float4* P, const uint8_t* cflags, int V, const float2* lam_in,
@@ -395,18 +120,11 @@ void launch_contact(float4* P, const uint8_t* cflags, int V, const float2* lam_i
   if (V > 0 && c.flags) k_contact<<<grid_for(V), kBlock, 0, s>>>(P, cflags, V, lam_in, lam_out, tape, c);
 }
 
-// Velocity update (Eq. xpbdUpdateRule): v_{n+1} = (x_{n+1} - x_n)/dt; flags non-finite state.
 __global__ void k_velocity(const float4* __restrict__ P, const float4* __restrict__ ckx_n,
                            float4* __restrict__ ckx_next, float4* __restrict__ ckv_next,
                            float inv_dt, int V, int* __restrict__ err) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  float4 p = P[i];
-  float4 x = ckx_n[i];
-  float4 v = make_float4((p.x - x.x) * inv_dt, (p.y - x.y) * inv_dt, (p.z - x.z) * inv_dt, 0.f);
-  ckx_next[i] = p;
-  ckv_next[i] = v;
-  if (!isfinite(p.x + p.y + p.z + v.x + v.y + v.z)) atomicOr(err, 1);
+  XPBD_TID_OR_RETURN(V);
+  velocity_elem(i, P, ckx_n, ckx_next, ckv_next, inv_dt, err);
 }
 
 void launch_velocity(const float4* P, const float4* ckx_n, float4* ckx_next, float4* ckv_next,
@@ -418,10 +136,8 @@ void launch_velocity(const float4* P, const float4* ckx_n, float4* ckx_next, flo
 
 __global__ void k_seed_adjoint(const float* __restrict__ sx, const float* __restrict__ sv,
                                float4* __restrict__ xbar, float4* __restrict__ vbar, int V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  xbar[i] = sx ? make_float4(sx[3 * i], sx[3 * i + 1], sx[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-  vbar[i] = sv ? make_float4(sv[3 * i], sv[3 * i + 1], sv[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  XPBD_TID_OR_RETURN(V);
+  seed_adjoint_elem(i, sx, sv, xbar, vbar);
 }
 
 void launch_seed_adjoint(const float* seed_x, const float* seed_v, float4* xbar, float4* vbar,
@@ -429,128 +145,35 @@ void launch_seed_adjoint(const float* seed_x, const float* seed_v, float4* xbar,
   if (V > 0) k_seed_adjoint<<<grid_for(V), kBlock, 0, s>>>(seed_x, seed_v, xbar, vbar, V);
 }
 
-// Adjoint of v_{n+1} = (p - x_n)/dt, x_{n+1} = p:  pbar = xbar + vbar/dt, xbar_n = -vbar/dt.
-// In place: xbar <- pbar, vbar <- the partial xbar_n.
 __global__ void k_adj_begin(float4* __restrict__ xbar, float4* __restrict__ vbar, float inv_dt, int V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  float4 xb = xbar[i], vb = vbar[i];
-  xbar[i] = make_float4(xb.x + vb.x * inv_dt, xb.y + vb.y * inv_dt, xb.z + vb.z * inv_dt, 0.f);
-  vbar[i] = make_float4(-vb.x * inv_dt, -vb.y * inv_dt, -vb.z * inv_dt, 0.f);
+  XPBD_TID_OR_RETURN(V);
+  adj_begin_elem(i, xbar, vbar, inv_dt);
 }
 
 void launch_adj_begin(float4* xbar, float4* vbar, float inv_dt, int V, cudaStream_t s) {
   if (V > 0) k_adj_begin<<<grid_for(V), kBlock, 0, s>>>(xbar, vbar, inv_dt, V);
 }
 
-// Reverse of one XPBD update.  With the pre-projection state from the tape, g = grad C,
-// D = sum w|g|^2 + alpha~, dlambda = (-C - alpha~ lambda)/D recomputed, and the adjoints
-// xbar', lambar' of the updated values:
-//   s = lambar' + sum_i w_i g_i . xbar'_i                 (adjoint of dlambda)
-//   u_i = dlambda w_i xbar'_i - 2 (s dlambda / D) w_i g_i (adjoint of g_i)
-//   xbar_i = xbar'_i - (s/D) g_i + (H u)_i,  lambar = lambar' - (alpha~/D) s,
-//   alphabar~ += -s (lambda + dlambda) / D.
-// These are the terms of Sec. 4.4 (J = D, dJ/dx dlambda, db/dx = -grad C - alpha~ ...)
-// applied in reverse mode to the sequence of single-constraint updates.
-__device__ __forceinline__ void lb_finish(int i, float lambar, float abar, float2* lb, double* acc,
-                                          bool last) {
-  if (last)
-    acc[i] += (double)abar;
-  else
-    lb[i] = make_float2(lambar, abar);
-}
-
 __global__ void k_vjp_dist(const DistRec* __restrict__ rec, int n, const float4* __restrict__ tape,
                            const float* __restrict__ lam_pre, float4* __restrict__ xbar,
                            float2* __restrict__ lb, double* __restrict__ acc, bool first, bool last) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const DistRec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  float4 pa = ld_stream(tape + 2 * i), pb = ld_stream(tape + 2 * i + 1);
-  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
-  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
-  f3 d = xyz(pa) - xyz(pb);
-  float l2 = dot(d, d);
-  float D = pa.w + pb.w + r.at;
-  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
-    float il = rsqrtf(l2);
-    float len = l2 * il;
-    f3 nrm = d * il;
-    float dl = (-(len - r.L) - r.at * lam) / D;
-    float4 xa4 = ld_vtx(xbar + r.a, pol), xb4 = ld_vtx(xbar + r.b, pol);
-    f3 xa = xyz(xa4), xb = xyz(xb4);
-    float s = l.x + pa.w * dot(nrm, xa) - pb.w * dot(nrm, xb);
-    // H u for the distance constraint: (P (u_a - u_b))/l on a, the negative on b, with
-    // P = I - n n^T; the n-parallel part of u drops out.
-    f3 t = (xa * pa.w - xb * pb.w) * dl;
-    f3 hv = (t - nrm * dot(nrm, t)) * il;
-    float sD = s / D;
-    xa = xa - nrm * sD + hv;
-    xb = xb + nrm * sD - hv;
-    st_vtx(xbar + r.a, with_w(xa, 0.f), pol);
-    st_vtx(xbar + r.b, with_w(xb, 0.f), pol);
-    l.y += -sD * (lam + dl);
-    l.x -= r.at * sD;
-  }
-  lb_finish(i, l.x, l.y, lb, acc, last);
+  XPBD_TID_OR_RETURN(n);
+  vjp_dist_elem(i, rec, tape, lam_pre, xbar, lb, acc, first, last);
 }
 
 // 3 resident blocks of 256 threads for the 4-vertex reverse passes (<= 85 registers; the
-// compiler spills 32-48 bytes): 11% faster than 2 blocks at 96-107 registers on the
+// compiler spills 24-48 bytes): 11% faster than 2 blocks at 96-107 registers on the
 // bending reverse pass.
 #ifndef XPBD_VJP_QUAD_MIN_BLOCKS
 #define XPBD_VJP_QUAD_MIN_BLOCKS 3
 #endif
 template <int KIND>
 __global__ void __launch_bounds__(kBlock, XPBD_VJP_QUAD_MIN_BLOCKS)
-k_vjp_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
-                           const float4* __restrict__ tape, const float* __restrict__ lam_pre,
-                           float4* __restrict__ xbar, float2* __restrict__ lb,
-                           double* __restrict__ acc, bool first, bool last) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  // every global read is independent of the arithmetic: issue them all first
-  float4 p[4], xb4[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) p[k] = ld_stream(tape + 4 * i + k);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) xb4[k] = ld_vtx(xbar + r.v[k], pol);
-  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
-  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
-  const f3 x0 = xyz(p[0]);
-  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
-  f3 g1, g2, g3;
-  float C;
-  if (Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
-    const f3 g0 = -(g1 + g2 + g3);
-    const float w0 = p[0].w, w1 = p[1].w, w2 = p[2].w, w3 = p[3].w;
-    float D = r.at + w0 * dot(g0, g0) + w1 * dot(g1, g1) + w2 * dot(g2, g2) + w3 * dot(g3, g3);
-    if (D > 0.f) {
-      float dl = (-C - r.at * lam) / D;
-      const f3 xb0 = xyz(xb4[0]), xb1 = xyz(xb4[1]), xb2 = xyz(xb4[2]), xb3 = xyz(xb4[3]);
-      float s = l.x + w0 * dot(g0, xb0) + w1 * dot(g1, xb1) + w2 * dot(g2, xb2) + w3 * dot(g3, xb3);
-      float sD = s / D;
-      float c2 = 2.f * sD * dl;
-      const f3 u0 = (xb0 * dl - g0 * c2) * w0;
-      const f3 du1 = (xb1 * dl - g1 * c2) * w1 - u0;
-      const f3 du2 = (xb2 * dl - g2 * c2) * w2 - u0;
-      const f3 du3 = (xb3 * dl - g3 * c2) * w3 - u0;
-      d3 h1, h2, h3;
-      Quad<KIND>::hvp(r, e1, e2, e3, du1, du2, du3, h1, h2, h3);
-      const f3 hu1 = dpart(h1), hu2 = dpart(h2), hu3 = dpart(h3);
-      const f3 hu0 = -(hu1 + hu2 + hu3);
-      st_vtx(xbar + r.v[0], with_w(xb0 - g0 * sD + hu0, 0.f), pol);
-      st_vtx(xbar + r.v[1], with_w(xb1 - g1 * sD + hu1, 0.f), pol);
-      st_vtx(xbar + r.v[2], with_w(xb2 - g2 * sD + hu2, 0.f), pol);
-      st_vtx(xbar + r.v[3], with_w(xb3 - g3 * sD + hu3, 0.f), pol);
-      l.y += -sD * (lam + dl);
-      l.x -= r.at * sD;
-    }
-  }
-  lb_finish(i, l.x, l.y, lb, acc, last);
+k_vjp_quad(const typename Quad<KIND>::Rec* __restrict__ rec, int n, const float4* __restrict__ tape,
+           const float* __restrict__ lam_pre, float4* __restrict__ xbar, float2* __restrict__ lb,
+           double* __restrict__ acc, bool first, bool last) {
+  XPBD_TID_OR_RETURN(n);
+  vjp_quad_elem<KIND>(i, rec, tape, lam_pre, xbar, lb, acc, first, last);
 }
 
 void launch_vjp(SegType t, const void* rec, int n, const float4* tape, const float* lam_pre,
@@ -572,65 +195,11 @@ void launch_vjp(SegType t, const void* rec, int n, const float4* tape, const flo
   }
 }
 
-// Reverse of the collision pass.  Plane (inputs p, h; grad_p = e_y, grad_h = -1, H = 0) and
-// sphere (inputs p, c, r; grad_p = n, grad_c = -n, grad_r = -1, H_pp = P/l, H_pc = -P/l;
-// the centre and radius are not moved, so u_c = 0).  Collider adjoints accumulate in the
-// per-vertex float32 scratch cgrad = (hbar, cbar_x, cbar_y, cbar_z, rbar) over the step.
 __global__ void k_vjp_contact(const float4* __restrict__ tape, const uint8_t* __restrict__ cflags,
                               int V, const float2* __restrict__ lam_pre, float4* __restrict__ xbar,
-                              float2* __restrict__ lbc, float* __restrict__ cgrad, bool first,
-                              Collide c) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  uint8_t f = cflags[i];
-  if (!f) return;
-  float4 p4 = tape[i];
-  float w = p4.w;
-  float2 lam = lam_pre ? lam_pre[i] : make_float2(0.f, 0.f);
-  float2 lb = first ? make_float2(0.f, 0.f) : lbc[i];
-  float cg[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  if (cgrad && !first)
-    for (int k = 0; k < 5; ++k) cg[k] = cgrad[5 * i + k];
-  f3 xb = xyz(xbar[i]);
-  f3 pre = xyz(p4);
-  f3 mid = pre;
-  if ((f & 1) && (f & 2)) {
-    float lp = lam.x;
-    plane_project(mid, w, lp, c);
-  }
-  float D = w + c.at;
-  if ((f & 2) && D > 0.f) {
-    f3 d = mid - mk3(c.cx, c.cy, c.cz);
-    float l2 = dot(d, d);
-    if (l2 >= XPBD_DEGEN2) {
-      float il = rsqrtf(l2);
-      float len = l2 * il;
-      f3 nrm = d * il;
-      float dl = (-(len - c.r - c.thick) - c.at * lam.y) / D;
-      float s = lb.y + w * dot(nrm, xb);
-      float sD = s / D;
-      f3 t = xb * (w * dl);
-      f3 hv = (t - nrm * dot(nrm, t)) * il;
-      xb = xb - nrm * sD + hv;
-      // centre: -(s/D) grad_c + (H u)_c = (s/D) n - hv ; radius: -(s/D) grad_r = s/D
-      cg[1] += nrm.x * sD - hv.x;
-      cg[2] += nrm.y * sD - hv.y;
-      cg[3] += nrm.z * sD - hv.z;
-      cg[4] += sD;
-      lb.y -= c.at * sD;
-    }
-  }
-  if ((f & 1) && D > 0.f) {
-    float s = lb.x + w * xb.y;
-    float sD = s / D;
-    xb.y -= sD;
-    cg[0] += sD;
-    lb.x -= c.at * sD;
-  }
-  xbar[i] = with_w(xb, 0.f);
-  lbc[i] = lb;
-  if (cgrad)
-    for (int k = 0; k < 5; ++k) cgrad[5 * i + k] = cg[k];
+                              float2* __restrict__ lbc, float* __restrict__ cgrad, bool first, Collide c) {
+  XPBD_TID_OR_RETURN(V);
+  vjp_contact_elem(i, tape, cflags, lam_pre, xbar, lbc, cgrad, first, c);
 }
 
 void launch_vjp_contact(const float4* tape, const uint8_t* cflags, int V, const float2* lam_pre,
@@ -640,15 +209,12 @@ void launch_vjp_contact(const float4* tape, const uint8_t* cflags, int V, const 
     k_vjp_contact<<<grid_for(V), kBlock, 0, s>>>(tape, cflags, V, lam_pre, xbar, lbc, cgrad, first, c);
 }
 
-// Per-block float64 sums of the per-vertex collider adjoints of this step (contact vertices
-// only: cgrad of other vertices is stale).
+// Per-block float64 sums of the per-vertex collider adjoints of this step.
 __global__ void k_collider_partials(const float* __restrict__ cgrad, const uint8_t* __restrict__ cflags,
                                     int V, double* __restrict__ partials) {
   double v[5] = {0, 0, 0, 0, 0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
-    if (cflags[i])
-      for (int k = 0; k < 5; ++k) v[k] += (double)cgrad[5 * i + k];
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x)
+    collider_contrib(i, cgrad, cflags, v);
   block_sum_store<5>(v, partials + 5 * blockIdx.x);
 }
 
@@ -657,40 +223,15 @@ void launch_collider_partials(const float* cgrad, const uint8_t* cflags, int V, 
   k_collider_partials<<<partial_blocks(V), kBlock, 0, s>>>(cgrad, cflags, V, partials);
 }
 
-// Adjoint of the prediction p = x_n + dt v_n + dt^2 (w (G_n + W_i) + [w>0] g):
-//   xbar_n = xbar_partial + pbar (+ dL/dx_n seed),  vbar_n = dt pbar,
-//   fbar_i = dt^2 w_i pbar_i  (Sec. 5.6: force gradients from the adjoint velocities),
-//   dL/dW_i += fbar_i (float64),  dL/dG_n = sum_i fbar_i (float64, fixed-order partials).
+// Adjoint of the prediction, with per-block float64 partial sums of the force adjoint
+// (dL/dG_n = sum_i fbar_i, reduced in a fixed order afterwards).
 __global__ void k_adj_predict(float4* __restrict__ xbar, float4* __restrict__ vbar,
                               const float4* __restrict__ ckx_n, const float* __restrict__ seed,
                               float dt, double* __restrict__ fv_acc, double* __restrict__ fg_partials,
                               int V) {
   double fs[3] = {0, 0, 0};
-  float dt2 = dt * dt;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
-    float4 pb = xbar[i];
-    float4 xp = vbar[i];
-    float w = ckx_n[i].w;
-    float4 xn = make_float4(xp.x + pb.x, xp.y + pb.y, xp.z + pb.z, 0.f);
-    if (seed) {
-      xn.x += seed[3 * i];
-      xn.y += seed[3 * i + 1];
-      xn.z += seed[3 * i + 2];
-    }
-    xbar[i] = xn;
-    vbar[i] = make_float4(dt * pb.x, dt * pb.y, dt * pb.z, 0.f);
-    double fx = (double)(dt2 * w) * (double)pb.x;
-    double fy = (double)(dt2 * w) * (double)pb.y;
-    double fz = (double)(dt2 * w) * (double)pb.z;
-    if (fv_acc) {
-      fv_acc[3 * i] += fx;
-      fv_acc[3 * i + 1] += fy;
-      fv_acc[3 * i + 2] += fz;
-    }
-    fs[0] += fx;
-    fs[1] += fy;
-    fs[2] += fz;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x)
+    adj_predict_elem(i, xbar, vbar, ckx_n, seed, dt, fv_acc, fs);
   if (fg_partials) block_sum_store<3>(fs, fg_partials + 3 * blockIdx.x);
 }
 
@@ -699,22 +240,9 @@ void launch_adj_predict(float4* xbar, float4* vbar, const float4* ckx_n, const f
   k_adj_predict<<<partial_blocks(V), kBlock, 0, s>>>(xbar, vbar, ckx_n, seed, dt, fv_acc, fg_partials, V);
 }
 
-// Sum of per-block partials in a fixed order (one block).
 __global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, int ncomp,
                                   double* __restrict__ out, bool accumulate) {
-  __shared__ double sh[kBlock];
-  for (int c = 0; c < ncomp; ++c) {
-    double t = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) t += partials[ncomp * b + c];
-    sh[threadIdx.x] = t;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[c] = accumulate ? out[c] + sh[0] : sh[0];
-    __syncthreads();
-  }
+  reduce_partials_block(partials, nblocks, ncomp, out, accumulate);
 }
 
 void launch_reduce_partials(const double* partials, int nblocks, int ncomp, double* out,
@@ -722,17 +250,12 @@ void launch_reduce_partials(const double* partials, int nblocks, int ncomp, doub
   k_reduce_partials<<<1, kBlock, 0, s>>>(partials, nblocks, ncomp, out, accumulate);
 }
 
-// dL/d compliance in the caller's constraint order: alpha~ = compliance / dt^2 (tets:
-// / (V_e dt^2)), so dL/dcompliance = alphabar~ / dt^2 (/ V_e).
 template <class Rec, bool VOL>
 __global__ void k_finalize_compliance(const Rec* __restrict__ rec, const int* __restrict__ perm,
                                       int n, const double* __restrict__ acc, float inv_dt2,
                                       double* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double a = acc[i] * (double)inv_dt2;
-  if constexpr (VOL) a = a / (double)rec[i].vol;
-  out[perm[i]] = a;
+  XPBD_TID_OR_RETURN(n);
+  finalize_elem<Rec, VOL>(i, rec, perm, acc, inv_dt2, out);
 }
 
 void launch_finalize_compliance(SegType t, const void* rec, const int* perm, int n,
@@ -751,12 +274,8 @@ void launch_finalize_compliance(SegType t, const void* rec, const int* perm, int
 }
 
 __global__ void k_to_double(const float4* __restrict__ a, double* __restrict__ out, int V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  float4 v = a[i];
-  out[3 * i] = v.x;
-  out[3 * i + 1] = v.y;
-  out[3 * i + 2] = v.z;
+  XPBD_TID_OR_RETURN(V);
+  to_double_elem(i, a, out);
 }
 
 void launch_to_double(const float4* a, double* out, int V, cudaStream_t s) {
@@ -765,20 +284,11 @@ void launch_to_double(const float4* a, double* out, int V, cudaStream_t s) {
 
 // ======================================================================== utilities
 
-// Goal function of Sec. 4.1 on one keyframe: seed = x - x*, partial sums of |x - x*|^2 / 2.
 __global__ void k_loss(const float4* __restrict__ ckx, const float* __restrict__ target,
                        float* __restrict__ seed_out, double* __restrict__ partials, int V) {
   double acc[1] = {0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
-    float4 x = ckx[i];
-    float dx = x.x - target[3 * i], dy = x.y - target[3 * i + 1], dz = x.z - target[3 * i + 2];
-    if (seed_out) {
-      seed_out[3 * i] = dx;
-      seed_out[3 * i + 1] = dy;
-      seed_out[3 * i + 2] = dz;
-    }
-    acc[0] += 0.5 * ((double)dx * dx + (double)dy * dy + (double)dz * dz);
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x)
+    loss_elem(i, ckx, target, seed_out, acc[0]);
   block_sum_store<1>(acc, partials + blockIdx.x);
 }
 
@@ -789,20 +299,8 @@ void launch_loss(const float4* ckx, const float* target, float* seed_out, double
 
 __global__ void k_read_state(const float4* __restrict__ ckx, const float4* __restrict__ ckv,
                              float* __restrict__ x_out, float* __restrict__ v_out, int V) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
-  if (x_out) {
-    float4 x = ckx[i];
-    x_out[3 * i] = x.x;
-    x_out[3 * i + 1] = x.y;
-    x_out[3 * i + 2] = x.z;
-  }
-  if (v_out) {
-    float4 v = ckv[i];
-    v_out[3 * i] = v.x;
-    v_out[3 * i + 1] = v.y;
-    v_out[3 * i + 2] = v.z;
-  }
+  XPBD_TID_OR_RETURN(V);
+  read_state_elem(i, ckx, ckv, x_out, v_out);
 }
 
 void launch_read_state(const float4* ckx, const float4* ckv, float* x_out, float* v_out, int V,

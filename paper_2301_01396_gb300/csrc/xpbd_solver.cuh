@@ -1,0 +1,165 @@
+// Internal definitions shared by the C-ABI runtime (xpbd_api.cu) and the batched serving
+// runtime (xpbd_serve.cu): the solver handle, its per-color segments and workspace, error
+// reporting and the counted/timed launch helper.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/diffxpbd.h"
+#include "xpbd_kernels.cuh"
+
+using namespace xpbd;
+
+inline thread_local std::string g_err;
+
+inline xpbd_status fail(xpbd_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CU_TRY(expr)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? XPBD_ERR_OOM : XPBD_ERR_CUDA,       \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+#define LAUNCH_CHECK()                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(XPBD_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Seg {
+  SegType type;
+  int begin;   // first record of the type array
+  int count;
+};
+
+// Device buffer that grows on demand and is freed with the handle.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need ? need : 16);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct xpbd_solver {
+  int V = 0, nd = 0, nb = 0, nt = 0, m = 0, K = 0;
+  std::vector<std::vector<Seg>> colors;
+  // type arrays in record order; rec_off[t] = offset of type t in the m-long record space
+  int n_rec[4] = {0, 0, 0, 0};
+  int rec_off[4] = {0, 0, 0, 0};
+  void* d_rec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* d_perm = nullptr;        // [m] record index -> global constraint id
+  float* d_w = nullptr;         // [V] inverse masses
+  int* d_err = nullptr;
+  // workspace
+  DevBuf P, lam, cflags, lamc;                       // forward
+  DevBuf tape, lam_tape, tape_c, lamc_tape;          // replay tapes
+  DevBuf xbar, vbar, lb, acc, lbc, cgrad, partials;  // reverse
+  // launch statistics per kernel class (always counted; timed with CUDA events on the
+  // launching stream while profiling is enabled)
+  bool prof_on = false;
+  int64_t launches[XPBD_KERNEL_CLASSES] = {0};
+  int64_t units[XPBD_KERNEL_CLASSES] = {0};
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Timed { int cls; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+  size_t tape_per_iter() const {  // float4 entries per iteration
+    return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
+  }
+};
+
+inline cudaEvent_t next_event(xpbd_solver* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Counts (and, while profiling, times) one kernel launch of class `cls` covering `units`
+// constraints or vertices.  Launches with no work are skipped by the launchers and not counted.
+template <class F>
+inline void launch(xpbd_solver* h, int cls, int64_t units, cudaStream_t s, F&& f) {
+  if (units <= 0) return;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->prof_on) {
+    a = next_event(h);
+    b = next_event(h);
+    if (a) cudaEventRecord(a, s);
+  }
+  f();
+  h->launches[cls] += 1;
+  h->units[cls] += units;
+  if (h->prof_on && a && b) {
+    cudaEventRecord(b, s);
+    h->timed.push_back({cls, a, b});
+  }
+}
+
+inline size_t tape_offset(const xpbd_solver* h, SegType t) {   // float4 offset of type t in one iteration
+  size_t o = 0;
+  for (int k = 0; k < (int)t; ++k) o += (size_t)h->n_rec[k] * kVerts[k];
+  return o;
+}
+
+inline void* rec_ptr(const xpbd_solver* h, SegType t, int begin) {
+  static const size_t sz[4] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec)};
+  return (char*)h->d_rec[t] + sz[t] * (size_t)begin;
+}
+
+inline Collide make_collide(const xpbd_params* p) {
+  Collide c;
+  c.flags = p->collider_flags & 3;
+  c.h = p->plane_h;
+  c.cx = p->sphere[0];
+  c.cy = p->sphere[1];
+  c.cz = p->sphere[2];
+  c.r = p->sphere[3];
+  c.at = p->contact_compliance / (p->dt * p->dt);
+  c.thick = p->thickness;
+  return c;
+}
+
+inline xpbd_status check_params(const xpbd_solver* h, const xpbd_params* p, int steps, int iters) {
+  if (!h || !p) return fail(XPBD_ERR_INVALID, "null handle or params");
+  if (steps < 0 || iters < 1) return fail(XPBD_ERR_INVALID, "steps must be >= 0 and iters >= 1");
+  if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(XPBD_ERR_INVALID, "dt must be positive");
+  if (h->m > 0 && !p->compliance) return fail(XPBD_ERR_INVALID, "compliance is NULL");
+  if (p->collider_flags & ~3) return fail(XPBD_ERR_INVALID, "unknown collider flag");
+  if ((p->collider_flags & XPBD_COLLIDE_SPHERE) && !(p->sphere[3] > 0.f))
+    return fail(XPBD_ERR_INVALID, "sphere radius must be positive");
+  if (p->collider_flags && !(p->contact_compliance >= 0.f))
+    return fail(XPBD_ERR_INVALID, "contact compliance must be >= 0");
+  return XPBD_OK;
+}
+
+inline const float4* ck_x(const float* ck, int V, int n) {
+  return reinterpret_cast<const float4*>(ck) + (size_t)2 * V * n;
+}
+inline const float4* ck_v(const float* ck, int V, int n) { return ck_x(ck, V, n) + V; }
+
