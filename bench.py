@@ -37,18 +37,10 @@ METRIC = "fwd+adjoint constraint-updates/s"
 UNIT = "constraint-updates/s"
 KEYFRAMES = (20, 40, 60)
 GRID = 2950
+TILE = 32
 
-# Algorithmic bytes per unit of each kernel class (steady-state iteration; float4 vertices):
-#   fwd   distance: record 16 + lambda r/w 8 + 2 vertices gathered and scattered 64 = 88
-#         bending / tet: record 32 / 64 + lambda 8 + 4 vertices r/w 128 = 168 / 200
-#   replay: forward + pre-projection tape write (16 B per vertex): 120 / 232 / 264
-#   vjp   distance: record 16 + tape 32 + lambda 4 + vertex adjoints r/w 64 + (lambar,
-#         alphabar) r/w 16 = 132;  bending: 32 + 64 + 4 + 128 + 16 = 244;  tets: 276
-BYTES_PER_UNIT = {
-    "fwd_dist": 88, "fwd_bend": 168, "fwd_tet_h": 200, "fwd_tet_d": 200,
-    "replay_dist": 120, "replay_bend": 232, "replay_tet_h": 264, "replay_tet_d": 264,
-    "vjp_dist": 132, "vjp_bend": 244, "vjp_tet_h": 276, "vjp_tet_d": 276,
-}
+# Algorithmic bytes of each kernel class come from the library (xpbd_profile_read: its byte
+# model counts records, multipliers, tapes and one read plus one write per vertex per launch).
 
 
 def parse():
@@ -58,6 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--grid", type=int, default=GRID, help="cloth side (default: the 2950^2 workload)")
+    ap.add_argument("--coloring", choices=("tiled", "pattern"), default="tiled",
+                    help="constraint coloring of the cloth (tiled: square vertex blocks in 4 classes)")
+    ap.add_argument("--tile", type=int, default=TILE, help="tile side of the tiled coloring")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=160)
@@ -168,9 +163,9 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workload
 
-def workload(grid: int):
+def workload(grid: int, coloring: str = "tiled", tile: int = TILE):
     t0 = time.time()
-    sc = scenes.sphere_cloth(grid)
+    sc = scenes.sphere_cloth(grid, coloring=coloring, tile=tile)
     return sc, time.time() - t0
 
 
@@ -236,7 +231,7 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc, t_gen = workload(args.grid)
+    sc, t_gen = workload(args.grid, args.coloring, args.tile)
     if args.sim_steps:
         sc.steps = args.sim_steps
         sc.f_global = sc.f_global[:args.sim_steps]
@@ -299,25 +294,29 @@ def run_ours(args, ws, rank, local):
     units = 2 * sc.m * I * N
     value = ws * units / (ms_max / 1e3)
 
-    # dominant kernel class and its roofline
-    timed = {k: v for k, v in stats.items() if v["timed_launches"] > 0}
-    dom = max((k for k in timed if k in BYTES_PER_UNIT), key=lambda k: timed[k]["ms"])
+    # dominant kernel class and its roofline: algorithmic bytes per launch (the library's
+    # byte model: records, multipliers, tapes, one read and one write per vertex per launch)
+    # over the class's mean CUDA-event launch time
+    timed = {k: v for k, v in stats.items() if v["timed_launches"] > 0 and v["alg_bytes"] > 0}
+    dom = max(timed, key=lambda k: timed[k]["ms"])
     d = timed[dom]
     avg_ms = d["ms"] / d["timed_launches"]
     upl = d["units"] / d["launches"]
-    achieved = upl * BYTES_PER_UNIT[dom] / (avg_ms / 1e3) / 1e9
+    bpl = d["alg_bytes"] / d["launches"]
+    achieved = bpl / (avg_ms / 1e3) / 1e9
     peak, peak_kind = measured_peak()
     tr = traffic_for(dom, upl)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None if tr is None else round(tr),
                 "kernel": dom, "launch_avg_ms": round(avg_ms, 4), "units_per_launch": round(upl),
-                "bytes_per_unit": BYTES_PER_UNIT[dom], "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": round(upl * BYTES_PER_UNIT[dom])}
+                "bytes_per_unit": round(bpl / upl, 2), "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": round(bpl)}
     launches = int(sum(v["launches"] for v in stats.values()))
     breakdown = {k: round(v["ms"] / args.steps, 2) for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])
                  if v["ms"] > 0}
     fwd_ms = sum(v["ms"] for k, v in stats.items() if k.startswith("fwd_") or k in ("predict", "velocity")) / args.steps
-    all_bytes = sum(stats[k]["units"] * b for k, b in BYTES_PER_UNIT.items()) / args.steps
+    plan = solver.exec_info()
+    all_bytes = sum(v["alg_bytes"] for v in stats.values()) / args.steps
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -327,6 +326,8 @@ def run_ours(args, ws, rank, local):
                                f"collider, keyframe loss at {list(keys)}, gradients for compliance/x0/v0/"
                                f"f_global/f_vertex/sphere",
                    "V": sc.V, "m": sc.m, "sim_steps": N, "iters": I, "colors": sc.n_colors,
+                   "coloring": args.coloring + (f" {args.tile}x{args.tile}" if args.coloring == "tiled" else ""),
+                   "launches_per_iteration": plan["launches_per_iteration"], "phase_kernels": plan["phases"],
                    "l2": "inputs larger than L2 (vertex state 139 MB, records 1.1 GB, tapes 36 GB)",
                    "parallelism": f"replicas x{ws}",
                    **({"profiling_override": f"sim_steps={N} iters={I} (not a bench value)"}

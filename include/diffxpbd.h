@@ -81,6 +81,11 @@ typedef struct {
   int32_t n_colors;
   const int32_t* color_offsets; /* [n_colors+1]; color c = color_order[offsets[c]..offsets[c+1]) */
   const int32_t* color_order;   /* [m] every constraint id exactly once                    */
+  int32_t exec_mode;            /* 0: run runs of consecutive colors whose constraints split
+                                   into small vertex-disjoint components as one launch per run
+                                   (vertices staged in shared memory), when that needs fewer
+                                   launches than colors; 1: one launch per color.  Both give
+                                   the same colored Gauss-Seidel results.                  */
 } xpbd_model;
 
 /* Per-call parameters.  The float fields are HOST values; the pointers are DEVICE. */
@@ -271,6 +276,7 @@ enum {
   XPBD_K_REPLAY_DIST, XPBD_K_REPLAY_BEND, XPBD_K_REPLAY_TETH, XPBD_K_REPLAY_TETD, XPBD_K_REPLAY_CONTACT,
   XPBD_K_VJP_DIST, XPBD_K_VJP_BEND, XPBD_K_VJP_TETH, XPBD_K_VJP_TETD, XPBD_K_VJP_CONTACT,
   XPBD_K_PREDICT, XPBD_K_VELOCITY, XPBD_K_ADJ_OTHER, XPBD_K_OTHER,
+  XPBD_K_FWD_PHASE, XPBD_K_REPLAY_PHASE, XPBD_K_VJP_PHASE,
   XPBD_KERNEL_CLASSES
 };
 
@@ -279,7 +285,14 @@ typedef struct {
   int64_t units;           /* constraints or vertices processed by them                    */
   double ms;               /* summed event time of the timed launches                      */
   int64_t timed_launches;  /* launches bracketed by events (0 while profiling is off)      */
+  double alg_bytes;        /* algorithmic bytes the launches must move: records, multipliers,
+                              tapes and vertex state at one read and one write per vertex
+                              per launch (0 for classes without a byte model)              */
 } xpbd_kernel_stat;
+
+/* Execution plan of a handle: *uses_phases = 1 when the forward and reverse sweeps run
+   multi-color launches, with *n_phases launches per iteration (else one per color). */
+xpbd_status xpbd_exec_info(xpbd_handle h, int32_t* uses_phases, int32_t* n_phases);
 
 /* Synchronise the device, reset the counters and turn event timing on (enable != 0) or
    off.  Timing adds two event records per launch on the launching stream. */

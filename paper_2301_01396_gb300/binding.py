@@ -34,7 +34,8 @@ class XpbdModel(C.Structure):
     _fields_ = [("n_vertices", C.c_int32), ("rest_x", _fp), ("inv_mass", _fp),
                 ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
                 ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _fp),
-                ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip)]
+                ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip),
+                ("exec_mode", C.c_int32)]
 
 
 class XpbdParams(C.Structure):
@@ -52,12 +53,12 @@ class XpbdGrads(C.Structure):
 KERNEL_CLASSES = ("fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
                   "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
                   "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
-                  "predict", "velocity", "adjoint_other", "other")
+                  "predict", "velocity", "adjoint_other", "other", "fwd_phase", "replay_phase", "vjp_phase")
 
 
 class XpbdKernelStat(C.Structure):
     _fields_ = [("launches", C.c_int64), ("units", C.c_int64), ("ms", C.c_double),
-                ("timed_launches", C.c_int64)]
+                ("timed_launches", C.c_int64), ("alg_bytes", C.c_double)]
 
 
 class XpbdRequest(C.Structure):
@@ -92,7 +93,7 @@ def lib():
         for name in ("xpbd_create", "xpbd_destroy", "xpbd_sizes", "xpbd_forward", "xpbd_read_state",
                      "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read", "xpbd_forward_static",
                      "xpbd_server_create", "xpbd_server_destroy", "xpbd_server_submit", "xpbd_server_run",
-                     "xpbd_server_poll", "xpbd_server_get_stats"):
+                     "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -154,7 +155,7 @@ class Solver:
     """One xpbd_handle: a mesh, its constraints and its coloring, resident on the GPU."""
 
     def __init__(self, rest_x, inv_mass, dist_idx=None, bend_idx=None, tet_idx=None, tet_gamma=None,
-                 color_offsets=None, color_order=None):
+                 color_offsets=None, color_order=None, exec_mode: int = 0):
         L = lib()
         keep = []
 
@@ -179,7 +180,7 @@ class Solver:
                        n_tet=int(tet_idx.shape[0]), tet_idx=i(tet_idx),
                        tet_gamma=f(tet_gamma) if (tet_gamma is not None and len(tet_gamma)) else None,
                        n_colors=int(len(color_offsets) - 1), color_offsets=i(color_offsets),
-                       color_order=i(color_order))
+                       color_order=i(color_order), exec_mode=int(exec_mode))
         h = C.c_void_p()
         _check(L.xpbd_create(C.byref(md), C.byref(h)))
         self._h = h
@@ -188,9 +189,15 @@ class Solver:
         self.V, self.m, self.n_colors = nv.value, nc.value, ncol.value
 
     @classmethod
-    def from_scene(cls, sc) -> "Solver":
+    def from_scene(cls, sc, exec_mode: int = 0) -> "Solver":
         return cls(sc.rest_x, sc.inv_mass, sc.dist_idx, sc.bend_idx, sc.tet_idx, sc.tet_gamma,
-                   sc.color_offsets, sc.color_order)
+                   sc.color_offsets, sc.color_order, exec_mode)
+
+    def exec_info(self) -> dict:
+        """{"phases": bool, "launches_per_iteration": int} of the handle's execution plan."""
+        u, n = C.c_int32(), C.c_int32()
+        _check(lib().xpbd_exec_info(self._h, C.byref(u), C.byref(n)))
+        return {"phases": bool(u.value), "launches_per_iteration": n.value}
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
@@ -287,8 +294,8 @@ class Solver:
         """{class: {launches, units, ms, timed_launches}} since the last profile() call."""
         arr = (XpbdKernelStat * len(KERNEL_CLASSES))()
         _check(lib().xpbd_profile_read(self._h, arr))
-        return {n: dict(launches=a.launches, units=a.units, ms=a.ms, timed_launches=a.timed_launches)
-                for n, a in zip(KERNEL_CLASSES, arr)}
+        return {n: dict(launches=a.launches, units=a.units, ms=a.ms, timed_launches=a.timed_launches,
+                        alg_bytes=a.alg_bytes) for n, a in zip(KERNEL_CLASSES, arr)}
 
 
 def params_from_scene(sc, device="cuda", compliance=None) -> Params:

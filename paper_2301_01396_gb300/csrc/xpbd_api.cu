@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -25,7 +26,7 @@ namespace {
 // Forward workspace (no tapes).
 xpbd_status ensure_forward_ws(xpbd_solver* h) {
   CU_TRY(h->P.ensure(sizeof(float4) * (size_t)h->V));
-  CU_TRY(h->lam.ensure(sizeof(float) * (size_t)std::max(h->m, 1)));
+  CU_TRY(h->lam.ensure(sizeof(float) * h->slots));
   CU_TRY(h->cflags.ensure((size_t)std::max(h->V, 1)));
   CU_TRY(h->lamc.ensure(sizeof(float2) * (size_t)std::max(h->V, 1)));
   return XPBD_OK;
@@ -34,8 +35,8 @@ xpbd_status ensure_forward_ws(xpbd_solver* h) {
 xpbd_status ensure_adjoint_ws(xpbd_solver* h, int iters, bool contacts) {
   xpbd_status st = ensure_forward_ws(h);
   if (st != XPBD_OK) return st;
-  size_t V = (size_t)h->V, m = (size_t)std::max(h->m, 1);
-  CU_TRY(h->tape.ensure(sizeof(float4) * h->tape_per_iter() * iters));
+  size_t V = (size_t)h->V, m = h->slots;
+  CU_TRY(h->tape.ensure(sizeof(float4) * std::max(h->tape_slots, (size_t)1) * iters));
   CU_TRY(h->lam_tape.ensure(sizeof(float) * m * iters));
   if (contacts) {
     CU_TRY(h->tape_c.ensure(sizeof(float4) * V * iters));
@@ -51,12 +52,19 @@ xpbd_status ensure_adjoint_ws(xpbd_solver* h, int iters, bool contacts) {
   return XPBD_OK;
 }
 
-xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s) {
+PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph);
+
+// alpha~ into the records a call will use: the phase-ordered copy when the phase plan runs
+// the sweep (`phase`), else the per-color records.
+xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool phase = false) {
   float inv_dt2 = 1.f / (p->dt * p->dt);
+  void* const* rec = phase ? h->d_prec : h->d_rec;
+  const int* perm = phase ? h->d_pperm : h->d_perm;
+  const int* off = phase ? h->pslot_off : h->rec_off;
+  const int* cnt = phase ? h->n_prec : h->n_rec;
   for (int t = 0; t < 4; ++t)
-    launch(h, XPBD_K_OTHER, h->n_rec[t], s, [&] {
-      launch_set_alpha((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t], p->compliance,
-                       inv_dt2, h->d_err, s);
+    launch(h, XPBD_K_OTHER, cnt[t], s, [&] {
+      launch_set_alpha((SegType)t, rec[t], perm + off[t], cnt[t], p->compliance, inv_dt2, h->d_err, s);
     });
   LAUNCH_CHECK();
   return XPBD_OK;
@@ -75,27 +83,40 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
                    p->dt, p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
   });
   LAUNCH_CHECK();
-  const size_t tpi = h->tape_per_iter();
+  const size_t tpi = h->tape_slots;
   for (int k = 0; k < iters; ++k) {
     float* lam_in;
     float* lam_out;
     float4* tape_k = nullptr;
     if (record) {
-      lam_in = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->m;
-      lam_out = h->lam_tape.as<float>() + (size_t)k * h->m;
+      lam_in = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->slots;
+      lam_out = h->lam_tape.as<float>() + (size_t)k * h->slots;
       tape_k = h->tape.as<float4>() + (size_t)k * tpi;
     } else {
       lam_in = k == 0 ? nullptr : h->lam.as<float>();
       lam_out = h->lam.as<float>();
     }
-    for (int col = 0; col < h->K; ++col) {
-      for (const Seg& g : h->colors[col]) {
-        size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-        float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
-        launch(h, (record ? XPBD_K_REPLAY_DIST : XPBD_K_FWD_DIST) + (int)g.type, g.count, s, [&] {
-          launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
-                         lam_out + ro, tp, s);
-        });
+    if (h->use_phases) {
+      for (const auto& ph : h->phases) {
+        PhaseLaunch a = phase_args(h, ph);
+        a.P = P;
+        a.lam_in = lam_in;
+        a.lam_out = lam_out;
+        a.tape = tape_k;
+        launch(h, record ? XPBD_K_REPLAY_PHASE : XPBD_K_FWD_PHASE, ph.units, s,
+               [&] { launch_phase_fwd(a, ph.shape(), record, s); },
+               record ? ph.bytes_replay : ph.bytes_fwd);
+      }
+    } else {
+      for (int col = 0; col < h->K; ++col) {
+        for (const Seg& g : h->colors[col]) {
+          size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+          float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
+          launch(h, (record ? XPBD_K_REPLAY_DIST : XPBD_K_FWD_DIST) + (int)g.type, g.count, s, [&] {
+            launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
+                           lam_out + ro, tp, s);
+          });
+        }
       }
     }
     if (c.flags) {
@@ -182,6 +203,340 @@ xpbd_status static_scratch_address(void** out) {
   *out = g_static_addr[dev];
   return XPBD_OK;
 }
+
+// ---------------------------------------------------------------- phase plan
+// Runs of consecutive colors whose constraints, taken together, split into connected
+// components of at most kPhaseMaxVerts vertices are launched as one phase kernel
+// (xpbd_phase.cu).  Components are packed into CTA groups; records are copied into a phase
+// order (phase, group, color, type, first vertex) with vertex indices local to the group.
+// The plan is used when it needs fewer launches per iteration than there are colors.
+template <class Rec>
+Rec localize(Rec r, const std::vector<int>& loc);
+template <>
+DistRec localize(DistRec r, const std::vector<int>& loc) {
+  r.a = loc[r.a];
+  r.b = loc[r.b];
+  return r;
+}
+template <>
+BendRec localize(BendRec r, const std::vector<int>& loc) {
+  for (int k = 0; k < 4; ++k) r.v[k] = loc[r.v[k]];
+  return r;
+}
+template <>
+TetRec localize(TetRec r, const std::vector<int>& loc) {
+  for (int k = 0; k < 4; ++k) r.v[k] = loc[r.v[k]];
+  return r;
+}
+
+xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, const std::vector<DistRec>& rd,
+                         const std::vector<BendRec>& rb, const std::vector<TetRec>& rh,
+                         const std::vector<TetRec>& rdv, const std::vector<int>& perm) {
+  const int V = h->V, K = h->K;
+  if (K == 0 || V == 0) return XPBD_OK;
+  // constraint id -> (type, index in its type's record array)
+  std::vector<int> type_of(h->m), idx_of(h->m);
+  for (int t = 0; t < 4; ++t)
+    for (int i = 0; i < h->n_rec[t]; ++i) {
+      int j = perm[h->rec_off[t] + i];
+      type_of[j] = t;
+      idx_of[j] = i;
+    }
+  auto verts_of = [&](int j, int* vs) -> int {
+    int t = type_of[j], i = idx_of[j];
+    if (t == 0) {
+      vs[0] = rd[i].a;
+      vs[1] = rd[i].b;
+      return 2;
+    }
+    const int* v = t == 1 ? rb[i].v : (t == 2 ? rh[i].v : rdv[i].v);
+    for (int k = 0; k < 4; ++k) vs[k] = v[k];
+    return 4;
+  };
+  std::vector<int> parent(V), csz(V, 1);
+  std::iota(parent.begin(), parent.end(), 0);
+  std::vector<char> in(V, 0);
+  std::vector<int> touched;
+  int maxc = 1;
+  auto find = [&](int x) {
+    while (parent[x] != x) {
+      parent[x] = parent[parent[x]];
+      x = parent[x];
+    }
+    return x;
+  };
+  auto reset = [&]() {
+    for (int v : touched) {
+      parent[v] = v;
+      csz[v] = 1;
+      in[v] = 0;
+    }
+    touched.clear();
+    maxc = 1;
+  };
+  auto add_color = [&](int c) {
+    int vs[4];
+    for (int t = offsets[c]; t < offsets[c + 1]; ++t) {
+      int nv = verts_of(order[t], vs);
+      for (int k = 0; k < nv; ++k)
+        if (!in[vs[k]]) {
+          in[vs[k]] = 1;
+          touched.push_back(vs[k]);
+        }
+      for (int k = 1; k < nv; ++k) {
+        int a = find(vs[0]), b = find(vs[k]);
+        if (a == b) continue;
+        if (csz[a] < csz[b]) std::swap(a, b);
+        parent[b] = a;
+        csz[a] += csz[b];
+        maxc = std::max(maxc, csz[a]);
+      }
+    }
+  };
+  // 1. runs of colors.  Greedy first: extend each run until the next color would make a
+  // component larger than kPhaseMaxVerts.  If that leaves a one-color run, take the fewest
+  // runs instead (dynamic program over each start's longest feasible run: an interval that
+  // is too large stays too large when extended).
+  std::vector<std::pair<int, int>> runs;
+  bool single = false;
+  for (int c = 0; c < K;) {
+    reset();
+    const int c0 = c;
+    while (c < K) {
+      add_color(c);
+      if (maxc > kPhaseMaxVerts) break;
+      ++c;
+    }
+    if (c == c0) ++c;
+    single |= (c - c0) < 2;
+    runs.push_back({c0, c});
+  }
+  if (single) {
+    std::vector<int> reach(K);
+    for (int a = 0; a < K; ++a) {
+      reset();
+      int b = a;
+      while (b < K) {
+        add_color(b);
+        if (maxc > kPhaseMaxVerts) break;
+        ++b;
+      }
+      reach[a] = std::max(b, a + 1);
+    }
+    std::vector<int> best(K + 1, 1 << 30), from(K + 1, -1);
+    best[0] = 0;
+    for (int a = 0; a < K; ++a) {
+      if (best[a] == (1 << 30)) continue;
+      for (int b = a + 1; b <= reach[a]; ++b)
+        if (best[a] + 1 < best[b]) {
+          best[b] = best[a] + 1;
+          from[b] = a;
+        }
+    }
+    runs.clear();
+    for (int b = K; b > 0; b = from[b]) runs.push_back({from[b], b});
+    std::reverse(runs.begin(), runs.end());
+  }
+  if ((int)runs.size() >= K) return XPBD_OK;   // no run of two colors or more: one launch per color
+  // 2. groups, chunks and the padded phase records
+  std::vector<DistRec> pd;
+  std::vector<BendRec> pb;
+  std::vector<TetRec> ph, pdv;
+  std::vector<int> pperm_t[4];
+  std::vector<PhaseGroup> groups;
+  std::vector<PhaseChunk> chunks;
+  std::vector<int> pverts;
+  std::vector<int> loc(V, -1), comp_of_root(V, -1), group_of_vertex(V, -1);
+  const double rec_bytes[4] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec)};
+  auto type_size = [&](int t) -> size_t {
+    return t == 0 ? pd.size() : (t == 1 ? pb.size() : (t == 2 ? ph.size() : pdv.size()));
+  };
+  // a padding record: every vertex is the group's dummy vertex, alpha~ = 0
+  auto push_pad = [&](int t, int dummy) {
+    if (t == 0) {
+      DistRec r{dummy, dummy, 0.f, 0.f};
+      pd.push_back(r);
+    } else if (t == 1) {
+      BendRec r{{dummy, dummy, dummy, dummy}, 0.f, 0.f, 0.f, 0.f};
+      pb.push_back(r);
+    } else {
+      TetRec r;
+      std::memset(&r, 0, sizeof(r));
+      for (int k = 0; k < 4; ++k) r.v[k] = dummy;
+      r.gamma = 1.f;
+      r.vol = 1.f;
+      (t == 2 ? ph : pdv).push_back(r);
+    }
+    pperm_t[t].push_back(-1);
+  };
+  for (auto& run : runs) {
+    reset();
+    for (int c = run.first; c < run.second; ++c) add_color(c);
+    const int ncol = run.second - run.first;
+    std::vector<int> tv(touched.begin(), touched.end());
+    std::sort(tv.begin(), tv.end());
+    // components in order of their smallest vertex
+    std::vector<std::vector<int>> comps;
+    for (int v : tv) {
+      int r = find(v);
+      if (comp_of_root[r] < 0) {
+        comp_of_root[r] = (int)comps.size();
+        comps.emplace_back();
+      }
+      comps[comp_of_root[r]].push_back(v);
+    }
+    xpbd_solver::PhaseHost ph_info;
+    ph_info.first_group = (int)groups.size();
+    ph_info.c0 = run.first;
+    ph_info.ncolors = ncol;
+    // groups: consecutive components packed up to kPhaseGroupVerts vertices (a larger
+    // component is a group of its own)
+    {
+      int cur = -1, cur_n = 0;
+      for (size_t k = 0; k < comps.size(); ++k) {
+        int sz = (int)comps[k].size();
+        if (cur < 0 || cur_n + sz > kPhaseGroupVerts) {
+          PhaseGroup g;
+          g.vert_begin = (int)pverts.size();
+          g.vert_count = 0;
+          g.chunk_begin = 0;
+          g.chunk_count = 0;
+          groups.push_back(g);
+          cur = (int)groups.size() - 1;
+          cur_n = 0;
+        }
+        for (int v : comps[k]) {
+          loc[v] = groups[cur].vert_count++;
+          group_of_vertex[v] = cur;
+          pverts.push_back(v);
+        }
+        cur_n += sz;
+      }
+    }
+    ph_info.n_groups = (int)groups.size() - ph_info.first_group;
+    // bucket the run's constraints by (group, color, type), keeping color order
+    std::vector<std::vector<int>> bucket((size_t)ph_info.n_groups * ncol * 4);
+    for (int c = run.first; c < run.second; ++c)
+      for (int t = offsets[c]; t < offsets[c + 1]; ++t) {
+        int j = order[t], vs[4];
+        verts_of(j, vs);
+        int g = group_of_vertex[vs[0]] - ph_info.first_group;
+        bucket[((size_t)g * ncol + (c - run.first)) * 4 + type_of[j]].push_back(j);
+      }
+    double vbytes = 0;
+    int64_t units = 0;
+    double rbytes_f = 0, rbytes_r = 0, rbytes_v = 0;
+    for (int g = 0; g < ph_info.n_groups; ++g) {
+      PhaseGroup& G = groups[ph_info.first_group + g];
+      G.chunk_begin = (int)chunks.size();
+      ph_info.max_verts = std::max(ph_info.max_verts, G.vert_count);
+      vbytes += 36.0 * G.vert_count;   // vertex index + one float4 read + one write
+      for (int ci = 0; ci < ncol; ++ci) {
+        for (int t = 0; t < 4; ++t) {
+          std::vector<int>& b = bucket[((size_t)g * ncol + ci) * 4 + t];
+          if (b.empty()) continue;
+          int vs0[4], vs1[4];
+          std::stable_sort(b.begin(), b.end(), [&](int x, int y) {
+            verts_of(x, vs0);
+            verts_of(y, vs1);
+            return loc[vs0[0]] < loc[vs1[0]];
+          });
+          const int begin = (int)type_size(t);   // a multiple of 4: every bucket is padded
+          for (int j : b) {
+            int i = idx_of[j];
+            if (t == 0) pd.push_back(localize(rd[i], loc));
+            else if (t == 1) pb.push_back(localize(rb[i], loc));
+            else if (t == 2) ph.push_back(localize(rh[i], loc));
+            else pdv.push_back(localize(rdv[i], loc));
+            pperm_t[t].push_back(j);
+          }
+          while (type_size(t) % 4) push_pad(t, G.vert_count);
+          const int total = (int)type_size(t) - begin;
+          for (int off = 0; off < total; off += kPhaseChunk) {
+            PhaseChunk ck;
+            ck.type = t;
+            ck.begin = begin + off;
+            ck.count = std::min(kPhaseChunk, total - off);
+            ck.pad = 0;
+            chunks.push_back(ck);
+          }
+          ph_info.type_mask |= 1 << t;
+          const double n = (double)b.size(), nv = kVerts[t];
+          units += (int64_t)b.size();
+          rbytes_f += n * (rec_bytes[t] + 8.0);
+          rbytes_r += n * (rec_bytes[t] + 8.0 + 16.0 * nv);
+          rbytes_v += n * (rec_bytes[t] + 16.0 * nv + 4.0 + 16.0);
+        }
+      }
+      G.chunk_count = (int)chunks.size() - G.chunk_begin;
+      ph_info.max_chunks = std::max(ph_info.max_chunks, G.chunk_count);
+    }
+    ph_info.units = units;
+    ph_info.bytes_fwd = rbytes_f + vbytes;
+    ph_info.bytes_replay = rbytes_r + vbytes;
+    ph_info.bytes_vjp = rbytes_v + vbytes;
+    if (!phase_smem_bytes(ph_info.shape(), true) || !phase_smem_bytes(ph_info.shape(), false)) {
+      h->phases.clear();   // cannot happen with kPhaseMaxVerts components; keep per-color launches
+      return XPBD_OK;
+    }
+    h->phases.push_back(ph_info);
+    for (int v : tv) {
+      comp_of_root[v] = -1;
+      comp_of_root[find(v)] = -1;
+    }
+  }
+  // slot space and tape layout of the phase records
+  size_t nslots = 0, ntape = 0;
+  std::vector<int> pperm;
+  for (int t = 0; t < 4; ++t) {
+    h->n_prec[t] = (int)type_size(t);
+    h->pslot_off[t] = (int)nslots;
+    h->ptape_off[t] = ntape;
+    nslots += (size_t)h->n_prec[t];
+    ntape += (size_t)h->n_prec[t] * kVerts[t];
+    pperm.insert(pperm.end(), pperm_t[t].begin(), pperm_t[t].end());
+  }
+  // upload
+  auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    *dst = nullptr;
+    if (!bytes) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = up(&h->d_prec[0], pd.data(), pd.size() * sizeof(DistRec));
+  if (e == cudaSuccess) e = up(&h->d_prec[1], pb.data(), pb.size() * sizeof(BendRec));
+  if (e == cudaSuccess) e = up(&h->d_prec[2], ph.data(), ph.size() * sizeof(TetRec));
+  if (e == cudaSuccess) e = up(&h->d_prec[3], pdv.data(), pdv.size() * sizeof(TetRec));
+  if (e == cudaSuccess) e = up((void**)&h->d_pperm, pperm.data(), pperm.size() * sizeof(int));
+  if (e == cudaSuccess) e = up((void**)&h->d_groups, groups.data(), groups.size() * sizeof(PhaseGroup));
+  if (e == cudaSuccess) e = up((void**)&h->d_chunks, chunks.data(), chunks.size() * sizeof(PhaseChunk));
+  if (e == cudaSuccess) e = up((void**)&h->d_pverts, pverts.data(), pverts.size() * sizeof(int));
+  if (e == cudaSuccess) e = phase_kernel_setup();
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? XPBD_ERR_OOM : XPBD_ERR_CUDA,
+                std::string("phase plan upload: ") + cudaGetErrorString(e));
+  h->slots = std::max(h->slots, (nslots + 3) / 4 * 4);
+  h->tape_slots = std::max(h->tape_slots, ntape);
+  h->use_phases = true;
+  return XPBD_OK;
+}
+
+PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph) {
+  PhaseLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.groups = h->d_groups + ph.first_group;
+  a.chunks = h->d_chunks;
+  a.pverts = h->d_pverts;
+  for (int t = 0; t < 4; ++t) {
+    a.slot_off[t] = h->pslot_off[t];
+    a.prec[t] = h->d_prec[t];
+    a.tape_off[t] = h->ptape_off[t];
+  }
+  a.err = h->d_err;
+  return a;
+}
+
 }  // namespace
 
 extern "C" {
@@ -252,6 +607,8 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   // records, grouped by color, then type, then first vertex
   xpbd_solver* h = new xpbd_solver();
   h->V = V; h->nd = nd; h->nb = nb; h->nt = nt; h->m = m; h->K = K;
+  h->slots = ((size_t)std::max(m, 1) + 3) / 4 * 4;
+  h->tape_slots = h->tape_per_iter();
   h->n_rec[0] = nd; h->n_rec[1] = nb; h->n_rec[2] = nt; h->n_rec[3] = nt;
   h->rec_off[0] = 0; h->rec_off[1] = nd; h->rec_off[2] = nd + nb; h->rec_off[3] = nd + nb + nt;
   std::vector<DistRec> rd; rd.reserve(nd);
@@ -362,6 +719,17 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     return fail(e == cudaErrorMemoryAllocation ? XPBD_ERR_OOM : XPBD_ERR_CUDA,
                 std::string("xpbd_create upload: ") + cudaGetErrorString(e));
   }
+  if (md->exec_mode < 0 || md->exec_mode > 1) {
+    xpbd_destroy(h);
+    return fail(XPBD_ERR_INVALID, "exec_mode must be 0 or 1");
+  }
+  if (md->exec_mode == 0) {
+    xpbd_status pst = build_phases(h, md->color_offsets, md->color_order, rd, rb, rh, rdv, perm);
+    if (pst != XPBD_OK) {
+      xpbd_destroy(h);
+      return pst;
+    }
+  }
   *out = h;
   return XPBD_OK;
 }
@@ -374,6 +742,11 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
   if (h->d_perm) cudaFree(h->d_perm);
   if (h->d_w) cudaFree(h->d_w);
   if (h->d_err) cudaFree(h->d_err);
+  for (int t = 0; t < 4; ++t)
+    if (h->d_prec[t]) cudaFree(h->d_prec[t]);
+  void* plan[] = {h->d_pperm, h->d_groups, h->d_chunks, h->d_pverts};
+  for (void* q : plan)
+    if (q) cudaFree(q);
   DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
                     &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
                     &h->partials};
@@ -398,9 +771,9 @@ size_t xpbd_checkpoint_bytes(xpbd_handle h, int32_t steps) {
 
 size_t xpbd_workspace_bytes(xpbd_handle h, int32_t iters) {
   if (!h || iters < 1) return 0;
-  size_t V = h->V, m = std::max(h->m, 1);
+  size_t V = h->V, m = h->slots;
   size_t b = 16 * V + 4 * m + V + 8 * V;                          // forward
-  b += 16 * h->tape_per_iter() * iters + 4 * m * iters;            // replay tapes
+  b += 16 * std::max(h->tape_slots, (size_t)1) * iters + 4 * m * iters;            // replay tapes
   b += (16 + 8) * V * iters + 8 * V + 20 * V;                      // contact tapes and scratch
   b += 32 * V + 8 * m + 8 * m + 40 * (size_t)partial_blocks(std::max(h->V, 1));
   return b;
@@ -416,7 +789,7 @@ xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_forward_ws(h);
   if (st != XPBD_OK) return st;
-  st = set_alpha(h, p, s);
+  st = set_alpha(h, p, s, h->use_phases);
   if (st != XPBD_OK) return st;
   float4* ck4 = reinterpret_cast<float4*>(ck);
   launch(h, XPBD_K_OTHER, h->V, s, [&] { launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + h->V, h->V, s); });
@@ -487,11 +860,11 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   const bool contacts = (p->collider_flags & 3) != 0;
   st = ensure_adjoint_ws(h, iters, contacts);
   if (st != XPBD_OK) return st;
-  st = set_alpha(h, p, s);
+  st = set_alpha(h, p, s, h->use_phases);
   if (st != XPBD_OK) return st;
   const int pb = partial_blocks(std::max(V, 1));
   double* partials = h->partials.as<double>();
-  CU_TRY(cudaMemsetAsync(h->acc.p, 0, sizeof(double) * (size_t)std::max(h->m, 1), s));
+  CU_TRY(cudaMemsetAsync(h->acc.p, 0, sizeof(double) * h->slots, s));
   if (out->d_f_vertex) CU_TRY(cudaMemsetAsync(out->d_f_vertex, 0, sizeof(double) * 3 * (size_t)V, s));
   if (out->d_collider) CU_TRY(cudaMemsetAsync(out->d_collider, 0, sizeof(double) * 5, s));
   if (out->d_f_global && steps > 0) CU_TRY(cudaMemsetAsync(out->d_f_global, 0, sizeof(double) * 3 * (size_t)steps, s));
@@ -503,7 +876,7 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   });
   LAUNCH_CHECK();
   const float inv_dt = 1.f / p->dt;
-  const size_t tpi = h->tape_per_iter();
+  const size_t tpi = h->tape_slots;
   Collide c = make_collide(p);
   for (int n = steps - 1; n >= 0; --n) {
     launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_adj_begin(xbar, vbar, inv_dt, V, s); });
@@ -519,8 +892,19 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
         });
       }
       const float4* tape_k = h->tape.as<float4>() + (size_t)k * tpi;
-      const float* lam_pre = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->m;
-      for (int col = h->K - 1; col >= 0; --col) {
+      const float* lam_pre = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->slots;
+      for (int q = h->use_phases ? (int)h->phases.size() - 1 : -1; q >= 0; --q) {
+        const auto& ph = h->phases[q];
+        PhaseLaunch a = phase_args(h, ph);
+        a.P = xbar;
+        a.lam_in = lam_pre;
+        a.tape = const_cast<float4*>(tape_k);
+        a.lb = h->lb.as<float2>();
+        a.acc = h->acc.as<double>();
+        launch(h, XPBD_K_VJP_PHASE, ph.units, s,
+               [&] { launch_phase_vjp(a, ph.shape(), first, last, s); }, ph.bytes_vjp);
+      }
+      for (int col = h->use_phases ? -1 : h->K - 1; col >= 0; --col) {
         const std::vector<Seg>& segs = h->colors[col];
         for (int q = (int)segs.size() - 1; q >= 0; --q) {
           const Seg& g = segs[q];
@@ -554,11 +938,14 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   if (out->d_v0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(vbar, out->d_v0, V, s); });
   if (out->d_compliance) {
     float inv_dt2 = 1.f / (p->dt * p->dt);
-    for (int t = 0; t < 4; ++t)
-      launch(h, XPBD_K_ADJ_OTHER, h->n_rec[t], s, [&] {
-        launch_finalize_compliance((SegType)t, h->d_rec[t], h->d_perm + h->rec_off[t], h->n_rec[t],
-                                   h->acc.as<double>() + h->rec_off[t], inv_dt2, out->d_compliance, s);
+    const bool ph = h->use_phases;
+    for (int t = 0; t < 4; ++t) {
+      const int off = ph ? h->pslot_off[t] : h->rec_off[t], cnt = ph ? h->n_prec[t] : h->n_rec[t];
+      launch(h, XPBD_K_ADJ_OTHER, cnt, s, [&] {
+        launch_finalize_compliance((SegType)t, ph ? h->d_prec[t] : h->d_rec[t], (ph ? h->d_pperm : h->d_perm) + off,
+                                   cnt, h->acc.as<double>() + off, inv_dt2, out->d_compliance, s);
       });
+    }
   }
   LAUNCH_CHECK();
   return XPBD_OK;
@@ -568,7 +955,7 @@ static const char* kClassNames[XPBD_KERNEL_CLASSES] = {
     "fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
     "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
     "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
-    "predict", "velocity", "adjoint_other", "other"};
+    "predict", "velocity", "adjoint_other", "other", "fwd_phase", "replay_phase", "vjp_phase"};
 
 const char* xpbd_kernel_class_name(int32_t cls) {
   return (cls >= 0 && cls < XPBD_KERNEL_CLASSES) ? kClassNames[cls] : "";
@@ -580,7 +967,10 @@ xpbd_status xpbd_profile(xpbd_handle h, int32_t enable) {
   h->prof_on = enable != 0;
   h->timed.clear();
   h->ev_used = 0;
-  for (int c = 0; c < XPBD_KERNEL_CLASSES; ++c) h->launches[c] = h->units[c] = 0;
+  for (int c = 0; c < XPBD_KERNEL_CLASSES; ++c) {
+    h->launches[c] = h->units[c] = 0;
+    h->alg_bytes[c] = 0.0;
+  }
   return XPBD_OK;
 }
 
@@ -592,6 +982,7 @@ xpbd_status xpbd_profile_read(xpbd_handle h, xpbd_kernel_stat* out) {
     out[c].units = h->units[c];
     out[c].ms = 0.0;
     out[c].timed_launches = 0;
+    out[c].alg_bytes = h->alg_bytes[c];
   }
   for (const auto& t : h->timed) {
     float ms = 0.f;
@@ -666,12 +1057,20 @@ xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t ste
   return XPBD_OK;
 }
 
+xpbd_status xpbd_exec_info(xpbd_handle h, int32_t* uses_phases, int32_t* n_phases) {
+  if (!h) return fail(XPBD_ERR_INVALID, "null handle");
+  if (uses_phases) *uses_phases = h->use_phases ? 1 : 0;
+  if (n_phases) *n_phases = h->use_phases ? (int32_t)h->phases.size() : h->K;
+  return XPBD_OK;
+}
+
 xpbd_status xpbd_sync_status(xpbd_handle h, void* stream) {
   if (!h) return fail(XPBD_ERR_INVALID, "null handle");
   CU_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int err = 0;
   CU_TRY(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CU_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+  if (err & 4) return fail(XPBD_ERR_TIMEOUT, "a phase kernel gave up waiting for its staged copies");
   if (err & 2) return fail(XPBD_ERR_NONFINITE, "a compliance value is negative or not finite");
   if (err & 1) return fail(XPBD_ERR_NONFINITE, "a step produced a non-finite position or velocity");
   return XPBD_OK;

@@ -79,6 +79,27 @@ __device__ __forceinline__ void st_vtx(float4* a, float4 v, uint64_t pol) {
 #endif
 }
 
+// Vertex access of the element functions: global memory with the L2 hint (SH = false), or a
+// shared-memory copy of a group's vertices addressed by local index (SH = true).
+template <bool SH>
+__device__ __forceinline__ float4 vload(const float4* a, uint64_t pol) {
+  if constexpr (SH) {
+    (void)pol;
+    return *a;
+  } else {
+    return ld_vtx(a, pol);
+  }
+}
+template <bool SH>
+__device__ __forceinline__ void vstore(float4* a, float4 v, uint64_t pol) {
+  if constexpr (SH) {
+    (void)pol;
+    *a = v;
+  } else {
+    st_vtx(a, v, pol);
+  }
+}
+
 // A record of 16, 32 or 64 bytes as 128-bit loads (streaming hint when XPBD_REC_STREAM).
 template <class Rec>
 __device__ __forceinline__ Rec ld_rec(const Rec* p) {
@@ -151,12 +172,15 @@ __device__ __forceinline__ void init_ckpt_elem(int i, const float* __restrict__ 
 }
 
 // alpha~ of record i from the caller's per-constraint compliance (caller order).  A
-// compliance that is negative or not finite sets bit 1 of the error word.
+// compliance that is negative or not finite sets bit 1 of the error word.  Padding records
+// (perm -1) keep alpha~ = 0.
 template <class Rec, bool VOL>
 __device__ __forceinline__ void set_alpha_elem(int i, Rec* __restrict__ rec, const int* __restrict__ perm,
                                                const float* __restrict__ compliance, float inv_dt2,
                                                int* __restrict__ err) {
-  float c = compliance[perm[i]];
+  const int j = perm[i];
+  if (j < 0) return;
+  float c = compliance[j];
   if (!(c >= 0.f) || isinf(c)) atomicOr(err, 2);
   float a = c * inv_dt2;
   if constexpr (VOL) a = a / rec[i].vol;
@@ -196,17 +220,16 @@ __device__ __forceinline__ void predict_elem(int i, const float4* __restrict__ c
 
 // ---- distance: C = |x_a - x_b| - L, grad_a = n = (x_a - x_b)/l, grad_b = -n.
 // lam_in and lam_out may alias (in-place forward), so they are not __restrict__.
-__device__ __forceinline__ void proj_dist_elem(int i, const DistRec* __restrict__ rec, float4* __restrict__ P,
-                                               const float* lam_in, float* lam_out, float4* __restrict__ tape) {
-  const DistRec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  float4 pa = ld_vtx(P + r.a, pol);
-  float4 pb = ld_vtx(P + r.b, pol);
-  if (tape) {
-    __stcs(tape + 2 * i, pa);
-    __stcs(tape + 2 * i + 1, pb);
+template <bool SH = false>
+__device__ __forceinline__ float proj_dist_core(const DistRec& r, float4* __restrict__ P, float lam,
+                                                float4* __restrict__ tape2) {
+  const uint64_t pol = SH ? 0 : vtx_policy();
+  float4 pa = vload<SH>(P + r.a, pol);
+  float4 pb = vload<SH>(P + r.b, pol);
+  if (tape2) {
+    __stcs(tape2, pa);
+    __stcs(tape2 + 1, pb);
   }
-  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
   f3 d = xyz(pa) - xyz(pb);
   float l2 = dot(d, d);
   float D = pa.w + pb.w + r.at;
@@ -218,10 +241,18 @@ __device__ __forceinline__ void proj_dist_elem(int i, const DistRec* __restrict_
     lam += dl;
     f3 a = xyz(pa) + nrm * (pa.w * dl);
     f3 b = xyz(pb) - nrm * (pb.w * dl);
-    st_vtx(P + r.a, with_w(a, pa.w), pol);
-    st_vtx(P + r.b, with_w(b, pb.w), pol);
+    vstore<SH>(P + r.a, with_w(a, pa.w), pol);
+    vstore<SH>(P + r.b, with_w(b, pb.w), pol);
   }
-  __stcs(lam_out + i, lam);
+  return lam;
+}
+
+template <bool SH = false>
+__device__ __forceinline__ void proj_dist_elem(int i, const DistRec* __restrict__ rec, float4* __restrict__ P,
+                                               const float* lam_in, float* lam_out, float4* __restrict__ tape) {
+  const DistRec r = ld_rec(rec + i);
+  const float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
+  __stcs(lam_out + i, proj_dist_core<SH>(r, P, lam, tape ? tape + 2 * i : nullptr));
 }
 
 // ---- 4-vertex constraints (bending, tet C_H, tet C_D), in relative coordinates
@@ -266,20 +297,17 @@ struct TetQuad {
 template <> struct Quad<2> : TetQuad<true> {};
 template <> struct Quad<3> : TetQuad<false> {};
 
-template <int KIND>
-__device__ __forceinline__ void proj_quad_elem(int i, const typename Quad<KIND>::Rec* __restrict__ rec,
-                                               float4* __restrict__ P, const float* lam_in, float* lam_out,
-                                               float4* __restrict__ tape) {
-  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
+template <int KIND, bool SH = false>
+__device__ __forceinline__ float proj_quad_core(const typename Quad<KIND>::Rec& r, float4* __restrict__ P,
+                                                float lam, float4* __restrict__ tape4) {
+  const uint64_t pol = SH ? 0 : vtx_policy();
   float4 p[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) p[k] = ld_vtx(P + r.v[k], pol);
-  if (tape) {
+  for (int k = 0; k < 4; ++k) p[k] = vload<SH>(P + r.v[k], pol);
+  if (tape4) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) __stcs(tape + 4 * i + k, p[k]);
+    for (int k = 0; k < 4; ++k) __stcs(tape4 + k, p[k]);
   }
-  float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
   const f3 x0 = xyz(p[0]);
   const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
   f3 g1, g2, g3;
@@ -291,13 +319,22 @@ __device__ __forceinline__ void proj_quad_elem(int i, const typename Quad<KIND>:
     if (D > 0.f) {
       float dl = (-C - r.at * lam) / D;
       lam += dl;
-      st_vtx(P + r.v[0], with_w(x0 + g0 * (p[0].w * dl), p[0].w), pol);
-      st_vtx(P + r.v[1], with_w(xyz(p[1]) + g1 * (p[1].w * dl), p[1].w), pol);
-      st_vtx(P + r.v[2], with_w(xyz(p[2]) + g2 * (p[2].w * dl), p[2].w), pol);
-      st_vtx(P + r.v[3], with_w(xyz(p[3]) + g3 * (p[3].w * dl), p[3].w), pol);
+      vstore<SH>(P + r.v[0], with_w(x0 + g0 * (p[0].w * dl), p[0].w), pol);
+      vstore<SH>(P + r.v[1], with_w(xyz(p[1]) + g1 * (p[1].w * dl), p[1].w), pol);
+      vstore<SH>(P + r.v[2], with_w(xyz(p[2]) + g2 * (p[2].w * dl), p[2].w), pol);
+      vstore<SH>(P + r.v[3], with_w(xyz(p[3]) + g3 * (p[3].w * dl), p[3].w), pol);
     }
   }
-  __stcs(lam_out + i, lam);
+  return lam;
+}
+
+template <int KIND, bool SH = false>
+__device__ __forceinline__ void proj_quad_elem(int i, const typename Quad<KIND>::Rec* __restrict__ rec,
+                                               float4* __restrict__ P, const float* lam_in, float* lam_out,
+                                               float4* __restrict__ tape) {
+  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
+  const float lam = lam_in ? ld_stream(lam_in + i) : 0.f;
+  __stcs(lam_out + i, proj_quad_core<KIND, SH>(r, P, lam, tape ? tape + 4 * i : nullptr));
 }
 
 // ---- contacts (Sec. 4.6): plane then sphere on the same vertex, equality springs for the
@@ -389,15 +426,12 @@ __device__ __forceinline__ void lb_finish(int i, float lambar, float abar, float
     lb[i] = make_float2(lambar, abar);
 }
 
-__device__ __forceinline__ void vjp_dist_elem(int i, const DistRec* __restrict__ rec, const float4* __restrict__ tape,
-                                              const float* __restrict__ lam_pre, float4* __restrict__ xbar,
-                                              float2* __restrict__ lb, double* __restrict__ acc, bool first,
-                                              bool last) {
-  const DistRec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  float4 pa = ld_stream(tape + 2 * i), pb = ld_stream(tape + 2 * i + 1);
-  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
-  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+// Reverse of one distance update from its tape (pa, pb), multiplier before the update and
+// (lambar', alphabar'); updates the two vertex adjoints and returns (lambar, alphabar).
+template <bool SH = false>
+__device__ __forceinline__ float2 vjp_dist_core(const DistRec& r, float4 pa, float4 pb, float lam, float2 l,
+                                                float4* __restrict__ xbar) {
+  const uint64_t pol = SH ? 0 : vtx_policy();
   f3 d = xyz(pa) - xyz(pb);
   float l2 = dot(d, d);
   float D = pa.w + pb.w + r.at;
@@ -406,7 +440,7 @@ __device__ __forceinline__ void vjp_dist_elem(int i, const DistRec* __restrict__
     float len = l2 * il;
     f3 nrm = d * il;
     float dl = (-(len - r.L) - r.at * lam) / D;
-    float4 xa4 = ld_vtx(xbar + r.a, pol), xb4 = ld_vtx(xbar + r.b, pol);
+    float4 xa4 = vload<SH>(xbar + r.a, pol), xb4 = vload<SH>(xbar + r.b, pol);
     f3 xa = xyz(xa4), xb = xyz(xb4);
     float s = l.x + pa.w * dot(nrm, xa) - pb.w * dot(nrm, xb);
     // H u for the distance constraint: (P (u_a - u_b))/l on a, the negative on b, with
@@ -416,29 +450,35 @@ __device__ __forceinline__ void vjp_dist_elem(int i, const DistRec* __restrict__
     float sD = s / D;
     xa = xa - nrm * sD + hv;
     xb = xb + nrm * sD - hv;
-    st_vtx(xbar + r.a, with_w(xa, 0.f), pol);
-    st_vtx(xbar + r.b, with_w(xb, 0.f), pol);
+    vstore<SH>(xbar + r.a, with_w(xa, 0.f), pol);
+    vstore<SH>(xbar + r.b, with_w(xb, 0.f), pol);
     l.y += -sD * (lam + dl);
     l.x -= r.at * sD;
   }
+  return l;
+}
+
+template <bool SH = false>
+__device__ __forceinline__ void vjp_dist_elem(int i, const DistRec* __restrict__ rec, const float4* __restrict__ tape,
+                                              const float* __restrict__ lam_pre, float4* __restrict__ xbar,
+                                              float2* __restrict__ lb, double* __restrict__ acc, bool first,
+                                              bool last) {
+  const DistRec r = ld_rec(rec + i);
+  float4 pa = ld_stream(tape + 2 * i), pb = ld_stream(tape + 2 * i + 1);
+  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  l = vjp_dist_core<SH>(r, pa, pb, lam, l, xbar);
   lb_finish(i, l.x, l.y, lb, acc, last);
 }
 
-template <int KIND>
-__device__ __forceinline__ void vjp_quad_elem(int i, const typename Quad<KIND>::Rec* __restrict__ rec,
-                                              const float4* __restrict__ tape, const float* __restrict__ lam_pre,
-                                              float4* __restrict__ xbar, float2* __restrict__ lb,
-                                              double* __restrict__ acc, bool first, bool last) {
-  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
-  const uint64_t pol = vtx_policy();
-  // every global read is independent of the arithmetic: issue them all first
-  float4 p[4], xb4[4];
+// Reverse of one 4-vertex update from its tape p[0..3]; see vjp_dist_core.
+template <int KIND, bool SH = false>
+__device__ __forceinline__ float2 vjp_quad_core(const typename Quad<KIND>::Rec& r, const float4 (&p)[4], float lam,
+                                                float2 l, float4* __restrict__ xbar) {
+  const uint64_t pol = SH ? 0 : vtx_policy();
+  float4 xb4[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) p[k] = ld_stream(tape + 4 * i + k);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) xb4[k] = ld_vtx(xbar + r.v[k], pol);
-  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
-  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  for (int k = 0; k < 4; ++k) xb4[k] = vload<SH>(xbar + r.v[k], pol);
   const f3 x0 = xyz(p[0]);
   const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
   f3 g1, g2, g3;
@@ -461,14 +501,30 @@ __device__ __forceinline__ void vjp_quad_elem(int i, const typename Quad<KIND>::
       Quad<KIND>::hvp(r, e1, e2, e3, du1, du2, du3, h1, h2, h3);
       const f3 hu1 = dpart(h1), hu2 = dpart(h2), hu3 = dpart(h3);
       const f3 hu0 = -(hu1 + hu2 + hu3);
-      st_vtx(xbar + r.v[0], with_w(xb0 - g0 * sD + hu0, 0.f), pol);
-      st_vtx(xbar + r.v[1], with_w(xb1 - g1 * sD + hu1, 0.f), pol);
-      st_vtx(xbar + r.v[2], with_w(xb2 - g2 * sD + hu2, 0.f), pol);
-      st_vtx(xbar + r.v[3], with_w(xb3 - g3 * sD + hu3, 0.f), pol);
+      vstore<SH>(xbar + r.v[0], with_w(xb0 - g0 * sD + hu0, 0.f), pol);
+      vstore<SH>(xbar + r.v[1], with_w(xb1 - g1 * sD + hu1, 0.f), pol);
+      vstore<SH>(xbar + r.v[2], with_w(xb2 - g2 * sD + hu2, 0.f), pol);
+      vstore<SH>(xbar + r.v[3], with_w(xb3 - g3 * sD + hu3, 0.f), pol);
       l.y += -sD * (lam + dl);
       l.x -= r.at * sD;
     }
   }
+  return l;
+}
+
+template <int KIND, bool SH = false>
+__device__ __forceinline__ void vjp_quad_elem(int i, const typename Quad<KIND>::Rec* __restrict__ rec,
+                                              const float4* __restrict__ tape, const float* __restrict__ lam_pre,
+                                              float4* __restrict__ xbar, float2* __restrict__ lb,
+                                              double* __restrict__ acc, bool first, bool last) {
+  const typename Quad<KIND>::Rec r = ld_rec(rec + i);
+  // every global read is independent of the arithmetic: issue them all first
+  float4 p[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p[k] = ld_stream(tape + 4 * i + k);
+  float lam = lam_pre ? ld_stream(lam_pre + i) : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : lb[i];
+  l = vjp_quad_core<KIND, SH>(r, p, lam, l, xbar);
   lb_finish(i, l.x, l.y, lb, acc, last);
 }
 
@@ -577,9 +633,11 @@ template <class Rec, bool VOL>
 __device__ __forceinline__ void finalize_elem(int i, const Rec* __restrict__ rec, const int* __restrict__ perm,
                                               const double* __restrict__ acc, float inv_dt2,
                                               double* __restrict__ out) {
+  const int j = perm[i];
+  if (j < 0) return;   // padding record
   double a = acc[i] * (double)inv_dt2;
   if constexpr (VOL) a = a / (double)rec[i].vol;
-  out[perm[i]] = a;
+  out[j] = a;
 }
 
 __device__ __forceinline__ void to_double_elem(int i, const float4* __restrict__ a, double* __restrict__ out) {

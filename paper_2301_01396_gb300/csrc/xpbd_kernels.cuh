@@ -62,6 +62,58 @@ void launch_finalize_compliance(SegType t, const void* rec, const int* perm, int
                                 const double* acc, float inv_dt2, double* out, cudaStream_t s);
 void launch_to_double(const float4* a, double* out, int V, cudaStream_t s);
 
+// ---- phase execution (xpbd_phase.cu): several consecutive colors per launch
+constexpr int kPhaseBlock = 256;                 // threads per CTA = constraints per chunk
+constexpr int kPhaseChunk = kPhaseBlock;
+constexpr int kPhaseMaxVerts = 6144;             // largest component a phase may hold
+constexpr int kPhaseGroupVerts = 1536;           // small components are packed up to this
+constexpr int kPhaseMaxStages = 8;
+constexpr int kPhaseSmemLimit = 226 * 1024;      // dynamic shared memory per CTA (below the 227 KB opt-in
+                                                 // maximum, leaving room for static shared memory)
+
+struct PhaseGroup {   // one CTA: a set of components of one phase
+  int vert_begin;     // first entry of its vertex list (global vertex ids, ascending)
+  int vert_count;     // local vertex vert_count is a zero-mass dummy that padding records use
+  int chunk_begin;    // its chunks, in forward execution order
+  int chunk_count;
+};
+struct PhaseChunk {   // up to kPhaseChunk constraints of one type and one color of a group
+  int type;
+  int begin;          // first record in the phase record array of its type (multiple of 4)
+  int count;          // multiple of 4
+  int pad;
+};
+struct PhaseLaunch {
+  const PhaseGroup* groups;
+  const PhaseChunk* chunks;
+  const int* pverts;
+  int slot_off[4];         // offset of each type in the multiplier slot space (multiples of 4)
+  const void* prec[4];     // phase records (vertex indices local to the group)
+  size_t tape_off[4];      // float4 offset of each type within one iteration's tape
+  float4* P;               // positions (forward / replay) or vertex adjoints (reverse)
+  const float* lam_in;     // multipliers before the iteration (NULL: zero)
+  float* lam_out;
+  float4* tape;            // this iteration's tape (written by replay, read by reverse)
+  float2* lb;              // reverse: (lambar, alphabar) per constraint
+  double* acc;             // reverse: float64 compliance-adjoint accumulator
+  int* err;                // device error word (bit 4: a bounded wait gave up)
+  // shared-memory layout, filled by the launcher: vertices, chunk table, stage ring
+  int vert_bytes;
+  int chunk_bytes;
+  int slot_bytes;          // bytes of one stage
+  int stages;              // stages in flight
+};
+// Sizes of one phase: its groups, the largest group's vertex and chunk counts and the
+// constraint types present (bit t set when type t occurs; selects the kernel).
+struct PhaseShape {
+  int n_groups, max_verts, max_chunks, type_mask;
+};
+cudaError_t phase_kernel_setup();
+// Shared memory a launch of this phase needs (0 if it cannot fit).
+size_t phase_smem_bytes(const PhaseShape& sh, bool reverse);
+void launch_phase_fwd(PhaseLaunch a, const PhaseShape& sh, bool record, cudaStream_t s);
+void launch_phase_vjp(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cudaStream_t s);
+
 // ---- utilities
 void launch_loss(const float4* ckx, const float* target, float* seed_out, double* partials,
                  int V, cudaStream_t s);

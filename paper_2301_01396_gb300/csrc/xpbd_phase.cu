@@ -1,0 +1,369 @@
+// Phase kernels: several consecutive colors in one launch.
+//
+// A phase is a run of consecutive colors whose constraints, taken together, split into
+// small connected components (constraints linked through shared vertices).  A component's
+// vertices are touched by no constraint of another component within the phase, so one
+// CTA can run all of the phase's colors on a group of components on its own: it stages the
+// group's vertices (forward) or vertex adjoints (reverse) in shared memory, runs the
+// colors in order (reverse order for the adjoint) with a barrier between colors, and
+// writes the vertices back once.  Every constraint sees exactly the values the color-by-
+// color launches would give it, in the same order, so results are those of the colored
+// Gauss-Seidel sweep; only the vertex traffic changes: one load and one store per vertex
+// per phase instead of one per color.
+//
+// The per-constraint streams (records, multipliers, tape, adjoint slots) are read once
+// each.  A group's constraints are cut into chunks of kPhaseChunk constraints of one type
+// and one color; thread 0 copies the streams of the next `stages` chunks into a ring of
+// shared-memory stages with bulk asynchronous copies (cp.async.bulk, completion counted on
+// one mbarrier per stage), so DRAM latency is hidden by copies in flight rather than by
+// resident threads, and the element code reads its record, multiplier and tape from
+// shared memory.  Each thread updates one constraint of a chunk; a barrier after every
+// chunk frees its stage and separates the colors.
+//
+// Padding: every chunk's count and start are multiples of 4 so that each stream starts on
+// a 16-byte boundary.  Padding constraints reference the group's dummy vertex (zero mass,
+// zero position, never written back) with alpha~ = 0, so they never move anything.
+//
+// Waits are bounded: a stage that has not arrived after about a second (far beyond any
+// copy) sets bit 4 of the error word; the CTA then waits, again bounded, for the copies it
+// has in flight and returns.
+#include "xpbd_elems.cuh"
+
+namespace xpbd {
+
+namespace {
+
+constexpr long long kWaitCycles = 1ll << 31;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity` of barrier b to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned);
+// completion is counted in bytes on barrier b.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+
+__host__ __device__ constexpr unsigned rec_size(int t) {
+  return t == SEG_DIST ? (unsigned)sizeof(DistRec) : (t == SEG_BEND ? (unsigned)sizeof(BendRec) : (unsigned)sizeof(TetRec));
+}
+__host__ __device__ constexpr unsigned nverts(int t) { return t == SEG_DIST ? 2u : 4u; }
+
+// Stage layout of a chunk of n constraints of type t: records (n R), multipliers in (4 n),
+// and for the reverse sweep the tape (16 nv n), (lambar, alphabar) (8 n) and the float64
+// accumulators (8 n).  Every part starts on a 16-byte boundary because n is a multiple of 4.
+struct StageLayout {
+  unsigned lam, tape, lb, acc;
+  __device__ StageLayout(int t, unsigned n) {
+    lam = n * rec_size(t);
+    tape = lam + 4 * n;
+    lb = tape + 16 * nverts(t) * n;
+    acc = lb + 8 * n;
+  }
+};
+
+// Issued by thread 0: copies of chunk c's streams into stage `st`, counted on barrier b.
+template <bool REVERSE>
+__device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChunk& c, unsigned char* st,
+                                            uint64_t* b, bool first, bool last) {
+  const int t = c.type;
+  const unsigned n = (unsigned)c.count, R = rec_size(t), nv = nverts(t);
+  const StageLayout L(t, n);
+  const size_t so = (size_t)a.slot_off[t] + c.begin;
+  unsigned total = n * R + (a.lam_in ? 4 * n : 0);
+  if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * n) + (last ? 8 * n : 0);
+  mbar_expect_tx(b, total);
+  bulk_g2s(st, (const char*)a.prec[t] + (size_t)c.begin * R, n * R, b);
+  if (a.lam_in) bulk_g2s(st + L.lam, a.lam_in + so, 4 * n, b);
+  if (REVERSE) {
+    bulk_g2s(st + L.tape, a.tape + a.tape_off[t] + (size_t)c.begin * nv, 16 * nv * n, b);
+    if (!first) bulk_g2s(st + L.lb, a.lb + so, 8 * n, b);
+    if (last) bulk_g2s(st + L.acc, a.acc + so, 8 * n, b);
+  }
+}
+
+template <int TM>
+__device__ __forceinline__ constexpr bool has(int t) {
+  return (TM >> t) & 1;
+}
+
+// Forward / replay update of constraint `tid` of chunk c from stage st.
+template <bool RECORD, int TM>
+__device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk& c, const unsigned char* st,
+                                          float4* sv) {
+  const int t = c.type, tid = threadIdx.x;
+  if (tid >= c.count) return;
+  const StageLayout L(t, (unsigned)c.count);
+  const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
+  const size_t gi = (size_t)a.slot_off[t] + c.begin + tid;
+  float4* tp = RECORD ? a.tape + a.tape_off[t] + (size_t)(c.begin + tid) * nverts(t) : nullptr;
+  float lo = lam;
+  if (has<TM>(SEG_DIST) && t == SEG_DIST)
+    lo = proj_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], sv, lam, tp);
+  else if (has<TM>(SEG_BEND) && t == SEG_BEND)
+    lo = proj_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], sv, lam, tp);
+  else if (has<TM>(SEG_TETH) && t == SEG_TETH)
+    lo = proj_quad_core<2, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp);
+  else if (has<TM>(SEG_TETD) && t == SEG_TETD)
+    lo = proj_quad_core<3, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp);
+  __stcs(a.lam_out + gi, lo);
+}
+
+// Reverse update of constraint `tid` of chunk c from stage st.
+template <int TM>
+__device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk& c, const unsigned char* st,
+                                          float4* sx, bool first, bool last) {
+  const int t = c.type, tid = threadIdx.x;
+  if (tid >= c.count) return;
+  const StageLayout L(t, (unsigned)c.count);
+  const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
+  float2 l = first ? make_float2(0.f, 0.f) : reinterpret_cast<const float2*>(st + L.lb)[tid];
+  const size_t gi = (size_t)a.slot_off[t] + c.begin + tid;
+  const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + (size_t)tid * nverts(t);
+  if (has<TM>(SEG_DIST) && t == SEG_DIST) {
+    l = vjp_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], tp[0], tp[1], lam, l, sx);
+  } else {
+    const float4 p[4] = {tp[0], tp[1], tp[2], tp[3]};
+    if (has<TM>(SEG_BEND) && t == SEG_BEND)
+      l = vjp_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], p, lam, l, sx);
+    else if (has<TM>(SEG_TETH) && t == SEG_TETH)
+      l = vjp_quad_core<2, true>(reinterpret_cast<const TetRec*>(st)[tid], p, lam, l, sx);
+    else if (has<TM>(SEG_TETD) && t == SEG_TETD)
+      l = vjp_quad_core<3, true>(reinterpret_cast<const TetRec*>(st)[tid], p, lam, l, sx);
+  }
+  if (last)
+    a.acc[gi] = reinterpret_cast<const double*>(st + L.acc)[tid] + (double)l.y;
+  else
+    a.lb[gi] = l;
+}
+
+}  // namespace
+
+// Resident CTAs per SM each kernel is compiled for.  The stage ring sizes shared memory for
+// three forward CTAs or two reverse CTAs per SM.
+#ifndef XPBD_PHASE_FWD_MIN_BLOCKS
+#define XPBD_PHASE_FWD_MIN_BLOCKS 3
+#endif
+#ifndef XPBD_PHASE_VJP_MIN_BLOCKS
+#define XPBD_PHASE_VJP_MIN_BLOCKS 2
+#endif
+
+// Gathers the group's vertices (or vertex adjoints) into shared memory, 8 independent
+// loads in flight per thread, and zeroes the dummy vertex.
+__device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, const int* __restrict__ vlist, int n,
+                                                float4* sv) {
+  constexpr int U = 8;
+  for (int v0 = threadIdx.x; v0 < n; v0 += U * blockDim.x) {
+    int idx[U];
+    float4 val[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = v0 + u * (int)blockDim.x;
+      idx[u] = v < n ? vlist[v] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (idx[u] >= 0) val[u] = P[idx[u]];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = v0 + u * (int)blockDim.x;
+      if (v < n) sv[v] = val[u];
+    }
+  }
+  if (threadIdx.x == 0) sv[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// MODE 0 forward, 1 replay (forward + tape), 2 reverse.  One CTA per group.
+template <int MODE, int TM>
+__global__ void __launch_bounds__(kPhaseBlock, MODE == 2 ? XPBD_PHASE_VJP_MIN_BLOCKS : XPBD_PHASE_FWD_MIN_BLOCKS)
+    k_phase(PhaseLaunch a, bool first, bool last) {
+  constexpr bool REV = MODE == 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar[kPhaseMaxStages];
+  __shared__ int abort_run;
+  float4* sv = reinterpret_cast<float4*>(smem);
+  PhaseChunk* sch = reinterpret_cast<PhaseChunk*>(smem + a.vert_bytes);
+  unsigned char* stage = smem + a.vert_bytes + a.chunk_bytes;
+  const PhaseGroup G = a.groups[blockIdx.x];
+  const PhaseChunk* ch = a.chunks + G.chunk_begin;
+  const int nch = G.chunk_count, S = a.stages;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    abort_run = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0 starts the first stages from the global chunk table; everyone else copies the
+  // table to shared memory and gathers the vertices meanwhile
+  if (threadIdx.x == 0)
+    for (int k = 0; k < S && k < nch; ++k)
+      issue_chunk<REV>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &bar[k], first, last);
+  for (int i = threadIdx.x; i < nch; i += blockDim.x) sch[i] = ch[i];
+  gather_vertices(a.P, a.pverts + G.vert_begin, G.vert_count, sv);
+  __syncthreads();
+  for (int k = 0; k < nch; ++k) {
+    const int s = k % S;
+    unsigned char* st = stage + (size_t)s * a.slot_bytes;
+    const PhaseChunk c = sch[REV ? nch - 1 - k : k];
+    if (mbar_wait(&bar[s], (unsigned)(k / S) & 1u)) {
+      if (REV)
+        vjp_chunk<TM>(a, c, st, sv, first, last);
+      else
+        fwd_chunk<MODE == 1, TM>(a, c, st, sv);
+    } else {
+      abort_run = 1;
+    }
+    __syncthreads();
+    if (abort_run) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.err, 4);
+        for (int j = k; j < k + S && j < nch; ++j) mbar_wait(&bar[j % S], (unsigned)(j / S) & 1u);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && k + S < nch)
+      issue_chunk<REV>(a, sch[REV ? nch - 1 - (k + S) : k + S], st, &bar[s], first, last);
+  }
+  const int* vlist = a.pverts + G.vert_begin;
+  for (int v = threadIdx.x; v < G.vert_count; v += blockDim.x) a.P[vlist[v]] = sv[v];
+}
+
+namespace {
+
+// Type sets with their own kernels: cloth (distance + bending), solids (the two tet
+// constraints, with or without distance constraints) and everything.
+constexpr int kMaskCloth = 0x3, kMaskSolid = 0xD, kMaskAll = 0xF;
+
+int kernel_mask(int type_mask) {
+  if ((type_mask & ~kMaskCloth) == 0) return kMaskCloth;
+  if ((type_mask & ~kMaskSolid) == 0) return kMaskSolid;
+  return kMaskAll;
+}
+
+unsigned elem_stage_bytes(int t, bool rev) {
+  return rec_size(t) + 4 + (rev ? 16 * nverts(t) + 16 : 0);
+}
+
+struct Plan {
+  int vert_bytes = 0, chunk_bytes = 0, slot_bytes = 0, stages = 0;
+  size_t smem() const { return (size_t)vert_bytes + chunk_bytes + (size_t)stages * slot_bytes; }
+};
+
+// Shared memory of a launch: the largest group's vertices (+ the dummy), its chunk table and
+// as many stages (2..kPhaseMaxStages) as fit in the shared memory of 3 (forward) or 2
+// (reverse) resident CTAs per SM.
+Plan stage_plan(const PhaseShape& sh, bool rev) {
+  Plan p;
+  p.vert_bytes = ((sh.max_verts + 1) * 16 + 127) / 128 * 128;
+  p.chunk_bytes = (sh.max_chunks * (int)sizeof(PhaseChunk) + 127) / 128 * 128;
+  unsigned e = 0;
+  for (int t = 0; t < 4; ++t)
+    if ((sh.type_mask >> t) & 1) e = std::max(e, elem_stage_bytes(t, rev));
+  p.slot_bytes = (int)(e * kPhaseChunk);
+  if (p.slot_bytes == 0) return p;
+  const int per_sm = 228 * 1024, ctas = rev ? XPBD_PHASE_VJP_MIN_BLOCKS : XPBD_PHASE_FWD_MIN_BLOCKS;
+  const int fixed = p.vert_bytes + p.chunk_bytes;
+  const int budget = per_sm / ctas - 1024 - 128;
+  int S = (budget - fixed) / p.slot_bytes;
+  S = std::min(std::max(S, 2), kPhaseMaxStages);
+  while (S >= 2 && fixed + S * p.slot_bytes > kPhaseSmemLimit) --S;
+  p.stages = S >= 2 ? S : 0;
+  return p;
+}
+
+template <int MODE, int TM>
+cudaError_t setup_one() {
+  cudaError_t e = cudaFuncSetAttribute(k_phase<MODE, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPhaseSmemLimit);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_phase<MODE, TM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+template <int TM>
+cudaError_t setup_mask() {
+  cudaError_t e = setup_one<0, TM>();
+  if (e == cudaSuccess) e = setup_one<1, TM>();
+  if (e == cudaSuccess) e = setup_one<2, TM>();
+  return e;
+}
+
+template <int MODE>
+void launch_mode(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cudaStream_t s) {
+  if (sh.n_groups <= 0) return;
+  const Plan p = stage_plan(sh, MODE == 2);
+  a.vert_bytes = p.vert_bytes;
+  a.chunk_bytes = p.chunk_bytes;
+  a.slot_bytes = p.slot_bytes;
+  a.stages = p.stages;
+  const size_t smem = p.smem();
+  switch (kernel_mask(sh.type_mask)) {
+    case kMaskCloth: k_phase<MODE, kMaskCloth><<<sh.n_groups, kPhaseBlock, smem, s>>>(a, first, last); break;
+    case kMaskSolid: k_phase<MODE, kMaskSolid><<<sh.n_groups, kPhaseBlock, smem, s>>>(a, first, last); break;
+    default: k_phase<MODE, kMaskAll><<<sh.n_groups, kPhaseBlock, smem, s>>>(a, first, last);
+  }
+}
+
+}  // namespace
+
+cudaError_t phase_kernel_setup() {
+  cudaError_t e = setup_mask<kMaskCloth>();
+  if (e == cudaSuccess) e = setup_mask<kMaskSolid>();
+  if (e == cudaSuccess) e = setup_mask<kMaskAll>();
+  return e;
+}
+
+size_t phase_smem_bytes(const PhaseShape& sh, bool reverse) {
+  const Plan p = stage_plan(sh, reverse);
+  return p.stages < 2 ? 0 : p.smem();
+}
+
+void launch_phase_fwd(PhaseLaunch a, const PhaseShape& sh, bool record, cudaStream_t s) {
+  if (record)
+    launch_mode<1>(a, sh, false, false, s);
+  else
+    launch_mode<0>(a, sh, false, false, s);
+}
+
+void launch_phase_vjp(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cudaStream_t s) {
+  launch_mode<2>(a, sh, first, last, s);
+}
+
+}  // namespace xpbd

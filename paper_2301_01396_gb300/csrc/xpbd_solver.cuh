@@ -83,11 +83,33 @@ struct xpbd_solver {
   bool prof_on = false;
   int64_t launches[XPBD_KERNEL_CLASSES] = {0};
   int64_t units[XPBD_KERNEL_CLASSES] = {0};
+  double alg_bytes[XPBD_KERNEL_CLASSES] = {0};
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   struct Timed { int cls; cudaEvent_t a, b; };
   std::vector<Timed> timed;
-  size_t tape_per_iter() const {  // float4 entries per iteration
+  // phase execution plan: runs of consecutive colors launched together (see xpbd_phase.cu)
+  bool use_phases = false;
+  struct PhaseHost {
+    int first_group = 0, n_groups = 0, c0 = 0, ncolors = 0, max_verts = 0, max_chunks = 0;
+    int type_mask = 0;                      // bit t: constraint type t occurs
+    PhaseShape shape() const { return PhaseShape{n_groups, max_verts, max_chunks, type_mask}; }
+    int64_t units = 0;                      // constraints updated by one launch
+    double bytes_fwd = 0, bytes_replay = 0, bytes_vjp = 0;   // algorithmic bytes per launch
+  };
+  std::vector<PhaseHost> phases;
+  void* d_prec[4] = {nullptr, nullptr, nullptr, nullptr};     // phase-ordered records (padded)
+  int n_prec[4] = {0, 0, 0, 0};                               // phase records per type
+  int pslot_off[4] = {0, 0, 0, 0};                            // their offsets in the slot space
+  size_t ptape_off[4] = {0, 0, 0, 0};                         // float4 offsets in an iteration's tape
+  int* d_pperm = nullptr;                                     // phase record -> constraint id (-1: pad)
+  PhaseGroup* d_groups = nullptr;
+  PhaseChunk* d_chunks = nullptr;
+  int* d_pverts = nullptr;
+  // Per-constraint slot space of the multiplier / adjoint buffers and float4 entries of
+  // one iteration's tape: large enough for the per-color layout and the padded phase layout.
+  size_t slots = 0, tape_slots = 0;
+  size_t tape_per_iter() const {  // float4 entries per iteration, per-color layout
     return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
   }
 };
@@ -101,11 +123,34 @@ inline cudaEvent_t next_event(xpbd_solver* h) {
   return h->ev_pool[h->ev_used++];
 }
 
+// Algorithmic bytes per constraint of the one-color launches (steady-state iteration):
+//   forward  distance: record 16 + lambda r/w 8 + two vertices read and written 64 = 88;
+//            bending / tet: record 32 / 64 + lambda 8 + four vertices r/w 128 = 168 / 200
+//   replay   forward + the pre-projection tape write (16 B per vertex): 120 / 232 / 264
+//   reverse  distance: record 16 + tape 32 + lambda 4 + vertex adjoints r/w 64 +
+//            (lambar, alphabar) r/w 16 = 132; bending 244; tets 276
+inline double unit_bytes(int cls) {
+  switch (cls) {
+    case XPBD_K_FWD_DIST: return 88;
+    case XPBD_K_FWD_BEND: return 168;
+    case XPBD_K_FWD_TETH: case XPBD_K_FWD_TETD: return 200;
+    case XPBD_K_REPLAY_DIST: return 120;
+    case XPBD_K_REPLAY_BEND: return 232;
+    case XPBD_K_REPLAY_TETH: case XPBD_K_REPLAY_TETD: return 264;
+    case XPBD_K_VJP_DIST: return 132;
+    case XPBD_K_VJP_BEND: return 244;
+    case XPBD_K_VJP_TETH: case XPBD_K_VJP_TETD: return 276;
+    default: return 0;
+  }
+}
+
 // Counts (and, while profiling, times) one kernel launch of class `cls` covering `units`
-// constraints or vertices.  Launches with no work are skipped by the launchers and not counted.
+// constraints or vertices and moving `bytes` algorithmic bytes (< 0: units x unit_bytes).
+// Launches with no work are skipped by the launchers and not counted.
 template <class F>
-inline void launch(xpbd_solver* h, int cls, int64_t units, cudaStream_t s, F&& f) {
+inline void launch(xpbd_solver* h, int cls, int64_t units, cudaStream_t s, F&& f, double bytes = -1.0) {
   if (units <= 0) return;
+  h->alg_bytes[cls] += bytes >= 0 ? bytes : (double)units * unit_bytes(cls);
   cudaEvent_t a = nullptr, b = nullptr;
   if (h->prof_on) {
     a = next_event(h);

@@ -228,8 +228,17 @@ def _grid_topology(n: int, diagonals: str, bending: bool):
 
 def cloth_grid(n: int, size: float = 1.0, *, vertex_mass: Optional[float] = None,
                areal_density: float = 2.56, diagonals: str = "both", bending: bool = False,
-               pins=((0, 0), (-1, 0)), y0: float = 0.0, origin=(0.0, 0.0)) -> dict:
+               pins=((0, 0), (-1, 0)), y0: float = 0.0, origin=(0.0, 0.0), coloring: str = "pattern",
+               tile: int = 32) -> dict:
     """An n x n vertex cloth square in the x-z plane at height y0.
+
+    coloring="pattern": one color per constraint family and parity (2 per edge family, 4
+    per hinge family).  coloring="tiled": the grid is cut into tile x tile blocks of
+    vertices, each constraint belongs to the block of its first vertex, and blocks are
+    classed by the parities of their block coordinates (4 classes); the colors are the
+    pattern colors restricted to one class, ordered class by class.  Blocks of one class
+    are a block apart, so within a class every block's constraints only touch that block
+    and its one-vertex border: a class's 16 colors run block by block.
 
     Returns the raw arrays (positions, masses, topology, coloring) of a cloth grid; the
     ``cloth_*`` config builders below turn them into a Scene."""
@@ -246,6 +255,20 @@ def cloth_grid(n: int, size: float = 1.0, *, vertex_mass: Optional[float] = None
         pj = pj % n
         w[pj * n + pi] = 0.0
     classes = _grid_topology(n, diagonals, bending)
+    if coloring == "tiled":
+        if tile < 4:
+            raise ValueError("tile must be >= 4 (a hinge spans three rows)")
+        tiled = []
+        for cls in range(4):
+            for kind, idx in classes:
+                first = idx[:, 0]
+                ti, tj = (first % n) // tile, (first // n) // tile
+                sel = ((ti % 2) + 2 * (tj % 2)) == cls
+                if np.any(sel):
+                    tiled.append((kind, idx[sel]))
+        classes = tiled
+    elif coloring != "pattern":
+        raise ValueError("coloring must be 'pattern' or 'tiled'")
     dist = [c[1] for c in classes if c[0] == "dist"]
     bend = [c[1] for c in classes if c[0] == "bend"]
     dist_idx = np.concatenate(dist).astype(np.int32) if dist else np.zeros((0, 2), np.int32)
@@ -321,11 +344,13 @@ def ground_cloth(n: int = 256, *, steps: int = 100, iters: int = 30, seed: int =
 
 
 def sphere_cloth(n: int = 2950, *, steps: int = 60, iters: int = 15, seed: int = 4,
-                 radius: float = 0.3, force_scale: float = 0.2) -> Scene:
+                 radius: float = 0.3, force_scale: float = 0.2, coloring: str = "pattern",
+                 tile: int = 32) -> Scene:
     """High-resolution cloth (structural + both diagonals + bending) with no pins, falling
     on an analytic sphere, driven by a per-frame global force G_n (3 per step) and a
     time-constant smooth per-vertex wind field W."""
-    g = cloth_grid(n, 1.0, areal_density=2.56, diagonals="both", bending=True, pins=())
+    g = cloth_grid(n, 1.0, areal_density=2.56, diagonals="both", bending=True, pins=(),
+                   coloring=coloring, tile=tile)
     rng = np.random.default_rng(seed)
     centre = np.array([0.5, -0.35, 0.5]) + rng.uniform(-0.05, 0.05, 3)
     alpha = lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0])

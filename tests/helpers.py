@@ -20,8 +20,9 @@ def single_spring(L=0.5, stretch0=0.0, mass=0.01, alpha=1e-3, dt=1.0 / 60.0):
 
 def small_cloth(n=5, *, bending=True, diagonals="both", pins=((0, 0), (-1, 0)), seed=0,
                 plane_h=None, steps=4, iters=3, gravity=(0.0, -9.81, 0.0), jitter=0.0,
-                v_scale=0.0, stretch=1e-3, bend=1e-2):
-    g = scenes.cloth_grid(n, 1.0, areal_density=2.56, diagonals=diagonals, bending=bending, pins=pins)
+                v_scale=0.0, stretch=1e-3, bend=1e-2, coloring="pattern", tile=48):
+    g = scenes.cloth_grid(n, 1.0, areal_density=2.56, diagonals=diagonals, bending=bending, pins=pins,
+                          coloring=coloring, tile=tile)
     rng = np.random.default_rng(seed)
     alpha = scenes.lognormal_cloth_compliance(rng, g["dist_idx"].shape[0], g["bend_idx"].shape[0],
                                               stretch=stretch, bend=bend)

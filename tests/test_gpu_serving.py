@@ -69,10 +69,11 @@ def test_alone_equals_mix_and_single_request_api():
         mixed = _host(srv.result(t))
         for k in alone[j]:
             assert np.array_equal(mixed[k], alone[j][k]), (j, k)
-    # the one-request API on the same inputs: the same element code compiled into other
-    # kernels, so the two agree to float32 rounding (not bitwise)
+    # the one-request API on the same inputs, launched color by color like the server (its
+    # multi-color phase launches are compared with this mode in the parity tests): the same
+    # element code compiled into other kernels, so the two agree to float32 rounding
     for j, (sc, target) in enumerate(reqs):
-        solver = binding.Solver.from_scene(sc)
+        solver = binding.Solver.from_scene(sc, exec_mode=1)
         p = binding.params_from_scene(sc)
         ck = solver.forward(p, sc.steps, sc.iters, to_dev(sc.x0), to_dev(sc.v0))
         loss, seeds = solver.loss(ck, {sc.steps: to_dev(target)})

@@ -23,7 +23,9 @@ def test_static_forward_matches_allocating_forward_on_two_calls():
     shared array), each compared with the allocating entry point on the same inputs."""
     sc = helpers.small_cloth(48, bending=True, diagonals="one", steps=6, iters=8, plane_h=-0.03,
                              v_scale=0.3, seed=33)
-    solver = binding.Solver.from_scene(sc)
+    # the allocating entry point in its color-by-color mode, the launch structure the static
+    # entry point uses (the multi-color phase mode is compared with it in the parity tests)
+    solver = binding.Solver.from_scene(sc, exec_mode=1)
     p = binding.params_from_scene(sc)
     x0 = to_dev(sc.x0)
     inputs = [to_dev(sc.v0), to_dev(0.5 * sc.v0 + np.array([0.0, -0.4, 0.0]) * (sc.inv_mass[:, None] > 0))]
@@ -38,7 +40,7 @@ def test_static_forward_matches_allocating_forward_on_two_calls():
 
 def test_static_forward_tet_block_with_contacts():
     sc = helpers.small_tets(4, steps=5, iters=6, y0=0.004, v_scale=0.05)
-    solver = binding.Solver.from_scene(sc)
+    solver = binding.Solver.from_scene(sc, exec_mode=1)
     p = binding.params_from_scene(sc)
     x0, v0 = to_dev(sc.x0), to_dev(sc.v0)
     ref = solver.forward(p, sc.steps, sc.iters, x0, v0)
