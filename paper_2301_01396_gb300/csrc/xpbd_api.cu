@@ -432,6 +432,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
       ph_info.max_verts = std::max(ph_info.max_verts, G.vert_count);
       vbytes += 36.0 * G.vert_count;   // vertex index + one float4 read + one write
       for (int ci = 0; ci < ncol; ++ci) {
+        const size_t color_first = chunks.size();
         for (int t = 0; t < 4; ++t) {
           std::vector<int>& b = bucket[((size_t)g * ncol + ci) * 4 + t];
           if (b.empty()) continue;
@@ -457,7 +458,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
             ck.type = t;
             ck.begin = begin + off;
             ck.count = std::min(kPhaseChunk, total - off);
-            ck.pad = 0;
+            ck.flags = 0;
             chunks.push_back(ck);
           }
           ph_info.type_mask |= 1 << t;
@@ -466,6 +467,10 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
           rbytes_f += n * (rec_bytes[t] + 8.0);
           rbytes_r += n * (rec_bytes[t] + 8.0 + 16.0 * nv);
           rbytes_v += n * (rec_bytes[t] + 16.0 * nv + 4.0 + 16.0);
+        }
+        if (chunks.size() > color_first) {
+          chunks[color_first].flags |= kChunkColorFirst;
+          chunks.back().flags |= kChunkColorLast;
         }
       }
       G.chunk_count = (int)chunks.size() - G.chunk_begin;

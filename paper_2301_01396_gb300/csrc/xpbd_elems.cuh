@@ -222,13 +222,13 @@ __device__ __forceinline__ void predict_elem(int i, const float4* __restrict__ c
 // lam_in and lam_out may alias (in-place forward), so they are not __restrict__.
 template <bool SH = false>
 __device__ __forceinline__ float proj_dist_core(const DistRec& r, float4* __restrict__ P, float lam,
-                                                float4* __restrict__ tape2) {
+                                                float4* __restrict__ tape2, int ts = 1) {
   const uint64_t pol = SH ? 0 : vtx_policy();
   float4 pa = vload<SH>(P + r.a, pol);
   float4 pb = vload<SH>(P + r.b, pol);
-  if (tape2) {
+  if (tape2) {   // the two pre-projection positions, ts float4 apart
     __stcs(tape2, pa);
-    __stcs(tape2 + 1, pb);
+    __stcs(tape2 + ts, pb);
   }
   f3 d = xyz(pa) - xyz(pb);
   float l2 = dot(d, d);
@@ -299,14 +299,14 @@ template <> struct Quad<3> : TetQuad<false> {};
 
 template <int KIND, bool SH = false>
 __device__ __forceinline__ float proj_quad_core(const typename Quad<KIND>::Rec& r, float4* __restrict__ P,
-                                                float lam, float4* __restrict__ tape4) {
+                                                float lam, float4* __restrict__ tape4, int ts = 1) {
   const uint64_t pol = SH ? 0 : vtx_policy();
   float4 p[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) p[k] = vload<SH>(P + r.v[k], pol);
   if (tape4) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) __stcs(tape4 + k, p[k]);
+    for (int k = 0; k < 4; ++k) __stcs(tape4 + k * ts, p[k]);
   }
   const f3 x0 = xyz(p[0]);
   const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;

@@ -81,8 +81,9 @@ struct PhaseChunk {   // up to kPhaseChunk constraints of one type and one color
   int type;
   int begin;          // first record in the phase record array of its type (multiple of 4)
   int count;          // multiple of 4
-  int pad;
+  int flags;          // kChunkColorFirst / kChunkColorLast: first / last chunk of its color
 };
+constexpr int kChunkColorFirst = 1, kChunkColorLast = 2;
 struct PhaseLaunch {
   const PhaseGroup* groups;
   const PhaseChunk* chunks;

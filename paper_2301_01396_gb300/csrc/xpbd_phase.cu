@@ -29,6 +29,13 @@
 // has in flight and returns.
 #include "xpbd_elems.cuh"
 
+// Tape layout of a chunk: struct of arrays (vertex k of constraint i at k * count + i, so
+// the staged reads of the reverse sweep are free of shared-memory bank conflicts) or one
+// constraint's vertices side by side.
+#ifndef XPBD_PHASE_TAPE_SOA
+#define XPBD_PHASE_TAPE_SOA 1
+#endif
+
 namespace xpbd {
 
 namespace {
@@ -133,16 +140,22 @@ __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk
   const StageLayout L(t, (unsigned)c.count);
   const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
   const size_t gi = (size_t)a.slot_off[t] + c.begin + tid;
+#if XPBD_PHASE_TAPE_SOA
+  float4* tp = RECORD ? a.tape + a.tape_off[t] + (size_t)c.begin * nverts(t) + tid : nullptr;
+  const int ts = c.count;
+#else
   float4* tp = RECORD ? a.tape + a.tape_off[t] + (size_t)(c.begin + tid) * nverts(t) : nullptr;
+  const int ts = 1;
+#endif
   float lo = lam;
   if (has<TM>(SEG_DIST) && t == SEG_DIST)
-    lo = proj_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], sv, lam, tp);
+    lo = proj_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], sv, lam, tp, ts);
   else if (has<TM>(SEG_BEND) && t == SEG_BEND)
-    lo = proj_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], sv, lam, tp);
+    lo = proj_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], sv, lam, tp, ts);
   else if (has<TM>(SEG_TETH) && t == SEG_TETH)
-    lo = proj_quad_core<2, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp);
+    lo = proj_quad_core<2, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp, ts);
   else if (has<TM>(SEG_TETD) && t == SEG_TETD)
-    lo = proj_quad_core<3, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp);
+    lo = proj_quad_core<3, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp, ts);
   __stcs(a.lam_out + gi, lo);
 }
 
@@ -156,11 +169,17 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
   const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
   float2 l = first ? make_float2(0.f, 0.f) : reinterpret_cast<const float2*>(st + L.lb)[tid];
   const size_t gi = (size_t)a.slot_off[t] + c.begin + tid;
+#if XPBD_PHASE_TAPE_SOA
+  const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + tid;
+  const int ts = c.count;
+#else
   const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + (size_t)tid * nverts(t);
+  const int ts = 1;
+#endif
   if (has<TM>(SEG_DIST) && t == SEG_DIST) {
-    l = vjp_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], tp[0], tp[1], lam, l, sx);
+    l = vjp_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], tp[0], tp[ts], lam, l, sx);
   } else {
-    const float4 p[4] = {tp[0], tp[1], tp[2], tp[3]};
+    const float4 p[4] = {tp[0], tp[ts], tp[2 * ts], tp[3 * ts]};
     if (has<TM>(SEG_BEND) && t == SEG_BEND)
       l = vjp_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], p, lam, l, sx);
     else if (has<TM>(SEG_TETH) && t == SEG_TETH)
@@ -176,10 +195,10 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
 
 }  // namespace
 
-// Resident CTAs per SM each kernel is compiled for.  The stage ring sizes shared memory for
-// three forward CTAs or two reverse CTAs per SM.
+// Resident CTAs per SM each kernel is compiled for; the stage ring is sized so that the
+// shared memory of that many CTAs fits in one SM.
 #ifndef XPBD_PHASE_FWD_MIN_BLOCKS
-#define XPBD_PHASE_FWD_MIN_BLOCKS 3
+#define XPBD_PHASE_FWD_MIN_BLOCKS 4
 #endif
 #ifndef XPBD_PHASE_VJP_MIN_BLOCKS
 #define XPBD_PHASE_VJP_MIN_BLOCKS 2
