@@ -63,8 +63,9 @@ void launch_finalize_compliance(SegType t, const void* rec, const int* perm, int
 void launch_to_double(const float4* a, double* out, int V, cudaStream_t s);
 
 // ---- phase execution (xpbd_phase.cu): several consecutive colors per launch
-constexpr int kPhaseBlock = 256;                 // threads per CTA = constraints per chunk
+constexpr int kPhaseBlock = 256;                 // consumer threads per CTA = constraints per chunk
 constexpr int kPhaseChunk = kPhaseBlock;
+constexpr int kPhaseThreads = kPhaseBlock + 32;  // + one producer warp
 constexpr int kPhaseMaxVerts = 6144;             // largest component a phase may hold
 constexpr int kPhaseGroupVerts = 1536;           // small components are packed up to this
 constexpr int kPhaseMaxStages = 8;

@@ -13,12 +13,12 @@
 //
 // The per-constraint streams (records, multipliers, tape, adjoint slots) are read once
 // each.  A group's constraints are cut into chunks of kPhaseChunk constraints of one type
-// and one color; thread 0 copies the streams of the next `stages` chunks into a ring of
+// and one color; a producer thread copies the streams of the next `stages` chunks into a ring of
 // shared-memory stages with bulk asynchronous copies (cp.async.bulk, completion counted on
 // one mbarrier per stage), so DRAM latency is hidden by copies in flight rather than by
 // resident threads, and the element code reads its record, multiplier and tape from
-// shared memory.  Each thread updates one constraint of a chunk; a barrier after every
-// chunk frees its stage and separates the colors.
+// shared memory.  Each consumer thread updates one constraint of a chunk; a producer warp
+// issues the copies, so no consumer carries that work on its critical path.
 //
 // Padding: every chunk's count and start are multiples of 4 so that each stream starts on
 // a 16-byte boundary.  Padding constraints reference the group's dummy vertex (zero mass,
@@ -106,7 +106,7 @@ struct StageLayout {
   }
 };
 
-// Issued by thread 0: copies of chunk c's streams into stage `st`, counted on barrier b.
+// Issued by the producer: copies of chunk c's streams into stage `st`, counted on barrier b.
 template <bool REVERSE>
 __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChunk& c, unsigned char* st,
                                             uint64_t* b, bool first, bool last) {
@@ -229,13 +229,26 @@ __device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, co
   if (threadIdx.x == 0) sv[n] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// MODE 0 forward, 1 replay (forward + tape), 2 reverse.  One CTA per group.
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Barrier among the consumer warps only (named barrier 1; the producer warp is not part).
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kPhaseBlock) : "memory");
+}
+
+// MODE 0 forward, 1 replay (forward + tape), 2 reverse.  One CTA per group: kPhaseBlock
+// consumer threads (one constraint of a chunk each) and one producer warp whose first lane
+// keeps the stage ring filled.  A stage is refilled once all consumer warps have released
+// it (`empty`, one arrival per warp); the consumers synchronise with each other only where
+// a color ends.
 template <int MODE, int TM>
-__global__ void __launch_bounds__(kPhaseBlock, MODE == 2 ? XPBD_PHASE_VJP_MIN_BLOCKS : XPBD_PHASE_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_BLOCKS : XPBD_PHASE_FWD_MIN_BLOCKS)
     k_phase(PhaseLaunch a, bool first, bool last) {
   constexpr bool REV = MODE == 2;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar[kPhaseMaxStages];
+  __shared__ uint64_t full[kPhaseMaxStages], empty[kPhaseMaxStages];
   __shared__ int abort_run;
   float4* sv = reinterpret_cast<float4*>(smem);
   PhaseChunk* sch = reinterpret_cast<PhaseChunk*>(smem + a.vert_bytes);
@@ -244,24 +257,42 @@ __global__ void __launch_bounds__(kPhaseBlock, MODE == 2 ? XPBD_PHASE_VJP_MIN_BL
   const PhaseChunk* ch = a.chunks + G.chunk_begin;
   const int nch = G.chunk_count, S = a.stages;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kPhaseBlock / 32);
+    }
     abort_run = 0;
     mbar_fence_init();
   }
   __syncthreads();
-  // thread 0 starts the first stages from the global chunk table; everyone else copies the
-  // table to shared memory and gathers the vertices meanwhile
-  if (threadIdx.x == 0)
+  // the producer starts the first stages from the global chunk table; everyone else copies
+  // the table to shared memory and gathers the vertices meanwhile
+  if (threadIdx.x == kPhaseBlock)
     for (int k = 0; k < S && k < nch; ++k)
-      issue_chunk<REV>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &bar[k], first, last);
+      issue_chunk<REV>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &full[k], first, last);
   for (int i = threadIdx.x; i < nch; i += blockDim.x) sch[i] = ch[i];
   gather_vertices(a.P, a.pverts + G.vert_begin, G.vert_count, sv);
   __syncthreads();
+  if (threadIdx.x >= kPhaseBlock) {   // producer warp
+    if (threadIdx.x == kPhaseBlock) {
+      int q = S;
+      for (; q < nch; ++q) {
+        const int s = q % S;
+        if (!mbar_wait(&empty[s], (unsigned)(q / S - 1) & 1u)) break;   // the consumers stopped
+        issue_chunk<REV>(a, sch[REV ? nch - 1 - q : q], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
+      }
+      if (q < nch)   // gave up: let the copies in flight land before the CTA ends
+        for (int j = q - S; j < q; ++j)
+          if (j >= 0) mbar_wait(&full[j % S], (unsigned)(j / S) & 1u);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < nch; ++k) {
     const int s = k % S;
-    unsigned char* st = stage + (size_t)s * a.slot_bytes;
+    const unsigned char* st = stage + (size_t)s * a.slot_bytes;
     const PhaseChunk c = sch[REV ? nch - 1 - k : k];
-    if (mbar_wait(&bar[s], (unsigned)(k / S) & 1u)) {
+    if (mbar_wait(&full[s], (unsigned)(k / S) & 1u)) {
       if (REV)
         vjp_chunk<TM>(a, c, st, sv, first, last);
       else
@@ -269,19 +300,18 @@ __global__ void __launch_bounds__(kPhaseBlock, MODE == 2 ? XPBD_PHASE_VJP_MIN_BL
     } else {
       abort_run = 1;
     }
-    __syncthreads();
-    if (abort_run) {
-      if (threadIdx.x == 0) {
-        atomicOr(a.err, 4);
-        for (int j = k; j < k + S && j < nch; ++j) mbar_wait(&bar[j % S], (unsigned)(j / S) & 1u);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if ((c.flags & (REV ? kChunkColorFirst : kChunkColorLast)) || k + 1 == nch) {
+      consumer_sync();
+      if (abort_run) {
+        if (threadIdx.x == 0) atomicOr(a.err, 4);
+        return;
       }
-      return;
     }
-    if (threadIdx.x == 0 && k + S < nch)
-      issue_chunk<REV>(a, sch[REV ? nch - 1 - (k + S) : k + S], st, &bar[s], first, last);
   }
   const int* vlist = a.pverts + G.vert_begin;
-  for (int v = threadIdx.x; v < G.vert_count; v += blockDim.x) a.P[vlist[v]] = sv[v];
+  for (int v = threadIdx.x; v < G.vert_count; v += kPhaseBlock) a.P[vlist[v]] = sv[v];
 }
 
 namespace {
@@ -319,7 +349,7 @@ Plan stage_plan(const PhaseShape& sh, bool rev) {
   if (p.slot_bytes == 0) return p;
   const int per_sm = 228 * 1024, ctas = rev ? XPBD_PHASE_VJP_MIN_BLOCKS : XPBD_PHASE_FWD_MIN_BLOCKS;
   const int fixed = p.vert_bytes + p.chunk_bytes;
-  const int budget = per_sm / ctas - 1024 - 128;
+  const int budget = per_sm / ctas - 1024 - 256;   // per-CTA reservation, static shared memory
   int S = (budget - fixed) / p.slot_bytes;
   S = std::min(std::max(S, 2), kPhaseMaxStages);
   while (S >= 2 && fixed + S * p.slot_bytes > kPhaseSmemLimit) --S;
@@ -354,9 +384,9 @@ void launch_mode(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cud
   a.stages = p.stages;
   const size_t smem = p.smem();
   switch (kernel_mask(sh.type_mask)) {
-    case kMaskCloth: k_phase<MODE, kMaskCloth><<<sh.n_groups, kPhaseBlock, smem, s>>>(a, first, last); break;
-    case kMaskSolid: k_phase<MODE, kMaskSolid><<<sh.n_groups, kPhaseBlock, smem, s>>>(a, first, last); break;
-    default: k_phase<MODE, kMaskAll><<<sh.n_groups, kPhaseBlock, smem, s>>>(a, first, last);
+    case kMaskCloth: k_phase<MODE, kMaskCloth><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
+    case kMaskSolid: k_phase<MODE, kMaskSolid><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
+    default: k_phase<MODE, kMaskAll><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last);
   }
 }
 
