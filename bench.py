@@ -215,12 +215,22 @@ def traffic_for(cls: str, units_per_launch: float):
         d = json.load(open(path))
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2301_01396_gb300", "csrc", "xpbd_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     e = d.get("classes", {}).get(cls)
-    if not e or d.get("kernel_source_sha256_16") != h:
+    if not e or d.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return float(e["dram_bytes_per_unit"]) * units_per_launch
+
+
+KERNEL_SOURCES = ("csrc/xpbd_phase.cu", "csrc/xpbd_kernels.cu", "csrc/xpbd_elems.cuh", "csrc/xpbd_math.cuh",
+                  "csrc/xpbd_kernels.cuh", "build.py")
+
+
+def kernel_source_hash() -> str:
+    """Fingerprint of the sources and build flags of the constraint kernels."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2301_01396_gb300", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -314,6 +324,11 @@ def run_ours(args, ws, rank, local):
     launches = int(sum(v["launches"] for v in stats.values()))
     breakdown = {k: round(v["ms"] / args.steps, 2) for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])
                  if v["ms"] > 0}
+    # per class: algorithmic bytes per constraint (or vertex) update and the rate they
+    # were moved at over the class's CUDA-event time
+    class_bytes = {k: {"bytes_per_unit": round(v["alg_bytes"] / v["units"], 2),
+                       "gbs": round(v["alg_bytes"] * v["timed_launches"] / v["launches"] / (v["ms"] / 1e3) / 1e9, 1)}
+                   for k, v in timed.items() if v["units"] > 0}
     fwd_ms = sum(v["ms"] for k, v in stats.items() if k.startswith("fwd_") or k in ("predict", "velocity")) / args.steps
     plan = solver.exec_info()
     all_bytes = sum(v["alg_bytes"] for v in stats.values()) / args.steps
@@ -336,6 +351,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clk,
         "gpu_launches": launches,
         "breakdown_ms_per_step": breakdown,
+        "class_bytes": class_bytes,
         "forward_ms_per_step": round(fwd_ms, 2),
         "adjoint_ms_per_step": round(ms - fwd_ms, 2),
         "algorithmic_gb_per_step": round(all_bytes / 1e9, 1),

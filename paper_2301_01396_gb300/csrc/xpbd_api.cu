@@ -293,23 +293,39 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
       }
     }
   };
-  // 1. runs of colors.  Greedy first: extend each run until the next color would make a
-  // component larger than kPhaseMaxVerts.  If that leaves a one-color run, take the fewest
-  // runs instead (dynamic program over each start's longest feasible run: an interval that
-  // is too large stays too large when extended).
-  std::vector<std::pair<int, int>> runs;
-  bool single = false;
-  for (int c = 0; c < K;) {
-    reset();
-    const int c0 = c;
-    while (c < K) {
-      add_color(c);
-      if (maxc > kPhaseMaxVerts) break;
-      ++c;
+  // 1. runs of colors.  Greedy: extend each run until the next color would make a
+  // component larger than the limit.  Smaller components mean less shared memory per CTA
+  // and more resident CTAs, so the smallest limit that needs no more runs than
+  // kPhaseMaxVerts does is taken.  If even that leaves a one-color run, take the fewest runs
+  // at kPhaseMaxVerts instead (dynamic program over each start's longest feasible run: an
+  // interval that is too large stays too large when extended).
+  auto greedy = [&](int limit, bool& single) {
+    std::vector<std::pair<int, int>> rr;
+    single = false;
+    for (int c = 0; c < K;) {
+      reset();
+      const int c0 = c;
+      while (c < K) {
+        add_color(c);
+        if (maxc > limit) break;
+        ++c;
+      }
+      if (c == c0) ++c;
+      single |= (c - c0) < 2;
+      rr.push_back({c0, c});
     }
-    if (c == c0) ++c;
-    single |= (c - c0) < 2;
-    runs.push_back({c0, c});
+    return rr;
+  };
+  bool single = false;
+  std::vector<std::pair<int, int>> runs = greedy(kPhaseMaxVerts, single);
+  for (int limit : {kPhaseGroupVerts, 2 * kPhaseGroupVerts}) {
+    bool s2 = false;
+    std::vector<std::pair<int, int>> r2 = greedy(limit, s2);
+    if (!s2 && r2.size() <= runs.size()) {
+      runs = r2;
+      single = false;
+      break;
+    }
   }
   if (single) {
     std::vector<int> reach(K);
