@@ -81,11 +81,16 @@ typedef struct {
   int32_t n_colors;
   const int32_t* color_offsets; /* [n_colors+1]; color c = color_order[offsets[c]..offsets[c+1]) */
   const int32_t* color_order;   /* [m] every constraint id exactly once                    */
-  int32_t exec_mode;            /* 0: run runs of consecutive colors whose constraints split
-                                   into small vertex-disjoint components as one launch per run
-                                   (vertices staged in shared memory), when that needs fewer
-                                   launches than colors; 1: one launch per color.  Both give
-                                   the same colored Gauss-Seidel results.                  */
+  int32_t exec_mode;            /* How the colored sweep is launched; all modes give the same
+                                   colored Gauss-Seidel results.  Phase plan: runs of
+                                   consecutive colors whose constraints split into small
+                                   vertex-disjoint components as one launch per run
+                                   (vertices staged in shared memory).
+                                   0: the phase plan when it needs at most a quarter of the
+                                      launches of one launch per color (below that, one
+                                      launch per color measured faster), else per color;
+                                   1: one launch per color;
+                                   2: the phase plan whenever it needs fewer launches.     */
 } xpbd_model;
 
 /* Per-call parameters.  The float fields are HOST values; the pointers are DEVICE. */
@@ -169,9 +174,20 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
                          void* stream);
 
 /* Synchronise `stream` and report (then clear) the device error word of the handle:
-   XPBD_ERR_NONFINITE if, since the last check, a call was given a negative or non-finite
-   compliance or a step produced a non-finite state. */
+   XPBD_ERR_TIMEOUT if, since the last check, a bounded wait of a phase kernel gave up;
+   XPBD_ERR_NONFINITE if a call was given a negative or non-finite compliance or a step
+   produced a non-finite state. */
 xpbd_status xpbd_sync_status(xpbd_handle h, void* stream);
+
+/* Self-test of failure detection in the phase kernels.  Every wait of a phase kernel (for a
+   staged copy, or for the consumers to release a stage) gives up after a bounded time,
+   latches bit 4 of the device error word and lets the kernel return, so the context stays
+   usable.  This call launches one CTA of the handle's first phase kernel whose producer
+   issues no copies and whose waits give up after ~2 ms: every consumer wait runs out.
+   Queued on `stream`; the caller then expects XPBD_ERR_TIMEOUT from xpbd_sync_status.
+   It writes no simulation state.  XPBD_ERR_INVALID if the handle runs no phase kernels.
+   The paper has no counterpart. */
+xpbd_status xpbd_selftest_wait_timeout(xpbd_handle h, void* stream);
 
 /* Allocation-free forward simulation.  The paper has no counterpart: this entry point
    exists for callers that cannot allocate device memory when they simulate, for example

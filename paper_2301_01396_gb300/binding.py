@@ -93,7 +93,8 @@ def lib():
         for name in ("xpbd_create", "xpbd_destroy", "xpbd_sizes", "xpbd_forward", "xpbd_read_state",
                      "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read", "xpbd_forward_static",
                      "xpbd_server_create", "xpbd_server_destroy", "xpbd_server_submit", "xpbd_server_run",
-                     "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info"):
+                     "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info",
+                     "xpbd_selftest_wait_timeout"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -152,7 +153,11 @@ class Params:
 
 
 class Solver:
-    """One xpbd_handle: a mesh, its constraints and its coloring, resident on the GPU."""
+    """One xpbd_handle: a mesh, its constraints and its coloring, resident on the GPU.
+
+    exec_mode: 0 picks the multi-color phase launches when they cut the launches per
+    iteration at least 4-fold, 1 launches one color at a time, 2 uses the phase launches
+    whenever the coloring allows any; all three compute the same colored sweep."""
 
     def __init__(self, rest_x, inv_mass, dist_idx=None, bend_idx=None, tet_idx=None, tet_gamma=None,
                  color_offsets=None, color_order=None, exec_mode: int = 0):
@@ -285,6 +290,11 @@ class Solver:
 
     def sync_status(self, stream=None):
         _check(lib().xpbd_sync_status(self._h, _stream(stream)))
+
+    def selftest_wait_timeout(self, stream=None):
+        """Queue one phase-kernel CTA whose bounded waits all run out (its producer issues
+        no copies); the next sync_status() raises XPBD_ERR_TIMEOUT."""
+        _check(lib().xpbd_selftest_wait_timeout(self._h, _stream(stream)))
 
     def profile(self, enable: bool = True):
         """Reset the launch counters; time every launch with CUDA events while enabled."""

@@ -231,7 +231,7 @@ TetRec localize(TetRec r, const std::vector<int>& loc) {
 
 xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, const std::vector<DistRec>& rd,
                          const std::vector<BendRec>& rb, const std::vector<TetRec>& rh,
-                         const std::vector<TetRec>& rdv, const std::vector<int>& perm) {
+                         const std::vector<TetRec>& rdv, const std::vector<int>& perm, int min_cut) {
   const int V = h->V, K = h->K;
   if (K == 0 || V == 0) return XPBD_OK;
   // constraint id -> (type, index in its type's record array)
@@ -353,7 +353,8 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
     for (int b = K; b > 0; b = from[b]) runs.push_back({from[b], b});
     std::reverse(runs.begin(), runs.end());
   }
-  if ((int)runs.size() >= K) return XPBD_OK;   // no run of two colors or more: one launch per color
+  // keep one launch per color unless the runs cut the launches per iteration min_cut-fold
+  if ((int)runs.size() >= K || (int64_t)runs.size() * min_cut > K) return XPBD_OK;
   // 2. groups, chunks and the padded phase records
   std::vector<DistRec> pd;
   std::vector<BendRec> pb;
@@ -555,6 +556,8 @@ PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph) {
     a.tape_off[t] = h->ptape_off[t];
   }
   a.err = h->d_err;
+  a.wait_cycles = 1ll << 31;   // ~1 s at 2 GHz, far beyond any copy
+  a.no_issue = 0;
   return a;
 }
 
@@ -740,12 +743,17 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     return fail(e == cudaErrorMemoryAllocation ? XPBD_ERR_OOM : XPBD_ERR_CUDA,
                 std::string("xpbd_create upload: ") + cudaGetErrorString(e));
   }
-  if (md->exec_mode < 0 || md->exec_mode > 1) {
+  if (md->exec_mode < 0 || md->exec_mode > 2) {
     xpbd_destroy(h);
-    return fail(XPBD_ERR_INVALID, "exec_mode must be 0 or 1");
+    return fail(XPBD_ERR_INVALID, "exec_mode must be 0, 1 or 2");
   }
-  if (md->exec_mode == 0) {
-    xpbd_status pst = build_phases(h, md->color_offsets, md->color_order, rd, rb, rh, rdv, perm);
+  if (md->exec_mode != 1) {
+    // Automatic mode: on GB300 the phase plan was faster than per-color launches of the
+    // same coloring by 1.7-3.4x where it cut launches per iteration 16x (cloth tiles), and
+    // slower (0.5-0.8x) where it cut them 1.8x (row-shaped components serialise many chunks
+    // per CTA), so it is used when it needs at most a quarter of the launches.
+    const int min_cut = md->exec_mode == 0 ? 4 : 1;
+    xpbd_status pst = build_phases(h, md->color_offsets, md->color_order, rd, rb, rh, rdv, perm, min_cut);
     if (pst != XPBD_OK) {
       xpbd_destroy(h);
       return pst;
@@ -1082,6 +1090,28 @@ xpbd_status xpbd_exec_info(xpbd_handle h, int32_t* uses_phases, int32_t* n_phase
   if (!h) return fail(XPBD_ERR_INVALID, "null handle");
   if (uses_phases) *uses_phases = h->use_phases ? 1 : 0;
   if (n_phases) *n_phases = h->use_phases ? (int32_t)h->phases.size() : h->K;
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_selftest_wait_timeout(xpbd_handle h, void* stream) {
+  g_err.clear();
+  if (!h) return fail(XPBD_ERR_INVALID, "null handle");
+  if (!h->use_phases || h->phases.empty())
+    return fail(XPBD_ERR_INVALID, "the handle runs no phase kernels (exec_mode 1 or a coloring without phases)");
+  xpbd_status st = ensure_forward_ws(h);
+  if (st != XPBD_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const auto& ph = h->phases[0];
+  PhaseLaunch a = phase_args(h, ph);
+  a.P = h->P.as<float4>();
+  a.lam_in = nullptr;
+  a.lam_out = h->lam.as<float>();
+  a.wait_cycles = 1ll << 22;   // ~2 ms
+  a.no_issue = 1;
+  PhaseShape one = ph.shape();
+  one.n_groups = 1;            // one CTA: its waits run out one after another
+  launch_phase_fwd(a, one, false, s);
+  LAUNCH_CHECK();
   return XPBD_OK;
 }
 

@@ -99,6 +99,8 @@ struct PhaseLaunch {
   float2* lb;              // reverse: (lambar, alphabar) per constraint
   double* acc;             // reverse: float64 compliance-adjoint accumulator
   int* err;                // device error word (bit 4: a bounded wait gave up)
+  long long wait_cycles;   // limit of every wait (SM clock cycles)
+  int no_issue;            // self-test of the bounded waits: the producer issues no copies
   // shared-memory layout, filled by the launcher: vertices, chunk table, stage ring
   int vert_bytes;
   int chunk_bytes;

@@ -25,8 +25,9 @@
 // zero position, never written back) with alpha~ = 0, so they never move anything.
 //
 // Waits are bounded: a stage that has not arrived after about a second (far beyond any
-// copy) sets bit 4 of the error word; the CTA then waits, again bounded, for the copies it
-// has in flight and returns.
+// copy) sets bit 4 of the error word; the consumers return at the next color end and the
+// producer waits, again bounded, for the copies it has in flight.  xpbd_selftest_wait_timeout
+// exercises this path with a launch whose producer issues nothing.
 #include "xpbd_elems.cuh"
 
 // Tape layout of a chunk: struct of arrays (vertex k of constraint i at k * count + i, so
@@ -40,7 +41,6 @@ namespace xpbd {
 
 namespace {
 
-constexpr long long kWaitCycles = 1ll << 31;   // ~1 s at 2 GHz
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -69,12 +69,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of parity `parity` of barrier b to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+// Bounded wait for the phase of parity `parity` of barrier b to complete: false once
+// `limit` SM clock cycles have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long long limit) {
   if (mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -267,23 +268,23 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
   __syncthreads();
   // the producer starts the first stages from the global chunk table; everyone else copies
   // the table to shared memory and gathers the vertices meanwhile
-  if (threadIdx.x == kPhaseBlock)
+  if (threadIdx.x == kPhaseBlock && !a.no_issue)
     for (int k = 0; k < S && k < nch; ++k)
       issue_chunk<REV>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &full[k], first, last);
   for (int i = threadIdx.x; i < nch; i += blockDim.x) sch[i] = ch[i];
   gather_vertices(a.P, a.pverts + G.vert_begin, G.vert_count, sv);
   __syncthreads();
   if (threadIdx.x >= kPhaseBlock) {   // producer warp
-    if (threadIdx.x == kPhaseBlock) {
+    if (threadIdx.x == kPhaseBlock && !a.no_issue) {
       int q = S;
       for (; q < nch; ++q) {
         const int s = q % S;
-        if (!mbar_wait(&empty[s], (unsigned)(q / S - 1) & 1u)) break;   // the consumers stopped
+        if (!mbar_wait(&empty[s], (unsigned)(q / S - 1) & 1u, a.wait_cycles)) break;   // the consumers stopped
         issue_chunk<REV>(a, sch[REV ? nch - 1 - q : q], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
       }
       if (q < nch)   // gave up: let the copies in flight land before the CTA ends
         for (int j = q - S; j < q; ++j)
-          if (j >= 0) mbar_wait(&full[j % S], (unsigned)(j / S) & 1u);
+          if (j >= 0) mbar_wait(&full[j % S], (unsigned)(j / S) & 1u, a.wait_cycles);
     }
     return;
   }
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     const int s = k % S;
     const unsigned char* st = stage + (size_t)s * a.slot_bytes;
     const PhaseChunk c = sch[REV ? nch - 1 - k : k];
-    if (mbar_wait(&full[s], (unsigned)(k / S) & 1u)) {
+    if (mbar_wait(&full[s], (unsigned)(k / S) & 1u, a.wait_cycles)) {
       if (REV)
         vjp_chunk<TM>(a, c, st, sv, first, last);
       else

@@ -203,7 +203,7 @@ def test_nonfinite_state_is_reported():
 
 @pytest.mark.parametrize("name", CASES)
 def test_phase_plan_matches_per_color_launches(name, cases):
-    """The multi-color phase launches (exec_mode 0) and one launch per color (exec_mode 1)
+    """The multi-color phase launches (exec_mode 2) and one launch per color (exec_mode 1)
     run the same constraint updates in the same order, and the phase plan is used for these
     colorings.  Built with FMA contraction off (nvcc -fmad=false) the two modes agree bit
     for bit on every case here; with contraction on, the compiler fuses a few multiply-adds
@@ -214,11 +214,11 @@ def test_phase_plan_matches_per_color_launches(name, cases):
     rng = np.random.default_rng(9)
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3)))}
     out = []
-    for mode in (0, 1):
+    for mode in (2, 1):   # 2: the phase plan whenever the coloring allows one
         solver = binding.Solver.from_scene(sc, exec_mode=mode)
         info = solver.exec_info()
-        assert info["phases"] == (mode == 0), info
-        if mode == 0:
+        assert info["phases"] == (mode == 2), info
+        if mode == 2:
             assert info["launches_per_iteration"] < sc.n_colors
         p = binding.params_from_scene(sc)
         ck = solver.forward(p, sc.steps, sc.iters, to_dev(sc.x0), to_dev(sc.v0))
