@@ -108,6 +108,9 @@ typedef struct {
   float sphere[4];              /* centre cx, cy, cz and radius r:  C = |x - c| - r - thickness */
   float contact_compliance;     /* compliance of every contact spring                     */
   float thickness;              /* separation kept from the colliders                     */
+  const float* f_vertex_steps;  /* DEVICE [steps*V*3] force on vertex i at step n, or NULL:
+                                   the keyframe example's control variables (Sec. "Keyframe
+                                   Simulation").  Not accepted by the serving API.         */
 } xpbd_params;
 
 /* Gradient outputs.  DEVICE float64 buffers owned by the caller; each non-NULL buffer is
@@ -119,6 +122,7 @@ typedef struct {
   double* d_f_global;           /* [steps*3] dL/dG_n                                      */
   double* d_f_vertex;           /* [V*3] dL/dW_i                                          */
   double* d_collider;           /* [5] dL/d(plane_h, cx, cy, cz, r)                        */
+  double* d_f_vertex_steps;     /* [steps*V*3] dL/dF_{n,i} (force per vertex per step)    */
 } xpbd_grads;
 
 /* Build a solver.  Validates indices (XPBD_ERR_INVALID), the coloring
@@ -172,6 +176,40 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
                          const float* checkpoints, int32_t n_seeds, const int32_t* seed_steps,
                          const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
                          void* stream);
+
+/* ---- Sparse checkpoints (recompute instead of storing every step) ----------------------
+   The paper stores every step's state for the adjoint pass and names the resulting memory
+   growth as a limitation (section "Discussion, Limitations, and Future Work").  These
+   calls store the state (x, v) only at every `stride`-th step and at the last step; the
+   reverse sweep recomputes the states inside
+   each stride from the stored one with the same forward kernels (one extra forward pass)
+   and then reverses them exactly as xpbd_adjoint does, so its gradients are bit-identical
+   to xpbd_adjoint's.  Checkpoint memory falls from (steps+1) to about steps/stride + 2
+   states, plus stride-1 recomputed states (32 B per vertex each). */
+
+/* Number of stored states for `steps` steps: steps/stride + 1, plus 1 when stride does not
+   divide steps (the last state).  -1 for steps < 0 or stride < 1.  Host only. */
+int32_t xpbd_sparse_slots(int32_t steps, int32_t stride);
+
+/* Slot of step `step` in a sparse checkpoint buffer, or -1 if that step is not stored.
+   Host only.  xpbd_read_state and xpbd_loss read a sparse buffer when given slot indices. */
+int32_t xpbd_sparse_slot(int32_t steps, int32_t stride, int32_t step);
+
+/* Forward simulation like xpbd_forward, writing only the stored states to `checkpoints`
+   (DEVICE [xpbd_sparse_slots(steps, stride) * V * 8], same per-state layout).  The states
+   in between pass through a two-state buffer the handle allocates on first use
+   (64 B per vertex).  XPBD_ERR_INVALID for stride < 1. */
+xpbd_status xpbd_forward_sparse(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                const float* x0, const float* v0, int32_t stride, float* checkpoints,
+                                void* stream);
+
+/* Reverse sweep from a sparse checkpoint buffer written by xpbd_forward_sparse with the same
+   params/steps/iters/stride.  Seeds, outputs and determinism as xpbd_adjoint (seeds may sit
+   at any step).  The handle allocates (stride-1) recomputed states on first use. */
+xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                const float* checkpoints, int32_t stride, int32_t n_seeds,
+                                const int32_t* seed_steps, const float* seed_dx, const float* seed_dv_T,
+                                const xpbd_grads* out, void* stream);
 
 /* Synchronise `stream` and report (then clear) the device error word of the handle:
    XPBD_ERR_TIMEOUT if, since the last check, a bounded wait of a phase kernel gave up;

@@ -32,12 +32,13 @@ class _Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("compliance", _dp),
                 ("f_global", _dp), ("f_vertex", _dp), ("collider_flags", C.c_int32),
                 ("plane_h", C.c_double), ("sphere", C.c_double * 4),
-                ("contact_compliance", C.c_double), ("thickness", C.c_double)]
+                ("contact_compliance", C.c_double), ("thickness", C.c_double),
+                ("f_vertex_steps", _dp)]
 
 
 class _Direction(C.Structure):
     _fields_ = [("d_compliance", _dp), ("d_x0", _dp), ("d_v0", _dp), ("d_f_global", _dp),
-                ("d_f_vertex", _dp), ("d_collider", _dp)]
+                ("d_f_vertex", _dp), ("d_collider", _dp), ("d_f_vertex_steps", _dp)]
 
 
 def lib():
@@ -70,7 +71,7 @@ class _Args:
     """Keeps the numpy buffers alive while the C structs point into them."""
 
     def __init__(self, scene, compliance=None, f_global=None, f_vertex=None, plane_h=None,
-                 sphere=None, steps=None):
+                 sphere=None, steps=None, f_vertex_steps=None):
         keep = []
 
         def d(a):
@@ -98,12 +99,18 @@ class _Args:
             fg = np.asarray(fg, np.float64).reshape(-1, 3)
             if fg.shape[0] < steps:
                 raise ValueError("f_global has fewer rows than steps")
+        fvs = getattr(s, "f_vertex_steps", None) if f_vertex_steps is None else f_vertex_steps
+        if fvs is not None and steps is not None:
+            fvs = np.asarray(fvs, np.float64).reshape(-1, s.V, 3)
+            if fvs.shape[0] < steps:
+                raise ValueError("f_vertex_steps has fewer steps than simulated")
         sph = s.sphere if sphere is None else sphere
         self.params = _Params(dt=s.dt, gravity=(C.c_double * 3)(*s.gravity), compliance=d(comp),
                               f_global=d(fg), f_vertex=d(fv), collider_flags=s.collider_flags,
                               plane_h=s.plane_h if plane_h is None else plane_h,
                               sphere=(C.c_double * 4)(*sph),
-                              contact_compliance=s.contact_compliance, thickness=s.thickness)
+                              contact_compliance=s.contact_compliance, thickness=s.thickness,
+                              f_vertex_steps=d(fvs))
         self.keep = keep
 
 
@@ -134,11 +141,11 @@ def num_threads() -> int:
 
 
 def forward(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, x0=None, v0=None,
-            compliance=None, f_global=None, f_vertex=None, plane_h=None, sphere=None):
+            compliance=None, f_global=None, f_vertex=None, plane_h=None, sphere=None, f_vertex_steps=None):
     """Run the FP64 forward simulation; returns (xs, vs), each [steps+1, V, 3]."""
     steps = scene.steps if steps is None else steps
     iters = scene.iters if iters is None else iters
-    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps)
+    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps, f_vertex_steps)
     x0a, x0p = _d(scene.x0 if x0 is None else x0)
     v0a, v0p = _d(scene.v0 if v0 is None else v0)
     xs = np.zeros((steps + 1, scene.V, 3))
@@ -150,13 +157,14 @@ def forward(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, 
 
 def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
             seed_dv_T=None, x0=None, v0=None, compliance=None, f_global=None, f_vertex=None,
-            plane_h=None, sphere=None) -> dict:
+            plane_h=None, sphere=None, f_vertex_steps=None) -> dict:
     """Reverse sweep.  ``seeds`` maps step n -> dL/dx_n [V,3].  Returns a dict of FP64
     gradients: compliance [m], x0 [V,3], v0 [V,3], f_global [steps,3], f_vertex [V,3],
-    collider [5] (plane h, sphere cx, cy, cz, r)."""
+    collider [5] (plane h, sphere cx, cy, cz, r), f_vertex_steps [steps,V,3] (the force on
+    each vertex at each step)."""
     steps = scene.steps if steps is None else steps
     iters = scene.iters if iters is None else iters
-    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps)
+    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps, f_vertex_steps)
     x0a, x0p = _d(scene.x0 if x0 is None else x0)
     v0a, v0p = _d(scene.v0 if v0 is None else v0)
     keys = sorted(seeds)
@@ -165,21 +173,22 @@ def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int
                  if keys else np.zeros(1))
     dv, dvp = _d(None if seed_dv_T is None else np.asarray(seed_dv_T).reshape(-1))
     out = dict(compliance=np.zeros(scene.m), x0=np.zeros((scene.V, 3)), v0=np.zeros((scene.V, 3)),
-               f_global=np.zeros((steps, 3)), f_vertex=np.zeros((scene.V, 3)), collider=np.zeros(5))
+               f_global=np.zeros((steps, 3)), f_vertex=np.zeros((scene.V, 3)), collider=np.zeros(5),
+               f_vertex_steps=np.zeros((steps, scene.V, 3)))
     P = lambda k: out[k].ctypes.data_as(_dp)
     lib().oracle_adjoint(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p, len(keys),
                          ssp, sdp, dvp, P("compliance"), P("x0"), P("v0"), P("f_global"),
-                         P("f_vertex"), P("collider"))
+                         P("f_vertex"), P("collider"), P("f_vertex_steps"))
     return out
 
 
 def tangent(scene, direction: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
-            x0=None, v0=None, compliance=None, f_global=None, f_vertex=None):
+            x0=None, v0=None, compliance=None, f_global=None, f_vertex=None, f_vertex_steps=None):
     """Forward-mode derivative along ``direction`` (keys as in ``adjoint``'s output).
     Returns (dxs, dvs), each [steps+1, V, 3]."""
     steps = scene.steps if steps is None else steps
     iters = scene.iters if iters is None else iters
-    a = _Args(scene, compliance, f_global, f_vertex, None, None, steps)
+    a = _Args(scene, compliance, f_global, f_vertex, None, None, steps, f_vertex_steps)
     x0a, x0p = _d(scene.x0 if x0 is None else x0)
     v0a, v0p = _d(scene.v0 if v0 is None else v0)
     keep = []
@@ -192,7 +201,8 @@ def tangent(scene, direction: dict, steps: Optional[int] = None, iters: Optional
         return p
 
     D = _Direction(d_compliance=dd("compliance"), d_x0=dd("x0"), d_v0=dd("v0"),
-                   d_f_global=dd("f_global"), d_f_vertex=dd("f_vertex"), d_collider=dd("collider"))
+                   d_f_global=dd("f_global"), d_f_vertex=dd("f_vertex"), d_collider=dd("collider"),
+                   d_f_vertex_steps=dd("f_vertex_steps"))
     dxs = np.zeros((steps + 1, scene.V, 3))
     dvs = np.zeros((steps + 1, scene.V, 3))
     lib().oracle_tangent(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p, C.byref(D),

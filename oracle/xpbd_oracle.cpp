@@ -326,6 +326,7 @@ struct Params {
   std::vector<T> compliance;     // [m]
   std::vector<T> f_global;       // [steps*3] (may be empty)
   std::vector<T> f_vertex;       // [V*3]    (may be empty)
+  std::vector<T> f_vertex_steps; // [steps*V*3] force on vertex i at step n (may be empty)
   int flags = 0;                 // bit0 plane, bit1 sphere
   T plane_h = T(0.0);
   T sphere[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
@@ -440,8 +441,9 @@ void detect_contacts(const Model& M, const Params<T>& P, Work<T>& W) {
   }
 }
 
-// Inertial prediction p = x + dt v + dt^2 w (m g + G_n + W_i)  (Eq. xpbdUpdateRule).
-// w m g = g for free vertices and 0 for pinned ones.
+// Inertial prediction p = x + dt v + dt^2 w (m g + G_n + W_i + F_{n,i})  (Eq. xpbdUpdateRule).
+// w m g = g for free vertices and 0 for pinned ones.  F_{n,i} is a force per vertex per step,
+// the control variables of the keyframe example (Sec. "Keyframe Simulation").
 template <class T>
 void predict(const Model& M, const Params<T>& P, int n, const std::vector<T>& x,
              const std::vector<T>& v, std::vector<T>& p) {
@@ -452,6 +454,7 @@ void predict(const Model& M, const Params<T>& P, int n, const std::vector<T>& x,
       T f = T(0.0);
       if (!P.f_global.empty()) f = f + P.f_global[3 * n + c];
       if (!P.f_vertex.empty()) f = f + P.f_vertex[3 * i + c];
+      if (!P.f_vertex_steps.empty()) f = f + P.f_vertex_steps[3 * ((size_t)M.V * n + i) + c];
       T acc = w * f + (w > 0.0 ? P.g[c] : 0.0);
       p[3 * i + c] = x[3 * i + c] + dt * v[3 * i + c] + dt * dt * acc;
       round32(p[3 * i + c]);
@@ -542,7 +545,7 @@ void vjp_one(int kind, const double* q, const double* wv, const Rest& r, double 
 }
 
 struct Grads {
-  std::vector<double> d_alpha, d_x0, d_v0, d_fg, d_fv;
+  std::vector<double> d_alpha, d_x0, d_v0, d_fg, d_fv, d_fvs;
   double d_coll[5] = {0, 0, 0, 0, 0};   // plane h, sphere cx, cy, cz, r
 };
 
@@ -565,6 +568,7 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
   G.d_alpha.assign(M.m(), 0.0);
   G.d_fg.assign(3 * (size_t)steps, 0.0);
   G.d_fv.assign(V3n, 0.0);
+  G.d_fvs.assign(V3n * (size_t)steps, 0.0);
   std::vector<double> abar_t(M.m(), 0.0);   // adjoint of alpha~ (converted at the end)
   Work<double> W;
   W.p.assign(V3n, 0.0);
@@ -668,7 +672,7 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
         }
       }
     }
-    // adjoint of the prediction p = x + dt v + dt^2 w (G_n + W_i) + dt^2 [w>0] g
+    // adjoint of the prediction p = x + dt v + dt^2 w (G_n + W_i + F_{n,i}) + dt^2 [w>0] g
     for (int i = 0; i < M.V; ++i) {
       double w = M.w[i];
       for (int c = 0; c < 3; ++c) {
@@ -678,6 +682,7 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
         double fb = dt * dt * w * pb;
         G.d_fg[3 * n + c] += fb;
         G.d_fv[3 * i + c] += fb;
+        G.d_fvs[V3n * n + 3 * i + c] = fb;
       }
     }
     add_seed(n);
@@ -723,6 +728,7 @@ typedef struct {
   double sphere[4];           // cx, cy, cz, r
   double contact_compliance;
   double thickness;
+  const double* f_vertex_steps;  // [steps*V*3] or NULL
 } om_params;
 
 typedef struct {              // tangent directions (NULL = zero)
@@ -732,6 +738,7 @@ typedef struct {              // tangent directions (NULL = zero)
   const double* d_f_global;   // [steps*3]
   const double* d_f_vertex;   // [V*3]
   const double* d_collider;   // [5] plane h, cx, cy, cz, r
+  const double* d_f_vertex_steps;  // [steps*V*3]
 } om_direction;
 
 static Model make_model(const om_model* in) {
@@ -769,6 +776,10 @@ static Params<T> make_params(const Model& M, const om_params* in, int steps) {
   if (in->f_vertex) {
     P.f_vertex.resize(3 * (size_t)M.V);
     for (size_t i = 0; i < P.f_vertex.size(); ++i) P.f_vertex[i] = T(in->f_vertex[i]);
+  }
+  if (in->f_vertex_steps) {
+    P.f_vertex_steps.resize(3 * (size_t)M.V * steps);
+    for (size_t i = 0; i < P.f_vertex_steps.size(); ++i) P.f_vertex_steps[i] = T(in->f_vertex_steps[i]);
   }
   P.flags = in->collider_flags;
   P.plane_h = T(in->plane_h);
@@ -828,12 +839,12 @@ int oracle_forward(const om_model* in, const om_params* pin, int32_t steps, int3
 
 // Reverse sweep.  Seeds: dL/dx_n for n = seed_steps[s] in seed_dx[s*V*3..], and
 // optionally dL/dv_N.  Outputs (NULL = not wanted): d_compliance [m], d_x0, d_v0 [V*3],
-// d_f_global [steps*3], d_f_vertex [V*3], d_collider [5].
+// d_f_global [steps*3], d_f_vertex [V*3], d_collider [5], d_f_vertex_steps [steps*V*3].
 int oracle_adjoint(const om_model* in, const om_params* pin, int32_t steps, int32_t iters,
                    const double* x0, const double* v0, int32_t n_seed, const int32_t* seed_steps,
                    const double* seed_dx, const double* seed_dv_T, double* d_compliance,
                    double* d_x0, double* d_v0, double* d_f_global, double* d_f_vertex,
-                   double* d_collider) {
+                   double* d_collider, double* d_f_vertex_steps) {
   Model M = make_model(in);
   Params<double> P = make_params<double>(M, pin, steps);
   std::vector<double> x(x0, x0 + 3 * (size_t)M.V), v(v0, v0 + 3 * (size_t)M.V);
@@ -846,6 +857,7 @@ int oracle_adjoint(const om_model* in, const om_params* pin, int32_t steps, int3
   if (d_f_global) std::copy(G.d_fg.begin(), G.d_fg.end(), d_f_global);
   if (d_f_vertex) std::copy(G.d_fv.begin(), G.d_fv.end(), d_f_vertex);
   if (d_collider) std::copy(G.d_coll, G.d_coll + 5, d_collider);
+  if (d_f_vertex_steps) std::copy(G.d_fvs.begin(), G.d_fvs.end(), d_f_vertex_steps);
   return 0;
 }
 
@@ -866,6 +878,10 @@ int oracle_tangent(const om_model* in, const om_params* pin, int32_t steps, int3
   if (dir->d_f_vertex) {
     if (P.f_vertex.empty()) P.f_vertex.assign(3 * (size_t)M.V, D1(0.0));
     for (size_t i = 0; i < P.f_vertex.size(); ++i) P.f_vertex[i].d = dir->d_f_vertex[i];
+  }
+  if (dir->d_f_vertex_steps) {
+    if (P.f_vertex_steps.empty()) P.f_vertex_steps.assign(3 * (size_t)M.V * steps, D1(0.0));
+    for (size_t i = 0; i < P.f_vertex_steps.size(); ++i) P.f_vertex_steps[i].d = dir->d_f_vertex_steps[i];
   }
   if (dir->d_collider) {
     P.plane_h.d = dir->d_collider[0];

@@ -42,12 +42,13 @@ class XpbdParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("gravity", C.c_float * 3), ("compliance", C.c_void_p),
                 ("f_global", C.c_void_p), ("f_vertex", C.c_void_p), ("collider_flags", C.c_int32),
                 ("plane_h", C.c_float), ("sphere", C.c_float * 4),
-                ("contact_compliance", C.c_float), ("thickness", C.c_float)]
+                ("contact_compliance", C.c_float), ("thickness", C.c_float), ("f_vertex_steps", C.c_void_p)]
 
 
 class XpbdGrads(C.Structure):
     _fields_ = [("d_compliance", C.c_void_p), ("d_x0", C.c_void_p), ("d_v0", C.c_void_p),
-                ("d_f_global", C.c_void_p), ("d_f_vertex", C.c_void_p), ("d_collider", C.c_void_p)]
+                ("d_f_global", C.c_void_p), ("d_f_vertex", C.c_void_p), ("d_collider", C.c_void_p),
+                ("d_f_vertex_steps", C.c_void_p)]
 
 
 KERNEL_CLASSES = ("fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
@@ -94,7 +95,8 @@ def lib():
                      "xpbd_loss", "xpbd_adjoint", "xpbd_sync_status", "xpbd_profile", "xpbd_profile_read", "xpbd_forward_static",
                      "xpbd_server_create", "xpbd_server_destroy", "xpbd_server_submit", "xpbd_server_run",
                      "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info",
-                     "xpbd_selftest_wait_timeout"):
+                     "xpbd_selftest_wait_timeout", "xpbd_forward_sparse", "xpbd_adjoint_sparse",
+                     "xpbd_sparse_slots", "xpbd_sparse_slot"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -140,16 +142,28 @@ class Params:
     sphere: Sequence[float] = (0.0, 0.0, 0.0, 0.0)
     contact_compliance: float = 1e-8
     thickness: float = 0.0
+    f_vertex_steps: Optional[torch.Tensor] = None   # [steps,V,3] float32 cuda: force per vertex per step
 
     def c_struct(self) -> XpbdParams:
-        for t in (self.compliance, self.f_global, self.f_vertex):
+        for t in (self.compliance, self.f_global, self.f_vertex, self.f_vertex_steps):
             if t is not None and t.dtype != torch.float32:
                 raise ValueError("params tensors must be float32")
         return XpbdParams(dt=self.dt, gravity=(C.c_float * 3)(*self.gravity),
                           compliance=_ptr(self.compliance), f_global=_ptr(self.f_global),
                           f_vertex=_ptr(self.f_vertex), collider_flags=int(self.collider_flags),
                           plane_h=float(self.plane_h), sphere=(C.c_float * 4)(*[float(v) for v in self.sphere]),
-                          contact_compliance=float(self.contact_compliance), thickness=float(self.thickness))
+                          contact_compliance=float(self.contact_compliance), thickness=float(self.thickness),
+                          f_vertex_steps=_ptr(self.f_vertex_steps))
+
+
+def sparse_slots(steps: int, stride: int) -> int:
+    """Stored states of a sparse checkpoint buffer (xpbd_sparse_slots); -1 if invalid."""
+    return int(lib().xpbd_sparse_slots(int(steps), int(stride)))
+
+
+def sparse_slot(steps: int, stride: int, step: int) -> int:
+    """Slot of `step` in a sparse checkpoint buffer, or -1 if it is not stored."""
+    return int(lib().xpbd_sparse_slot(int(steps), int(stride), int(step)))
 
 
 class Solver:
@@ -239,6 +253,20 @@ class Solver:
                                   _ptr(ck), _stream(stream)))
         return ck
 
+    def forward_sparse(self, params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
+                       stride: int, checkpoints: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """xpbd_forward_sparse: stores the state only at every `stride`-th step and the last
+        step.  Returns [sparse_slots(steps, stride), 2, V, 4]; slot of step n: sparse_slot()."""
+        n = sparse_slots(steps, stride)
+        if n < 0:
+            raise XpbdError(1, f"bad steps/stride: {steps}/{stride}")
+        ck = (torch.empty((n, 2, self.V, 4), dtype=torch.float32, device=x0.device)
+              if checkpoints is None else checkpoints)
+        p = params.c_struct()
+        _check(lib().xpbd_forward_sparse(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
+                                         int(stride), _ptr(ck), _stream(stream)))
+        return ck
+
     def forward_static(self, params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
                        checkpoints: torch.Tensor, stream=None) -> torch.Tensor:
         """xpbd_forward_static: the forward simulation without any device allocation by the
@@ -270,22 +298,29 @@ class Solver:
     def adjoint(self, params: Params, steps: int, iters: int, checkpoints: torch.Tensor, seeds: dict,
                 seed_dv_T: Optional[torch.Tensor] = None, want=("compliance", "x0", "v0", "f_global",
                                                                  "f_vertex", "collider"),
-                out: Optional[dict] = None, stream=None) -> dict:
-        """seeds: {step: dL/dx_step [V,3] float32 cuda}.  Returns float64 gradients."""
+                out: Optional[dict] = None, stream=None, stride: Optional[int] = None) -> dict:
+        """seeds: {step: dL/dx_step [V,3] float32 cuda}.  Returns float64 gradients.  With
+        `stride`, `checkpoints` is a sparse buffer from forward_sparse with that stride."""
         dev = checkpoints.device
         keys = sorted(seeds)
         sd = torch.stack([seeds[k] for k in keys]).contiguous() if keys else None
         shapes = dict(compliance=(self.m,), x0=(self.V, 3), v0=(self.V, 3), f_global=(max(steps, 1), 3),
-                      f_vertex=(self.V, 3), collider=(5,))
+                      f_vertex=(self.V, 3), collider=(5,), f_vertex_steps=(max(steps, 1), self.V, 3))
         if out is None:
             out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
         g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
                       d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
-                      d_f_vertex=_ptr(out.get("f_vertex")), d_collider=_ptr(out.get("collider")))
+                      d_f_vertex=_ptr(out.get("f_vertex")), d_collider=_ptr(out.get("collider")),
+                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")))
         p = params.c_struct()
         ks = (C.c_int32 * max(len(keys), 1))(*keys)
-        _check(lib().xpbd_adjoint(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
-                                  len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), _stream(stream)))
+        if stride is None:
+            _check(lib().xpbd_adjoint(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
+                                      len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), _stream(stream)))
+        else:
+            _check(lib().xpbd_adjoint_sparse(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
+                                             int(stride), len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g),
+                                             _stream(stream)))
         return out
 
     def sync_status(self, stream=None):
@@ -315,7 +350,7 @@ def params_from_scene(sc, device="cuda", compliance=None) -> Params:
                   gravity=tuple(float(g) for g in sc.gravity), f_global=t(sc.f_global), f_vertex=t(sc.f_vertex),
                   collider_flags=int(sc.collider_flags), plane_h=float(sc.plane_h),
                   sphere=tuple(float(v) for v in sc.sphere), contact_compliance=float(sc.contact_compliance),
-                  thickness=float(sc.thickness))
+                  thickness=float(sc.thickness), f_vertex_steps=t(getattr(sc, "f_vertex_steps", None)))
 
 
 class XPBDSolve(torch.autograd.Function):

@@ -53,6 +53,8 @@ xpbd_status ensure_adjoint_ws(xpbd_solver* h, int iters, bool contacts) {
 }
 
 PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph);
+xpbd_status forward_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t iters, const float4* ckx_n,
+                         const float4* ckv_n, float4* nx, cudaStream_t s);
 
 // alpha~ into the records a call will use: the phase-ordered copy when the phase plan runs
 // the sweep (`phase`), else the per-color records.
@@ -80,6 +82,7 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
   uint8_t* cf = h->cflags.as<uint8_t>();
   launch(h, XPBD_K_PREDICT, h->V, s, [&] {
     launch_predict(ckx_n, ckv_n, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex,
+                   p->f_vertex_steps ? p->f_vertex_steps + 3 * (size_t)h->V * n : nullptr,
                    p->dt, p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
   });
   LAUNCH_CHECK();
@@ -778,7 +781,7 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
                     &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
-                    &h->partials};
+                    &h->partials, &h->roll, &h->seg};
   for (DevBuf* b : bufs) b->release();
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -823,15 +826,9 @@ xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   float4* ck4 = reinterpret_cast<float4*>(ck);
   launch(h, XPBD_K_OTHER, h->V, s, [&] { launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + h->V, h->V, s); });
   LAUNCH_CHECK();
-  const float inv_dt = 1.f / p->dt;
   for (int n = 0; n < steps; ++n) {
-    st = run_step(h, p, n, iters, ck_x(ck, h->V, n), ck_v(ck, h->V, n), false, s);
+    st = forward_step(h, p, n, iters, ck_x(ck, h->V, n), ck_v(ck, h->V, n), ck4 + (size_t)2 * h->V * (n + 1), s);
     if (st != XPBD_OK) return st;
-    float4* nx = ck4 + (size_t)2 * h->V * (n + 1);
-    launch(h, XPBD_K_VELOCITY, h->V, s, [&] {
-      launch_velocity(h->P.as<float4>(), ck_x(ck, h->V, n), nx, nx + h->V, inv_dt, h->V, h->d_err, s);
-    });
-    LAUNCH_CHECK();
   }
   return XPBD_OK;
 }
@@ -868,103 +865,124 @@ xpbd_status xpbd_loss(xpbd_handle h, const float* ck, int32_t n_keys, const int3
   return XPBD_OK;
 }
 
-xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
-                         const float* ck, int32_t n_seeds, const int32_t* seed_steps,
-                         const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
-                         void* stream) {
-  g_err.clear();
-  xpbd_status st = check_params(h, p, steps, iters);
-  if (st != XPBD_OK) return st;
-  if (!ck || !out || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
-    return fail(XPBD_ERR_INVALID, "bad argument");
-  std::vector<int> seed_of(steps + 1, -1);
+}  // extern "C"
+
+namespace {
+
+// State of one reverse sweep shared by its steps.
+struct AdjointSweep {
+  std::vector<int> seed_of;   // step -> index of its dL/dx seed, or -1
+  const float* seed_dx = nullptr;
+  const xpbd_grads* out = nullptr;
+  bool contacts = false;
+  int pb = 0;
+};
+
+// Validation, workspace, alpha~, zeroed outputs and the seeds at the last step.
+xpbd_status adjoint_begin(xpbd_solver* h, const xpbd_params* p, int32_t steps, int32_t iters, int32_t n_seeds,
+                          const int32_t* seed_steps, const float* seed_dx, const float* seed_dv_T,
+                          const xpbd_grads* out, cudaStream_t s, AdjointSweep& A) {
+  A.seed_of.assign(steps + 1, -1);
   for (int k = 0; k < n_seeds; ++k) {
     int n = seed_steps[k];
     if (n < 0 || n > steps) return fail(XPBD_ERR_INVALID, "seed step out of range");
-    if (seed_of[n] >= 0) return fail(XPBD_ERR_INVALID, "two seeds for one step");
-    seed_of[n] = k;
+    if (A.seed_of[n] >= 0) return fail(XPBD_ERR_INVALID, "two seeds for one step");
+    A.seed_of[n] = k;
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  A.seed_dx = seed_dx;
+  A.out = out;
   const int V = h->V;
-  const bool contacts = (p->collider_flags & 3) != 0;
-  st = ensure_adjoint_ws(h, iters, contacts);
+  A.contacts = (p->collider_flags & 3) != 0;
+  xpbd_status st = ensure_adjoint_ws(h, iters, A.contacts);
   if (st != XPBD_OK) return st;
   st = set_alpha(h, p, s, h->use_phases);
   if (st != XPBD_OK) return st;
-  const int pb = partial_blocks(std::max(V, 1));
-  double* partials = h->partials.as<double>();
+  A.pb = partial_blocks(std::max(V, 1));
   CU_TRY(cudaMemsetAsync(h->acc.p, 0, sizeof(double) * h->slots, s));
   if (out->d_f_vertex) CU_TRY(cudaMemsetAsync(out->d_f_vertex, 0, sizeof(double) * 3 * (size_t)V, s));
   if (out->d_collider) CU_TRY(cudaMemsetAsync(out->d_collider, 0, sizeof(double) * 5, s));
   if (out->d_f_global && steps > 0) CU_TRY(cudaMemsetAsync(out->d_f_global, 0, sizeof(double) * 3 * (size_t)steps, s));
-  float4* xbar = h->xbar.as<float4>();
-  float4* vbar = h->vbar.as<float4>();
   launch(h, XPBD_K_ADJ_OTHER, V, s, [&] {
-    launch_seed_adjoint(seed_of[steps] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[steps] : nullptr, seed_dv_T,
-                        xbar, vbar, V, s);
+    launch_seed_adjoint(A.seed_of[steps] >= 0 ? seed_dx + 3 * (size_t)V * A.seed_of[steps] : nullptr, seed_dv_T,
+                        h->xbar.as<float4>(), h->vbar.as<float4>(), V, s);
   });
   LAUNCH_CHECK();
-  const float inv_dt = 1.f / p->dt;
+  return XPBD_OK;
+}
+
+// Reverse of step n from its state (x_n, v_n): replay with tapes, then the reverse
+// iterations, then the adjoint of the prediction.
+xpbd_status adjoint_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t iters, const float4* ckx_n,
+                         const float4* ckv_n, const AdjointSweep& A, cudaStream_t s) {
+  const int V = h->V;
+  const xpbd_grads* out = A.out;
+  float4* xbar = h->xbar.as<float4>();
+  float4* vbar = h->vbar.as<float4>();
+  double* partials = h->partials.as<double>();
   const size_t tpi = h->tape_slots;
-  Collide c = make_collide(p);
-  for (int n = steps - 1; n >= 0; --n) {
-    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_adj_begin(xbar, vbar, inv_dt, V, s); });
-    st = run_step(h, p, n, iters, ck_x(ck, V, n), ck_v(ck, V, n), true, s);
-    if (st != XPBD_OK) return st;
-    for (int k = iters - 1; k >= 0; --k) {
-      const bool first = k == iters - 1, last = k == 0;
-      if (contacts) {
-        launch(h, XPBD_K_VJP_CONTACT, V, s, [&] {
-          launch_vjp_contact(h->tape_c.as<float4>() + (size_t)k * V, h->cflags.as<uint8_t>(), V,
-                             k == 0 ? nullptr : h->lamc_tape.as<float2>() + (size_t)(k - 1) * V, xbar,
-                             h->lbc.as<float2>(), out->d_collider ? h->cgrad.as<float>() : nullptr, first, c, s);
+  const Collide c = make_collide(p);
+  launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_adj_begin(xbar, vbar, 1.f / p->dt, V, s); });
+  xpbd_status st = run_step(h, p, n, iters, ckx_n, ckv_n, true, s);
+  if (st != XPBD_OK) return st;
+  for (int k = iters - 1; k >= 0; --k) {
+    const bool first = k == iters - 1, last = k == 0;
+    if (A.contacts) {
+      launch(h, XPBD_K_VJP_CONTACT, V, s, [&] {
+        launch_vjp_contact(h->tape_c.as<float4>() + (size_t)k * V, h->cflags.as<uint8_t>(), V,
+                           k == 0 ? nullptr : h->lamc_tape.as<float2>() + (size_t)(k - 1) * V, xbar,
+                           h->lbc.as<float2>(), out->d_collider ? h->cgrad.as<float>() : nullptr, first, c, s);
+      });
+    }
+    const float4* tape_k = h->tape.as<float4>() + (size_t)k * tpi;
+    const float* lam_pre = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->slots;
+    for (int q = h->use_phases ? (int)h->phases.size() - 1 : -1; q >= 0; --q) {
+      const auto& ph = h->phases[q];
+      PhaseLaunch a = phase_args(h, ph);
+      a.P = xbar;
+      a.lam_in = lam_pre;
+      a.tape = const_cast<float4*>(tape_k);
+      a.lb = h->lb.as<float2>();
+      a.acc = h->acc.as<double>();
+      launch(h, XPBD_K_VJP_PHASE, ph.units, s,
+             [&] { launch_phase_vjp(a, ph.shape(), first, last, s); }, ph.bytes_vjp);
+    }
+    for (int col = h->use_phases ? -1 : h->K - 1; col >= 0; --col) {
+      const std::vector<Seg>& segs = h->colors[col];
+      for (int q = (int)segs.size() - 1; q >= 0; --q) {
+        const Seg& g = segs[q];
+        size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+        launch(h, XPBD_K_VJP_DIST + (int)g.type, g.count, s, [&] {
+          launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count,
+                     tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type],
+                     lam_pre ? lam_pre + ro : nullptr, xbar, h->lb.as<float2>() + ro,
+                     h->acc.as<double>() + ro, first, last, s);
         });
       }
-      const float4* tape_k = h->tape.as<float4>() + (size_t)k * tpi;
-      const float* lam_pre = k == 0 ? nullptr : h->lam_tape.as<float>() + (size_t)(k - 1) * h->slots;
-      for (int q = h->use_phases ? (int)h->phases.size() - 1 : -1; q >= 0; --q) {
-        const auto& ph = h->phases[q];
-        PhaseLaunch a = phase_args(h, ph);
-        a.P = xbar;
-        a.lam_in = lam_pre;
-        a.tape = const_cast<float4*>(tape_k);
-        a.lb = h->lb.as<float2>();
-        a.acc = h->acc.as<double>();
-        launch(h, XPBD_K_VJP_PHASE, ph.units, s,
-               [&] { launch_phase_vjp(a, ph.shape(), first, last, s); }, ph.bytes_vjp);
-      }
-      for (int col = h->use_phases ? -1 : h->K - 1; col >= 0; --col) {
-        const std::vector<Seg>& segs = h->colors[col];
-        for (int q = (int)segs.size() - 1; q >= 0; --q) {
-          const Seg& g = segs[q];
-          size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-          launch(h, XPBD_K_VJP_DIST + (int)g.type, g.count, s, [&] {
-            launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count,
-                       tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type],
-                       lam_pre ? lam_pre + ro : nullptr, xbar, h->lb.as<float2>() + ro,
-                       h->acc.as<double>() + ro, first, last, s);
-          });
-        }
-      }
-      LAUNCH_CHECK();
     }
-    if (contacts && out->d_collider) {
-      launch(h, XPBD_K_ADJ_OTHER, V, s,
-             [&] { launch_collider_partials(h->cgrad.as<float>(), h->cflags.as<uint8_t>(), V, partials, s); });
-      launch(h, XPBD_K_ADJ_OTHER, 1, s, [&] { launch_reduce_partials(partials, pb, 5, out->d_collider, true, s); });
-    }
-    const float* seed = seed_of[n] >= 0 ? seed_dx + 3 * (size_t)V * seed_of[n] : nullptr;
-    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] {
-      launch_adj_predict(xbar, vbar, ck_x(ck, V, n), seed, p->dt, out->d_f_vertex,
-                         out->d_f_global ? partials : nullptr, V, s);
-    });
-    if (out->d_f_global)
-      launch(h, XPBD_K_ADJ_OTHER, 1, s,
-             [&] { launch_reduce_partials(partials, pb, 3, out->d_f_global + 3 * (size_t)n, false, s); });
     LAUNCH_CHECK();
   }
-  if (out->d_x0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(xbar, out->d_x0, V, s); });
-  if (out->d_v0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(vbar, out->d_v0, V, s); });
+  if (A.contacts && out->d_collider) {
+    launch(h, XPBD_K_ADJ_OTHER, V, s,
+           [&] { launch_collider_partials(h->cgrad.as<float>(), h->cflags.as<uint8_t>(), V, partials, s); });
+    launch(h, XPBD_K_ADJ_OTHER, 1, s, [&] { launch_reduce_partials(partials, A.pb, 5, out->d_collider, true, s); });
+  }
+  const float* seed = A.seed_of[n] >= 0 ? A.seed_dx + 3 * (size_t)V * A.seed_of[n] : nullptr;
+  launch(h, XPBD_K_ADJ_OTHER, V, s, [&] {
+    launch_adj_predict(xbar, vbar, ckx_n, seed, p->dt, out->d_f_vertex, out->d_f_global ? partials : nullptr,
+                       out->d_f_vertex_steps ? out->d_f_vertex_steps + 3 * (size_t)V * n : nullptr, V, s);
+  });
+  if (out->d_f_global)
+    launch(h, XPBD_K_ADJ_OTHER, 1, s,
+           [&] { launch_reduce_partials(partials, A.pb, 3, out->d_f_global + 3 * (size_t)n, false, s); });
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+// dL/dx0, dL/dv0 and the compliance gradient in caller order.
+xpbd_status adjoint_end(xpbd_solver* h, const xpbd_params* p, const xpbd_grads* out, cudaStream_t s) {
+  const int V = h->V;
+  if (out->d_x0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(h->xbar.as<float4>(), out->d_x0, V, s); });
+  if (out->d_v0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(h->vbar.as<float4>(), out->d_v0, V, s); });
   if (out->d_compliance) {
     float inv_dt2 = 1.f / (p->dt * p->dt);
     const bool ph = h->use_phases;
@@ -978,6 +996,125 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   }
   LAUNCH_CHECK();
   return XPBD_OK;
+}
+
+// Forward step n from state (x_n, v_n) to (x_{n+1}, v_{n+1}) at nx (positions; velocities follow).
+xpbd_status forward_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t iters, const float4* ckx_n,
+                         const float4* ckv_n, float4* nx, cudaStream_t s) {
+  xpbd_status st = run_step(h, p, n, iters, ckx_n, ckv_n, false, s);
+  if (st != XPBD_OK) return st;
+  const float inv_dt = 1.f / p->dt;
+  launch(h, XPBD_K_VELOCITY, h->V, s, [&] {
+    launch_velocity(h->P.as<float4>(), ckx_n, nx, nx + h->V, inv_dt, h->V, h->d_err, s);
+  });
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t xpbd_sparse_slots(int32_t steps, int32_t stride) {
+  if (steps < 0 || stride < 1) return -1;
+  return steps / stride + 1 + (steps % stride ? 1 : 0);
+}
+
+int32_t xpbd_sparse_slot(int32_t steps, int32_t stride, int32_t step) {
+  if (steps < 0 || stride < 1 || step < 0 || step > steps) return -1;
+  if (step % stride == 0) return step / stride;
+  return step == steps ? steps / stride + 1 : -1;
+}
+
+xpbd_status xpbd_forward_sparse(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                const float* x0, const float* v0, int32_t stride, float* ck, void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (stride < 1) return fail(XPBD_ERR_INVALID, "stride must be >= 1");
+  if (h->V > 0 && (!x0 || !v0 || !ck)) return fail(XPBD_ERR_INVALID, "x0/v0/checkpoints NULL");
+  if (h->V == 0) return XPBD_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_forward_ws(h);
+  if (st != XPBD_OK) return st;
+  CU_TRY(h->roll.ensure(sizeof(float4) * 4 * (size_t)h->V));
+  st = set_alpha(h, p, s, h->use_phases);
+  if (st != XPBD_OK) return st;
+  const size_t V = (size_t)h->V;
+  float4* ck4 = reinterpret_cast<float4*>(ck);
+  float4* roll = h->roll.as<float4>();
+  launch(h, XPBD_K_OTHER, h->V, s, [&] { launch_init_ckpt(x0, v0, h->d_w, ck4, ck4 + V, h->V, s); });
+  LAUNCH_CHECK();
+  const float4* cur = ck4;   // state n: a stored slot or the rolling buffer
+  for (int n = 0; n < steps; ++n) {
+    const int slot = xpbd_sparse_slot(steps, stride, n + 1);
+    float4* nx = slot >= 0 ? ck4 + 2 * V * slot : roll + 2 * V * ((n + 1) & 1);
+    st = forward_step(h, p, n, iters, cur, cur + V, nx, s);
+    if (st != XPBD_OK) return st;
+    cur = nx;
+  }
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                const float* ck, int32_t stride, int32_t n_seeds, const int32_t* seed_steps,
+                                const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
+                                void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (stride < 1) return fail(XPBD_ERR_INVALID, "stride must be >= 1");
+  if (!ck || !out || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  AdjointSweep A;
+  st = adjoint_begin(h, p, steps, iters, n_seeds, seed_steps, seed_dx, seed_dv_T, out, s, A);
+  if (st != XPBD_OK) return st;
+  const size_t V = (size_t)h->V;
+  if (steps > 0 && V > 0) {
+    CU_TRY(h->seg.ensure(sizeof(float4) * 2 * V * (size_t)std::max(stride - 1, 1)));
+    const float4* ck4 = reinterpret_cast<const float4*>(ck);
+    float4* seg = h->seg.as<float4>();
+    // segments [s0, s0 + len) from the last to the first: recompute the states inside a
+    // segment from its stored first state, then reverse its steps
+    for (int s0 = ((steps - 1) / stride) * stride; s0 >= 0; s0 -= stride) {
+      const int len = std::min(stride, steps - s0);
+      const float4* first = ck4 + 2 * V * (size_t)(s0 / stride);
+      const float4* cur = first;
+      for (int j = 0; j + 1 < len; ++j) {
+        float4* nx = seg + 2 * V * (size_t)j;
+        st = forward_step(h, p, s0 + j, iters, cur, cur + V, nx, s);
+        if (st != XPBD_OK) return st;
+        cur = nx;
+      }
+      for (int n = s0 + len - 1; n >= s0; --n) {
+        const float4* x_n = n == s0 ? first : seg + 2 * V * (size_t)(n - s0 - 1);
+        st = adjoint_step(h, p, n, iters, x_n, x_n + V, A, s);
+        if (st != XPBD_OK) return st;
+      }
+    }
+  }
+  return adjoint_end(h, p, out, s);
+}
+
+xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                         const float* ck, int32_t n_seeds, const int32_t* seed_steps,
+                         const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
+                         void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (!ck || !out || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  AdjointSweep A;
+  st = adjoint_begin(h, p, steps, iters, n_seeds, seed_steps, seed_dx, seed_dv_T, out, s, A);
+  if (st != XPBD_OK) return st;
+  for (int n = steps - 1; n >= 0; --n) {
+    st = adjoint_step(h, p, n, iters, ck_x(ck, h->V, n), ck_v(ck, h->V, n), A, s);
+    if (st != XPBD_OK) return st;
+  }
+  return adjoint_end(h, p, out, s);
 }
 
 static const char* kClassNames[XPBD_KERNEL_CLASSES] = {
@@ -1060,7 +1197,8 @@ xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t ste
     const float4* xn = ck_x(ck, h->V, n);
     const float4* vn = ck_v(ck, h->V, n);
     launch(h, XPBD_K_PREDICT, h->V, s, [&] {
-      launch_predict(xn, vn, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex, p->dt,
+      launch_predict(xn, vn, P, p->f_global ? p->f_global + 3 * (size_t)n : nullptr, p->f_vertex,
+                     p->f_vertex_steps ? p->f_vertex_steps + 3 * (size_t)h->V * n : nullptr, p->dt,
                      p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
     });
     for (int k = 0; k < iters; ++k) {

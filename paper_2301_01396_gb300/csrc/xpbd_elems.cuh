@@ -187,18 +187,21 @@ __device__ __forceinline__ void set_alpha_elem(int i, Rec* __restrict__ rec, con
   rec[i].at = a;
 }
 
-// Inertial prediction (Eq. xpbdUpdateRule): p = x + dt v + dt^2 (w (G_n + W_i) + [w > 0] g),
+// Inertial prediction (Eq. xpbdUpdateRule): p = x + dt v + dt^2 (w (G_n + W_i + F_{n,i}) + [w > 0] g),
 // and contact detection at p: a contact is active for the whole step when C(p) < 0.
+// fvs_n: step n's force per vertex F_{n,i} (the keyframe example's controls), or NULL.
 __device__ __forceinline__ void predict_elem(int i, const float4* __restrict__ ckx, const float4* __restrict__ ckv,
                                              float4* __restrict__ P, const float* __restrict__ fg_n,
-                                             const float* __restrict__ fv, float dt, float gx, float gy,
-                                             float gz, const Collide& c, uint8_t* __restrict__ cflags) {
+                                             const float* __restrict__ fv, const float* __restrict__ fvs_n,
+                                             float dt, float gx, float gy, float gz, const Collide& c,
+                                             uint8_t* __restrict__ cflags) {
   float4 x = ckx[i];
   float4 v = ckv[i];
   float w = x.w;
   float fx = 0.f, fy = 0.f, fz = 0.f;
   if (fg_n) { fx = fg_n[0]; fy = fg_n[1]; fz = fg_n[2]; }
   if (fv) { fx += fv[3 * i]; fy += fv[3 * i + 1]; fz += fv[3 * i + 2]; }
+  if (fvs_n) { fx += fvs_n[3 * i]; fy += fvs_n[3 * i + 1]; fz += fvs_n[3 * i + 2]; }
   float free_ = w > 0.f ? 1.f : 0.f;
   float dt2 = dt * dt;
   float4 p;
@@ -599,9 +602,11 @@ __device__ __forceinline__ void collider_contrib(int i, const float* __restrict_
 //   xbar_n = xbar_partial + pbar (+ dL/dx_n seed),  vbar_n = dt pbar,
 //   fbar_i = dt^2 w_i pbar_i  (Sec. 5.6: force gradients from the adjoint velocities),
 //   dL/dW_i += fbar_i (float64); fbar_i is added to fs for dL/dG_n.
+// fvs_out: step n's per-vertex force gradient dt^2 w pbar (written, float64), or NULL.
 __device__ __forceinline__ void adj_predict_elem(int i, float4* __restrict__ xbar, float4* __restrict__ vbar,
                                                  const float4* __restrict__ ckx_n, const float* __restrict__ seed,
-                                                 float dt, double* __restrict__ fv_acc, double fs[3]) {
+                                                 float dt, double* __restrict__ fv_acc, double fs[3],
+                                                 double* __restrict__ fvs_out = nullptr) {
   float dt2 = dt * dt;
   float4 pb = xbar[i];
   float4 xp = vbar[i];
@@ -621,6 +626,11 @@ __device__ __forceinline__ void adj_predict_elem(int i, float4* __restrict__ xba
     fv_acc[3 * i] += fx;
     fv_acc[3 * i + 1] += fy;
     fv_acc[3 * i + 2] += fz;
+  }
+  if (fvs_out) {
+    fvs_out[3 * i] = fx;
+    fvs_out[3 * i + 1] = fy;
+    fvs_out[3 * i + 2] = fz;
   }
   fs[0] += fx;
   fs[1] += fy;

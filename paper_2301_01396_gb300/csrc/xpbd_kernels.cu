@@ -60,17 +60,17 @@ void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float*
 
 __global__ void k_predict(const float4* __restrict__ ckx, const float4* __restrict__ ckv,
                           float4* __restrict__ P, const float* __restrict__ fg_n,
-                          const float* __restrict__ fv, float dt, float gx, float gy, float gz,
-                          Collide c, uint8_t* __restrict__ cflags, int V) {
+                          const float* __restrict__ fv, const float* __restrict__ fvs_n, float dt, float gx,
+                          float gy, float gz, Collide c, uint8_t* __restrict__ cflags, int V) {
   XPBD_TID_OR_RETURN(V);
-  predict_elem(i, ckx, ckv, P, fg_n, fv, dt, gx, gy, gz, c, cflags);
+  predict_elem(i, ckx, ckv, P, fg_n, fv, fvs_n, dt, gx, gy, gz, c, cflags);
 }
 
 void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float* fg_n,
-                    const float* fv, float dt, float gx, float gy, float gz, Collide c,
+                    const float* fv, const float* fvs_n, float dt, float gx, float gy, float gz, Collide c,
                     uint8_t* cflags, int V, cudaStream_t s) {
   if (V > 0)
-    k_predict<<<grid_for(V), kBlock, 0, s>>>(ckx, ckv, P, fg_n, fv, dt, gx, gy, gz, c, cflags, V);
+    k_predict<<<grid_for(V), kBlock, 0, s>>>(ckx, ckv, P, fg_n, fv, fvs_n, dt, gx, gy, gz, c, cflags, V);
 }
 
 __global__ void k_proj_dist(const DistRec* __restrict__ rec, int n, float4* __restrict__ P,
@@ -228,16 +228,16 @@ void launch_collider_partials(const float* cgrad, const uint8_t* cflags, int V, 
 __global__ void k_adj_predict(float4* __restrict__ xbar, float4* __restrict__ vbar,
                               const float4* __restrict__ ckx_n, const float* __restrict__ seed,
                               float dt, double* __restrict__ fv_acc, double* __restrict__ fg_partials,
-                              int V) {
+                              double* __restrict__ fvs_out, int V) {
   double fs[3] = {0, 0, 0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x)
-    adj_predict_elem(i, xbar, vbar, ckx_n, seed, dt, fv_acc, fs);
+    adj_predict_elem(i, xbar, vbar, ckx_n, seed, dt, fv_acc, fs, fvs_out);
   if (fg_partials) block_sum_store<3>(fs, fg_partials + 3 * blockIdx.x);
 }
 
 void launch_adj_predict(float4* xbar, float4* vbar, const float4* ckx_n, const float* seed,
-                        float dt, double* fv_acc, double* fg_partials, int V, cudaStream_t s) {
-  k_adj_predict<<<partial_blocks(V), kBlock, 0, s>>>(xbar, vbar, ckx_n, seed, dt, fv_acc, fg_partials, V);
+                        float dt, double* fv_acc, double* fg_partials, double* fvs_out, int V, cudaStream_t s) {
+  k_adj_predict<<<partial_blocks(V), kBlock, 0, s>>>(xbar, vbar, ckx_n, seed, dt, fv_acc, fg_partials, fvs_out, V);
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, int ncomp,

@@ -29,7 +29,7 @@ void launch_init_ckpt(const float* x0, const float* v0, const float* w, float4* 
 void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float* compliance,
                       float inv_dt2, int* err, cudaStream_t s);
 void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float* fg_n,
-                    const float* fv, float dt, float gx, float gy, float gz, Collide c,
+                    const float* fv, const float* fvs_n, float dt, float gx, float gy, float gz, Collide c,
                     uint8_t* cflags, int V, cudaStream_t s);
 // lam_in == nullptr means lambda = 0 (first iteration of a step); tape == nullptr skips the
 // record of pre-projection positions (forward only)
@@ -55,7 +55,7 @@ int partial_blocks(int V);
 void launch_collider_partials(const float* cgrad, const uint8_t* cflags, int V, double* partials,
                               cudaStream_t s);
 void launch_adj_predict(float4* xbar, float4* vbar, const float4* ckx_n, const float* seed,
-                        float dt, double* fv_acc, double* fg_partials, int V, cudaStream_t s);
+                        float dt, double* fv_acc, double* fg_partials, double* fvs_out, int V, cudaStream_t s);
 void launch_reduce_partials(const double* partials, int nblocks, int ncomp, double* out,
                             bool accumulate, cudaStream_t s);
 void launch_finalize_compliance(SegType t, const void* rec, const int* perm, int n,

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_tick(const TickItem* __restrict__
     case IK_PREDICT:
       if (ok)
         predict_elem(i, (const float4*)it.p[0], (const float4*)it.p[1], (float4*)it.p[2], (const float*)it.p[3],
-                     (const float*)it.p[4], it.f[0], it.f[1], it.f[2], it.f[3], it.col, (uint8_t*)it.p[5]);
+                     (const float*)it.p[4], nullptr, it.f[0], it.f[1], it.f[2], it.f[3], it.col, (uint8_t*)it.p[5]);
       break;
     case IK_PROJ:
       if (ok) {
@@ -726,6 +726,8 @@ xpbd_status xpbd_server_submit(xpbd_server s, const xpbd_request* r, uint64_t* t
   if (st != XPBD_OK) return st;
   if (r->handle->V > 0 && (!r->x0 || !r->v0 || !r->target))
     return fail(XPBD_ERR_INVALID, "x0/v0/target NULL");
+  if (r->params.f_vertex_steps || r->grads.d_f_vertex_steps)
+    return fail(XPBD_ERR_INVALID, "per-step per-vertex forces are not served (use xpbd_forward/xpbd_adjoint)");
   std::unique_ptr<Request> q(new Request());
   q->r = *r;
   q->h = r->handle;

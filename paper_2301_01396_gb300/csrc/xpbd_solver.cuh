@@ -78,6 +78,7 @@ struct xpbd_solver {
   DevBuf P, lam, cflags, lamc;                       // forward
   DevBuf tape, lam_tape, tape_c, lamc_tape;          // replay tapes
   DevBuf xbar, vbar, lb, acc, lbc, cgrad, partials;  // reverse
+  DevBuf roll, seg;                                  // sparse checkpoints: rolling / segment states
   // launch statistics per kernel class (always counted; timed with CUDA events on the
   // launching stream while profiling is enabled)
   bool prof_on = false;

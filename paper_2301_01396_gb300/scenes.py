@@ -66,6 +66,7 @@ class Scene:
     thickness: float = 0.0
     f_global: Optional[np.ndarray] = None  # [steps,3] force added to every vertex at step n
     f_vertex: Optional[np.ndarray] = None  # [V,3] time-constant per-vertex force
+    f_vertex_steps: Optional[np.ndarray] = None  # [steps,V,3] force on each vertex at each step
     name: str = "scene"
     meta: dict = field(default_factory=dict)
 

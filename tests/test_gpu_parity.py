@@ -88,6 +88,36 @@ def test_adjoint_matches_oracle(name, cases):
         assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
 
 
+def _keyframe_force_scene():
+    """A cloth on the sphere driven by a force per vertex per step (the keyframe example's
+    control variables) on top of the global and wind forces."""
+    sc = helpers.small_sphere_cloth(10, steps=5, iters=3, seed=4)
+    rng = np.random.default_rng(31)
+    m_i = 2.56 / sc.V
+    sc.f_vertex_steps = scenes.f32(0.3 * m_i * 9.81 * rng.standard_normal((sc.steps, sc.V, 3)))
+    return sc
+
+
+def test_per_step_vertex_forces_match_oracle():
+    sc = _keyframe_force_scene()
+    xs_ref, vs_ref = oracle.forward(sc)
+    assert contact_margin(sc, xs_ref, vs_ref) > 1e-5
+    solver, p, ck, xs, vs = gpu_forward(sc)
+    assert contact_signs_agree(sc, xs, vs, xs_ref, vs_ref)
+    assert np.abs(xs - xs_ref).max() < POS_TOL
+    rng = np.random.default_rng(32)
+    seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3))), 2: scenes.f32(rng.standard_normal((sc.V, 3)))}
+    ref = oracle.adjoint(sc, seeds)
+    got = solver.adjoint(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
+                         want=GRAD_KEYS + ("f_vertex_steps",))
+    torch.cuda.synchronize()
+    for k in ("compliance", "x0", "v0", "f_global", "f_vertex", "f_vertex_steps"):
+        e = rel_err(got[k].cpu().numpy().reshape(ref[k].shape), ref[k])
+        assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
+    fvs = got["f_vertex_steps"].cpu().numpy()
+    assert np.allclose(fvs.sum(0), got["f_vertex"].cpu().numpy(), rtol=1e-12, atol=0)
+
+
 def test_loss_and_seed_match_definition():
     sc = helpers.small_cloth(9, steps=5, iters=4)
     solver, p, ck, xs, _ = gpu_forward(sc)

@@ -306,6 +306,7 @@ def test_adjoint_equals_tangent(oracle_mod, name):
         "f_global": rng.standard_normal((N, 3)),
         "f_vertex": rng.standard_normal((sc.V, 3)),
         "collider": rng.standard_normal(5),
+        "f_vertex_steps": rng.standard_normal((N, sc.V, 3)),
     }
     for key, d in dirs.items():
         dxs, _ = oracle_mod.tangent(sc, {key: d})
@@ -381,6 +382,48 @@ def test_force_gradient_identity(oracle_mod):
     rng = np.random.default_rng(5)
     gr = oracle_mod.adjoint(sc, {sc.steps: rng.standard_normal((sc.V, 3))})
     assert rel(gr["f_vertex"].sum(0), gr["f_global"].sum(0)) < 1e-12
+
+
+def test_per_step_vertex_force_gradient_identities(oracle_mod):
+    """The keyframe example's control variables, one force per vertex per step (Sec.
+    "Keyframe Simulation"): their gradient dt^2 w pbar_n, summed over steps, is the
+    time-constant per-vertex force gradient, and summed over vertices, each step's global
+    force gradient; pinned vertices (w = 0) get none."""
+    sc = small_sphere_cloth(6, steps=4, iters=2)
+    sc.inv_mass = sc.inv_mass.copy()
+    sc.inv_mass[0] = 0.0
+    sc.v0 = sc.v0.copy()
+    sc.v0[0] = 0.0
+    rng = np.random.default_rng(6)
+    gr = oracle_mod.adjoint(sc, {sc.steps: rng.standard_normal((sc.V, 3)), 2: rng.standard_normal((sc.V, 3))})
+    fvs = gr["f_vertex_steps"]
+    assert fvs.shape == (sc.steps, sc.V, 3)
+    assert rel(fvs.sum(0), gr["f_vertex"]) < 1e-12
+    assert rel(fvs.sum(1), gr["f_global"]) < 1e-12
+    assert np.all(fvs[:, 0] == 0.0)
+
+
+def test_per_step_vertex_force_matches_central_fd(oracle_mod):
+    """The forward applies F_{n,i} at step n and the reverse sweep's gradient for it agrees
+    with central finite differences of the loss."""
+    sc = small_cloth(5, bending=True, steps=5, iters=3, plane_h=-0.02, v_scale=0.2, seed=21)
+    rng = np.random.default_rng(22)
+    sc.f_vertex_steps = 0.05 * rng.standard_normal((sc.steps, sc.V, 3))
+    xs, _ = oracle_mod.forward(sc)
+    x_free, _ = oracle_mod.forward(sc, f_vertex_steps=np.zeros_like(sc.f_vertex_steps))
+    assert np.abs(xs[-1] - x_free[-1]).max() > 1e-6          # the forces move the cloth
+    target = xs[-1] + 0.01 * rng.standard_normal((sc.V, 3))
+    gr = oracle_mod.adjoint(sc, {sc.steps: xs[-1] - target})
+    for n, i, c in [(0, 7, 1), (2, 12, 0), (4, 18, 2)]:
+        h = 1e-4
+        fp, fm = sc.f_vertex_steps.copy(), sc.f_vertex_steps.copy()
+        fp[n, i, c] += h
+        fm[n, i, c] -= h
+        lp = 0.5 * np.sum((oracle_mod.forward(sc, f_vertex_steps=fp)[0][-1] - target) ** 2)
+        lm = 0.5 * np.sum((oracle_mod.forward(sc, f_vertex_steps=fm)[0][-1] - target) ** 2)
+        fd = (lp - lm) / (2 * h)
+        g = gr["f_vertex_steps"][n, i, c]
+        assert abs(fd - g) <= 1e-6 * abs(g) + 1e-10, (n, i, c, fd, g)
 
 
 def test_total_gradient_is_sum_of_constraint_contributions(oracle_mod):
