@@ -155,6 +155,27 @@ def forward(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, 
     return xs, vs
 
 
+def forward_multipliers(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, x0=None, v0=None,
+                        compliance=None, f_global=None, f_vertex=None, f_vertex_steps=None):
+    """Forward simulation returning also what each step ended with: (xs, vs, lam [steps, m]
+    by constraint id, lam_c [steps, V, 2] of the plane / sphere contact of each vertex,
+    active [steps, V, 2] the contact set)."""
+    steps = scene.steps if steps is None else steps
+    iters = scene.iters if iters is None else iters
+    a = _Args(scene, compliance, f_global, f_vertex, None, None, steps, f_vertex_steps)
+    x0a, x0p = _d(scene.x0 if x0 is None else x0)
+    v0a, v0p = _d(scene.v0 if v0 is None else v0)
+    xs = np.zeros((steps + 1, scene.V, 3))
+    vs = np.zeros((steps + 1, scene.V, 3))
+    lam = np.zeros((steps, scene.m))
+    lamc = np.zeros((steps, scene.V, 2))
+    act = np.zeros((steps, scene.V, 2), np.uint8)
+    lib().oracle_forward_multipliers(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p,
+                                     xs.ctypes.data_as(_dp), vs.ctypes.data_as(_dp), lam.ctypes.data_as(_dp),
+                                     lamc.ctypes.data_as(_dp), act.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return xs, vs, lam, lamc, act.astype(bool)
+
+
 def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
             seed_dv_T=None, x0=None, v0=None, compliance=None, f_global=None, f_vertex=None,
             plane_h=None, sphere=None, f_vertex_steps=None) -> dict:

@@ -482,7 +482,9 @@ void solve_iteration(const Model& M, const Params<T>& P, Work<T>& W) {
 // Forward simulation over `steps` steps; xs/vs receive x_0..x_N and v_0..v_N.
 template <class T>
 void forward(const Model& M, const Params<T>& P, int steps, int iters, const std::vector<T>& x0,
-             const std::vector<T>& v0, std::vector<T>& xs, std::vector<T>& vs) {
+             const std::vector<T>& v0, std::vector<T>& xs, std::vector<T>& vs,
+             std::vector<T>* lam_steps = nullptr, std::vector<T>* lamc_steps = nullptr,
+             std::vector<uint8_t>* active_steps = nullptr) {
   size_t V3n = (size_t)M.V * 3;
   xs.assign(V3n * (steps + 1), T(0.0));
   vs.assign(V3n * (steps + 1), T(0.0));
@@ -502,6 +504,10 @@ void forward(const Model& M, const Params<T>& P, int steps, int iters, const std
     std::fill(W.lam_c.begin(), W.lam_c.end(), T(0.0));
     detect_contacts(M, P, W);
     for (int k = 0; k < iters; ++k) solve_iteration(M, P, W);
+    // the multipliers and contact set the step ended with
+    if (lam_steps) lam_steps->insert(lam_steps->end(), W.lam.begin(), W.lam.end());
+    if (lamc_steps) lamc_steps->insert(lamc_steps->end(), W.lam_c.begin(), W.lam_c.end());
+    if (active_steps) active_steps->insert(active_steps->end(), W.active.begin(), W.active.end());
     for (size_t i = 0; i < V3n; ++i) {
       xs[V3n * (n + 1) + i] = W.p[i];
       vs[V3n * (n + 1) + i] = (W.p[i] - x[i]) / P.dt;
@@ -834,6 +840,26 @@ int oracle_forward(const om_model* in, const om_params* pin, int32_t steps, int3
   forward(M, P, steps, iters, x, v, xs, vs);
   std::copy(xs.begin(), xs.end(), xs_out);
   if (vs_out) std::copy(vs.begin(), vs.end(), vs_out);
+  return 0;
+}
+
+// Forward simulation that also returns, per step, the multipliers the step ended with:
+// lam_out [steps*m] (constraint id order), lamc_out [steps*V*2] (plane, sphere contact of
+// each vertex) and active_out [steps*V*2] (1 where that contact was active).  Any output
+// may be NULL.
+int oracle_forward_multipliers(const om_model* in, const om_params* pin, int32_t steps, int32_t iters,
+                               const double* x0, const double* v0, double* xs_out, double* vs_out,
+                               double* lam_out, double* lamc_out, uint8_t* active_out) {
+  Model M = make_model(in);
+  Params<double> P = make_params<double>(M, pin, steps);
+  std::vector<double> x(x0, x0 + 3 * (size_t)M.V), v(v0, v0 + 3 * (size_t)M.V), xs, vs, lam, lamc;
+  std::vector<uint8_t> act;
+  forward(M, P, steps, iters, x, v, xs, vs, &lam, &lamc, &act);
+  if (xs_out) std::copy(xs.begin(), xs.end(), xs_out);
+  if (vs_out) std::copy(vs.begin(), vs.end(), vs_out);
+  if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
+  if (lamc_out) std::copy(lamc.begin(), lamc.end(), lamc_out);
+  if (active_out) std::copy(act.begin(), act.end(), active_out);
   return 0;
 }
 
