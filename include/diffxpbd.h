@@ -211,6 +211,35 @@ xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t ste
                                 const int32_t* seed_steps, const float* seed_dx, const float* seed_dv_T,
                                 const xpbd_grads* out, void* stream);
 
+/* ---- The paper's implicit adjoint (Sec. "Adjoint State Computation", Eq. adjointXPBD) ----
+   Instead of reversing the iterations, each step is differentiated as if solved exactly:
+   with x_{n+1} and the multipliers lambda the step ended with,
+     A = M + sum_j B_j,  B_j = grad C_j^T grad C_j / alpha~_j - lambda_j hess C_j
+   over the constraints and the step's active contacts, each block projected to positive
+   semi-definite in the constraint's relative coordinates when pd_project
+   (Sec. "Positive Definite Projection"); A y = xbar_{n+1} + vbar_{n+1}/dt is solved on the
+   free vertices by block-Jacobi preconditioned conjugate gradients, pinned vertices
+   filtered out (Sec. "Linear System Filtering"); then pbar = M y (free), pbar = b - A y
+   (pinned), alphabar~_j += -(lambda_j / alpha~_j) grad C_j . y, and the prediction adjoint
+   as in xpbd_adjoint.  The gradient differs from xpbd_adjoint's by design: XPBD's
+   iterations leave the primal residual M (x - p) - grad C^T lambda nonzero, so this is the
+   derivative of the exactly solved step at XPBD's end state. */
+typedef struct {
+  double cg_tol;                /* stop when |r| <= cg_tol |b| (free vertices, float64)   */
+  int32_t cg_max_iters;         /* per step                                                */
+  int32_t pd_project;           /* 1: project every block (the paper); 0: raw blocks       */
+  int32_t* cg_iters_out;        /* HOST [steps] iterations used per step, or NULL          */
+} xpbd_implicit_opts;
+
+/* Implicit-adjoint gradients from dense checkpoints (as xpbd_adjoint: seeds, outputs,
+   determinism).  Every compliance must be > 0.  d_collider must be NULL (no collider
+   gradient is formed).  Synchronises `stream` a few times per step (convergence checks).
+   Works on the per-color records whatever exec_mode the handle has. */
+xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                  const float* checkpoints, int32_t n_seeds, const int32_t* seed_steps,
+                                  const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
+                                  const xpbd_implicit_opts* opts, void* stream);
+
 /* Synchronise `stream` and report (then clear) the device error word of the handle:
    XPBD_ERR_TIMEOUT if, since the last check, a bounded wait of a phase kernel gave up;
    XPBD_ERR_NONFINITE if a call was given a negative or non-finite compliance or a step

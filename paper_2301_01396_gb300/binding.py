@@ -51,6 +51,11 @@ class XpbdGrads(C.Structure):
                 ("d_f_vertex_steps", C.c_void_p)]
 
 
+class XpbdImplicitOpts(C.Structure):
+    _fields_ = [("cg_tol", C.c_double), ("cg_max_iters", C.c_int32), ("pd_project", C.c_int32),
+                ("cg_iters_out", _ip)]
+
+
 KERNEL_CLASSES = ("fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
                   "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
                   "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
@@ -96,7 +101,7 @@ def lib():
                      "xpbd_server_create", "xpbd_server_destroy", "xpbd_server_submit", "xpbd_server_run",
                      "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info",
                      "xpbd_selftest_wait_timeout", "xpbd_forward_sparse", "xpbd_adjoint_sparse",
-                     "xpbd_sparse_slots", "xpbd_sparse_slot"):
+                     "xpbd_sparse_slots", "xpbd_sparse_slot", "xpbd_adjoint_implicit"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -322,6 +327,32 @@ class Solver:
                                              int(stride), len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g),
                                              _stream(stream)))
         return out
+
+    def adjoint_implicit(self, params: Params, steps: int, iters: int, checkpoints: torch.Tensor, seeds: dict,
+                         seed_dv_T: Optional[torch.Tensor] = None,
+                         want=("compliance", "x0", "v0", "f_global", "f_vertex"), cg_tol: float = 1e-10,
+                         cg_max_iters: int = 5000, pd_project: bool = True, stream=None):
+        """The paper's implicit adjoint (xpbd_adjoint_implicit).  Returns (float64 gradients,
+        conjugate-gradient iterations per step)."""
+        dev = checkpoints.device
+        keys = sorted(seeds)
+        sd = torch.stack([seeds[k] for k in keys]).contiguous() if keys else None
+        shapes = dict(compliance=(self.m,), x0=(self.V, 3), v0=(self.V, 3), f_global=(max(steps, 1), 3),
+                      f_vertex=(self.V, 3), f_vertex_steps=(max(steps, 1), self.V, 3))
+        out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
+        g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
+                      d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
+                      d_f_vertex=_ptr(out.get("f_vertex")), d_collider=None,
+                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")))
+        its = (C.c_int32 * max(steps, 1))()
+        o = XpbdImplicitOpts(cg_tol=float(cg_tol), cg_max_iters=int(cg_max_iters), pd_project=int(bool(pd_project)),
+                             cg_iters_out=C.cast(its, _ip))
+        p = params.c_struct()
+        ks = (C.c_int32 * max(len(keys), 1))(*keys)
+        _check(lib().xpbd_adjoint_implicit(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
+                                           len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), C.byref(o),
+                                           _stream(stream)))
+        return out, list(its)[:steps]
 
     def sync_status(self, stream=None):
         _check(lib().xpbd_sync_status(self._h, _stream(stream)))

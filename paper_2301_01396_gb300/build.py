@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(OUT_DIR, "libdiffxpbd.so")
-SOURCES = ["xpbd_kernels.cu", "xpbd_phase.cu", "xpbd_api.cu", "xpbd_serve.cu"]
+SOURCES = ["xpbd_kernels.cu", "xpbd_phase.cu", "xpbd_implicit.cu", "xpbd_api.cu", "xpbd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Division and square root use the approximate hardware forms (about 1 ulp): the kernels
 # are latency-bound and the IEEE sequences lengthen every constraint's dependency chain;

@@ -76,7 +76,8 @@ xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool
 // With `record`, the multipliers of iteration k go to lam_tape[k] and the pre-projection
 // positions to tape[k] (replay for the reverse sweep); otherwise lambda is updated in place.
 xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, const float4* ckx_n,
-                     const float4* ckv_n, bool record, cudaStream_t s) {
+                     const float4* ckv_n, bool record, cudaStream_t s, bool per_color = false) {
+  const bool phases = h->use_phases && !per_color;
   Collide c = make_collide(p);
   float4* P = h->P.as<float4>();
   uint8_t* cf = h->cflags.as<uint8_t>();
@@ -99,7 +100,7 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
       lam_in = k == 0 ? nullptr : h->lam.as<float>();
       lam_out = h->lam.as<float>();
     }
-    if (h->use_phases) {
+    if (phases) {
       for (const auto& ph : h->phases) {
         PhaseLaunch a = phase_args(h, ph);
         a.P = P;
@@ -781,7 +782,8 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
                     &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
-                    &h->partials, &h->roll, &h->seg};
+                    &h->partials, &h->roll, &h->seg, &h->imp_blocks, &h->imp_vec, &h->imp_dinv,
+                    &h->imp_sc};
   for (DevBuf* b : bufs) b->release();
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -910,6 +912,9 @@ xpbd_status adjoint_begin(xpbd_solver* h, const xpbd_params* p, int32_t steps, i
   return XPBD_OK;
 }
 
+xpbd_status adjoint_predict(xpbd_solver* h, const xpbd_params* p, int n, const float4* ckx_n, const AdjointSweep& A,
+                            cudaStream_t s);
+
 // Reverse of step n from its state (x_n, v_n): replay with tapes, then the reverse
 // iterations, then the adjoint of the prediction.
 xpbd_status adjoint_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t iters, const float4* ckx_n,
@@ -966,9 +971,20 @@ xpbd_status adjoint_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t it
            [&] { launch_collider_partials(h->cgrad.as<float>(), h->cflags.as<uint8_t>(), V, partials, s); });
     launch(h, XPBD_K_ADJ_OTHER, 1, s, [&] { launch_reduce_partials(partials, A.pb, 5, out->d_collider, true, s); });
   }
+  return adjoint_predict(h, p, n, ckx_n, A, s);
+}
+
+// Adjoint of step n's prediction, xbar holding pbar: dL/dx_n, dL/dv_n, the seed at step n
+// and the force gradients.
+xpbd_status adjoint_predict(xpbd_solver* h, const xpbd_params* p, int n, const float4* ckx_n, const AdjointSweep& A,
+                            cudaStream_t s) {
+  const int V = h->V;
+  const xpbd_grads* out = A.out;
+  double* partials = h->partials.as<double>();
   const float* seed = A.seed_of[n] >= 0 ? A.seed_dx + 3 * (size_t)V * A.seed_of[n] : nullptr;
   launch(h, XPBD_K_ADJ_OTHER, V, s, [&] {
-    launch_adj_predict(xbar, vbar, ckx_n, seed, p->dt, out->d_f_vertex, out->d_f_global ? partials : nullptr,
+    launch_adj_predict(h->xbar.as<float4>(), h->vbar.as<float4>(), ckx_n, seed, p->dt, out->d_f_vertex,
+                       out->d_f_global ? partials : nullptr,
                        out->d_f_vertex_steps ? out->d_f_vertex_steps + 3 * (size_t)V * n : nullptr, V, s);
   });
   if (out->d_f_global)
@@ -978,14 +994,16 @@ xpbd_status adjoint_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t it
   return XPBD_OK;
 }
 
-// dL/dx0, dL/dv0 and the compliance gradient in caller order.
-xpbd_status adjoint_end(xpbd_solver* h, const xpbd_params* p, const xpbd_grads* out, cudaStream_t s) {
+// dL/dx0, dL/dv0 and the compliance gradient in caller order (the accumulators in the
+// phase-plan slot order when `phase_layout`, else in the per-color one).
+xpbd_status adjoint_end(xpbd_solver* h, const xpbd_params* p, const xpbd_grads* out, cudaStream_t s,
+                        bool phase_layout) {
   const int V = h->V;
   if (out->d_x0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(h->xbar.as<float4>(), out->d_x0, V, s); });
   if (out->d_v0) launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_to_double(h->vbar.as<float4>(), out->d_v0, V, s); });
   if (out->d_compliance) {
     float inv_dt2 = 1.f / (p->dt * p->dt);
-    const bool ph = h->use_phases;
+    const bool ph = phase_layout;
     for (int t = 0; t < 4; ++t) {
       const int off = ph ? h->pslot_off[t] : h->rec_off[t], cnt = ph ? h->n_prec[t] : h->n_rec[t];
       launch(h, XPBD_K_ADJ_OTHER, cnt, s, [&] {
@@ -1094,7 +1112,126 @@ xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t ste
       }
     }
   }
-  return adjoint_end(h, p, out, s);
+  return adjoint_end(h, p, out, s, h->use_phases);
+}
+
+xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
+                                  const float* ck, int32_t n_seeds, const int32_t* seed_steps, const float* seed_dx,
+                                  const float* seed_dv_T, const xpbd_grads* out, const xpbd_implicit_opts* o,
+                                  void* stream) {
+  g_err.clear();
+  xpbd_status st = check_params(h, p, steps, iters);
+  if (st != XPBD_OK) return st;
+  if (!ck || !out || !o || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  if (out->d_collider)
+    return fail(XPBD_ERR_INVALID, "the implicit adjoint forms no collider-parameter gradient (d_collider must be NULL)");
+  if (!(o->cg_tol > 0.0) || o->cg_max_iters < 1) return fail(XPBD_ERR_INVALID, "cg_tol must be > 0 and cg_max_iters >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  AdjointSweep A;
+  st = adjoint_begin(h, p, steps, iters, n_seeds, seed_steps, seed_dx, seed_dv_T, out, s, A);
+  if (st != XPBD_OK) return st;
+  if (h->use_phases) {   // the solve runs on the per-color records (global vertex indices)
+    st = set_alpha(h, p, s, false);
+    if (st != XPBD_OK) return st;
+  }
+  const int V = h->V;
+  const size_t V3 = 3 * (size_t)V;
+  const int64_t nq = (int64_t)h->n_rec[1] + h->n_rec[2] + h->n_rec[3];
+  CU_TRY(h->imp_blocks.ensure(sizeof(float) * 45 * (size_t)std::max<int64_t>(nq, 1)));
+  CU_TRY(h->imp_vec.ensure(sizeof(double) * 6 * std::max<size_t>(V3, 1)));
+  CU_TRY(h->imp_dinv.ensure(sizeof(double) * 9 * (size_t)std::max(V, 1)));
+  CU_TRY(h->imp_sc.ensure(sizeof(double) * 8));
+  double* vb = h->imp_vec.as<double>();
+  double *b = vb, *y = vb + V3, *r = vb + 2 * V3, *z = vb + 3 * V3, *pd_dir = vb + 4 * V3, *q = vb + 5 * V3;
+  double* dinv = h->imp_dinv.as<double>();
+  double* sc = h->imp_sc.as<double>();
+  double* partials = h->partials.as<double>();
+  float* blocks = h->imp_blocks.as<float>();
+  const int64_t boff[4] = {0, 0, h->n_rec[1], (int64_t)h->n_rec[1] + h->n_rec[2]};
+  const float* lam = h->lam.as<float>();
+  const Collide c = make_collide(p);
+  const bool pd = o->pd_project != 0;
+  const double tol2 = o->cg_tol * o->cg_tol;
+  float4* xbar = h->xbar.as<float4>();
+  float4* vbar = h->vbar.as<float4>();
+  for (int n = steps - 1; n >= 0 && V > 0; --n) {
+    const float4* X = ck_x(ck, V, n + 1);
+    const uint8_t* cf = c.flags ? h->cflags.as<uint8_t>() : nullptr;
+    const float2* lamc = h->lamc.as<float2>();
+    auto spmv = [&](const double* pin, double* qout) {   // q = A pin, color by color
+      launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_apply_mass_contacts(X, cf, lamc, c, pd, pin, qout, V, s); });
+      for (int col = 0; col < h->K; ++col)
+        for (const Seg& g : h->colors[col]) {
+          const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+          launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+            launch_apply_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
+                               blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, pin, qout, s);
+          });
+        }
+    };
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_adj_begin(xbar, vbar, 1.f / p->dt, V, s); });
+    st = run_step(h, p, n, iters, ck_x(ck, V, n), ck_v(ck, V, n), false, s, true);   // lambda, contacts
+    if (st != XPBD_OK) return st;
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_xbar_to_b(xbar, b, V, s); });
+    for (int t = 1; t < 4; ++t)
+      launch(h, XPBD_K_ADJ_OTHER, h->n_rec[t], s, [&] {
+        launch_quad_blocks((SegType)t, h->d_rec[t], h->n_rec[t], X, lam + h->rec_off[t],
+                           blocks + 45 * (size_t)boff[t], pd, s);
+      });
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_mass_contacts(X, cf, lamc, c, pd, dinv, V, s); });
+    for (int col = 0; col < h->K; ++col)
+      for (const Seg& g : h->colors[col]) {
+        const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+        launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+          launch_diag_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
+                            blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, dinv, s);
+        });
+      }
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_invert(X, dinv, V, s); });
+    LAUNCH_CHECK();
+    // preconditioned conjugate gradients on the free vertices
+    const int pb = partial_blocks(V);
+    launch_cg_start(X, b, dinv, y, r, z, pd_dir, partials, V, s);
+    launch_reduce_partials(partials, pb, 3, sc + 1, false, s);
+    double host[2];
+    CU_TRY(cudaMemcpyAsync(host, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    const double bb = host[0];
+    int used = 0;
+    if (bb > 0.0) {
+      for (int it = 0; it < o->cg_max_iters; ++it) {
+        const int old_slot = (it & 1) ? 4 : 1, new_slot = (it & 1) ? 1 : 4;
+        spmv(pd_dir, q);
+        launch_cg_pq(X, pd_dir, q, partials, V, s);
+        launch_reduce_partials(partials, pb, 1, sc, false, s);
+        launch_cg_step(sc, old_slot, pd_dir, q, dinv, y, r, z, partials, V, s);
+        launch_reduce_partials(partials, pb, 2, sc + new_slot, false, s);
+        launch_cg_dir(sc, old_slot, new_slot, z, pd_dir, V, s);
+        used = it + 1;
+        if ((it & 3) == 3 || it + 1 == o->cg_max_iters) {
+          LAUNCH_CHECK();
+          CU_TRY(cudaMemcpyAsync(host, sc + new_slot + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+          CU_TRY(cudaStreamSynchronize(s));
+          if (host[0] <= tol2 * bb) break;
+        }
+      }
+    } else {
+      CU_TRY(cudaMemsetAsync(y, 0, sizeof(double) * V3, s));
+    }
+    if (o->cg_iters_out) o->cg_iters_out[n] = used;
+    spmv(y, q);   // A y, pinned rows included
+    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_implicit_finish(X, b, y, q, xbar, V, s); });
+    for (int t = 0; t < 4; ++t)
+      launch(h, XPBD_K_ADJ_OTHER, h->n_rec[t], s, [&] {
+        launch_abar((SegType)t, h->d_rec[t], h->n_rec[t], X, lam + h->rec_off[t], y,
+                    h->acc.as<double>() + h->rec_off[t], s);
+      });
+    LAUNCH_CHECK();
+    st = adjoint_predict(h, p, n, ck_x(ck, V, n), A, s);
+    if (st != XPBD_OK) return st;
+  }
+  return adjoint_end(h, p, out, s, false);
 }
 
 xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
@@ -1114,7 +1251,7 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
     st = adjoint_step(h, p, n, iters, ck_x(ck, h->V, n), ck_v(ck, h->V, n), A, s);
     if (st != XPBD_OK) return st;
   }
-  return adjoint_end(h, p, out, s);
+  return adjoint_end(h, p, out, s, h->use_phases);
 }
 
 static const char* kClassNames[XPBD_KERNEL_CLASSES] = {

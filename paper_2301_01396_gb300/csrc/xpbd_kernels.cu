@@ -7,13 +7,7 @@ namespace xpbd {
 
 namespace {
 
-inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
-
 constexpr int kMaxPartialBlocks = 1024;
-
-#define XPBD_TID_OR_RETURN(n)                          \
-  const int i = blockIdx.x * blockDim.x + threadIdx.x; \
-  if (i >= (n)) return
 
 }  // namespace
 

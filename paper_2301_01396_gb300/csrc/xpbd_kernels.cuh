@@ -19,6 +19,12 @@ struct Collide {
   float thick;
 };
 
+// Blocks of kBlock threads covering n items; a kernel's thread index i, returning past n.
+inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
+#define XPBD_TID_OR_RETURN(n)                          \
+  const int i = blockIdx.x * blockDim.x + threadIdx.x; \
+  if (i >= (n)) return
+
 // Types of constraint records (segments of a color).
 enum SegType { SEG_DIST = 0, SEG_BEND = 1, SEG_TETH = 2, SEG_TETD = 3 };
 constexpr int kVerts[4] = {2, 4, 4, 4};
@@ -117,6 +123,30 @@ cudaError_t phase_kernel_setup();
 size_t phase_smem_bytes(const PhaseShape& sh, bool reverse);
 void launch_phase_fwd(PhaseLaunch a, const PhaseShape& sh, bool record, cudaStream_t s);
 void launch_phase_vjp(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cudaStream_t s);
+
+// ---- implicit adjoint (xpbd_implicit.cu): blocks, matrix-free products, PCG pieces
+void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, float* blocks, bool pd,
+                        cudaStream_t s);
+void launch_apply_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
+                                const double* p, double* q, int V, cudaStream_t s);
+void launch_apply_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const float* blocks,
+                        bool pd, const double* p, double* q, cudaStream_t s);
+void launch_diag_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
+                               double* dg, int V, cudaStream_t s);
+void launch_diag_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const float* blocks,
+                       bool pd, double* dg, cudaStream_t s);
+void launch_diag_invert(const float4* X, double* dg, int V, cudaStream_t s);
+void launch_cg_start(const float4* X, const double* b, const double* dinv, double* y, double* r, double* z, double* p,
+                     double* partials, int V, cudaStream_t s);
+void launch_cg_pq(const float4* X, const double* p, double* q, double* partials, int V, cudaStream_t s);
+void launch_cg_step(const double* sc, int rz_slot, const double* p, const double* q, const double* dinv, double* y,
+                    double* r, double* z, double* partials, int V, cudaStream_t s);
+void launch_cg_dir(const double* sc, int old_slot, int new_slot, const double* z, double* p, int V, cudaStream_t s);
+void launch_implicit_finish(const float4* X, const double* b, const double* y, const double* ay, float4* xbar, int V,
+                            cudaStream_t s);
+void launch_xbar_to_b(const float4* xbar, double* b, int V, cudaStream_t s);
+void launch_abar(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* y, double* acc,
+                 cudaStream_t s);
 
 // ---- utilities
 void launch_loss(const float4* ckx, const float* target, float* seed_out, double* partials,

@@ -1,0 +1,82 @@
+"""The paper's implicit adjoint on the GPU (xpbd_adjoint_implicit) against the dense
+implicit-adjoint oracle: same linearisation states (the XPBD forward), block projection,
+pinned-vertex filtering and contact blocks; the GPU solves by preconditioned CG."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import implicit
+from paper_2301_01396_gb300 import binding, scenes
+from tests import helpers
+from tests.gpu_common import contact_margin, gpu_forward, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3
+KEYS = ("compliance", "x0", "v0", "f_global", "f_vertex")
+
+
+def _cases():
+    ground = helpers.small_cloth(8, bending=True, diagonals="one", pins=(), steps=4, iters=6, v_scale=0.3,
+                                 plane_h=-0.02, seed=33)
+    ground.v0 = scenes.f32(ground.v0 + np.array([0.0, -0.6, 0.0]))
+    return {
+        "pinned_cloth": helpers.small_cloth(8, bending=True, diagonals="both", pins=((0, 0), (-1, 0)), steps=4,
+                                            iters=6, v_scale=0.3, seed=12),
+        "ground_cloth": ground,
+        "tets": helpers.small_tets(2, steps=3, iters=6, y0=0.05, plane=False, v_scale=0.05),
+    }
+
+
+@pytest.mark.parametrize("name", ["pinned_cloth", "ground_cloth", "tets"])
+@pytest.mark.parametrize("pd", [True, False])
+def test_implicit_adjoint_matches_oracle(name, pd):
+    sc = _cases()[name]
+    xs_ref, vs_ref, lam, lamc, act = oracle.forward_multipliers(sc)
+    if sc.collider_flags:
+        assert contact_margin(sc, xs_ref, vs_ref) > 1e-5
+        assert act.any()
+    rng = np.random.default_rng(8)
+    seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3))), 1: scenes.f32(rng.standard_normal((sc.V, 3)))}
+    ref = implicit.adjoint(sc, seeds, pd=pd)
+    solver, p, ck, xs, _ = gpu_forward(sc)
+    got, its = solver.adjoint_implicit(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
+                                       want=KEYS + ("f_vertex_steps",), pd_project=pd)
+    torch.cuda.synchronize()
+    solver.sync_status()
+    assert all(0 < n < 5000 for n in its), its
+    for k in KEYS + ("f_vertex_steps",):
+        e = rel_err(got[k].cpu().numpy().reshape(ref[k].shape), ref[k])
+        assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
+
+
+def test_phase_plan_handle_gives_the_same_gradient():
+    """The solve runs on the per-color records whatever execution mode the handle has."""
+    sc = helpers.small_cloth(64, bending=True, diagonals="both", pins=(), steps=2, iters=4, v_scale=0.3, seed=70,
+                             coloring="tiled", tile=16)
+    rng = np.random.default_rng(9)
+    seeds = {sc.steps: to_dev(rng.standard_normal((sc.V, 3)))}
+    out = []
+    for mode in (2, 1):
+        solver = binding.Solver.from_scene(sc, exec_mode=mode)
+        p = binding.params_from_scene(sc)
+        ck = solver.forward(p, sc.steps, sc.iters, to_dev(sc.x0), to_dev(sc.v0))
+        g, _ = solver.adjoint_implicit(p, sc.steps, sc.iters, ck, seeds)
+        torch.cuda.synchronize()
+        out.append({k: v.cpu().numpy() for k, v in g.items()})
+    for k in KEYS:
+        assert rel_err(out[0][k], out[1][k]) < 1e-4, k
+
+
+def test_collider_gradient_is_refused():
+    sc = _cases()["ground_cloth"]
+    solver, p, ck, _, _ = gpu_forward(sc)
+    g = binding.XpbdGrads(d_compliance=None, d_x0=None, d_v0=None, d_f_global=None, d_f_vertex=None,
+                          d_collider=ck.data_ptr(), d_f_vertex_steps=None)
+    import ctypes as C
+    o = binding.XpbdImplicitOpts(cg_tol=1e-8, cg_max_iters=10, pd_project=1, cg_iters_out=None)
+    pc = p.c_struct()
+    st = binding.lib().xpbd_adjoint_implicit(solver._h, C.byref(pc), sc.steps, sc.iters, C.c_void_p(ck.data_ptr()),
+                                             0, None, None, None, C.byref(g), C.byref(o), None)
+    assert st == 1
