@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--keyframe-scale", action="store_true",
                     help="the paper's keyframe-example scale instead of the default workload: 900 steps x 20 "
                          "iterations on a 90x90 cloth with a force per vertex per step (21.9M controls)")
+    ap.add_argument("--implicit", action="store_true",
+                    help="time the paper's implicit adjoint next to the discrete one on the 256^2 ground cloth")
+    ap.add_argument("--implicit-grid", type=int, default=256)
+    ap.add_argument("--cg-tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=160)
@@ -529,6 +533,63 @@ def run_keyframe(args, local):
     }
 
 
+# ----------------------------------------------------------------------------- implicit adjoint
+
+def run_implicit(args, local):
+    """The paper's implicit adjoint next to the discrete one on the 256^2 ground cloth (one
+    diagonal, bending, ground plane; 40 steps x 30 iterations, contacts from step ~20):
+    time per simulated step of each, conjugate-gradient iterations, and how far the two
+    gradients are apart (they differ by design: XPBD's end state is not the exactly solved
+    step the implicit adjoint differentiates)."""
+    import torch
+    from paper_2301_01396_gb300 import binding
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = args.sim_steps or 40
+    sc = scenes.ground_cloth(args.implicit_grid, steps=N)
+    solver = binding.Solver.from_scene(sc)
+    p = binding.params_from_scene(sc, device=dev)
+    x0 = torch.as_tensor(sc.x0.astype(np.float32), device=dev)
+    v0 = torch.as_tensor(sc.v0.astype(np.float32), device=dev)
+    I = sc.iters
+    ck = solver.forward(p, N, I, x0, v0)
+    rng = np.random.default_rng(3)
+    seed = {N: torch.as_tensor(rng.standard_normal((sc.V, 3)).astype(np.float32), device=dev)}
+    want = ("compliance", "x0", "v0", "f_global", "f_vertex")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    solver.adjoint(p, N, I, ck, seed, want=want)   # warm-up (allocations)
+    solver.adjoint_implicit(p, N, I, ck, seed, want=want, cg_tol=args.cg_tol, cg_max_iters=20000)
+    torch.cuda.synchronize()
+    ev[0].record()
+    solver.forward(p, N, I, x0, v0, checkpoints=ck)
+    ev[1].record()
+    gd = solver.adjoint(p, N, I, ck, seed, want=want)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gi, its = solver.adjoint_implicit(p, N, I, ck, seed, want=want, cg_tol=args.cg_tol, cg_max_iters=20000)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_imp = (time.perf_counter() - t0) * 1e3
+    solver.sync_status()
+    diff = {}
+    for k in want:
+        a, b = gi[k].double(), gd[k].double()
+        diff[k] = float((a - b).norm() / b.norm().clamp_min(1e-300))
+    return {
+        "metric": "implicit adjoint: ms per simulated step", "impl": "ours", "mode": "implicit",
+        "value": round(t_imp / N, 3), "unit": "ms/step", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": f"ground_cloth_{args.implicit_grid}x{args.implicit_grid}: {sc.V} vertices, {sc.m} "
+                               f"constraints, {N} steps x {I} iterations, ground plane",
+                   "cg_tol": args.cg_tol, "pd_project": True, "preconditioner": "block Jacobi (3x3 per vertex)"},
+        "forward_ms_per_step": round(ev[0].elapsed_time(ev[1]) / N, 3),
+        "discrete_adjoint_ms_per_step": round(ev[1].elapsed_time(ev[2]) / N, 3),
+        "implicit_adjoint_ms_per_step": round(t_imp / N, 3),
+        "cg_iterations": {"mean": round(float(np.mean(its)), 1), "max": int(np.max(its)), "min": int(np.min(its))},
+        "relative_difference_implicit_vs_discrete": diff,
+    }
+
+
 # ----------------------------------------------------------------------------- serving
 
 def run_serving(args):
@@ -691,6 +752,10 @@ def main():
     if args.keyframe_scale:
         if rank == 0:
             print(json.dumps(run_keyframe(args, local)))
+        return
+    if args.implicit:
+        if rank == 0:
+            print(json.dumps(run_implicit(args, local)))
         return
     res = run_ours(args, ws, rank, local)
     if res is not None and rank == 0:

@@ -1138,7 +1138,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   const int V = h->V;
   const size_t V3 = 3 * (size_t)V;
   const int64_t nq = (int64_t)h->n_rec[1] + h->n_rec[2] + h->n_rec[3];
-  CU_TRY(h->imp_blocks.ensure(sizeof(float) * 45 * (size_t)std::max<int64_t>(nq, 1)));
+  CU_TRY(h->imp_blocks.ensure(sizeof(double) * 45 * (size_t)std::max<int64_t>(nq, 1)));
   CU_TRY(h->imp_vec.ensure(sizeof(double) * 6 * std::max<size_t>(V3, 1)));
   CU_TRY(h->imp_dinv.ensure(sizeof(double) * 9 * (size_t)std::max(V, 1)));
   CU_TRY(h->imp_sc.ensure(sizeof(double) * 8));
@@ -1147,7 +1147,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   double* dinv = h->imp_dinv.as<double>();
   double* sc = h->imp_sc.as<double>();
   double* partials = h->partials.as<double>();
-  float* blocks = h->imp_blocks.as<float>();
+  double* blocks = h->imp_blocks.as<double>();
   const int64_t boff[4] = {0, 0, h->n_rec[1], (int64_t)h->n_rec[1] + h->n_rec[2]};
   const float* lam = h->lam.as<float>();
   const Collide c = make_collide(p);

@@ -16,7 +16,7 @@
 // Blocks: distance and contact blocks are applied analytically (B_rel = nn^T / alpha~ +
 // c P with P = I - nn^T, c = -lambda / l, clamped at 0 under projection); a bending or tet
 // block is formed once per step from the analytic gradient and nine Hessian-vector
-// products, projected with cyclic Jacobi rotations and stored packed (45 floats).
+// products, projected with cyclic Jacobi rotations and stored packed (45 float64).
 // Matrix-vector products run color by color (a color's constraints share no vertex), so
 // every sum has a fixed order and the solve is deterministic.
 #include "xpbd_elems.cuh"
@@ -31,47 +31,49 @@ __device__ __forceinline__ int pk9(int i, int j) {   // packed upper triangle of
 }
 
 // Positive semi-definite part of a symmetric 9x9 matrix (row-major in a), by cyclic
-// Jacobi rotations: a = V D V^T, then sum over max(d_i, 0) v_i v_i^T.
-__device__ void psd_part9(float* a) {
-  float v[81];
-  for (int i = 0; i < 81; ++i) v[i] = (i % 10 == 0) ? 1.f : 0.f;
-  float scale = 0.f;
-  for (int i = 0; i < 81; ++i) scale = fmaxf(scale, fabsf(a[i]));
-  if (scale == 0.f) return;
-  for (int sweep = 0; sweep < 16; ++sweep) {
-    float off = 0.f;
+// Jacobi rotations: a = V D V^T, then sum over max(d_i, 0) v_i v_i^T.  In float64: the
+// projected block must stay semi-definite to well below a vertex mass, which float32
+// round-off of a stiff bending block (entries ~1e3) does not guarantee.
+__device__ void psd_part9(double* a) {
+  double v[81];
+  for (int i = 0; i < 81; ++i) v[i] = (i % 10 == 0) ? 1.0 : 0.0;
+  double scale = 0.0;
+  for (int i = 0; i < 81; ++i) scale = fmax(scale, fabs(a[i]));
+  if (scale == 0.0) return;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0;
     for (int p = 0; p < 9; ++p)
       for (int q = p + 1; q < 9; ++q) off += a[p * 9 + q] * a[p * 9 + q];
-    if (off <= 1e-14f * scale * scale) break;
+    if (off <= 1e-28 * scale * scale) break;
     for (int p = 0; p < 9; ++p)
       for (int q = p + 1; q < 9; ++q) {
-        const float apq = a[p * 9 + q];
-        if (fabsf(apq) <= 1e-12f * scale) continue;
-        const float theta = (a[q * 9 + q] - a[p * 9 + p]) / (2.f * apq);
-        const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-        const float c = rsqrtf(t * t + 1.f), s = t * c;
+        const double apq = a[p * 9 + q];
+        if (fabs(apq) <= 1e-30 * scale) continue;
+        const double theta = (a[q * 9 + q] - a[p * 9 + p]) / (2.0 * apq);
+        const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
         for (int k = 0; k < 9; ++k) {   // columns p, q
-          const float akp = a[k * 9 + p], akq = a[k * 9 + q];
+          const double akp = a[k * 9 + p], akq = a[k * 9 + q];
           a[k * 9 + p] = c * akp - s * akq;
           a[k * 9 + q] = s * akp + c * akq;
         }
         for (int k = 0; k < 9; ++k) {   // rows p, q
-          const float apk = a[p * 9 + k], aqk = a[q * 9 + k];
+          const double apk = a[p * 9 + k], aqk = a[q * 9 + k];
           a[p * 9 + k] = c * apk - s * aqk;
           a[q * 9 + k] = s * apk + c * aqk;
         }
         for (int k = 0; k < 9; ++k) {
-          const float vkp = v[k * 9 + p], vkq = v[k * 9 + q];
+          const double vkp = v[k * 9 + p], vkq = v[k * 9 + q];
           v[k * 9 + p] = c * vkp - s * vkq;
           v[k * 9 + q] = s * vkp + c * vkq;
         }
       }
   }
-  float d[9];
-  for (int i = 0; i < 9; ++i) d[i] = fmaxf(a[i * 9 + i], 0.f);
+  double d[9];
+  for (int i = 0; i < 9; ++i) d[i] = fmax(a[i * 9 + i], 0.0);
   for (int i = 0; i < 9; ++i)
     for (int j = 0; j < 9; ++j) {
-      float s = 0.f;
+      double s = 0.0;
       for (int k = 0; k < 9; ++k) s += v[i * 9 + k] * d[k] * v[j * 9 + k];
       a[i * 9 + j] = s;
     }
@@ -137,20 +139,20 @@ __device__ __forceinline__ void contact_block(int i, const float4* X, uint8_t f,
 template <int KIND>
 __global__ void __launch_bounds__(kBlock) k_quad_blocks(const typename Quad<KIND>::Rec* __restrict__ rec, int n,
                                                         const float4* __restrict__ X, const float* __restrict__ lam,
-                                                        float* __restrict__ blocks, bool pd) {
+                                                        double* __restrict__ blocks, bool pd) {
   XPBD_TID_OR_RETURN(n);
   const typename Quad<KIND>::Rec r = rec[i];
-  float* out = blocks + 45 * (size_t)i;
+  double* out = blocks + 45 * (size_t)i;
   const f3 x0 = xyz(X[r.v[0]]);
   const f3 e1 = xyz(X[r.v[1]]) - x0, e2 = xyz(X[r.v[2]]) - x0, e3 = xyz(X[r.v[3]]) - x0;
   f3 g1, g2, g3;
   float C;
   if (r.at <= 0.f || !Quad<KIND>::eval(r, e1, e2, e3, g1, g2, g3, C)) {
-    for (int k = 0; k < 45; ++k) out[k] = 0.f;
+    for (int k = 0; k < 45; ++k) out[k] = 0.0;
     return;
   }
-  const float g[9] = {g1.x, g1.y, g1.z, g2.x, g2.y, g2.z, g3.x, g3.y, g3.z};
-  float a[81];
+  const double g[9] = {g1.x, g1.y, g1.z, g2.x, g2.y, g2.z, g3.x, g3.y, g3.z};
+  double a[81];
   const f3 zero = mk3(0.f, 0.f, 0.f);
   for (int col = 0; col < 9; ++col) {
     const int vtx = col / 3, comp = col % 3;
@@ -161,11 +163,11 @@ __global__ void __launch_bounds__(kBlock) k_quad_blocks(const typename Quad<KIND
     const float hc[9] = {c1.x, c1.y, c1.z, c2.x, c2.y, c2.z, c3.x, c3.y, c3.z};
     for (int row = 0; row < 9; ++row) a[row * 9 + col] = hc[row];
   }
-  const float inv_at = 1.f / r.at, l = lam[i];
+  const double inv_at = 1.0 / (double)r.at, l = lam[i];
   for (int row = 0; row < 9; ++row)
     for (int col = row; col < 9; ++col) {
-      const float h = 0.5f * (a[row * 9 + col] + a[col * 9 + row]);
-      const float b = g[row] * g[col] * inv_at - l * h;
+      const double h = 0.5 * (a[row * 9 + col] + a[col * 9 + row]);
+      const double b = g[row] * g[col] * inv_at - l * h;
       a[row * 9 + col] = b;
       a[col * 9 + row] = b;
     }
@@ -210,11 +212,11 @@ __global__ void __launch_bounds__(kBlock) k_apply_dist(const DistRec* __restrict
 }
 
 template <class Rec>
-__global__ void __launch_bounds__(kBlock) k_apply_quad(const Rec* __restrict__ rec, int n, const float* __restrict__ blocks,
+__global__ void __launch_bounds__(kBlock) k_apply_quad(const Rec* __restrict__ rec, int n, const double* __restrict__ blocks,
                                                        const double* __restrict__ p, double* __restrict__ q) {
   XPBD_TID_OR_RETURN(n);
   const Rec r = rec[i];
-  const float* B = blocks + 45 * (size_t)i;
+  const double* B = blocks + 45 * (size_t)i;
   const D3 p0 = ld3(p, r.v[0]);
   double u[9];
   for (int k = 0; k < 3; ++k) {
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_quad(const Rec* __restrict__ r
   double s[3] = {0.0, 0.0, 0.0};
   for (int row = 0; row < 9; ++row) {
     double t = 0.0;
-    for (int col = 0; col < 9; ++col) t += (double)B[pk9(row, col)] * u[col];
+    for (int col = 0; col < 9; ++col) t += B[pk9(row, col)] * u[col];
     const int k = row / 3;
     q[3 * r.v[k + 1] + row % 3] += t;
     s[row % 3] += t;
@@ -263,17 +265,17 @@ __global__ void __launch_bounds__(kBlock) k_diag_dist(const DistRec* __restrict_
 }
 
 template <class Rec>
-__global__ void __launch_bounds__(kBlock) k_diag_quad(const Rec* __restrict__ rec, int n, const float* __restrict__ blocks,
+__global__ void __launch_bounds__(kBlock) k_diag_quad(const Rec* __restrict__ rec, int n, const double* __restrict__ blocks,
                                                       double* __restrict__ dg) {
   XPBD_TID_OR_RETURN(n);
   const Rec r = rec[i];
-  const float* B = blocks + 45 * (size_t)i;
+  const double* B = blocks + 45 * (size_t)i;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
       double s0 = 0.0;
       for (int k = 0; k < 3; ++k) {
-        for (int l = 0; l < 3; ++l) s0 += (double)B[pk9(3 * k + a, 3 * l + b)];
-        dg[9 * r.v[k + 1] + 3 * a + b] += (double)B[pk9(3 * k + a, 3 * k + b)];
+        for (int l = 0; l < 3; ++l) s0 += B[pk9(3 * k + a, 3 * l + b)];
+        dg[9 * r.v[k + 1] + 3 * a + b] += B[pk9(3 * k + a, 3 * k + b)];
       }
       dg[9 * r.v[0] + 3 * a + b] += s0;
     }
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(kBlock) k_abar_quad(const typename Quad<KIND>:
 
 }  // namespace
 
-void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, float* blocks, bool pd,
+void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, double* blocks, bool pd,
                         cudaStream_t s) {
   if (n <= 0) return;
   switch (t) {
@@ -460,7 +462,7 @@ void launch_apply_mass_contacts(const float4* X, const uint8_t* cflags, const fl
   if (V > 0) k_apply_mass_contacts<<<grid_for(V), kBlock, 0, s>>>(X, cflags, lamc, c, pd, p, q, V);
 }
 
-void launch_apply_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const float* blocks,
+void launch_apply_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* blocks,
                         bool pd, const double* p, double* q, cudaStream_t s) {
   if (n <= 0) return;
   if (t == SEG_DIST)
@@ -476,7 +478,7 @@ void launch_diag_mass_contacts(const float4* X, const uint8_t* cflags, const flo
   if (V > 0) k_diag_mass_contacts<<<grid_for(V), kBlock, 0, s>>>(X, cflags, lamc, c, pd, dg, V);
 }
 
-void launch_diag_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const float* blocks,
+void launch_diag_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* blocks,
                        bool pd, double* dg, cudaStream_t s) {
   if (n <= 0) return;
   if (t == SEG_DIST)

@@ -125,15 +125,15 @@ void launch_phase_fwd(PhaseLaunch a, const PhaseShape& sh, bool record, cudaStre
 void launch_phase_vjp(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cudaStream_t s);
 
 // ---- implicit adjoint (xpbd_implicit.cu): blocks, matrix-free products, PCG pieces
-void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, float* blocks, bool pd,
+void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, double* blocks, bool pd,
                         cudaStream_t s);
 void launch_apply_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
                                 const double* p, double* q, int V, cudaStream_t s);
-void launch_apply_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const float* blocks,
+void launch_apply_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* blocks,
                         bool pd, const double* p, double* q, cudaStream_t s);
 void launch_diag_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
                                double* dg, int V, cudaStream_t s);
-void launch_diag_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const float* blocks,
+void launch_diag_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* blocks,
                        bool pd, double* dg, cudaStream_t s);
 void launch_diag_invert(const float4* X, double* dg, int V, cudaStream_t s);
 void launch_cg_start(const float4* X, const double* b, const double* dinv, double* y, double* r, double* z, double* p,
