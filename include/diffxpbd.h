@@ -240,6 +240,26 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
                                   const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
                                   const xpbd_implicit_opts* opts, void* stream);
 
+/* ---- Tet materials (Sec. "Volumetric Material Parameter Estimation") -------------------
+   An object of several materials: material k has Lame parameters mu_k = a_k^2 and
+   lambda_k = b_k^2 (optimising over a, b keeps them positive).  A tet of material k then
+   has the inverse moduli alpha_hat_D = 1/a_k^2 (deviatoric) and alpha_hat_H = 1/b_k^2
+   (hydrostatic), the tet entries of xpbd_params.compliance. */
+
+/* Writes the tet entries of `compliance` (DEVICE [m], caller order: hydrostatic constraints
+   at n_dist+n_bend+t, deviatoric at n_dist+n_bend+n_tet+t) from tet_material (DEVICE
+   [n_tet], 0..n_materials-1), a and b (DEVICE [n_materials]); other entries untouched.
+   A material id out of range latches XPBD_ERR_INVALID for xpbd_sync_status. */
+xpbd_status xpbd_material_compliance(xpbd_handle h, int32_t n_materials, const int32_t* tet_material,
+                                     const float* a, const float* b, float* compliance, void* stream);
+
+/* Chain rule to the material parameters: from d_compliance (DEVICE [m] float64, as written
+   by an adjoint call) writes dL/da and dL/db (DEVICE [n_materials] float64; either may be
+   NULL), each a fixed-order sum over the material's tets (deterministic). */
+xpbd_status xpbd_material_gradient(xpbd_handle h, int32_t n_materials, const int32_t* tet_material, const float* a,
+                                   const float* b, const double* d_compliance, double* d_a, double* d_b,
+                                   void* stream);
+
 /* Synchronise `stream` and report (then clear) the device error word of the handle:
    XPBD_ERR_TIMEOUT if, since the last check, a bounded wait of a phase kernel gave up;
    XPBD_ERR_NONFINITE if a call was given a negative or non-finite compliance or a step

@@ -101,7 +101,8 @@ def lib():
                      "xpbd_server_create", "xpbd_server_destroy", "xpbd_server_submit", "xpbd_server_run",
                      "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info",
                      "xpbd_selftest_wait_timeout", "xpbd_forward_sparse", "xpbd_adjoint_sparse",
-                     "xpbd_sparse_slots", "xpbd_sparse_slot", "xpbd_adjoint_implicit"):
+                     "xpbd_sparse_slots", "xpbd_sparse_slot", "xpbd_adjoint_implicit",
+                     "xpbd_material_compliance", "xpbd_material_gradient"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -353,6 +354,23 @@ class Solver:
                                            len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), C.byref(o),
                                            _stream(stream)))
         return out, list(its)[:steps]
+
+    def material_compliance(self, tet_material: torch.Tensor, a: torch.Tensor, b: torch.Tensor,
+                            compliance: torch.Tensor, stream=None) -> torch.Tensor:
+        """Writes the tet entries of `compliance` from materials mu = a^2, lambda = b^2
+        (xpbd_material_compliance); returns `compliance`."""
+        _check(lib().xpbd_material_compliance(self._h, int(a.numel()), _ptr(tet_material), _ptr(a), _ptr(b),
+                                              _ptr(compliance), _stream(stream)))
+        return compliance
+
+    def material_gradient(self, tet_material: torch.Tensor, a: torch.Tensor, b: torch.Tensor,
+                          d_compliance: torch.Tensor, stream=None):
+        """(dL/da, dL/db) float64 from a compliance gradient (xpbd_material_gradient)."""
+        da = torch.empty(a.numel(), dtype=torch.float64, device=a.device)
+        db = torch.empty_like(da)
+        _check(lib().xpbd_material_gradient(self._h, int(a.numel()), _ptr(tet_material), _ptr(a), _ptr(b),
+                                            _ptr(d_compliance), _ptr(da), _ptr(db), _stream(stream)))
+        return da, db
 
     def sync_status(self, stream=None):
         _check(lib().xpbd_sync_status(self._h, _stream(stream)))

@@ -1390,6 +1390,35 @@ xpbd_status xpbd_selftest_wait_timeout(xpbd_handle h, void* stream) {
   return XPBD_OK;
 }
 
+xpbd_status xpbd_material_compliance(xpbd_handle h, int32_t n_materials, const int32_t* tet_material,
+                                     const float* a, const float* b, float* compliance, void* stream) {
+  g_err.clear();
+  if (!h || n_materials < 1 || !a || !b || !compliance || (h->nt > 0 && !tet_material))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  const size_t off = (size_t)h->nd + h->nb;
+  launch(h, XPBD_K_OTHER, h->nt, (cudaStream_t)stream, [&] {
+    launch_material_compliance(tet_material, a, b, h->nt, n_materials, compliance + off, compliance + off + h->nt,
+                               h->d_err, (cudaStream_t)stream);
+  });
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
+xpbd_status xpbd_material_gradient(xpbd_handle h, int32_t n_materials, const int32_t* tet_material, const float* a,
+                                   const float* b, const double* d_compliance, double* d_a, double* d_b,
+                                   void* stream) {
+  g_err.clear();
+  if (!h || n_materials < 1 || !a || !b || !d_compliance || (h->nt > 0 && !tet_material))
+    return fail(XPBD_ERR_INVALID, "bad argument");
+  const size_t off = (size_t)h->nd + h->nb;
+  launch(h, XPBD_K_OTHER, n_materials, (cudaStream_t)stream, [&] {
+    launch_material_gradient(tet_material, a, b, h->nt, n_materials, d_compliance + off, d_compliance + off + h->nt,
+                             d_a, d_b, (cudaStream_t)stream);
+  });
+  LAUNCH_CHECK();
+  return XPBD_OK;
+}
+
 xpbd_status xpbd_sync_status(xpbd_handle h, void* stream) {
   if (!h) return fail(XPBD_ERR_INVALID, "null handle");
   CU_TRY(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1397,6 +1426,7 @@ xpbd_status xpbd_sync_status(xpbd_handle h, void* stream) {
   CU_TRY(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CU_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
   if (err & 4) return fail(XPBD_ERR_TIMEOUT, "a phase kernel gave up waiting for its staged copies");
+  if (err & 8) return fail(XPBD_ERR_INVALID, "a tet material id is out of range");
   if (err & 2) return fail(XPBD_ERR_NONFINITE, "a compliance value is negative or not finite");
   if (err & 1) return fail(XPBD_ERR_NONFINITE, "a step produced a non-finite position or velocity");
   return XPBD_OK;

@@ -303,3 +303,75 @@ void launch_read_state(const float4* ckx, const float4* ckv, float* x_out, float
 }
 
 }  // namespace xpbd
+
+// ======================================================================== materials
+// Tet materials (Sec. "Volumetric Material Parameter Estimation"): material k has Lame
+// parameters mu = a_k^2 and lambda = b_k^2, so the inverse moduli of a tet of material k
+// are alpha_hat_D = 1/a_k^2 (deviatoric) and alpha_hat_H = 1/b_k^2 (hydrostatic).
+namespace xpbd {
+
+namespace {
+
+__global__ void k_material_compliance(const int* __restrict__ mat, const float* __restrict__ a,
+                                      const float* __restrict__ b, int nt, int n_mat, float* __restrict__ comp_h,
+                                      float* __restrict__ comp_d, int* __restrict__ err) {
+  XPBD_TID_OR_RETURN(nt);
+  const int k = mat[i];
+  if (k < 0 || k >= n_mat) {
+    atomicOr(err, 8);
+    return;
+  }
+  const float ak = a[k], bk = b[k];
+  comp_h[i] = 1.f / (bk * bk);
+  comp_d[i] = 1.f / (ak * ak);
+}
+
+// dL/da_k = sum over the tets of material k of dL/dalpha_hat_D * (-2 / a_k^3), and b_k with
+// the hydrostatic entries.  One block per material sums its tets in a fixed order.
+__global__ void __launch_bounds__(kBlock) k_material_gradient(const int* __restrict__ mat, const float* __restrict__ a,
+                                                              const float* __restrict__ b, int nt,
+                                                              const double* __restrict__ g_h,
+                                                              const double* __restrict__ g_d, double* __restrict__ da,
+                                                              double* __restrict__ db) {
+  __shared__ double sh[2][kBlock / 32];
+  const int k = blockIdx.x;
+  double sd = 0.0, sh_ = 0.0;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x)
+    if (mat[t] == k) {
+      sd += g_d[t];
+      sh_ += g_h[t];
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    sd += __shfl_down_sync(0xffffffffu, sd, o);
+    sh_ += __shfl_down_sync(0xffffffffu, sh_, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = sd;
+    sh[1][threadIdx.x >> 5] = sh_;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double td = 0.0, th = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      td += sh[0][w];
+      th += sh[1][w];
+    }
+    const double ak = a[k], bk = b[k];
+    if (da) da[k] = td * (-2.0 / (ak * ak * ak));
+    if (db) db[k] = th * (-2.0 / (bk * bk * bk));
+  }
+}
+
+}  // namespace
+
+void launch_material_compliance(const int* mat, const float* a, const float* b, int nt, int n_mat, float* comp_h,
+                                float* comp_d, int* err, cudaStream_t s) {
+  if (nt > 0) k_material_compliance<<<grid_for(nt), kBlock, 0, s>>>(mat, a, b, nt, n_mat, comp_h, comp_d, err);
+}
+
+void launch_material_gradient(const int* mat, const float* a, const float* b, int nt, int n_mat, const double* g_h,
+                              const double* g_d, double* da, double* db, cudaStream_t s) {
+  if (n_mat > 0) k_material_gradient<<<n_mat, kBlock, 0, s>>>(mat, a, b, nt, g_h, g_d, da, db);
+}
+
+}  // namespace xpbd

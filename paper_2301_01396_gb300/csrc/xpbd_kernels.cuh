@@ -148,6 +148,12 @@ void launch_xbar_to_b(const float4* xbar, double* b, int V, cudaStream_t s);
 void launch_abar(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* y, double* acc,
                  cudaStream_t s);
 
+// ---- tet materials (mu = a^2, lambda = b^2)
+void launch_material_compliance(const int* mat, const float* a, const float* b, int nt, int n_mat, float* comp_h,
+                                float* comp_d, int* err, cudaStream_t s);
+void launch_material_gradient(const int* mat, const float* a, const float* b, int nt, int n_mat, const double* g_h,
+                              const double* g_d, double* da, double* db, cudaStream_t s);
+
 // ---- utilities
 void launch_loss(const float4* ckx, const float* target, float* seed_out, double* partials,
                  int V, cudaStream_t s);

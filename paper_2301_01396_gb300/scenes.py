@@ -486,3 +486,15 @@ def perturbed_target_compliance(scene: Scene, seed: int, sigma: float = 0.5) -> 
     'ground truth' material used to make target trajectories."""
     rng = np.random.default_rng(seed)
     return f32(scene.compliance * np.exp(sigma * rng.standard_normal(scene.m)))
+
+
+def tet_materials(n_tet: int, n_materials: int, *, seed: int = 7, mu=(1e3, 1e6), lam_over_mu=(1.0, 4.0)):
+    """Materials randomly distributed over the tets (the paper's volumetric example uses 100
+    over all tets): returns (tet_material [n_tet] int32, a [n_materials], b [n_materials])
+    with mu = a^2 log-uniform in `mu` and lambda = b^2 = mu * U(lam_over_mu) (lambda >= mu, the
+    same ordering as tet_block's moduli)."""
+    rng = np.random.default_rng(seed)
+    mat = rng.integers(0, n_materials, n_tet).astype(np.int32)
+    mu_k = np.exp(rng.uniform(np.log(mu[0]), np.log(mu[1]), n_materials))
+    lam_k = mu_k * rng.uniform(lam_over_mu[0], lam_over_mu[1], n_materials)
+    return mat, f32(np.sqrt(mu_k)), f32(np.sqrt(lam_k))

@@ -466,3 +466,31 @@ def test_fp32_rounding_emulation_is_off_by_default(oracle_mod):
     assert np.array_equal(b, b.astype(np.float32).astype(np.float64))
     assert np.array_equal(vb, vb.astype(np.float32).astype(np.float64))
     assert 0 < np.abs(a - b).max() < 1e-5
+
+
+def test_material_gradient_matches_central_fd(oracle_mod):
+    """Tet materials (mu = a^2, lambda = b^2): the chain rule from the compliance gradient to
+    (a, b) agrees with central finite differences of the loss over the material parameters."""
+    from oracle import materials
+    sc = small_tets(2, steps=4, iters=4, y0=0.004, v_scale=0.05, plane=False)   # smooth: no contact set
+    mat, a, b = scenes.tet_materials(sc.n_tet, 3, seed=4)
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    rng = np.random.default_rng(14)
+    comp = materials.compliance(sc, mat, a, b)
+    xs, _ = oracle_mod.forward(sc, compliance=comp)
+    target = xs[-1] + 0.005 * rng.standard_normal((sc.V, 3))
+    gr = oracle_mod.adjoint(sc, {sc.steps: xs[-1] - target}, compliance=comp)
+    da, db = materials.gradient(sc, gr["compliance"], mat, a, b)
+
+    def loss(a_, b_):
+        x, _ = oracle_mod.forward(sc, compliance=materials.compliance(sc, mat, a_, b_))
+        return 0.5 * np.sum((x[-1] - target) ** 2)
+
+    for k in range(3):
+        for arr, g in ((a, da), (b, db)):
+            h = 1e-7 * arr[k]   # the loss is strongly curved in a, b (compliance ~ 1/a^2)
+            ap, am = arr.copy(), arr.copy()
+            ap[k] += h
+            am[k] -= h
+            fd = (loss(ap, b) - loss(am, b)) / (2 * h) if arr is a else (loss(a, ap) - loss(a, am)) / (2 * h)
+            assert abs(fd - g[k]) <= 1e-5 * abs(g[k]) + 1e-9 * np.abs(g).max(), (k, fd, g[k])
