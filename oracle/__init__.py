@@ -25,7 +25,8 @@ class _Model(C.Structure):
     _fields_ = [("V", C.c_int32), ("rest_x", _dp), ("inv_mass", _dp),
                 ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
                 ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _dp),
-                ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip)]
+                ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip),
+                ("tet_coupled", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -91,7 +92,8 @@ class _Args:
                             n_tet=s.n_tet, tet_idx=i(s.tet_idx.reshape(-1)),
                             tet_gamma=d(s.tet_gamma) if s.n_tet else None,
                             n_colors=s.n_colors, color_offsets=i(s.color_offsets),
-                            color_order=i(s.color_order))
+                            color_order=i(s.color_order),
+                            tet_coupled=int(bool(getattr(s, "tet_coupled", False))))
         comp = s.compliance if compliance is None else compliance
         fg = s.f_global if f_global is None else f_global
         fv = s.f_vertex if f_vertex is None else f_vertex
@@ -281,3 +283,29 @@ def vjp_one(kind, q, w, rest12, lam, alpha_tilde, qbar, lambar):
     lib().oracle_vjp_one(k, qp, wp, rp, C.c_double(lam), C.c_double(alpha_tilde),
                          qb.ctypes.data_as(_dp), C.byref(lb), C.byref(ab))
     return qb, lb.value, ab.value
+
+
+def project_pair(q, w, rest12, lam, alpha_tilde):
+    """One coupled (C_H, C_D) update of one tet; returns (q', lambda'[2])."""
+    q = np.array(q, np.float64).reshape(-1)
+    wa, wp = _d(np.asarray(w, np.float64))
+    ra, rp = _d(np.asarray(rest12, np.float64))
+    l = np.array(lam, np.float64)
+    aa, ap = _d(np.asarray(alpha_tilde, np.float64))
+    lib().oracle_project_pair(q.ctypes.data_as(_dp), wp, rp, l.ctypes.data_as(_dp), ap)
+    return q, l
+
+
+def vjp_pair(q, w, rest12, lam, alpha_tilde, qbar, lambar):
+    """Reverse of ``project_pair``: returns (qbar, lambar[2], alpha_tilde_bar[2])."""
+    qa, qp = _d(np.asarray(q, np.float64).reshape(-1))
+    wa, wp = _d(np.asarray(w, np.float64))
+    ra, rp = _d(np.asarray(rest12, np.float64))
+    la, lp = _d(np.asarray(lam, np.float64))
+    aa, ap = _d(np.asarray(alpha_tilde, np.float64))
+    qb = np.array(qbar, np.float64).reshape(-1)
+    lb = np.array(lambar, np.float64)
+    ab = np.zeros(2)
+    lib().oracle_vjp_pair(qp, wp, rp, lp, ap, qb.ctypes.data_as(_dp), lb.ctypes.data_as(_dp),
+                          ab.ctypes.data_as(_dp))
+    return qb, lb, ab

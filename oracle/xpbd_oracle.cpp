@@ -260,6 +260,7 @@ struct Model {
   int K = 0;
   std::vector<int> offsets, order;
   std::vector<Rest> rest;   // per constraint id
+  bool coupled = false;     // a tet's two constraints are projected together (its C_H id in the coloring)
   int m() const { return nd + nb + 2 * nt; }
   int kind(int j) const {
     if (j < nd) return K_DIST;
@@ -397,6 +398,46 @@ void project_one(int kind, T* q, const double* wv, const Rest& r, T& lam, const 
     }
 }
 
+// Coupled update of a tet's hydrostatic (h) and deviatoric (d) constraints, the
+// formulation the paper's volumetric model follows (Macklin and Mueller 2021): both
+// multipliers from one 2x2 system,
+//   S dlambda = -C - A~ lambda,  S = G W G^T + A~ (G: the two gradients as rows),
+// then x += W G^T dlambda.  When C_D is degenerate only C_H is projected.
+template <class T>
+void project_pair(T* q, const double* wv, const Rest& rh, const Rest& rd, T& lh, T& ld, const T& ath,
+                  const T& atd) {
+  if (degenerate<T>(K_TETD, q, rd)) {
+    project_one<T>(K_TETH, q, wv, rh, lh, ath);
+    return;
+  }
+  T gh[12], gd[12];
+  constraint_grad<T>(K_TETH, q, rh, gh);
+  constraint_grad<T>(K_TETD, q, rd, gd);
+  const T Ch = constraint_C<T>(K_TETH, q, rh), Cd = constraint_C<T>(K_TETD, q, rd);
+  T s11 = ath, s22 = atd, s12 = T(0.0);
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * a + c;
+      s11 = s11 + wv[a] * gh[i] * gh[i];
+      s22 = s22 + wv[a] * gd[i] * gd[i];
+      s12 = s12 + wv[a] * gh[i] * gd[i];
+    }
+  const T det = s11 * s22 - s12 * s12;
+  if (!(val(det) > 0.0)) return;
+  const T rhh = -Ch - ath * lh, rdd = -Cd - atd * ld;
+  const T dlh = (s22 * rhh - s12 * rdd) / det, dld = (s11 * rdd - s12 * rhh) / det;
+  lh = lh + dlh;
+  ld = ld + dld;
+  round32(lh);
+  round32(ld);
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * a + c;
+      q[i] = q[i] + wv[a] * (gh[i] * dlh + gd[i] * dld);
+      round32(q[i]);
+    }
+}
+
 template <class T>
 void project_constraint(const Model& M, const Params<T>& P, int j, Work<T>& W) {
   T q[12];
@@ -405,7 +446,12 @@ void project_constraint(const Model& M, const Params<T>& P, int j, Work<T>& W) {
   double wv[4];
   for (int a = 0; a < n_verts(k); ++a) wv[a] = M.w[vs[a]];
   T at = alpha_tilde(M, P, j);
-  project_one<T>(k, q, wv, M.rest[j], W.lam[j], at);
+  if (M.coupled && k == K_TETH) {
+    const int jd = j + M.nt;
+    project_pair<T>(q, wv, M.rest[j], M.rest[jd], W.lam[j], W.lam[jd], at, alpha_tilde(M, P, jd));
+  } else {
+    project_one<T>(k, q, wv, M.rest[j], W.lam[j], at);
+  }
   for (int a = 0; a < n_verts(k); ++a)
     for (int c = 0; c < 3; ++c) W.p[3 * vs[a] + c] = q[3 * a + c];
 }
@@ -550,6 +596,58 @@ void vjp_one(int kind, const double* q, const double* wv, const Rest& r, double 
   lambar -= (at / D) * s;
 }
 
+// Adjoint of project_pair.  With S, dlambda recomputed and the adjoints qbar', lambar' of
+// the updated values:  sbar = lambar' + G W qbar',  q = S^-1 sbar,
+//   Gbar_k = dlambda_k W qbar' - sum_l (q_k dlambda_l + dlambda_k q_l) W g_l,
+//   qbar = qbar' - sum_k q_k g_k + sum_k hess C_k Gbar_k,
+//   lambar_k = lambar'_k - alpha~_k q_k,  alphabar~_k += -q_k (lambda_k + dlambda_k).
+void vjp_pair(const double* q, const double* wv, const Rest& rh, const Rest& rd, double lh, double ld, double ath,
+              double atd, double* qbar, double& lbh, double& lbd, double& abh, double& abd) {
+  if (degenerate<double>(K_TETD, q, rd)) {
+    vjp_one(K_TETH, q, wv, rh, lh, ath, qbar, lbh, abh);
+    return;
+  }
+  double gh[12], gd[12];
+  constraint_grad<double>(K_TETH, q, rh, gh);
+  constraint_grad<double>(K_TETD, q, rd, gd);
+  const double Ch = constraint_C<double>(K_TETH, q, rh), Cd = constraint_C<double>(K_TETD, q, rd);
+  double s11 = ath, s22 = atd, s12 = 0.0;
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * a + c;
+      s11 += wv[a] * gh[i] * gh[i];
+      s22 += wv[a] * gd[i] * gd[i];
+      s12 += wv[a] * gh[i] * gd[i];
+    }
+  const double det = s11 * s22 - s12 * s12;
+  if (!(det > 0.0)) return;
+  const double rhh = -Ch - ath * lh, rdd = -Cd - atd * ld;
+  const double dlh = (s22 * rhh - s12 * rdd) / det, dld = (s11 * rdd - s12 * rhh) / det;
+  double sh = lbh, sd = lbd;
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * a + c;
+      sh += wv[a] * gh[i] * qbar[i];
+      sd += wv[a] * gd[i] * qbar[i];
+    }
+  const double qh = (s22 * sh - s12 * sd) / det, qd = (s11 * sd - s12 * sh) / det;
+  double uh[12], ud[12];
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * a + c;
+      uh[i] = dlh * wv[a] * qbar[i] - (2.0 * qh * dlh) * wv[a] * gh[i] - (qh * dld + dlh * qd) * wv[a] * gd[i];
+      ud[i] = dld * wv[a] * qbar[i] - (qd * dlh + dld * qh) * wv[a] * gh[i] - (2.0 * qd * dld) * wv[a] * gd[i];
+    }
+  double huh[12], hud[12];
+  constraint_hvp(K_TETH, q, rh, uh, huh);
+  constraint_hvp(K_TETD, q, rd, ud, hud);
+  for (int i = 0; i < 12; ++i) qbar[i] += -qh * gh[i] - qd * gd[i] + huh[i] + hud[i];
+  abh += -qh * (lh + dlh);
+  abd += -qd * (ld + dld);
+  lbh -= ath * qh;
+  lbd -= atd * qd;
+}
+
 struct Grads {
   std::vector<double> d_alpha, d_x0, d_v0, d_fg, d_fv, d_fvs;
   double d_coll[5] = {0, 0, 0, 0, 0};   // plane h, sphere cx, cy, cz, r
@@ -671,8 +769,15 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
             }
           }
           double at = alpha_tilde(M, P, j);
-          vjp_one(kind, q, wv, M.rest[j], lam_before[(size_t)k * M.m() + j], at, qb, lambar[j],
-                  abar_t[j]);
+          if (M.coupled && kind == K_TETH) {
+            const int jd = j + M.nt;
+            vjp_pair(q, wv, M.rest[j], M.rest[jd], lam_before[(size_t)k * M.m() + j],
+                     lam_before[(size_t)k * M.m() + jd], at, alpha_tilde(M, P, jd), qb, lambar[j], lambar[jd],
+                     abar_t[j], abar_t[jd]);
+          } else {
+            vjp_one(kind, q, wv, M.rest[j], lam_before[(size_t)k * M.m() + j], at, qb, lambar[j],
+                    abar_t[j]);
+          }
           for (int a = 0; a < n_verts(kind); ++a)
             for (int cc = 0; cc < 3; ++cc) pbar[3 * vs4[a] + cc] = qb[3 * a + cc];
         }
@@ -720,7 +825,9 @@ typedef struct {
   const double* tet_gamma;  // [n_tet] or NULL (1.0)
   int32_t n_colors;
   const int32_t* color_offsets;   // [n_colors+1]
-  const int32_t* color_order;     // [m]
+  const int32_t* color_order;     // [offsets[n_colors]]
+  int32_t tet_coupled;            // 1: a tet's C_H and C_D are projected together; the
+                                  // coloring then lists its C_H id only
 } om_model;
 
 typedef struct {
@@ -763,7 +870,8 @@ static Model make_model(const om_model* in) {
   }
   M.K = in->n_colors;
   M.offsets.assign(in->color_offsets, in->color_offsets + M.K + 1);
-  M.order.assign(in->color_order, in->color_order + M.m());
+  M.order.assign(in->color_order, in->color_order + M.offsets[M.K]);
+  M.coupled = in->tet_coupled != 0;
   build_rest(M);
   return M;
 }
@@ -967,6 +1075,26 @@ int oracle_vjp_one(int32_t kind, const double* q, const double* wv, const double
   r.gamma = rest12[11];
   r.thickness = (kind == K_PLANE || kind == K_SPHERE) ? rest12[11] : 0.0;
   vjp_one(kind, q, wv, r, lam, at, qbar, *lambar, *abar);
+  return 0;
+}
+
+// The coupled tet update and its reverse in isolation.  q [12] the tet's vertices,
+// rest12 (B[9] at 2..10, gamma at 11) shared by both constraints, lam[2] and at[2] the
+// (C_H, C_D) multipliers and alpha~; the reverse accumulates lambar[2] and abar[2].
+int oracle_project_pair(double* q, const double* wv, const double* rest12, double* lam, const double* at) {
+  Rest r;
+  for (int i = 0; i < 9; ++i) r.B[i] = rest12[2 + i];
+  r.gamma = rest12[11];
+  project_pair<double>(q, wv, r, r, lam[0], lam[1], at[0], at[1]);
+  return 0;
+}
+
+int oracle_vjp_pair(const double* q, const double* wv, const double* rest12, const double* lam, const double* at,
+                    double* qbar, double* lambar, double* abar) {
+  Rest r;
+  for (int i = 0; i < 9; ++i) r.B[i] = rest12[2 + i];
+  r.gamma = rest12[11];
+  vjp_pair(q, wv, r, r, lam[0], lam[1], at[0], at[1], qbar, lambar[0], lambar[1], abar[0], abar[1]);
   return 0;
 }
 

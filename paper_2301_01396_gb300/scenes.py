@@ -67,6 +67,8 @@ class Scene:
     f_global: Optional[np.ndarray] = None  # [steps,3] force added to every vertex at step n
     f_vertex: Optional[np.ndarray] = None  # [V,3] time-constant per-vertex force
     f_vertex_steps: Optional[np.ndarray] = None  # [steps,V,3] force on each vertex at each step
+    tet_coupled: bool = False           # project each tet's C_H and C_D together (2x2 solve);
+                                        # the coloring then lists C_H ids only
     name: str = "scene"
     meta: dict = field(default_factory=dict)
 
@@ -89,6 +91,12 @@ class Scene:
     @property
     def m(self) -> int:
         return self.n_dist + self.n_bend + 2 * self.n_tet
+
+    @property
+    def n_colored(self) -> int:
+        """Constraint ids the coloring lists: all of them, or all but the C_D ids when
+        each tet's two constraints are projected together."""
+        return self.m - (self.n_tet if self.tet_coupled else 0)
 
     @property
     def n_colors(self) -> int:
@@ -130,9 +138,10 @@ def validate_coloring(scene: Scene) -> None:
     constraints of one color share a vertex."""
     order = np.asarray(scene.color_order, np.int64)
     offs = np.asarray(scene.color_offsets, np.int64)
-    if offs[0] != 0 or offs[-1] != scene.m or np.any(np.diff(offs) < 0):
+    n = scene.n_colored
+    if offs[0] != 0 or offs[-1] != n or np.any(np.diff(offs) < 0):
         raise ValueError("bad color offsets")
-    if order.shape[0] != scene.m or np.any(np.sort(order) != np.arange(scene.m)):
+    if order.shape[0] != n or np.any(np.sort(order) != np.arange(n)):
         raise ValueError("coloring is not a permutation of the constraints")
     table = _vertex_table(scene)
     for c in range(scene.n_colors):
@@ -447,6 +456,25 @@ def tet_block(n: int = 32, *, size: float = 1.0, density: float = 1000.0, y0: fl
                  v0=np.zeros((V, 3)), compliance=f32(np.concatenate([aH, aD])),
                  dt=1.0 / 120.0, steps=steps, iters=iters, collider_flags=COLLIDE_PLANE,
                  plane_h=plane_h, contact_compliance=1e-8, name=f"tet_block_{n}")
+
+
+def couple_tets(scene: Scene) -> Scene:
+    """The same scene with each tet's C_H and C_D projected together: the C_D ids
+    (n_dist + n_bend + n_tet ...) leave the coloring, colors left empty are dropped, and
+    every C_H id stands for its tet's pair."""
+    first_d = scene.n_dist + scene.n_bend + scene.n_tet
+    order = np.asarray(scene.color_order, np.int64)
+    offs = np.asarray(scene.color_offsets, np.int64)
+    new_order, new_offs = [], [0]
+    for c in range(scene.n_colors):
+        ids = order[offs[c]:offs[c + 1]]
+        ids = ids[ids < first_d]
+        if ids.shape[0]:
+            new_order.append(ids)
+            new_offs.append(new_offs[-1] + ids.shape[0])
+    return scene.with_(tet_coupled=True, color_offsets=np.asarray(new_offs, np.int32),
+                       color_order=(np.concatenate(new_order).astype(np.int32) if new_order
+                                    else np.zeros(0, np.int32)))
 
 
 # ----------------------------------------------------------------------------------------

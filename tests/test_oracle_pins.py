@@ -272,6 +272,7 @@ def _scenes_for_adjoint():
         "cloth_plane": small_cloth(5, bending=True, steps=6, iters=3, plane_h=-0.02, jitter=0.002,
                                    v_scale=0.2, seed=7),
         "tets_plane": small_tets(2, steps=6, iters=3, y0=0.004, v_scale=0.05),
+        "tets_coupled": scenes.couple_tets(small_tets(2, steps=6, iters=3, y0=0.004, v_scale=0.05)),
         "cloth_sphere": small_sphere_cloth(6, steps=5, iters=3),
         "cloth_both": _both_colliders(),
     }
@@ -287,7 +288,7 @@ def _both_colliders():
     return sc
 
 
-@pytest.mark.parametrize("name", ["cloth_plane", "tets_plane", "cloth_sphere", "cloth_both"])
+@pytest.mark.parametrize("name", ["cloth_plane", "tets_plane", "tets_coupled", "cloth_sphere", "cloth_both"])
 def test_adjoint_equals_tangent(oracle_mod, name):
     """<dL/du, du> from the reverse sweep equals <dL/dx_N, dx_N/du du> from the
     forward-mode tangent, for every parameter group."""
@@ -315,7 +316,7 @@ def test_adjoint_equals_tangent(oracle_mod, name):
         assert abs(lhs - rhs) <= 1e-9 * max(abs(rhs), 1e-12) + 1e-14, (key, lhs, rhs)
 
 
-@pytest.mark.parametrize("name", ["cloth_plane", "tets_plane", "cloth_sphere", "cloth_both"])
+@pytest.mark.parametrize("name", ["cloth_plane", "tets_plane", "tets_coupled", "cloth_sphere", "cloth_both"])
 def test_adjoint_matches_central_fd(oracle_mod, name):
     """Central finite differences of the FP64 forward simulation, on seeded parameter
     subsets; parameters whose perturbation changes the contact set are skipped."""
