@@ -80,7 +80,8 @@ typedef struct {
   const float* tet_gamma;       /* [n_tet] hydrostatic rest offset, or NULL for 1          */
   int32_t n_colors;
   const int32_t* color_offsets; /* [n_colors+1]; color c = color_order[offsets[c]..offsets[c+1]) */
-  const int32_t* color_order;   /* [m] every constraint id exactly once                    */
+  const int32_t* color_order;   /* [offsets[n_colors]] every colored constraint id exactly
+                                   once: all m ids, or with tet_coupled all but the C_D ids */
   int32_t exec_mode;            /* How the colored sweep is launched; all modes give the same
                                    colored Gauss-Seidel results.  Phase plan: runs of
                                    consecutive colors whose constraints split into small
@@ -91,6 +92,18 @@ typedef struct {
                                       launch per color measured faster), else per color;
                                    1: one launch per color;
                                    2: the phase plan whenever it needs fewer launches.     */
+  int32_t tet_coupled;          /* 0: each constraint is colored and updated on its own.
+                                   1: each tet's C_H and C_D are updated together by one
+                                   2x2 solve (S dlambda = -C - A~ lambda, S = G W G^T + A~;
+                                   the neo-Hookean constraint pair of Sec. 3.2 follows
+                                   Macklin and Mueller 2021, who update it this way);
+                                   color_order then lists every id but the C_D ids
+                                   n_dist + n_bend + n_tet + t, and the C_H id of tet t
+                                   stands for the pair.  Multipliers, compliances and their
+                                   gradients keep one entry per constraint (m).  Such
+                                   models run one launch per color whatever exec_mode
+                                   says; the serving entry points refuse them.  Other
+                                   values fail with XPBD_ERR_INVALID.                       */
 } xpbd_model;
 
 /* Per-call parameters.  The float fields are HOST values; the pointers are DEVICE. */

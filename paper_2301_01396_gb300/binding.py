@@ -35,7 +35,7 @@ class XpbdModel(C.Structure):
                 ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
                 ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _fp),
                 ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip),
-                ("exec_mode", C.c_int32)]
+                ("exec_mode", C.c_int32), ("tet_coupled", C.c_int32)]
 
 
 class XpbdParams(C.Structure):
@@ -177,10 +177,12 @@ class Solver:
 
     exec_mode: 0 picks the multi-color phase launches when they cut the launches per
     iteration at least 4-fold, 1 launches one color at a time, 2 uses the phase launches
-    whenever the coloring allows any; all three compute the same colored sweep."""
+    whenever the coloring allows any; all three compute the same colored sweep.
+    tet_coupled: update each tet's C_H and C_D together by one 2x2 solve; the coloring
+    then lists the C_H ids only (``scenes.couple_tets``)."""
 
     def __init__(self, rest_x, inv_mass, dist_idx=None, bend_idx=None, tet_idx=None, tet_gamma=None,
-                 color_offsets=None, color_order=None, exec_mode: int = 0):
+                 color_offsets=None, color_order=None, exec_mode: int = 0, tet_coupled: bool = False):
         L = lib()
         keep = []
 
@@ -205,7 +207,8 @@ class Solver:
                        n_tet=int(tet_idx.shape[0]), tet_idx=i(tet_idx),
                        tet_gamma=f(tet_gamma) if (tet_gamma is not None and len(tet_gamma)) else None,
                        n_colors=int(len(color_offsets) - 1), color_offsets=i(color_offsets),
-                       color_order=i(color_order), exec_mode=int(exec_mode))
+                       color_order=i(color_order), exec_mode=int(exec_mode),
+                       tet_coupled=int(bool(tet_coupled)))
         h = C.c_void_p()
         _check(L.xpbd_create(C.byref(md), C.byref(h)))
         self._h = h
@@ -216,7 +219,7 @@ class Solver:
     @classmethod
     def from_scene(cls, sc, exec_mode: int = 0) -> "Solver":
         return cls(sc.rest_x, sc.inv_mass, sc.dist_idx, sc.bend_idx, sc.tet_idx, sc.tet_gamma,
-                   sc.color_offsets, sc.color_order, exec_mode)
+                   sc.color_offsets, sc.color_order, exec_mode, getattr(sc, "tet_coupled", False))
 
     def exec_info(self) -> dict:
         """{"phases": bool, "launches_per_iteration": int} of the handle's execution plan."""

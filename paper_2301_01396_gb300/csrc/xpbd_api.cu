@@ -72,6 +72,50 @@ xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool
   return XPBD_OK;
 }
 
+// Forward update of one color segment; `tape_k` (replay) receives the pre-projection
+// positions.  With coupled tets a C_H segment updates its tets' C_D constraints too.
+void project_segment(xpbd_solver* h, const Seg& g, float4* P, const float* lam_in, float* lam_out,
+                     float4* tape_k, cudaStream_t s) {
+  const bool record = tape_k != nullptr;
+  const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+  float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
+  if (h->coupled && g.type == SEG_TETH) {
+    // per tet: C_H record 64 + C_D alpha~ 4 + two multipliers r/w 16 + four vertices r/w 128
+    // (+ 64 tape)
+    launch(h, record ? XPBD_K_REPLAY_TETH : XPBD_K_FWD_TETH, 2 * (int64_t)g.count, s, [&] {
+      launch_project_tet_pair((const TetRec*)rec_ptr(h, SEG_TETH, g.begin),
+                              (const TetRec*)rec_ptr(h, SEG_TETD, g.begin), g.count, P,
+                              lam_in ? lam_in + ro : nullptr, lam_out + ro, h->rec_off[3] - h->rec_off[2], tp, s);
+    }, (double)g.count * (record ? 276 : 212));
+    return;
+  }
+  launch(h, (record ? XPBD_K_REPLAY_DIST : XPBD_K_FWD_DIST) + (int)g.type, g.count, s, [&] {
+    launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
+                   lam_out + ro, tp, s);
+  });
+}
+
+// Reverse of project_segment from iteration k's tape and multipliers before it.
+void vjp_segment(xpbd_solver* h, const Seg& g, const float4* tape_k, const float* lam_pre, float4* xbar,
+                 bool first, bool last, cudaStream_t s) {
+  const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+  const float4* tp = tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type];
+  if (h->coupled && g.type == SEG_TETH) {
+    // per tet: record 64 + 4, tape 64, multipliers 8, vertex adjoints r/w 128, two
+    // (lambar, alphabar) r/w 32
+    launch(h, XPBD_K_VJP_TETH, 2 * (int64_t)g.count, s, [&] {
+      launch_vjp_tet_pair((const TetRec*)rec_ptr(h, SEG_TETH, g.begin), (const TetRec*)rec_ptr(h, SEG_TETD, g.begin),
+                          g.count, tp, lam_pre ? lam_pre + ro : nullptr, h->rec_off[3] - h->rec_off[2], xbar,
+                          h->lb.as<float2>() + ro, h->acc.as<double>() + ro, first, last, s);
+    }, (double)g.count * 300);
+    return;
+  }
+  launch(h, XPBD_K_VJP_DIST + (int)g.type, g.count, s, [&] {
+    launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count, tp, lam_pre ? lam_pre + ro : nullptr, xbar,
+               h->lb.as<float2>() + ro, h->acc.as<double>() + ro, first, last, s);
+  });
+}
+
 // One step: prediction from checkpoint n, `iters` colored iterations, collision passes.
 // With `record`, the multipliers of iteration k go to lam_tape[k] and the pre-projection
 // positions to tape[k] (replay for the reverse sweep); otherwise lambda is updated in place.
@@ -112,16 +156,8 @@ xpbd_status run_step(xpbd_solver* h, const xpbd_params* p, int n, int iters, con
                record ? ph.bytes_replay : ph.bytes_fwd);
       }
     } else {
-      for (int col = 0; col < h->K; ++col) {
-        for (const Seg& g : h->colors[col]) {
-          size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-          float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
-          launch(h, (record ? XPBD_K_REPLAY_DIST : XPBD_K_FWD_DIST) + (int)g.type, g.count, s, [&] {
-            launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, lam_in ? lam_in + ro : nullptr,
-                           lam_out + ro, tp, s);
-          });
-        }
-      }
+      for (int col = 0; col < h->K; ++col)
+        for (const Seg& g : h->colors[col]) project_segment(h, g, P, lam_in, lam_out, tape_k, s);
     }
     if (c.flags) {
       float2* li;
@@ -607,17 +643,23 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
         if (vs[q] == vs[k]) return fail(XPBD_ERR_INVALID, "constraint " + std::to_string(j) + " repeats a vertex");
     }
   }
-  // coloring: offsets monotone, a permutation of [0, m), vertex-disjoint colors
-  if (md->color_offsets[0] != 0 || md->color_offsets[K] != m)
-    return fail(XPBD_ERR_COLORING, "color offsets must start at 0 and end at m");
-  std::vector<char> seen(m, 0);
+  // coloring: offsets monotone, a permutation of the colored ids, vertex-disjoint colors.
+  // Coupled tets: the C_D ids (nd + nb + nt ...) are not colored; each C_H id stands for
+  // its tet's pair.
+  if (md->tet_coupled != 0 && md->tet_coupled != 1) return fail(XPBD_ERR_INVALID, "tet_coupled must be 0 or 1");
+  const bool coupled = md->tet_coupled == 1 && nt > 0;
+  const int mc = coupled ? m - nt : m;
+  if (md->color_offsets[0] != 0 || md->color_offsets[K] != mc)
+    return fail(XPBD_ERR_COLORING, coupled ? "color offsets must start at 0 and end at m - n_tet (coupled tets)"
+                                           : "color offsets must start at 0 and end at m");
+  std::vector<char> seen(mc, 0);
   std::vector<int> stamp(V, -1);
   for (int c = 0; c < K; ++c) {
     int b = md->color_offsets[c], e = md->color_offsets[c + 1];
     if (e < b) return fail(XPBD_ERR_COLORING, "color offsets decrease");
     for (int t = b; t < e; ++t) {
       int j = md->color_order[t];
-      if (j < 0 || j >= m) return fail(XPBD_ERR_COLORING, "constraint id out of range in coloring");
+      if (j < 0 || j >= mc) return fail(XPBD_ERR_COLORING, "constraint id out of range in coloring");
       if (seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " appears twice");
       seen[j] = 1;
       int vs[4];
@@ -629,12 +671,13 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
       }
     }
   }
-  for (int j = 0; j < m; ++j)
+  for (int j = 0; j < mc; ++j)
     if (!seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " has no color");
 
   // records, grouped by color, then type, then first vertex
   xpbd_solver* h = new xpbd_solver();
   h->V = V; h->nd = nd; h->nb = nb; h->nt = nt; h->m = m; h->K = K;
+  h->coupled = coupled;
   h->slots = ((size_t)std::max(m, 1) + 3) / 4 * 4;
   h->tape_slots = h->tape_per_iter();
   h->n_rec[0] = nd; h->n_rec[1] = nb; h->n_rec[2] = nt; h->n_rec[3] = nt;
@@ -716,6 +759,10 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
           if (type == 2) {
             perm[h->rec_off[2] + rh.size()] = j;
             rh.push_back(r);
+            if (coupled) {   // the C_D shadow: same tet, same slot index
+              perm[h->rec_off[3] + rdv.size()] = j + nt;
+              rdv.push_back(r);
+            }
           } else {
             perm[h->rec_off[3] + rdv.size()] = j;
             rdv.push_back(r);
@@ -751,7 +798,7 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     xpbd_destroy(h);
     return fail(XPBD_ERR_INVALID, "exec_mode must be 0, 1 or 2");
   }
-  if (md->exec_mode != 1) {
+  if (md->exec_mode != 1 && !coupled) {
     // Automatic mode: on GB300 the phase plan was faster than per-color launches of the
     // same coloring by 1.7-3.4x where it cut launches per iteration 16x (cloth tiles), and
     // slower (0.5-0.8x) where it cut them 1.8x (row-shaped components serialise many chunks
@@ -953,16 +1000,7 @@ xpbd_status adjoint_step(xpbd_solver* h, const xpbd_params* p, int n, int32_t it
     }
     for (int col = h->use_phases ? -1 : h->K - 1; col >= 0; --col) {
       const std::vector<Seg>& segs = h->colors[col];
-      for (int q = (int)segs.size() - 1; q >= 0; --q) {
-        const Seg& g = segs[q];
-        size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-        launch(h, XPBD_K_VJP_DIST + (int)g.type, g.count, s, [&] {
-          launch_vjp(g.type, rec_ptr(h, g.type, g.begin), g.count,
-                     tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type],
-                     lam_pre ? lam_pre + ro : nullptr, xbar, h->lb.as<float2>() + ro,
-                     h->acc.as<double>() + ro, first, last, s);
-        });
-      }
+      for (int q = (int)segs.size() - 1; q >= 0; --q) vjp_segment(h, segs[q], tape_k, lam_pre, xbar, first, last, s);
     }
     LAUNCH_CHECK();
   }
@@ -1162,13 +1200,14 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
     auto spmv = [&](const double* pin, double* qout) {   // q = A pin, color by color
       launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_apply_mass_contacts(X, cf, lamc, c, pd, pin, qout, V, s); });
       for (int col = 0; col < h->K; ++col)
-        for (const Seg& g : h->colors[col]) {
-          const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-          launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
-            launch_apply_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
-                               blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, pin, qout, s);
+        for (const Seg& cg : h->colors[col])
+          for_each_record_seg(h, cg, [&](const Seg& g) {
+            const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+            launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+              launch_apply_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
+                                 blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, pin, qout, s);
+            });
           });
-        }
     };
     launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_adj_begin(xbar, vbar, 1.f / p->dt, V, s); });
     st = run_step(h, p, n, iters, ck_x(ck, V, n), ck_v(ck, V, n), false, s, true);   // lambda, contacts
@@ -1181,13 +1220,14 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
       });
     launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_mass_contacts(X, cf, lamc, c, pd, dinv, V, s); });
     for (int col = 0; col < h->K; ++col)
-      for (const Seg& g : h->colors[col]) {
-        const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-        launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
-          launch_diag_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
-                            blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, dinv, s);
+      for (const Seg& cg : h->colors[col])
+        for_each_record_seg(h, cg, [&](const Seg& g) {
+          const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+          launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+            launch_diag_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
+                              blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, dinv, s);
+          });
         });
-      }
     launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_invert(X, dinv, V, s); });
     LAUNCH_CHECK();
     // preconditioned conjugate gradients on the free vertices
@@ -1339,15 +1379,8 @@ xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t ste
                      p->gravity[0], p->gravity[1], p->gravity[2], c, cf, h->V, s);
     });
     for (int k = 0; k < iters; ++k) {
-      for (int col = 0; col < h->K; ++col) {
-        for (const Seg& g : h->colors[col]) {
-          size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-          launch(h, XPBD_K_FWD_DIST + (int)g.type, g.count, s, [&] {
-            launch_project(g.type, rec_ptr(h, g.type, g.begin), g.count, P, k == 0 ? nullptr : lam + ro,
-                           lam + ro, nullptr, s);
-          });
-        }
-      }
+      for (int col = 0; col < h->K; ++col)
+        for (const Seg& g : h->colors[col]) project_segment(h, g, P, k == 0 ? nullptr : lam, lam, nullptr, s);
       if (c.flags)
         launch(h, XPBD_K_FWD_CONTACT, h->V, s,
                [&] { launch_contact(P, cf, h->V, k == 0 ? nullptr : lamc, lamc, nullptr, c, s); });

@@ -531,6 +531,200 @@ __device__ __forceinline__ void vjp_quad_elem(int i, const typename Quad<KIND>::
   lb_finish(i, l.x, l.y, lb, acc, last);
 }
 
+// ---- coupled tet update: a tet's C_H and C_D from one 2x2 system (the update of the
+// neo-Hookean constraint pair that the volumetric model of Sec. 3.2 follows, Macklin and
+// Mueller 2021):  S dlambda = -C - A~ lambda,  S = G W G^T + A~,  x += W G^T dlambda.
+// det S is formed as a (b_perp + at_D) + at_H (b + at_D), a = |g_H|^2_W, b = |g_D|^2_W and
+// b_perp the W-norm of the part of g_D orthogonal to g_H: non-negative terms only, free of
+// the cancellation in s11 s22 - s12^2 when the gradients are nearly parallel (at the rest
+// shape they are parallel).  When C_D is degenerate only C_H is projected.
+struct TetPair {
+  f3 h[4], d[4];   // per-vertex gradients of C_H and C_D (d unset unless `both`)
+  float Ch, Cd, s11, s12, s22, det;
+  bool both;       // false: C_D degenerate, C_H alone with D = s11
+};
+
+__device__ __forceinline__ void tet_pair_eval(const TetRec& r, float atd, const float4 (&p)[4], TetPair& T) {
+  const f3 x0 = xyz(p[0]);
+  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
+  tet_grad_rel<true, float>(e1, e2, e3, r.B, T.h[1], T.h[2], T.h[3], &T.Ch, r.gamma);
+  T.h[0] = -(T.h[1] + T.h[2] + T.h[3]);
+  float a = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a += p[k].w * dot(T.h[k], T.h[k]);
+  T.s11 = r.at + a;
+  tet_grad_rel<false, float>(e1, e2, e3, r.B, T.d[1], T.d[2], T.d[3], &T.Cd, r.gamma);
+  T.both = !(T.Cd * T.Cd < XPBD_DEGEN2);
+  if (!T.both) return;
+  T.d[0] = -(T.d[1] + T.d[2] + T.d[3]);
+  float b = 0.f, c = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    b += p[k].w * dot(T.d[k], T.d[k]);
+    c += p[k].w * dot(T.h[k], T.d[k]);
+  }
+  float bp = b;
+  if (a > 0.f) {
+    const float beta = c / a;
+    bp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const f3 o = T.d[k] - T.h[k] * beta;
+      bp += p[k].w * dot(o, o);
+    }
+  }
+  T.s12 = c;
+  T.s22 = atd + b;
+  T.det = a * (bp + atd) + r.at * (b + atd);
+}
+
+// Multiplier increments of the pair (dlambda_D = 0 when C_D is degenerate); false when
+// the system is singular and nothing moves.
+__device__ __forceinline__ bool tet_pair_solve(const TetPair& T, float ath, float atd, float2 lam, float& dlh,
+                                               float& dld) {
+  if (!T.both) {
+    if (!(T.s11 > 0.f)) return false;
+    dlh = (-T.Ch - ath * lam.x) / T.s11;
+    dld = 0.f;
+    return true;
+  }
+  if (!(T.det > 0.f)) return false;
+  const float rh = -T.Ch - ath * lam.x, rd = -T.Cd - atd * lam.y;
+  const float inv = 1.f / T.det;
+  dlh = (T.s22 * rh - T.s12 * rd) * inv;
+  dld = (T.s11 * rd - T.s12 * rh) * inv;
+  return true;
+}
+
+template <bool SH = false>
+__device__ __forceinline__ float2 proj_pair_core(const TetRec& r, float atd, float4* __restrict__ P, float2 lam,
+                                                 float4* __restrict__ tape4, int ts = 1) {
+  const uint64_t pol = SH ? 0 : vtx_policy();
+  float4 p[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p[k] = vload<SH>(P + r.v[k], pol);
+  if (tape4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) __stcs(tape4 + k * ts, p[k]);
+  }
+  TetPair T;
+  tet_pair_eval(r, atd, p, T);
+  float dlh, dld;
+  if (!tet_pair_solve(T, r.at, atd, lam, dlh, dld)) return lam;
+  lam.x += dlh;
+  lam.y += dld;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const f3 dx = T.both ? T.h[k] * dlh + T.d[k] * dld : T.h[k] * dlh;
+    vstore<SH>(P + r.v[k], with_w(xyz(p[k]) + dx * p[k].w, p[k].w), pol);
+  }
+  return lam;
+}
+
+// rh / rd: the C_H records of a color segment and their C_D shadows (same tets, same
+// order); the C_D multipliers sit doff slots after the C_H ones.
+__device__ __forceinline__ void proj_pair_elem(int i, const TetRec* __restrict__ rh, const TetRec* __restrict__ rd,
+                                               float4* __restrict__ P, const float* lam_in, float* lam_out, int doff,
+                                               float4* __restrict__ tape) {
+  const TetRec r = ld_rec(rh + i);
+  const float atd = ld_stream(&rd[i].at);
+  float2 lam = lam_in ? make_float2(ld_stream(lam_in + i), ld_stream(lam_in + i + doff)) : make_float2(0.f, 0.f);
+  lam = proj_pair_core(r, atd, P, lam, tape ? tape + 4 * i : nullptr);
+  __stcs(lam_out + i, lam.x);
+  __stcs(lam_out + i + doff, lam.y);
+}
+
+// Reverse of the coupled update.  With S, dlambda recomputed from the tape and the adjoints
+// xbar', lambar' of the updated values:  sbar = lambar' + G W xbar',  q = S^-1 sbar,
+//   Gbar_k = dlambda_k W xbar' - sum_l (q_k dlambda_l + dlambda_k q_l) W g_l,
+//   xbar = xbar' - sum_k q_k g_k + sum_k H_k Gbar_k,
+//   lambar_k = lambar'_k - alpha~_k q_k,  alphabar~_k += -q_k (lambda_k + dlambda_k).
+// With one constraint this is vjp_quad_core's update (q = s/D).  lh, ld: (lambar, alphabar)
+// of C_H and C_D.
+__device__ __forceinline__ void vjp_pair_core(const TetRec& r, float atd, const float4 (&p)[4], float2 lam,
+                                              float2& lh, float2& ld, float4* __restrict__ xbar) {
+  const uint64_t pol = vtx_policy();
+  float4 xb4[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) xb4[k] = vload<false>(xbar + r.v[k], pol);
+  TetPair T;
+  tet_pair_eval(r, atd, p, T);
+  float dlh, dld;
+  if (!tet_pair_solve(T, r.at, atd, lam, dlh, dld)) return;
+  f3 xb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) xb[k] = xyz(xb4[k]);
+  float sh = lh.x, sd = ld.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sh += p[k].w * dot(T.h[k], xb[k]);
+  float qh, qd = 0.f;
+  if (T.both) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sd += p[k].w * dot(T.d[k], xb[k]);
+    const float inv = 1.f / T.det;
+    qh = (T.s22 * sh - T.s12 * sd) * inv;
+    qd = (T.s11 * sd - T.s12 * sh) * inv;
+  } else {
+    qh = sh / T.s11;
+  }
+  const f3 x0 = xyz(p[0]);
+  const f3 e1 = xyz(p[1]) - x0, e2 = xyz(p[2]) - x0, e3 = xyz(p[3]) - x0;
+  f3 out[4];
+  {   // C_H: u_H = W (dlambda_H xbar' - 2 q_H dlambda_H g_H - (q_H dlambda_D + dlambda_H q_D) g_D)
+    const float chh = 2.f * qh * dlh, chd = qh * dld + dlh * qd;
+    f3 u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      f3 t = xb[k] * dlh - T.h[k] * chh;
+      if (T.both) t = t - T.d[k] * chd;
+      u[k] = t * p[k].w;
+    }
+    d3 g1, g2, g3;
+    Quad<2>::hvp(r, e1, e2, e3, u[1] - u[0], u[2] - u[0], u[3] - u[0], g1, g2, g3);
+    const f3 hu1 = dpart(g1), hu2 = dpart(g2), hu3 = dpart(g3);
+    out[0] = xb[0] - T.h[0] * qh - (hu1 + hu2 + hu3);
+    out[1] = xb[1] - T.h[1] * qh + hu1;
+    out[2] = xb[2] - T.h[2] * qh + hu2;
+    out[3] = xb[3] - T.h[3] * qh + hu3;
+  }
+  if (T.both) {   // C_D: u_D = W (dlambda_D xbar' - (q_D dlambda_H + dlambda_D q_H) g_H - 2 q_D dlambda_D g_D)
+    const float cdh = qd * dlh + dld * qh, cdd = 2.f * qd * dld;
+    f3 u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = (xb[k] * dld - T.h[k] * cdh - T.d[k] * cdd) * p[k].w;
+    d3 g1, g2, g3;
+    Quad<3>::hvp(r, e1, e2, e3, u[1] - u[0], u[2] - u[0], u[3] - u[0], g1, g2, g3);
+    const f3 hu1 = dpart(g1), hu2 = dpart(g2), hu3 = dpart(g3);
+    out[0] = out[0] - T.d[0] * qd - (hu1 + hu2 + hu3);
+    out[1] = out[1] - T.d[1] * qd + hu1;
+    out[2] = out[2] - T.d[2] * qd + hu2;
+    out[3] = out[3] - T.d[3] * qd + hu3;
+    ld.y += -qd * (lam.y + dld);
+    ld.x -= atd * qd;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) vstore<false>(xbar + r.v[k], with_w(out[k], 0.f), pol);
+  lh.y += -qh * (lam.x + dlh);
+  lh.x -= r.at * qh;
+}
+
+__device__ __forceinline__ void vjp_pair_elem(int i, const TetRec* __restrict__ rh, const TetRec* __restrict__ rd,
+                                              const float4* __restrict__ tape, const float* __restrict__ lam_pre,
+                                              int doff, float4* __restrict__ xbar, float2* __restrict__ lb,
+                                              double* __restrict__ acc, bool first, bool last) {
+  const TetRec r = ld_rec(rh + i);
+  const float atd = ld_stream(&rd[i].at);
+  float4 p[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p[k] = ld_stream(tape + 4 * i + k);
+  const float2 lam = lam_pre ? make_float2(ld_stream(lam_pre + i), ld_stream(lam_pre + i + doff)) : make_float2(0.f, 0.f);
+  float2 lh = first ? make_float2(0.f, 0.f) : lb[i];
+  float2 ld = first ? make_float2(0.f, 0.f) : lb[i + doff];
+  vjp_pair_core(r, atd, p, lam, lh, ld, xbar);
+  lb_finish(i, lh.x, lh.y, lb, acc, last);
+  lb_finish(i + doff, ld.x, ld.y, lb, acc, last);
+}
+
 // Reverse of the collision pass.  Plane (inputs p, h; grad_p = e_y, grad_h = -1, H = 0) and
 // sphere (inputs p, c, r; grad_p = n, grad_c = -n, grad_r = -1, H_pp = P/l, H_pc = -P/l;
 // the centre and radius are not moved, so u_c = 0).  Collider adjoints accumulate in the

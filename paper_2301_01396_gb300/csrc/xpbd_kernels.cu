@@ -103,6 +103,18 @@ void launch_project(SegType t, const void* rec, int n, float4* P, const float* l
   }
 }
 
+__global__ void __launch_bounds__(kBlock, XPBD_PROJ_QUAD_MIN_BLOCKS)
+k_proj_tet_pair(const TetRec* __restrict__ rh, const TetRec* __restrict__ rd, int n, float4* __restrict__ P,
+                const float* lam_in, float* lam_out, int doff, float4* __restrict__ tape) {
+  XPBD_TID_OR_RETURN(n);
+  proj_pair_elem(i, rh, rd, P, lam_in, lam_out, doff, tape);
+}
+
+void launch_project_tet_pair(const TetRec* rh, const TetRec* rd, int n, float4* P, const float* lam_in,
+                             float* lam_out, int doff, float4* tape, cudaStream_t s) {
+  if (n > 0) k_proj_tet_pair<<<grid_for(n), kBlock, 0, s>>>(rh, rd, n, P, lam_in, lam_out, doff, tape);
+}
+
 __global__ void k_contact(float4* __restrict__ P, const uint8_t* __restrict__ cflags, int V,
                           const float2* lam_in, float2* lam_out, float4* __restrict__ tape, Collide c) {
   XPBD_TID_OR_RETURN(V);
@@ -187,6 +199,22 @@ void launch_vjp(SegType t, const void* rec, int n, const float4* tape, const flo
       k_vjp_quad<3><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, tape, lam_pre, xbar, lb, acc, first, last);
       break;
   }
+}
+
+// Two resident blocks: the pair reverse holds both gradients and both Hessian products
+// (84 bytes of spills at the 85-register cap of three blocks).
+__global__ void __launch_bounds__(kBlock, 2)
+k_vjp_tet_pair(const TetRec* __restrict__ rh, const TetRec* __restrict__ rd, int n, const float4* __restrict__ tape,
+               const float* __restrict__ lam_pre, int doff, float4* __restrict__ xbar, float2* __restrict__ lb,
+               double* __restrict__ acc, bool first, bool last) {
+  XPBD_TID_OR_RETURN(n);
+  vjp_pair_elem(i, rh, rd, tape, lam_pre, doff, xbar, lb, acc, first, last);
+}
+
+void launch_vjp_tet_pair(const TetRec* rh, const TetRec* rd, int n, const float4* tape, const float* lam_pre,
+                         int doff, float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s) {
+  if (n > 0)
+    k_vjp_tet_pair<<<grid_for(n), kBlock, 0, s>>>(rh, rd, n, tape, lam_pre, doff, xbar, lb, acc, first, last);
 }
 
 __global__ void k_vjp_contact(const float4* __restrict__ tape, const uint8_t* __restrict__ cflags,

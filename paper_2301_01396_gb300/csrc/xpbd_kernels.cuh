@@ -41,6 +41,10 @@ void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float
 // record of pre-projection positions (forward only)
 void launch_project(SegType t, const void* rec, int n, float4* P, const float* lam_in,
                     float* lam_out, float4* tape, cudaStream_t s);
+// Coupled tets: the C_H records rh of a color segment with their C_D shadows rd; the C_D
+// multipliers are doff slots after the C_H ones, the tape holds the C_H layout.
+void launch_project_tet_pair(const TetRec* rh, const TetRec* rd, int n, float4* P, const float* lam_in,
+                             float* lam_out, int doff, float4* tape, cudaStream_t s);
 void launch_contact(float4* P, const uint8_t* cflags, int V, const float2* lam_in,
                     float2* lam_out, float4* tape, Collide c, cudaStream_t s);
 void launch_velocity(const float4* P, const float4* ckx_n, float4* ckx_next, float4* ckv_next,
@@ -54,6 +58,8 @@ void launch_adj_begin(float4* xbar, float4* vbar, float inv_dt, int V, cudaStrea
 // last: the final one (fold the step's alpha-bar into the float64 accumulator)
 void launch_vjp(SegType t, const void* rec, int n, const float4* tape, const float* lam_pre,
                 float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s);
+void launch_vjp_tet_pair(const TetRec* rh, const TetRec* rd, int n, const float4* tape, const float* lam_pre,
+                         int doff, float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s);
 void launch_vjp_contact(const float4* tape, const uint8_t* cflags, int V, const float2* lam_pre,
                         float4* xbar, float2* lbc, float* cgrad, bool first, Collide c,
                         cudaStream_t s);

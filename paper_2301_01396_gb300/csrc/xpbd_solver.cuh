@@ -66,6 +66,9 @@ struct DevBuf {
 
 struct xpbd_solver {
   int V = 0, nd = 0, nb = 0, nt = 0, m = 0, K = 0;
+  // Coupled tets: the colors hold C_H segments only, and the C_D records (type 3) are
+  // shadows of the C_H records in the same order, updated with them by one 2x2 solve.
+  bool coupled = false;
   std::vector<std::vector<Seg>> colors;
   // type arrays in record order; rec_off[t] = offset of type t in the m-long record space
   int n_rec[4] = {0, 0, 0, 0};
@@ -177,6 +180,15 @@ inline size_t tape_offset(const xpbd_solver* h, SegType t) {   // float4 offset 
 inline void* rec_ptr(const xpbd_solver* h, SegType t, int begin) {
   static const size_t sz[4] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec)};
   return (char*)h->d_rec[t] + sz[t] * (size_t)begin;
+}
+
+// The record segments a color segment stands for: itself, and for coupled tets the C_D
+// shadow of a C_H segment as well (launched after it: same vertices, so the two launches
+// of an assembly pass over one color never write the same vertex at once).
+template <class F>
+inline void for_each_record_seg(const xpbd_solver* h, const Seg& g, F&& f) {
+  f(g);
+  if (h->coupled && g.type == SEG_TETH) f(Seg{SEG_TETD, g.begin, g.count});
 }
 
 inline Collide make_collide(const xpbd_params* p) {

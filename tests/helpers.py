@@ -41,9 +41,9 @@ def small_cloth(n=5, *, bending=True, diagonals="both", pins=((0, 0), (-1, 0)), 
 
 
 def small_tets(n=2, *, steps=3, iters=3, seed=3, y0=0.02, plane=True, gravity=(0.0, -9.81, 0.0),
-               jitter=0.0, v_scale=0.0):
-    sc = scenes.tet_block(n, size=0.2, y0=y0, steps=steps, iters=iters, seed=seed, alpha_lo=1e-5,
-                          alpha_hi=1e-3)
+               jitter=0.0, v_scale=0.0, alpha=(1e-5, 1e-3)):
+    sc = scenes.tet_block(n, size=0.2, y0=y0, steps=steps, iters=iters, seed=seed, alpha_lo=alpha[0],
+                          alpha_hi=alpha[1])
     sc.gravity = gravity
     rng = np.random.default_rng(seed + 100)
     if jitter:

@@ -26,10 +26,12 @@ def _cases():
                                             iters=6, v_scale=0.3, seed=12),
         "ground_cloth": ground,
         "tets": helpers.small_tets(2, steps=3, iters=6, y0=0.05, plane=False, v_scale=0.05),
+        "tets_coupled": scenes.couple_tets(helpers.small_tets(2, steps=3, iters=6, y0=0.05, plane=False,
+                                                              v_scale=0.05)),
     }
 
 
-@pytest.mark.parametrize("name", ["pinned_cloth", "ground_cloth", "tets"])
+@pytest.mark.parametrize("name", ["pinned_cloth", "ground_cloth", "tets", "tets_coupled"])
 @pytest.mark.parametrize("pd", [True, False])
 def test_implicit_adjoint_matches_oracle(name, pd):
     sc = _cases()[name]

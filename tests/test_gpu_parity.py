@@ -31,6 +31,11 @@ def _cases():
         "ground_cloth_32": helpers.small_cloth(32, bending=True, diagonals="one", steps=8, iters=10,
                                                plane_h=-0.03, v_scale=0.3, seed=33),
         "tets_4": helpers.small_tets(4, steps=8, iters=6, y0=0.004, v_scale=0.05),
+        # each tet's C_H and C_D by one 2x2 solve (per-color launches in every mode), on
+        # softer tets: with inverse moduli down to 1e-5 the coupled sweep amplifies float32
+        # rounding past these bounds within 3 steps (tests/test_oracle_coupled.py)
+        "tets_4_coupled": scenes.couple_tets(helpers.small_tets(4, steps=8, iters=6, y0=0.004, v_scale=0.05,
+                                                                alpha=(1e-4, 1e-2))),
         "sphere_cloth_24": helpers.small_sphere_cloth(24, steps=6, iters=8),
         "both_colliders_24": both,
         # 16,384 vertices: more than one shared-memory group, so the phase plan has many
@@ -247,8 +252,9 @@ def test_phase_plan_matches_per_color_launches(name, cases):
     for mode in (2, 1):   # 2: the phase plan whenever the coloring allows one
         solver = binding.Solver.from_scene(sc, exec_mode=mode)
         info = solver.exec_info()
-        assert info["phases"] == (mode == 2), info
-        if mode == 2:
+        # coupled tets run one launch per color in every mode
+        assert info["phases"] == (mode == 2 and not sc.tet_coupled), info
+        if mode == 2 and not sc.tet_coupled:
             assert info["launches_per_iteration"] < sc.n_colors
         p = binding.params_from_scene(sc)
         ck = solver.forward(p, sc.steps, sc.iters, to_dev(sc.x0), to_dev(sc.v0))

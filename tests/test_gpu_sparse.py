@@ -26,10 +26,11 @@ def _scenes():
         "ground_cloth_tiled": helpers.small_cloth(64, bending=True, diagonals="both", pins=(), steps=7, iters=3,
                                                   v_scale=0.3, plane_h=-0.02, seed=33, coloring="tiled", tile=16),
         "tets": helpers.small_tets(3, steps=7, iters=3, y0=0.004, v_scale=0.05),
+        "tets_coupled": scenes.couple_tets(helpers.small_tets(3, steps=7, iters=3, y0=0.004, v_scale=0.05)),
     }
 
 
-@pytest.mark.parametrize("name", ["sphere_cloth", "ground_cloth_tiled", "tets"])
+@pytest.mark.parametrize("name", ["sphere_cloth", "ground_cloth_tiled", "tets", "tets_coupled"])
 @pytest.mark.parametrize("stride", [1, 2, 3, 7, 10])
 def test_sparse_equals_dense(name, stride):
     sc = _scenes()[name]

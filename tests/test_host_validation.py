@@ -59,3 +59,15 @@ def test_degenerate_rest_tet_rejected():
     t = sc.tet_idx[0]
     x[t[3]] = x[t[0]] + 0.5 * (x[t[1]] - x[t[0]])    # flat tet
     assert _status(sc.with_(rest_x=x)) == 1
+
+
+def test_coupled_tet_coloring_rules():
+    """With coupled tets the coloring lists the C_H ids only: the uncoupled coloring (which
+    also lists C_D) and a C_D id in place of a C_H id are rejected."""
+    from tests.helpers import small_tets
+    sc = small_tets(2)
+    assert _status(sc.with_(tet_coupled=True)) == 2
+    cs = scenes.couple_tets(sc)
+    order = cs.color_order.copy()
+    order[0] = sc.n_tet + order[0]
+    assert _status(cs.with_(color_order=order)) == 2

@@ -50,6 +50,18 @@ def test_static_forward_tet_block_with_contacts():
         assert (got - ref)[:, :, :, :3].abs().max().item() <= POS_TOL
 
 
+def test_static_forward_coupled_tets():
+    sc = scenes.couple_tets(helpers.small_tets(4, steps=5, iters=6, y0=0.004, v_scale=0.05))
+    solver = binding.Solver.from_scene(sc)
+    p = binding.params_from_scene(sc)
+    x0, v0 = to_dev(sc.x0), to_dev(sc.v0)
+    ref = solver.forward(p, sc.steps, sc.iters, x0, v0)
+    got = solver.forward_static(p, sc.steps, sc.iters, x0, v0, solver.new_checkpoints(sc.steps))
+    torch.cuda.synchronize()
+    solver.sync_status()
+    assert torch.equal(got, ref)
+
+
 def test_static_forward_rejects_models_beyond_its_limit():
     sc = scenes.plain_cloth(257, steps=1, iters=1)          # 66,049 vertices > 65,536
     assert sc.V > binding.STATIC_MAX_VERTICES
