@@ -26,7 +26,7 @@ class _Model(C.Structure):
                 ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
                 ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _dp),
                 ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip),
-                ("tet_coupled", C.c_int32)]
+                ("tet_coupled", C.c_int32), ("n_memb", C.c_int32), ("memb_idx", _ip), ("memb_uv", _dp)]
 
 
 class _Params(C.Structure):
@@ -34,12 +34,13 @@ class _Params(C.Structure):
                 ("f_global", _dp), ("f_vertex", _dp), ("collider_flags", C.c_int32),
                 ("plane_h", C.c_double), ("sphere", C.c_double * 4),
                 ("contact_compliance", C.c_double), ("thickness", C.c_double),
-                ("f_vertex_steps", _dp)]
+                ("f_vertex_steps", _dp), ("memb_stiffness", _dp)]
 
 
 class _Direction(C.Structure):
     _fields_ = [("d_compliance", _dp), ("d_x0", _dp), ("d_v0", _dp), ("d_f_global", _dp),
-                ("d_f_vertex", _dp), ("d_collider", _dp), ("d_f_vertex_steps", _dp)]
+                ("d_f_vertex", _dp), ("d_collider", _dp), ("d_f_vertex_steps", _dp),
+                ("d_memb_stiffness", _dp)]
 
 
 def lib():
@@ -72,7 +73,7 @@ class _Args:
     """Keeps the numpy buffers alive while the C structs point into them."""
 
     def __init__(self, scene, compliance=None, f_global=None, f_vertex=None, plane_h=None,
-                 sphere=None, steps=None, f_vertex_steps=None):
+                 sphere=None, steps=None, f_vertex_steps=None, memb_stiffness=None):
         keep = []
 
         def d(a):
@@ -93,7 +94,10 @@ class _Args:
                             tet_gamma=d(s.tet_gamma) if s.n_tet else None,
                             n_colors=s.n_colors, color_offsets=i(s.color_offsets),
                             color_order=i(s.color_order),
-                            tet_coupled=int(bool(getattr(s, "tet_coupled", False))))
+                            tet_coupled=int(bool(getattr(s, "tet_coupled", False))),
+                            n_memb=s.n_memb,
+                            memb_idx=i(s.memb_idx.reshape(-1)) if s.n_memb else None,
+                            memb_uv=d(s.memb_uv.reshape(-1)) if s.n_memb else None)
         comp = s.compliance if compliance is None else compliance
         fg = s.f_global if f_global is None else f_global
         fv = s.f_vertex if f_vertex is None else f_vertex
@@ -112,7 +116,9 @@ class _Args:
                               plane_h=s.plane_h if plane_h is None else plane_h,
                               sphere=(C.c_double * 4)(*sph),
                               contact_compliance=s.contact_compliance, thickness=s.thickness,
-                              f_vertex_steps=d(fvs))
+                              f_vertex_steps=d(fvs),
+                              memb_stiffness=(d(s.memb_stiffness if memb_stiffness is None else memb_stiffness)
+                                              if s.n_memb else None))
         self.keep = keep
 
 
@@ -143,11 +149,12 @@ def num_threads() -> int:
 
 
 def forward(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, x0=None, v0=None,
-            compliance=None, f_global=None, f_vertex=None, plane_h=None, sphere=None, f_vertex_steps=None):
+            compliance=None, f_global=None, f_vertex=None, plane_h=None, sphere=None, f_vertex_steps=None,
+            memb_stiffness=None):
     """Run the FP64 forward simulation; returns (xs, vs), each [steps+1, V, 3]."""
     steps = scene.steps if steps is None else steps
     iters = scene.iters if iters is None else iters
-    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps, f_vertex_steps)
+    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps, f_vertex_steps, memb_stiffness)
     x0a, x0p = _d(scene.x0 if x0 is None else x0)
     v0a, v0p = _d(scene.v0 if v0 is None else v0)
     xs = np.zeros((steps + 1, scene.V, 3))
@@ -180,14 +187,14 @@ def forward_multipliers(scene, steps: Optional[int] = None, iters: Optional[int]
 
 def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
             seed_dv_T=None, x0=None, v0=None, compliance=None, f_global=None, f_vertex=None,
-            plane_h=None, sphere=None, f_vertex_steps=None) -> dict:
+            plane_h=None, sphere=None, f_vertex_steps=None, memb_stiffness=None) -> dict:
     """Reverse sweep.  ``seeds`` maps step n -> dL/dx_n [V,3].  Returns a dict of FP64
     gradients: compliance [m], x0 [V,3], v0 [V,3], f_global [steps,3], f_vertex [V,3],
     collider [5] (plane h, sphere cx, cy, cz, r), f_vertex_steps [steps,V,3] (the force on
-    each vertex at each step)."""
+    each vertex at each step), memb_stiffness [n_memb,4] (C00, C11, C01, C22)."""
     steps = scene.steps if steps is None else steps
     iters = scene.iters if iters is None else iters
-    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps, f_vertex_steps)
+    a = _Args(scene, compliance, f_global, f_vertex, plane_h, sphere, steps, f_vertex_steps, memb_stiffness)
     x0a, x0p = _d(scene.x0 if x0 is None else x0)
     v0a, v0p = _d(scene.v0 if v0 is None else v0)
     keys = sorted(seeds)
@@ -197,11 +204,11 @@ def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int
     dv, dvp = _d(None if seed_dv_T is None else np.asarray(seed_dv_T).reshape(-1))
     out = dict(compliance=np.zeros(scene.m), x0=np.zeros((scene.V, 3)), v0=np.zeros((scene.V, 3)),
                f_global=np.zeros((steps, 3)), f_vertex=np.zeros((scene.V, 3)), collider=np.zeros(5),
-               f_vertex_steps=np.zeros((steps, scene.V, 3)))
+               f_vertex_steps=np.zeros((steps, scene.V, 3)), memb_stiffness=np.zeros((scene.n_memb, 4)))
     P = lambda k: out[k].ctypes.data_as(_dp)
     lib().oracle_adjoint(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p, len(keys),
                          ssp, sdp, dvp, P("compliance"), P("x0"), P("v0"), P("f_global"),
-                         P("f_vertex"), P("collider"), P("f_vertex_steps"))
+                         P("f_vertex"), P("collider"), P("f_vertex_steps"), P("memb_stiffness"))
     return out
 
 
@@ -225,7 +232,7 @@ def tangent(scene, direction: dict, steps: Optional[int] = None, iters: Optional
 
     D = _Direction(d_compliance=dd("compliance"), d_x0=dd("x0"), d_v0=dd("v0"),
                    d_f_global=dd("f_global"), d_f_vertex=dd("f_vertex"), d_collider=dd("collider"),
-                   d_f_vertex_steps=dd("f_vertex_steps"))
+                   d_f_vertex_steps=dd("f_vertex_steps"), d_memb_stiffness=dd("memb_stiffness"))
     dxs = np.zeros((steps + 1, scene.V, 3))
     dvs = np.zeros((steps + 1, scene.V, 3))
     lib().oracle_tangent(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p, C.byref(D),
@@ -241,8 +248,8 @@ def rest_data(scene) -> np.ndarray:
     return out
 
 
-KIND = dict(dist=0, bend=1, tet_h=2, tet_d=3, plane=4, sphere=5)
-N_INPUTS = {0: 6, 1: 12, 2: 12, 3: 12, 4: 4, 5: 7}
+KIND = dict(dist=0, bend=1, tet_h=2, tet_d=3, plane=4, sphere=5, memb_uu=6, memb_vv=7, memb_uv=8)
+N_INPUTS = {0: 6, 1: 12, 2: 12, 3: 12, 4: 4, 5: 7, 6: 9, 7: 9, 8: 9}
 
 
 def constraint(kind, q, rest12=None, u=None):
@@ -307,5 +314,32 @@ def vjp_pair(q, w, rest12, lam, alpha_tilde, qbar, lambar):
     lb = np.array(lambar, np.float64)
     ab = np.zeros(2)
     lib().oracle_vjp_pair(qp, wp, rp, lp, ap, qb.ctypes.data_as(_dp), lb.ctypes.data_as(_dp),
+                          ab.ctypes.data_as(_dp))
+    return qb, lb, ab
+
+
+def project_memb(q, w, B2, lam, alpha_tilde):
+    """One membrane update (3x3 multiplier solve); returns (q' [9], lambda' [3])."""
+    q = np.array(q, np.float64).reshape(-1)
+    wa, wp = _d(np.asarray(w, np.float64))
+    ba, bp = _d(np.asarray(B2, np.float64).reshape(-1))
+    l = np.array(lam, np.float64)
+    aa, ap = _d(np.asarray(alpha_tilde, np.float64).reshape(-1))
+    lib().oracle_project_memb(q.ctypes.data_as(_dp), wp, bp, l.ctypes.data_as(_dp), ap)
+    return q, l
+
+
+def vjp_memb(q, w, B2, lam, alpha_tilde, qbar, lambar):
+    """Reverse of ``project_memb``: returns (qbar [9], lambar [3], abar4 [4]) with abar4 the
+    adjoint of the alpha~ entries (00, 11, 01 = 10, 22)."""
+    qa, qp = _d(np.asarray(q, np.float64).reshape(-1))
+    wa, wp = _d(np.asarray(w, np.float64))
+    ba, bp = _d(np.asarray(B2, np.float64).reshape(-1))
+    la, lp = _d(np.asarray(lam, np.float64))
+    aa, ap = _d(np.asarray(alpha_tilde, np.float64).reshape(-1))
+    qb = np.array(qbar, np.float64).reshape(-1)
+    lb = np.array(lambar, np.float64)
+    ab = np.zeros(4)
+    lib().oracle_vjp_memb(qp, wp, bp, lp, ap, qb.ctypes.data_as(_dp), lb.ctypes.data_as(_dp),
                           ab.ctypes.data_as(_dp))
     return qb, lb, ab

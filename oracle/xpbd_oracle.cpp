@@ -28,6 +28,11 @@
  *   bending   C = theta - theta0, theta the signed dihedral angle atan2 form (Sec. 5.1)
  *   tet       C_H = det F - gamma,  C_D = sqrt(tr F^T F)          (Sec. 5.2)
  *   plane     C = y - h - thickness;  sphere  C = |x - c| - r - thickness   (Sec. 4.6)
+ *   membrane  C = (E_uu, E_vv, 2 E_uv), E = (F^T F - I)/2 the Green strain of a triangle,
+ *             F = Ds Dm^-1 (3x2) from the warp/weft (u, v) rest coordinates, with the 3x3
+ *             compliance block (A K)^-1, K = [C00 C01 .; C01 C11 .; . . C22]
+ *             (Sec. "Cloth Material Parameter Estimation", orthotropic StVK); its three
+ *             multipliers are solved together (3x3 system)
  * Readings where the paper is silent (lambda reset per step, Gauss-Seidel over colors,
  * contact set fixed per step at the predicted positions, degenerate-constraint skip) are
  * listed in the design notes of the repository.
@@ -112,15 +117,16 @@ inline void round32(T& v) {
 }
 
 // ------------------------------------------------------------------ constraint definitions
-enum Kind { K_DIST = 0, K_BEND = 1, K_TETH = 2, K_TETD = 3, K_PLANE = 4, K_SPHERE = 5 };
+enum Kind { K_DIST = 0, K_BEND = 1, K_TETH = 2, K_TETD = 3, K_PLANE = 4, K_SPHERE = 5,
+            K_MEMB0 = 6, K_MEMB1 = 7, K_MEMB2 = 8 };   // membrane components E_uu, E_vv, 2 E_uv
 
 // Constant (non-differentiated) rest data of one constraint.
 struct Rest {
   double L = 0.0;        // distance rest length
   double theta0 = 0.0;   // bending rest angle
-  double B[9] = {0};     // tet Dm^-1, row-major
+  double B[9] = {0};     // tet Dm^-1, row-major (membrane: the 2x2 Dm^-1 in B[0..3])
   double gamma = 1.0;    // tet hydrostatic rest offset
-  double vol = 0.0;      // tet rest volume
+  double vol = 0.0;      // tet rest volume (membrane: rest area)
   double thickness = 0.0;
 };
 
@@ -132,6 +138,7 @@ inline int n_inputs(int kind) {
     case K_BEND: case K_TETH: case K_TETD: return 12;
     case K_PLANE: return 4;
     case K_SPHERE: return 7;
+    case K_MEMB0: case K_MEMB1: case K_MEMB2: return 9;
   }
   return 0;
 }
@@ -139,6 +146,7 @@ inline int n_verts(int kind) {
   switch (kind) {
     case K_DIST: return 2;
     case K_BEND: case K_TETH: case K_TETD: return 4;
+    case K_MEMB0: case K_MEMB1: case K_MEMB2: return 3;
     default: return 1;
   }
 }
@@ -193,6 +201,17 @@ S constraint_C(int kind, const S* q, const Rest& r) {
     case K_SPHERE: {
       V3<S> d = sub(load3(q), load3(q + 3));
       return sqrt(dot(d, d)) - q[6] - r.thickness;
+    }
+    case K_MEMB0:
+    case K_MEMB1:
+    case K_MEMB2: {
+      // F = [x1-x0, x2-x0] Dm^-1 (3x2); columns f_u, f_v; Green strain E = (F^T F - I)/2
+      V3<S> x0 = load3(q), d1 = sub(load3(q + 3), x0), d2 = sub(load3(q + 6), x0);
+      V3<S> fu = {d1.x * r.B[0] + d2.x * r.B[2], d1.y * r.B[0] + d2.y * r.B[2], d1.z * r.B[0] + d2.z * r.B[2]};
+      V3<S> fv = {d1.x * r.B[1] + d2.x * r.B[3], d1.y * r.B[1] + d2.y * r.B[3], d1.z * r.B[1] + d2.z * r.B[3]};
+      if (kind == K_MEMB0) return 0.5 * (dot(fu, fu) - 1.0);
+      if (kind == K_MEMB1) return 0.5 * (dot(fv, fv) - 1.0);
+      return dot(fu, fv);
     }
   }
   return S(0.0);
@@ -261,14 +280,21 @@ struct Model {
   std::vector<int> offsets, order;
   std::vector<Rest> rest;   // per constraint id
   bool coupled = false;     // a tet's two constraints are projected together (its C_H id in the coloring)
+  // membrane triangles: coloring ids m() + t; vertices, warp/weft rest coordinates, rest data
+  int nm = 0;
+  std::vector<int> memb_idx;      // [nm*3]
+  std::vector<double> memb_uv;    // [nm*6] (u, v) of each triangle's three vertices
+  std::vector<Rest> mrest;        // [nm] Dm^-1 in B[0..3], area in vol
   int m() const { return nd + nb + 2 * nt; }
   int kind(int j) const {
     if (j < nd) return K_DIST;
     if (j < nd + nb) return K_BEND;
     if (j < nd + nb + nt) return K_TETH;
-    return K_TETD;
+    if (j < nd + nb + 2 * nt) return K_TETD;
+    return K_MEMB0;
   }
   void verts(int j, int* out) const {
+    if (j >= m()) { for (int i = 0; i < 3; ++i) out[i] = memb_idx[3 * (j - m()) + i]; return; }
     if (j < nd) { out[0] = dist_idx[2 * j]; out[1] = dist_idx[2 * j + 1]; return; }
     j -= nd;
     if (j < nb) { for (int i = 0; i < 4; ++i) out[i] = bend_idx[4 * j + i]; return; }
@@ -319,6 +345,24 @@ void build_rest(Model& M) {
   }
 }
 
+// Membrane rest data from the warp/weft coordinates: Dm = [uv1 - uv0, uv2 - uv0] (columns),
+// B = Dm^-1, area = |det Dm| / 2.
+void build_memb_rest(Model& M) {
+  M.mrest.assign(M.nm, Rest());
+  for (int t = 0; t < M.nm; ++t) {
+    const double* uv = &M.memb_uv[6 * (size_t)t];
+    double a = uv[2] - uv[0], b = uv[4] - uv[0];   // first row (u) of Dm
+    double c = uv[3] - uv[1], d = uv[5] - uv[1];   // second row (v)
+    double det = a * d - b * c;
+    Rest& r = M.mrest[t];
+    r.B[0] = d / det;
+    r.B[1] = -b / det;
+    r.B[2] = -c / det;
+    r.B[3] = a / det;
+    r.vol = std::fabs(det) / 2.0;
+  }
+}
+
 // ------------------------------------------------------------------ parameters (generic)
 template <class T>
 struct Params {
@@ -333,6 +377,7 @@ struct Params {
   T sphere[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
   double contact_alpha = 0.0;
   double thickness = 0.0;
+  std::vector<T> memb_k;         // [nm*4] (C00, C11, C01, C22) per membrane triangle
 };
 
 // alpha~ = alpha / dt^2, with the tet compliance alpha = alpha_hat / V_e.
@@ -344,12 +389,29 @@ T alpha_tilde(const Model& M, const Params<T>& P, int j) {
   return a / (P.dt * P.dt);
 }
 
+// The membrane's 3x3 alpha~ = (A K)^-1 / dt^2, row-major, from K = [C00 C01 0; C01 C11 0;
+// 0 0 C22] of triangle t.
+template <class T>
+void memb_alpha_tilde(const Model& M, const Params<T>& P, int t, T* at) {
+  const T c00 = P.memb_k[4 * (size_t)t + 0], c11 = P.memb_k[4 * (size_t)t + 1];
+  const T c01 = P.memb_k[4 * (size_t)t + 2], c22 = P.memb_k[4 * (size_t)t + 3];
+  const double s = 1.0 / (M.mrest[t].vol * P.dt * P.dt);
+  const T det = c00 * c11 - c01 * c01;
+  for (int i = 0; i < 9; ++i) at[i] = T(0.0);
+  at[0] = s * c11 / det;
+  at[1] = -(s * c01) / det;
+  at[3] = at[1];
+  at[4] = s * c00 / det;
+  at[8] = s / c22;
+}
+
 // State of one solve: positions p [V*3], multipliers lambda [m], per-vertex contact
-// multipliers and activity (plane, sphere).
+// multipliers and activity (plane, sphere), membrane multipliers [nm*3].
 template <class T>
 struct Work {
   std::vector<T> p, lam, lam_c;   // lam_c [V*2]
   std::vector<uint8_t> active;    // [V*2]
+  std::vector<T> lam_m;           // [nm*3]
 };
 
 // Gather the differentiated inputs of constraint j (vertex coordinates) or of a contact.
@@ -438,8 +500,69 @@ void project_pair(T* q, const double* wv, const Rest& rh, const Rest& rd, T& lh,
     }
 }
 
+// Solve the 3x3 system S x = r by Cramer's rule (S symmetric positive definite here).
+template <class T>
+bool solve3(const T* S, const T* r, T* x) {
+  const T c0 = S[4] * S[8] - S[5] * S[7], c1 = S[5] * S[6] - S[3] * S[8], c2 = S[3] * S[7] - S[4] * S[6];
+  const T det = S[0] * c0 + S[1] * c1 + S[2] * c2;
+  if (!(val(det) > 0.0)) return false;
+  // x = adj(S) r / det
+  x[0] = (c0 * r[0] + (S[2] * S[7] - S[1] * S[8]) * r[1] + (S[1] * S[5] - S[2] * S[4]) * r[2]) / det;
+  x[1] = (c1 * r[0] + (S[0] * S[8] - S[2] * S[6]) * r[1] + (S[2] * S[3] - S[0] * S[5]) * r[2]) / det;
+  x[2] = (c2 * r[0] + (S[1] * S[6] - S[0] * S[7]) * r[1] + (S[0] * S[4] - S[1] * S[3]) * r[2]) / det;
+  return true;
+}
+
+// XPBD update of one membrane (Eq. xpbd for a vector constraint): the three multipliers
+// from S dlambda = -C - A~ lambda with S = G W G^T + A~ (G: the three component gradients
+// as rows), then x += W G^T dlambda.
+template <class T>
+void project_memb(T* q, const double* wv, const Rest& r, T* lam, const T* at) {
+  T g[3][9], C[3];
+  for (int k = 0; k < 3; ++k) {
+    constraint_grad<T>(K_MEMB0 + k, q, r, g[k]);
+    C[k] = constraint_C<T>(K_MEMB0 + k, q, r);
+  }
+  T S[9], rhs[3], dl[3];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      T s = at[3 * k + l];
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) s = s + wv[a] * g[k][3 * a + c] * g[l][3 * a + c];
+      S[3 * k + l] = s;
+    }
+  for (int k = 0; k < 3; ++k) rhs[k] = -C[k] - (at[3 * k] * lam[0] + at[3 * k + 1] * lam[1] + at[3 * k + 2] * lam[2]);
+  if (!solve3(S, rhs, dl)) return;
+  for (int k = 0; k < 3; ++k) {
+    lam[k] = lam[k] + dl[k];
+    round32(lam[k]);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      const int i = 3 * a + c;
+      q[i] = q[i] + wv[a] * (g[0][i] * dl[0] + g[1][i] * dl[1] + g[2][i] * dl[2]);
+      round32(q[i]);
+    }
+}
+
 template <class T>
 void project_constraint(const Model& M, const Params<T>& P, int j, Work<T>& W) {
+  if (j >= M.m()) {   // membrane triangle
+    const int t = j - M.m();
+    T q[9], at[9];
+    int vs[3];
+    double wv[3];
+    M.verts(j, vs);
+    for (int a = 0; a < 3; ++a) {
+      wv[a] = M.w[vs[a]];
+      for (int c = 0; c < 3; ++c) q[3 * a + c] = W.p[3 * vs[a] + c];
+    }
+    memb_alpha_tilde(M, P, t, at);
+    project_memb<T>(q, wv, M.mrest[t], &W.lam_m[3 * (size_t)t], at);
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) W.p[3 * vs[a] + c] = q[3 * a + c];
+    return;
+  }
   T q[12];
   int vs[4];
   int k = gather(M, j, W.p, q, vs);
@@ -541,6 +664,7 @@ void forward(const Model& M, const Params<T>& P, int steps, int iters, const std
   W.lam.assign(M.m(), T(0.0));
   W.lam_c.assign(2 * M.V, T(0.0));
   W.active.assign(2 * M.V, 0);
+  W.lam_m.assign(3 * (size_t)M.nm, T(0.0));
   std::vector<T> x(V3n), v(V3n);
   for (int n = 0; n < steps; ++n) {
     std::copy(xs.begin() + V3n * n, xs.begin() + V3n * (n + 1), x.begin());
@@ -548,6 +672,7 @@ void forward(const Model& M, const Params<T>& P, int steps, int iters, const std
     predict(M, P, n, x, v, W.p);
     std::fill(W.lam.begin(), W.lam.end(), T(0.0));
     std::fill(W.lam_c.begin(), W.lam_c.end(), T(0.0));
+    std::fill(W.lam_m.begin(), W.lam_m.end(), T(0.0));
     detect_contacts(M, P, W);
     for (int k = 0; k < iters; ++k) solve_iteration(M, P, W);
     // the multipliers and contact set the step ended with
@@ -648,7 +773,57 @@ void vjp_pair(const double* q, const double* wv, const Rest& rh, const Rest& rd,
   lbd -= atd * qd;
 }
 
+// Adjoint of project_memb (3x3 generalisation of vjp_pair).  With S, dlambda recomputed:
+//   sbar = lambar' + G W qbar',  q = S^-1 sbar,
+//   Gbar_k = dlambda_k W qbar' - sum_l (q_k dlambda_l + dlambda_k q_l) W g_l,
+//   qbar = qbar' - G^T q + sum_k H_k Gbar_k,  lambar = lambar' - A~ q,
+//   Abar~ += -q (lambda + dlambda)^T, kept on the entries A~ depends on:
+//   abar4 += (a00, a11, a01 + a10, a22).
+void vjp_memb(const double* q, const double* wv, const Rest& r, const double* lam, const double* at,
+              double* qbar, double* lambar, double* abar4) {
+  double g[3][9], C[3];
+  for (int k = 0; k < 3; ++k) {
+    constraint_grad<double>(K_MEMB0 + k, q, r, g[k]);
+    C[k] = constraint_C<double>(K_MEMB0 + k, q, r);
+  }
+  double S[9], rhs[3], dl[3];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      double sv = at[3 * k + l];
+      for (int i = 0; i < 9; ++i) sv += wv[i / 3] * g[k][i] * g[l][i];
+      S[3 * k + l] = sv;
+    }
+  for (int k = 0; k < 3; ++k) rhs[k] = -C[k] - (at[3 * k] * lam[0] + at[3 * k + 1] * lam[1] + at[3 * k + 2] * lam[2]);
+  if (!solve3(S, rhs, dl)) return;
+  double sb[3], qv[3];
+  for (int k = 0; k < 3; ++k) {
+    sb[k] = lambar[k];
+    for (int i = 0; i < 9; ++i) sb[k] += wv[i / 3] * g[k][i] * qbar[i];
+  }
+  solve3(S, sb, qv);   // S symmetric: S^-T = S^-1
+  double out[9];
+  for (int i = 0; i < 9; ++i) out[i] = qbar[i] - (g[0][i] * qv[0] + g[1][i] * qv[1] + g[2][i] * qv[2]);
+  for (int k = 0; k < 3; ++k) {
+    double u[9], hu[9];
+    for (int i = 0; i < 9; ++i) {
+      double t = dl[k] * wv[i / 3] * qbar[i];
+      for (int l = 0; l < 3; ++l) t -= (qv[k] * dl[l] + dl[k] * qv[l]) * wv[i / 3] * g[l][i];
+      u[i] = t;
+    }
+    constraint_hvp(K_MEMB0 + k, q, r, u, hu);
+    for (int i = 0; i < 9; ++i) out[i] += hu[i];
+  }
+  for (int i = 0; i < 9; ++i) qbar[i] = out[i];
+  double mm[3] = {lam[0] + dl[0], lam[1] + dl[1], lam[2] + dl[2]};
+  abar4[0] += -qv[0] * mm[0];
+  abar4[1] += -qv[1] * mm[1];
+  abar4[2] += -(qv[0] * mm[1] + qv[1] * mm[0]);
+  abar4[3] += -qv[2] * mm[2];
+  for (int k = 0; k < 3; ++k) lambar[k] -= at[3 * k] * qv[0] + at[3 * k + 1] * qv[1] + at[3 * k + 2] * qv[2];
+}
+
 struct Grads {
+  std::vector<double> d_memb;   // [nm*4] dL/d(C00, C11, C01, C22)
   std::vector<double> d_alpha, d_x0, d_v0, d_fg, d_fv, d_fvs;
   double d_coll[5] = {0, 0, 0, 0, 0};   // plane h, sphere cx, cy, cz, r
 };
@@ -679,7 +854,9 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
   W.lam.assign(M.m(), 0.0);
   W.lam_c.assign(2 * M.V, 0.0);
   W.active.assign(2 * M.V, 0);
+  W.lam_m.assign(3 * (size_t)M.nm, 0.0);
   std::vector<double> lambar(M.m()), lambar_c(2 * M.V);
+  std::vector<double> lambar_m(3 * (size_t)M.nm), abar_m(4 * (size_t)M.nm, 0.0), lam_before_m((size_t)iters * 3 * M.nm);
   // per-step replay records: positions before every color pass and before the
   // collision pass, multipliers before every iteration
   int passes = M.K + 1;
@@ -701,9 +878,11 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
     predict(M, P, n, x, v, W.p);
     std::fill(W.lam.begin(), W.lam.end(), 0.0);
     std::fill(W.lam_c.begin(), W.lam_c.end(), 0.0);
+    std::fill(W.lam_m.begin(), W.lam_m.end(), 0.0);
     detect_contacts(M, P, W);
     for (int k = 0; k < iters; ++k) {
       std::copy(W.lam.begin(), W.lam.end(), lam_before.begin() + (size_t)k * M.m());
+      std::copy(W.lam_m.begin(), W.lam_m.end(), lam_before_m.begin() + (size_t)k * 3 * M.nm);
       std::copy(W.lam_c.begin(), W.lam_c.end(), lamc_before.begin() + (size_t)k * 2 * M.V);
       for (int c = 0; c < M.K; ++c) {
         std::copy(W.p.begin(), W.p.end(), p_before.begin() + ((size_t)k * passes + c) * V3n);
@@ -720,6 +899,7 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
     // reverse the iterations
     std::fill(lambar.begin(), lambar.end(), 0.0);
     std::fill(lambar_c.begin(), lambar_c.end(), 0.0);
+    std::fill(lambar_m.begin(), lambar_m.end(), 0.0);
     for (int k = iters - 1; k >= 0; --k) {
       if (P.flags) {
         const double* pb = &p_before[((size_t)k * passes + M.K) * V3n];
@@ -757,6 +937,25 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
         int b = M.offsets[c], e = M.offsets[c + 1];
         for (int t = b; t < e; ++t) {
           int j = M.order[t];
+          if (j >= M.m()) {   // membrane triangle
+            const int tm = j - M.m();
+            int vs3[3];
+            M.verts(j, vs3);
+            double q[9], qb[9], wv[3], at[9];
+            for (int a = 0; a < 3; ++a) {
+              wv[a] = M.w[vs3[a]];
+              for (int cc = 0; cc < 3; ++cc) {
+                q[3 * a + cc] = pb[3 * vs3[a] + cc];
+                qb[3 * a + cc] = pbar[3 * vs3[a] + cc];
+              }
+            }
+            memb_alpha_tilde(M, P, tm, at);
+            vjp_memb(q, wv, M.mrest[tm], &lam_before_m[(size_t)k * 3 * M.nm + 3 * (size_t)tm], at, qb,
+                     &lambar_m[3 * (size_t)tm], &abar_m[4 * (size_t)tm]);
+            for (int a = 0; a < 3; ++a)
+              for (int cc = 0; cc < 3; ++cc) pbar[3 * vs3[a] + cc] = qb[3 * a + cc];
+            continue;
+          }
           int kind = M.kind(j);
           int vs4[4];
           M.verts(j, vs4);
@@ -804,6 +1003,24 @@ void adjoint(const Model& M, const Params<double>& P, int steps, int iters,
     if (k == K_TETH || k == K_TETD) scale /= M.rest[j].vol;
     G.d_alpha[j] = abar_t[j] * scale;
   }
+  // membranes: chain rule from the entries of alpha~ to (C00, C11, C01, C22), the
+  // derivative of memb_alpha_tilde taken by forward-mode AD, one parameter at a time
+  G.d_memb.assign(4 * (size_t)M.nm, 0.0);
+  {
+    using D1 = Dual<double>;
+    Params<D1> PD;
+    PD.dt = P.dt;
+    PD.memb_k.resize(P.memb_k.size());
+    for (int t = 0; t < M.nm; ++t)
+      for (int pi = 0; pi < 4; ++pi) {
+        for (int qi = 0; qi < 4; ++qi)
+          PD.memb_k[4 * (size_t)t + qi] = D1(P.memb_k[4 * (size_t)t + qi], qi == pi ? 1.0 : 0.0);
+        D1 at[9];
+        memb_alpha_tilde(M, PD, t, at);
+        const double* ab = &abar_m[4 * (size_t)t];
+        G.d_memb[4 * (size_t)t + pi] = ab[0] * at[0].d + ab[1] * at[4].d + ab[2] * at[1].d + ab[3] * at[8].d;
+      }
+  }
   G.d_x0 = xbar;
   G.d_v0 = vbar;
 }
@@ -828,6 +1045,9 @@ typedef struct {
   const int32_t* color_order;     // [offsets[n_colors]]
   int32_t tet_coupled;            // 1: a tet's C_H and C_D are projected together; the
                                   // coloring then lists its C_H id only
+  int32_t n_memb;                 // membrane triangles (coloring ids m + t)
+  const int32_t* memb_idx;        // [n_memb*3]
+  const double* memb_uv;          // [n_memb*6] warp/weft rest coordinates per triangle vertex
 } om_model;
 
 typedef struct {
@@ -842,6 +1062,7 @@ typedef struct {
   double contact_compliance;
   double thickness;
   const double* f_vertex_steps;  // [steps*V*3] or NULL
+  const double* memb_stiffness;  // [n_memb*4] (C00, C11, C01, C22) or NULL when n_memb = 0
 } om_params;
 
 typedef struct {              // tangent directions (NULL = zero)
@@ -852,6 +1073,7 @@ typedef struct {              // tangent directions (NULL = zero)
   const double* d_f_vertex;   // [V*3]
   const double* d_collider;   // [5] plane h, cx, cy, cz, r
   const double* d_f_vertex_steps;  // [steps*V*3]
+  const double* d_memb_stiffness;  // [n_memb*4]
 } om_direction;
 
 static Model make_model(const om_model* in) {
@@ -872,7 +1094,13 @@ static Model make_model(const om_model* in) {
   M.offsets.assign(in->color_offsets, in->color_offsets + M.K + 1);
   M.order.assign(in->color_order, in->color_order + M.offsets[M.K]);
   M.coupled = in->tet_coupled != 0;
+  M.nm = in->n_memb;
+  if (M.nm) {
+    M.memb_idx.assign(in->memb_idx, in->memb_idx + 3 * (size_t)M.nm);
+    M.memb_uv.assign(in->memb_uv, in->memb_uv + 6 * (size_t)M.nm);
+  }
   build_rest(M);
+  build_memb_rest(M);
   return M;
 }
 
@@ -900,6 +1128,8 @@ static Params<T> make_params(const Model& M, const om_params* in, int steps) {
   for (int c = 0; c < 4; ++c) P.sphere[c] = T(in->sphere[c]);
   P.contact_alpha = in->contact_compliance;
   P.thickness = in->thickness;
+  P.memb_k.assign(4 * (size_t)M.nm, T(0.0));
+  for (size_t i = 0; i < P.memb_k.size(); ++i) P.memb_k[i] = T(in->memb_stiffness[i]);
   return P;
 }
 
@@ -973,12 +1203,13 @@ int oracle_forward_multipliers(const om_model* in, const om_params* pin, int32_t
 
 // Reverse sweep.  Seeds: dL/dx_n for n = seed_steps[s] in seed_dx[s*V*3..], and
 // optionally dL/dv_N.  Outputs (NULL = not wanted): d_compliance [m], d_x0, d_v0 [V*3],
-// d_f_global [steps*3], d_f_vertex [V*3], d_collider [5], d_f_vertex_steps [steps*V*3].
+// d_f_global [steps*3], d_f_vertex [V*3], d_collider [5], d_f_vertex_steps [steps*V*3],
+// d_memb_stiffness [n_memb*4].
 int oracle_adjoint(const om_model* in, const om_params* pin, int32_t steps, int32_t iters,
                    const double* x0, const double* v0, int32_t n_seed, const int32_t* seed_steps,
                    const double* seed_dx, const double* seed_dv_T, double* d_compliance,
                    double* d_x0, double* d_v0, double* d_f_global, double* d_f_vertex,
-                   double* d_collider, double* d_f_vertex_steps) {
+                   double* d_collider, double* d_f_vertex_steps, double* d_memb_stiffness) {
   Model M = make_model(in);
   Params<double> P = make_params<double>(M, pin, steps);
   std::vector<double> x(x0, x0 + 3 * (size_t)M.V), v(v0, v0 + 3 * (size_t)M.V);
@@ -992,6 +1223,7 @@ int oracle_adjoint(const om_model* in, const om_params* pin, int32_t steps, int3
   if (d_f_vertex) std::copy(G.d_fv.begin(), G.d_fv.end(), d_f_vertex);
   if (d_collider) std::copy(G.d_coll, G.d_coll + 5, d_collider);
   if (d_f_vertex_steps) std::copy(G.d_fvs.begin(), G.d_fvs.end(), d_f_vertex_steps);
+  if (d_memb_stiffness) std::copy(G.d_memb.begin(), G.d_memb.end(), d_memb_stiffness);
   return 0;
 }
 
@@ -1021,6 +1253,8 @@ int oracle_tangent(const om_model* in, const om_params* pin, int32_t steps, int3
     P.plane_h.d = dir->d_collider[0];
     for (int c = 0; c < 4; ++c) P.sphere[c].d = dir->d_collider[1 + c];
   }
+  if (dir->d_memb_stiffness)
+    for (size_t i = 0; i < P.memb_k.size(); ++i) P.memb_k[i].d = dir->d_memb_stiffness[i];
   size_t V3n = 3 * (size_t)M.V;
   std::vector<D1> x(V3n), v(V3n), xs, vs;
   for (size_t i = 0; i < V3n; ++i) {
@@ -1095,6 +1329,24 @@ int oracle_vjp_pair(const double* q, const double* wv, const double* rest12, con
   for (int i = 0; i < 9; ++i) r.B[i] = rest12[2 + i];
   r.gamma = rest12[11];
   vjp_pair(q, wv, r, r, lam[0], lam[1], at[0], at[1], qbar, lambar[0], lambar[1], abar[0], abar[1]);
+  return 0;
+}
+
+// One membrane update and its reverse in isolation.  q [9] the triangle's vertices,
+// B2 the 2x2 Dm^-1 (row-major), at [9] the 3x3 alpha~ (row-major), lam [3]; the reverse
+// accumulates lambar [3] and abar4 [4] (alpha~ entries 00, 11, 01 + 10, 22).
+int oracle_project_memb(double* q, const double* wv, const double* B2, double* lam, const double* at) {
+  Rest r;
+  for (int i = 0; i < 4; ++i) r.B[i] = B2[i];
+  project_memb<double>(q, wv, r, lam, at);
+  return 0;
+}
+
+int oracle_vjp_memb(const double* q, const double* wv, const double* B2, const double* lam, const double* at,
+                    double* qbar, double* lambar, double* abar4) {
+  Rest r;
+  for (int i = 0; i < 4; ++i) r.B[i] = B2[i];
+  vjp_memb(q, wv, r, lam, at, qbar, lambar, abar4);
   return 0;
 }
 

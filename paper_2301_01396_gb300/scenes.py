@@ -69,6 +69,11 @@ class Scene:
     f_vertex_steps: Optional[np.ndarray] = None  # [steps,V,3] force on each vertex at each step
     tet_coupled: bool = False           # project each tet's C_H and C_D together (2x2 solve);
                                         # the coloring then lists C_H ids only
+    # orthotropic StVK membrane triangles (coloring ids m + t): vertices, the warp/weft (u, v)
+    # rest coordinates of each triangle's vertices, and (C00, C11, C01, C22) per triangle
+    memb_idx: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.int32))
+    memb_uv: np.ndarray = field(default_factory=lambda: np.zeros((0, 3, 2)))
+    memb_stiffness: np.ndarray = field(default_factory=lambda: np.zeros((0, 4)))
     name: str = "scene"
     meta: dict = field(default_factory=dict)
 
@@ -93,10 +98,14 @@ class Scene:
         return self.n_dist + self.n_bend + 2 * self.n_tet
 
     @property
+    def n_memb(self) -> int:
+        return int(self.memb_idx.shape[0])
+
+    @property
     def n_colored(self) -> int:
-        """Constraint ids the coloring lists: all of them, or all but the C_D ids when
-        each tet's two constraints are projected together."""
-        return self.m - (self.n_tet if self.tet_coupled else 0)
+        """Constraint ids the coloring lists: the scalar ones (all but the C_D ids when each
+        tet's two constraints are projected together), then one id m + t per membrane."""
+        return self.m - (self.n_tet if self.tet_coupled else 0) + self.n_memb
 
     @property
     def n_colors(self) -> int:
@@ -120,6 +129,9 @@ def constraint_vertices(scene: Scene, cid: int) -> tuple:
     cid -= nb
     if cid < 2 * nt:
         return tuple(int(v) for v in scene.tet_idx[cid % nt])
+    cid -= 2 * nt
+    if cid < scene.n_memb:
+        return tuple(int(v) for v in scene.memb_idx[cid])
     raise IndexError("constraint id out of range")
 
 
@@ -130,6 +142,8 @@ def _vertex_table(scene: Scene) -> np.ndarray:
     rows.append(scene.bend_idx.astype(np.int64) if scene.n_bend else np.zeros((0, 4), np.int64))
     rows.append(scene.tet_idx.astype(np.int64) if scene.n_tet else np.zeros((0, 4), np.int64))
     rows.append(scene.tet_idx.astype(np.int64) if scene.n_tet else np.zeros((0, 4), np.int64))
+    rows.append(np.pad(scene.memb_idx.astype(np.int64), ((0, 0), (0, 1)), constant_values=-1) if scene.n_memb
+                else np.zeros((0, 4), np.int64))
     return np.concatenate(rows, axis=0)
 
 
@@ -141,7 +155,9 @@ def validate_coloring(scene: Scene) -> None:
     n = scene.n_colored
     if offs[0] != 0 or offs[-1] != n or np.any(np.diff(offs) < 0):
         raise ValueError("bad color offsets")
-    if order.shape[0] != n or np.any(np.sort(order) != np.arange(n)):
+    ids = np.concatenate([np.arange(scene.m - (scene.n_tet if scene.tet_coupled else 0)),
+                          scene.m + np.arange(scene.n_memb)])
+    if order.shape[0] != n or np.any(np.sort(order) != ids):
         raise ValueError("coloring is not a permutation of the constraints")
     table = _vertex_table(scene)
     for c in range(scene.n_colors):
@@ -325,6 +341,74 @@ def plain_cloth(n: int = 16, *, compliance: float = 1e-7, steps: int = 50, iters
         alpha = alpha * np.exp(0.5 * rng.standard_normal(nd))
     return _cloth_scene(g, alpha, dt=1.0 / 60.0, steps=steps, iters=iters,
                         name=f"plain_cloth_{n}")
+
+
+def membrane_cloth(n: int = 32, size: float = 1.0, *, areal_density: float = 0.2, pins=((0, 0), (-1, 0)),
+                   stiffness=(2000.0, 800.0, 300.0, 400.0), spread: float = 0.3, bend: float = 1e-2,
+                   bending: bool = True, seed: int = 9, steps: int = 30, iters: int = 10,
+                   dt: float = 1.0 / 60.0) -> Scene:
+    """Orthotropic StVK membrane cloth (Sec. "Cloth Material Parameter Estimation"): an
+    n x n vertex sheet in the x-z plane, warp u along x and weft v along z (the rest
+    positions are the pattern coordinates), two triangles per grid cell, each carrying the
+    Green-strain membrane constraint with its own stiffness (C00, C11, C01, C22): the
+    base ``stiffness`` with C00, C11, C22 scaled by exp(spread z) (seeded normal z) and
+    C01 = nu sqrt(C00 C11) with the base's nu, so every K stays positive definite; plus
+    dihedral bending with lognormal compliance around ``bend`` on interior edges.
+    Colors: 8 membrane colors (cell parities x triangle), then the bending colors."""
+    if n < 2:
+        raise ValueError("grid needs n >= 2")
+    h = size / (n - 1)
+    I, J = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    x = np.stack([I.ravel() * h, np.zeros(n * n), J.ravel() * h], axis=1)
+    w = np.full(n * n, n * n / (areal_density * size * size))
+    for (pi, pj) in pins:
+        w[(pj % n) * n + (pi % n)] = 0.0
+    vid = lambda i, j: j * n + i
+    ci, cj = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="xy")
+    ci, cj = ci.ravel(), cj.ravel()
+    tris, order_m, offsets = [], [], [0]
+    t0 = 0
+    for tri in (0, 1):
+        for pi in (0, 1):
+            for pj in (0, 1):
+                sel = ((ci % 2) == pi) & ((cj % 2) == pj)
+                i, j = ci[sel], cj[sel]
+                if tri == 0:
+                    t = np.stack([vid(i, j), vid(i + 1, j), vid(i + 1, j + 1)], axis=1)
+                else:
+                    t = np.stack([vid(i, j), vid(i + 1, j + 1), vid(i, j + 1)], axis=1)
+                tris.append(t)
+                order_m.append(np.arange(t0, t0 + t.shape[0]))
+                t0 += t.shape[0]
+                offsets.append(offsets[-1] + t.shape[0])
+    memb_idx = np.concatenate(tris).astype(np.int32)
+    nm = memb_idx.shape[0]
+    uv = x[:, [0, 2]][memb_idx]                                  # [nm, 3, 2]
+    bend_cls = [c[1] for c in _grid_topology(n, "none", bending) if c[0] == "bend"] if bending else []
+    bend_idx = np.concatenate(bend_cls).astype(np.int32) if bend_cls else np.zeros((0, 4), np.int32)
+    nb = bend_idx.shape[0]
+    order = [o + nb for o in order_m]                            # membrane ids m + t (m = nb)
+    b0 = 0
+    for c in bend_cls:
+        order.append(np.arange(b0, b0 + c.shape[0]))
+        b0 += c.shape[0]
+        offsets.append(offsets[-1] + c.shape[0])
+    rng = np.random.default_rng(seed)
+    c00, c11, c01, c22 = stiffness
+    nu = c01 / np.sqrt(c00 * c11)
+    z = rng.standard_normal((nm, 3))
+    k00 = c00 * np.exp(spread * z[:, 0])
+    k11 = c11 * np.exp(spread * z[:, 1])
+    k22 = c22 * np.exp(spread * z[:, 2])
+    K = np.stack([k00, k11, nu * np.sqrt(k00 * k11), k22], axis=1)
+    alpha_b = bend * np.exp(0.5 * rng.standard_normal(nb))
+    xr = f32(x)
+    return Scene(rest_x=xr, inv_mass=f32(w), dist_idx=np.zeros((0, 2), np.int32), bend_idx=bend_idx,
+                 tet_idx=np.zeros((0, 4), np.int32), tet_gamma=np.zeros(0),
+                 color_offsets=np.asarray(offsets, np.int32),
+                 color_order=np.concatenate(order).astype(np.int32), x0=xr.copy(), v0=np.zeros((n * n, 3)),
+                 compliance=f32(alpha_b), dt=dt, steps=steps, iters=iters,
+                 memb_idx=memb_idx, memb_uv=f32(uv), memb_stiffness=f32(K), name=f"membrane_cloth_{n}")
 
 
 def lognormal_cloth_compliance(rng, nd: int, nb: int, stretch: float = 1e-4,
