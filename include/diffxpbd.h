@@ -104,6 +104,20 @@ typedef struct {
                                    models run one launch per color whatever exec_mode
                                    says; the serving entry points refuse them.  Other
                                    values fail with XPBD_ERR_INVALID.                       */
+  int32_t n_memb;               /* orthotropic StVK membrane triangles (Sec. "Cloth Material
+                                   Parameter Estimation"), coloring ids m + t.  Triangle t:
+                                   C = (E_uu, E_vv, 2 E_uv) of the Green strain
+                                   E = (F^T F - I)/2, F = [x1-x0, x2-x0] Dm^-1, Dm from the
+                                   warp/weft rest coordinates; compliance block (A K)^-1
+                                   with A the rest area and K = [C00 C01 0; C01 C11 0;
+                                   0 0 C22] (xpbd_params.memb_stiffness); its three
+                                   multipliers are solved together.  Models with membranes
+                                   run one launch per color; the serving entry points and
+                                   the implicit adjoint refuse them.                        */
+  const int32_t* memb_idx;      /* [n_memb*3] vertices of each triangle                     */
+  const float* memb_uv;         /* [n_memb*6] (u, v) rest coordinates of each triangle's
+                                   three vertices (u warp, v weft); a triangle whose rest
+                                   area is 0 fails with XPBD_ERR_INVALID                   */
 } xpbd_model;
 
 /* Per-call parameters.  The float fields are HOST values; the pointers are DEVICE. */
@@ -124,6 +138,10 @@ typedef struct {
   const float* f_vertex_steps;  /* DEVICE [steps*V*3] force on vertex i at step n, or NULL:
                                    the keyframe example's control variables (Sec. "Keyframe
                                    Simulation").  Not accepted by the serving API.         */
+  const float* memb_stiffness;  /* DEVICE [n_memb*4] (C00, C11, C01, C22) per membrane
+                                   triangle (NULL when n_memb = 0).  K must be finite and
+                                   positive definite (C22 > 0); otherwise xpbd_sync_status
+                                   reports XPBD_ERR_NONFINITE, as for a bad compliance.    */
 } xpbd_params;
 
 /* Gradient outputs.  DEVICE float64 buffers owned by the caller; each non-NULL buffer is
@@ -136,6 +154,7 @@ typedef struct {
   double* d_f_vertex;           /* [V*3] dL/dW_i                                          */
   double* d_collider;           /* [5] dL/d(plane_h, cx, cy, cz, r)                        */
   double* d_f_vertex_steps;     /* [steps*V*3] dL/dF_{n,i} (force per vertex per step)    */
+  double* d_memb_stiffness;     /* [n_memb*4] dL/d(C00, C11, C01, C22) per membrane         */
 } xpbd_grads;
 
 /* Build a solver.  Validates indices (XPBD_ERR_INVALID), the coloring
@@ -393,6 +412,7 @@ enum {
   XPBD_K_VJP_DIST, XPBD_K_VJP_BEND, XPBD_K_VJP_TETH, XPBD_K_VJP_TETD, XPBD_K_VJP_CONTACT,
   XPBD_K_PREDICT, XPBD_K_VELOCITY, XPBD_K_ADJ_OTHER, XPBD_K_OTHER,
   XPBD_K_FWD_PHASE, XPBD_K_REPLAY_PHASE, XPBD_K_VJP_PHASE,
+  XPBD_K_FWD_MEMB, XPBD_K_REPLAY_MEMB, XPBD_K_VJP_MEMB,
   XPBD_KERNEL_CLASSES
 };
 

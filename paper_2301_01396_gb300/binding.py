@@ -35,20 +35,22 @@ class XpbdModel(C.Structure):
                 ("n_dist", C.c_int32), ("dist_idx", _ip), ("n_bend", C.c_int32), ("bend_idx", _ip),
                 ("n_tet", C.c_int32), ("tet_idx", _ip), ("tet_gamma", _fp),
                 ("n_colors", C.c_int32), ("color_offsets", _ip), ("color_order", _ip),
-                ("exec_mode", C.c_int32), ("tet_coupled", C.c_int32)]
+                ("exec_mode", C.c_int32), ("tet_coupled", C.c_int32),
+                ("n_memb", C.c_int32), ("memb_idx", _ip), ("memb_uv", _fp)]
 
 
 class XpbdParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("gravity", C.c_float * 3), ("compliance", C.c_void_p),
                 ("f_global", C.c_void_p), ("f_vertex", C.c_void_p), ("collider_flags", C.c_int32),
                 ("plane_h", C.c_float), ("sphere", C.c_float * 4),
-                ("contact_compliance", C.c_float), ("thickness", C.c_float), ("f_vertex_steps", C.c_void_p)]
+                ("contact_compliance", C.c_float), ("thickness", C.c_float), ("f_vertex_steps", C.c_void_p),
+                ("memb_stiffness", C.c_void_p)]
 
 
 class XpbdGrads(C.Structure):
     _fields_ = [("d_compliance", C.c_void_p), ("d_x0", C.c_void_p), ("d_v0", C.c_void_p),
                 ("d_f_global", C.c_void_p), ("d_f_vertex", C.c_void_p), ("d_collider", C.c_void_p),
-                ("d_f_vertex_steps", C.c_void_p)]
+                ("d_f_vertex_steps", C.c_void_p), ("d_memb_stiffness", C.c_void_p)]
 
 
 class XpbdImplicitOpts(C.Structure):
@@ -59,7 +61,8 @@ class XpbdImplicitOpts(C.Structure):
 KERNEL_CLASSES = ("fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
                   "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
                   "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
-                  "predict", "velocity", "adjoint_other", "other", "fwd_phase", "replay_phase", "vjp_phase")
+                  "predict", "velocity", "adjoint_other", "other", "fwd_phase", "replay_phase", "vjp_phase",
+                  "fwd_memb", "replay_memb", "vjp_memb")
 
 
 class XpbdKernelStat(C.Structure):
@@ -149,9 +152,10 @@ class Params:
     contact_compliance: float = 1e-8
     thickness: float = 0.0
     f_vertex_steps: Optional[torch.Tensor] = None   # [steps,V,3] float32 cuda: force per vertex per step
+    memb_stiffness: Optional[torch.Tensor] = None   # [n_memb,4] float32 cuda: (C00, C11, C01, C22)
 
     def c_struct(self) -> XpbdParams:
-        for t in (self.compliance, self.f_global, self.f_vertex, self.f_vertex_steps):
+        for t in (self.compliance, self.f_global, self.f_vertex, self.f_vertex_steps, self.memb_stiffness):
             if t is not None and t.dtype != torch.float32:
                 raise ValueError("params tensors must be float32")
         return XpbdParams(dt=self.dt, gravity=(C.c_float * 3)(*self.gravity),
@@ -159,7 +163,7 @@ class Params:
                           f_vertex=_ptr(self.f_vertex), collider_flags=int(self.collider_flags),
                           plane_h=float(self.plane_h), sphere=(C.c_float * 4)(*[float(v) for v in self.sphere]),
                           contact_compliance=float(self.contact_compliance), thickness=float(self.thickness),
-                          f_vertex_steps=_ptr(self.f_vertex_steps))
+                          f_vertex_steps=_ptr(self.f_vertex_steps), memb_stiffness=_ptr(self.memb_stiffness))
 
 
 def sparse_slots(steps: int, stride: int) -> int:
@@ -182,7 +186,8 @@ class Solver:
     then lists the C_H ids only (``scenes.couple_tets``)."""
 
     def __init__(self, rest_x, inv_mass, dist_idx=None, bend_idx=None, tet_idx=None, tet_gamma=None,
-                 color_offsets=None, color_order=None, exec_mode: int = 0, tet_coupled: bool = False):
+                 color_offsets=None, color_order=None, exec_mode: int = 0, tet_coupled: bool = False,
+                 memb_idx=None, memb_uv=None):
         L = lib()
         keep = []
 
@@ -208,18 +213,23 @@ class Solver:
                        tet_gamma=f(tet_gamma) if (tet_gamma is not None and len(tet_gamma)) else None,
                        n_colors=int(len(color_offsets) - 1), color_offsets=i(color_offsets),
                        color_order=i(color_order), exec_mode=int(exec_mode),
-                       tet_coupled=int(bool(tet_coupled)))
+                       tet_coupled=int(bool(tet_coupled)),
+                       n_memb=int(0 if memb_idx is None else np.asarray(memb_idx).shape[0]),
+                       memb_idx=i(memb_idx) if memb_idx is not None and len(memb_idx) else None,
+                       memb_uv=f(memb_uv) if memb_uv is not None and len(memb_uv) else None)
         h = C.c_void_p()
         _check(L.xpbd_create(C.byref(md), C.byref(h)))
         self._h = h
         nv, nc, ncol = C.c_int32(), C.c_int32(), C.c_int32()
         _check(L.xpbd_sizes(h, C.byref(nv), C.byref(nc), C.byref(ncol)))
         self.V, self.m, self.n_colors = nv.value, nc.value, ncol.value
+        self.n_memb = int(md.n_memb)
 
     @classmethod
     def from_scene(cls, sc, exec_mode: int = 0) -> "Solver":
         return cls(sc.rest_x, sc.inv_mass, sc.dist_idx, sc.bend_idx, sc.tet_idx, sc.tet_gamma,
-                   sc.color_offsets, sc.color_order, exec_mode, getattr(sc, "tet_coupled", False))
+                   sc.color_offsets, sc.color_order, exec_mode, getattr(sc, "tet_coupled", False),
+                   getattr(sc, "memb_idx", None), getattr(sc, "memb_uv", None))
 
     def exec_info(self) -> dict:
         """{"phases": bool, "launches_per_iteration": int} of the handle's execution plan."""
@@ -314,13 +324,15 @@ class Solver:
         keys = sorted(seeds)
         sd = torch.stack([seeds[k] for k in keys]).contiguous() if keys else None
         shapes = dict(compliance=(self.m,), x0=(self.V, 3), v0=(self.V, 3), f_global=(max(steps, 1), 3),
-                      f_vertex=(self.V, 3), collider=(5,), f_vertex_steps=(max(steps, 1), self.V, 3))
+                      f_vertex=(self.V, 3), collider=(5,), f_vertex_steps=(max(steps, 1), self.V, 3),
+                      memb_stiffness=(self.n_memb, 4))
         if out is None:
             out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
         g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
                       d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
                       d_f_vertex=_ptr(out.get("f_vertex")), d_collider=_ptr(out.get("collider")),
-                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")))
+                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")),
+                      d_memb_stiffness=_ptr(out.get("memb_stiffness")))
         p = params.c_struct()
         ks = (C.c_int32 * max(len(keys), 1))(*keys)
         if stride is None:
@@ -402,7 +414,8 @@ def params_from_scene(sc, device="cuda", compliance=None) -> Params:
                   gravity=tuple(float(g) for g in sc.gravity), f_global=t(sc.f_global), f_vertex=t(sc.f_vertex),
                   collider_flags=int(sc.collider_flags), plane_h=float(sc.plane_h),
                   sphere=tuple(float(v) for v in sc.sphere), contact_compliance=float(sc.contact_compliance),
-                  thickness=float(sc.thickness), f_vertex_steps=t(getattr(sc, "f_vertex_steps", None)))
+                  thickness=float(sc.thickness), f_vertex_steps=t(getattr(sc, "f_vertex_steps", None)),
+                  memb_stiffness=t(sc.memb_stiffness) if getattr(sc, "n_memb", 0) else None)
 
 
 class XPBDSolve(torch.autograd.Function):

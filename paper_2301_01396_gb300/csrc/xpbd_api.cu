@@ -68,6 +68,9 @@ xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool
     launch(h, XPBD_K_OTHER, cnt[t], s, [&] {
       launch_set_alpha((SegType)t, rec[t], perm + off[t], cnt[t], p->compliance, inv_dt2, h->d_err, s);
     });
+  launch(h, XPBD_K_OTHER, h->nm, s, [&] {
+    launch_memb_set_alpha(h->d_mrec, h->d_mperm, h->nm, p->memb_stiffness, inv_dt2, h->d_err, s);
+  });
   LAUNCH_CHECK();
   return XPBD_OK;
 }
@@ -77,6 +80,14 @@ xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool
 void project_segment(xpbd_solver* h, const Seg& g, float4* P, const float* lam_in, float* lam_out,
                      float4* tape_k, cudaStream_t s) {
   const bool record = tape_k != nullptr;
+  if (g.type == SEG_MEMB) {
+    const size_t mo = (size_t)h->mslot + g.begin;
+    float4* tp = tape_k ? tape_k + h->mtape + 3 * (size_t)g.begin : nullptr;
+    launch(h, record ? XPBD_K_REPLAY_MEMB : XPBD_K_FWD_MEMB, g.count, s, [&] {
+      launch_project_memb(h->d_mrec + g.begin, g.count, P, lam_in ? lam_in + mo : nullptr, lam_out + mo, h->nm, tp, s);
+    });
+    return;
+  }
   const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
   float4* tp = tape_k ? tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type] : nullptr;
   if (h->coupled && g.type == SEG_TETH) {
@@ -98,6 +109,15 @@ void project_segment(xpbd_solver* h, const Seg& g, float4* P, const float* lam_i
 // Reverse of project_segment from iteration k's tape and multipliers before it.
 void vjp_segment(xpbd_solver* h, const Seg& g, const float4* tape_k, const float* lam_pre, float4* xbar,
                  bool first, bool last, cudaStream_t s) {
+  if (g.type == SEG_MEMB) {
+    const size_t mo = (size_t)h->mslot + g.begin;
+    launch(h, XPBD_K_VJP_MEMB, g.count, s, [&] {
+      launch_vjp_memb(h->d_mrec + g.begin, g.count, tape_k + h->mtape + 3 * (size_t)g.begin,
+                      lam_pre ? lam_pre + mo : nullptr, h->nm, xbar, h->lb.as<float2>() + mo,
+                      h->acc.as<double>() + mo, first, last, s);
+    });
+    return;
+  }
   const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
   const float4* tp = tape_k + tape_offset(h, g.type) + (size_t)g.begin * kVerts[g.type];
   if (h->coupled && g.type == SEG_TETH) {
@@ -612,10 +632,12 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   if (!md || !out) return fail(XPBD_ERR_INVALID, "null argument");
   *out = nullptr;
   const int V = md->n_vertices, nd = md->n_dist, nb = md->n_bend, nt = md->n_tet, K = md->n_colors;
-  if (V < 0 || nd < 0 || nb < 0 || nt < 0 || K < 0) return fail(XPBD_ERR_INVALID, "negative size");
+  const int nm = md->n_memb;
+  if (V < 0 || nd < 0 || nb < 0 || nt < 0 || K < 0 || nm < 0) return fail(XPBD_ERR_INVALID, "negative size");
   const long long mll = (long long)nd + nb + 2LL * nt;
-  if (mll > 0x7fffffffLL) return fail(XPBD_ERR_INVALID, "too many constraints");
+  if (mll + 4LL * nm + 8 > 0x7fffffffLL) return fail(XPBD_ERR_INVALID, "too many constraints");
   const int m = (int)mll;
+  if (nm && (!md->memb_idx || !md->memb_uv)) return fail(XPBD_ERR_INVALID, "membrane arrays NULL");
   if (V > 0 && (!md->rest_x || !md->inv_mass)) return fail(XPBD_ERR_INVALID, "rest_x/inv_mass NULL");
   if ((nd && !md->dist_idx) || (nb && !md->bend_idx) || (nt && !md->tet_idx))
     return fail(XPBD_ERR_INVALID, "index array NULL");
@@ -626,6 +648,7 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     if (!(md->inv_mass[i] >= 0.f) || !std::isfinite(md->inv_mass[i]))
       return fail(XPBD_ERR_INVALID, "inverse mass must be finite and >= 0");
   auto verts_of = [&](int j, int* vs) -> int {
+    if (j >= m) { for (int k = 0; k < 3; ++k) vs[k] = md->memb_idx[3 * (size_t)(j - m) + k]; return 3; }
     if (j < nd) { vs[0] = md->dist_idx[2 * (size_t)j]; vs[1] = md->dist_idx[2 * (size_t)j + 1]; return 2; }
     j -= nd;
     if (j < nb) { for (int k = 0; k < 4; ++k) vs[k] = md->bend_idx[4 * (size_t)j + k]; return 4; }
@@ -634,7 +657,7 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     for (int k = 0; k < 4; ++k) vs[k] = md->tet_idx[4 * (size_t)t + k];
     return 4;
   };
-  for (int j = 0; j < m; ++j) {
+  for (int j = 0; j < m + nm; ++j) {
     int vs[4];
     int nv = verts_of(j, vs);
     for (int k = 0; k < nv; ++k) {
@@ -649,17 +672,26 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   if (md->tet_coupled != 0 && md->tet_coupled != 1) return fail(XPBD_ERR_INVALID, "tet_coupled must be 0 or 1");
   const bool coupled = md->tet_coupled == 1 && nt > 0;
   const int mc = coupled ? m - nt : m;
-  if (md->color_offsets[0] != 0 || md->color_offsets[K] != mc)
-    return fail(XPBD_ERR_COLORING, coupled ? "color offsets must start at 0 and end at m - n_tet (coupled tets)"
-                                           : "color offsets must start at 0 and end at m");
-  std::vector<char> seen(mc, 0);
+  // colored ids: [0, mc) and the membranes' [m, m + nm)
+  auto colored = [&](int j) { return (j >= 0 && j < mc) || (j >= m && j < m + nm); };
+  for (int t = 0; t < nm; ++t) {
+    const float* uv = md->memb_uv + 6 * (size_t)t;
+    for (int k = 0; k < 6; ++k)
+      if (!std::isfinite(uv[k])) return fail(XPBD_ERR_INVALID, "non-finite membrane rest coordinate");
+    const double det = ((double)uv[2] - uv[0]) * ((double)uv[5] - uv[1]) - ((double)uv[4] - uv[0]) * ((double)uv[3] - uv[1]);
+    if (!(std::fabs(det) > 1e-30)) return fail(XPBD_ERR_INVALID, "membrane " + std::to_string(t) + " has zero rest area");
+  }
+  if (md->color_offsets[0] != 0 || md->color_offsets[K] != mc + nm)
+    return fail(XPBD_ERR_COLORING, coupled ? "color offsets must start at 0 and end at m - n_tet + n_memb (coupled tets)"
+                                           : "color offsets must start at 0 and end at m + n_memb");
+  std::vector<char> seen(m + nm, 0);
   std::vector<int> stamp(V, -1);
   for (int c = 0; c < K; ++c) {
     int b = md->color_offsets[c], e = md->color_offsets[c + 1];
     if (e < b) return fail(XPBD_ERR_COLORING, "color offsets decrease");
     for (int t = b; t < e; ++t) {
       int j = md->color_order[t];
-      if (j < 0 || j >= mc) return fail(XPBD_ERR_COLORING, "constraint id out of range in coloring");
+      if (!colored(j)) return fail(XPBD_ERR_COLORING, "constraint id out of range in coloring");
       if (seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " appears twice");
       seen[j] = 1;
       int vs[4];
@@ -671,32 +703,36 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
       }
     }
   }
-  for (int j = 0; j < mc; ++j)
-    if (!seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " has no color");
+  for (int j = 0; j < m + nm; ++j)
+    if (colored(j) && !seen[j]) return fail(XPBD_ERR_COLORING, "constraint " + std::to_string(j) + " has no color");
 
   // records, grouped by color, then type, then first vertex
   xpbd_solver* h = new xpbd_solver();
   h->V = V; h->nd = nd; h->nb = nb; h->nt = nt; h->m = m; h->K = K;
   h->coupled = coupled;
-  h->slots = ((size_t)std::max(m, 1) + 3) / 4 * 4;
+  h->nm = nm;
+  h->mslot = (int)(((size_t)std::max(m, 1) + 3) / 4 * 4);
+  h->slots = (size_t)h->mslot + ((size_t)4 * nm + 3) / 4 * 4;
+  h->mtape = (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
   h->tape_slots = h->tape_per_iter();
   h->n_rec[0] = nd; h->n_rec[1] = nb; h->n_rec[2] = nt; h->n_rec[3] = nt;
   h->rec_off[0] = 0; h->rec_off[1] = nd; h->rec_off[2] = nd + nb; h->rec_off[3] = nd + nb + nt;
   std::vector<DistRec> rd; rd.reserve(nd);
   std::vector<BendRec> rb; rb.reserve(nb);
   std::vector<TetRec> rh, rdv; rh.reserve(nt); rdv.reserve(nt);
-  std::vector<int> perm(m);
+  std::vector<MembRec> rmb; rmb.reserve(nm);
+  std::vector<int> perm(m), mperm(nm);
   auto X = [&](int v, double* o) { for (int c = 0; c < 3; ++c) o[c] = md->rest_x[3 * (size_t)v + c]; };
   h->colors.resize(K);
   for (int c = 0; c < K; ++c) {
     int b = md->color_offsets[c], e = md->color_offsets[c + 1];
-    std::vector<int> ids[4];
+    std::vector<int> ids[5];
     for (int t = b; t < e; ++t) {
       int j = md->color_order[t];
-      int type = j < nd ? 0 : (j < nd + nb ? 1 : (j < nd + nb + nt ? 2 : 3));
+      int type = j >= m ? 4 : (j < nd ? 0 : (j < nd + nb ? 1 : (j < nd + nb + nt ? 2 : 3)));
       ids[type].push_back(j);
     }
-    for (int type = 0; type < 4; ++type) {
+    for (int type = 0; type < 5; ++type) {
       if (ids[type].empty()) continue;
       auto by_first_vertex = [&](int a, int bb) {
         int va[4], vb[4];
@@ -709,10 +745,29 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
       Seg sg;
       sg.type = (SegType)type;
       sg.count = (int)ids[type].size();
-      sg.begin = type == 0 ? (int)rd.size() : type == 1 ? (int)rb.size() : type == 2 ? (int)rh.size() : (int)rdv.size();
+      sg.begin = type == 0 ? (int)rd.size() : type == 1 ? (int)rb.size() : type == 2 ? (int)rh.size()
+                 : type == 3 ? (int)rdv.size() : (int)rmb.size();
       for (int j : ids[type]) {
         int vs[4];
         verts_of(j, vs);
+        if (type == 4) {
+          // Dm = [uv1 - uv0, uv2 - uv0] (columns), B = Dm^-1 row-major, A = |det Dm| / 2
+          const float* uv = md->memb_uv + 6 * (size_t)(j - m);
+          const double a = (double)uv[2] - uv[0], bb = (double)uv[4] - uv[0];
+          const double c = (double)uv[3] - uv[1], d = (double)uv[5] - uv[1];
+          const double det = a * d - bb * c;
+          MembRec r;
+          for (int k = 0; k < 3; ++k) r.v[k] = vs[k];
+          r.B[0] = (float)(d / det);
+          r.B[1] = (float)(-bb / det);
+          r.B[2] = (float)(-c / det);
+          r.B[3] = (float)(a / det);
+          r.A = (float)(std::fabs(det) / 2.0);
+          r.a00 = r.a11 = r.a01 = r.a22 = 0.f;
+          mperm[rmb.size()] = j - m;
+          rmb.push_back(r);
+          continue;
+        }
         if (type == 0) {
           double a[3], bb[3];
           X(vs[0], a);
@@ -786,6 +841,8 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   if (e == cudaSuccess) e = up(&h->d_rec[2], rh.data(), rh.size() * sizeof(TetRec));
   if (e == cudaSuccess) e = up(&h->d_rec[3], rdv.data(), rdv.size() * sizeof(TetRec));
   if (e == cudaSuccess) e = up((void**)&h->d_perm, perm.data(), perm.size() * sizeof(int));
+  if (e == cudaSuccess) e = up((void**)&h->d_mrec, rmb.data(), rmb.size() * sizeof(MembRec));
+  if (e == cudaSuccess) e = up((void**)&h->d_mperm, mperm.data(), mperm.size() * sizeof(int));
   if (e == cudaSuccess) e = up((void**)&h->d_w, md->inv_mass, (size_t)V * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
@@ -798,7 +855,7 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     xpbd_destroy(h);
     return fail(XPBD_ERR_INVALID, "exec_mode must be 0, 1 or 2");
   }
-  if (md->exec_mode != 1 && !coupled) {
+  if (md->exec_mode != 1 && !coupled && nm == 0) {
     // Automatic mode: on GB300 the phase plan was faster than per-color launches of the
     // same coloring by 1.7-3.4x where it cut launches per iteration 16x (cloth tiles), and
     // slower (0.5-0.8x) where it cut them 1.8x (row-shaped components serialise many chunks
@@ -820,6 +877,8 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
   for (int t = 0; t < 4; ++t)
     if (h->d_rec[t]) cudaFree(h->d_rec[t]);
   if (h->d_perm) cudaFree(h->d_perm);
+  if (h->d_mrec) cudaFree(h->d_mrec);
+  if (h->d_mperm) cudaFree(h->d_mperm);
   if (h->d_w) cudaFree(h->d_w);
   if (h->d_err) cudaFree(h->d_err);
   for (int t = 0; t < 4; ++t)
@@ -1050,6 +1109,11 @@ xpbd_status adjoint_end(xpbd_solver* h, const xpbd_params* p, const xpbd_grads* 
       });
     }
   }
+  if (out->d_memb_stiffness)
+    launch(h, XPBD_K_ADJ_OTHER, h->nm, s, [&] {
+      launch_memb_gradient(h->d_mrec, h->d_mperm, h->nm, p->memb_stiffness, 1.f / (p->dt * p->dt),
+                           h->acc.as<double>() + h->mslot, h->nm, out->d_memb_stiffness, s);
+    });
   LAUNCH_CHECK();
   return XPBD_OK;
 }
@@ -1165,6 +1229,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   if (out->d_collider)
     return fail(XPBD_ERR_INVALID, "the implicit adjoint forms no collider-parameter gradient (d_collider must be NULL)");
   if (!(o->cg_tol > 0.0) || o->cg_max_iters < 1) return fail(XPBD_ERR_INVALID, "cg_tol must be > 0 and cg_max_iters >= 1");
+  if (h->nm > 0) return fail(XPBD_ERR_INVALID, "the implicit adjoint does not take membranes");
   cudaStream_t s = (cudaStream_t)stream;
   AdjointSweep A;
   st = adjoint_begin(h, p, steps, iters, n_seeds, seed_steps, seed_dx, seed_dv_T, out, s, A);
@@ -1347,7 +1412,7 @@ xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t ste
   g_err.clear();
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
-  if (h->V > XPBD_STATIC_MAX_VERTICES || h->m > XPBD_STATIC_MAX_CONSTRAINTS)
+  if (h->V > XPBD_STATIC_MAX_VERTICES || h->slots > (size_t)XPBD_STATIC_MAX_CONSTRAINTS)
     return fail(XPBD_ERR_BOUNDS, "xpbd_forward_static supports at most " + std::to_string(XPBD_STATIC_MAX_VERTICES) +
                                      " vertices and " + std::to_string(XPBD_STATIC_MAX_CONSTRAINTS) +
                                      " constraints; this model has " + std::to_string(h->V) + " and " +
@@ -1460,7 +1525,9 @@ xpbd_status xpbd_sync_status(xpbd_handle h, void* stream) {
   CU_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
   if (err & 4) return fail(XPBD_ERR_TIMEOUT, "a phase kernel gave up waiting for its staged copies");
   if (err & 8) return fail(XPBD_ERR_INVALID, "a tet material id is out of range");
-  if (err & 2) return fail(XPBD_ERR_NONFINITE, "a compliance value is negative or not finite");
+  if (err & 2)
+    return fail(XPBD_ERR_NONFINITE, "a compliance value is negative or not finite, or a membrane stiffness is not "
+                                    "finite and positive definite");
   if (err & 1) return fail(XPBD_ERR_NONFINITE, "a step produced a non-finite position or velocity");
   return XPBD_OK;
 }

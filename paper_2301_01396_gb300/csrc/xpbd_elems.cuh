@@ -725,6 +725,243 @@ __device__ __forceinline__ void vjp_pair_elem(int i, const TetRec* __restrict__ 
   lb_finish(i + doff, ld.x, ld.y, lb, acc, last);
 }
 
+// ---- orthotropic StVK membrane (Sec. "Cloth Material Parameter Estimation"):
+// C = (E_uu, E_vv, 2 E_uv), E = (F^T F - I)/2, F = [x1-x0, x2-x0] Dm^-1 = [f_u f_v].  With
+// b_u = (-(B00+B10), B00, B10), b_v = (-(B01+B11), B01, B11) the per-vertex weights of f_u
+// and f_v:  grad_i E_uu = b_u,i f_u,  grad_i E_vv = b_v,i f_v,
+// grad_i 2E_uv = b_u,i f_v + b_v,i f_u, and the Hessians are constant:
+// (H_uu y)_i = b_u,i Y_u, (H_vv y)_i = b_v,i Y_v, (H_uv y)_i = b_u,i Y_v + b_v,i Y_u with
+// Y_u = sum_j b_u,j y_j, Y_v = sum_j b_v,j y_j.  The three multipliers come from
+// S dlambda = -C - A~ lambda, S = G W G^T + A~ (3x3 SPD, Cholesky), x += W G^T dlambda.
+struct MembEval {
+  float bu[3], bv[3];
+  f3 fu, fv;
+  float C[3];
+  float Wuu, Wvv, Wuv;   // sum_i w_i b_u,i^2, w_i b_v,i^2, w_i b_u,i b_v,i
+  float L[6];            // Cholesky factor of S: L00, L11, L22 (inverses), L10, L20, L21
+};
+
+// Fills M and factors S; false when S is not positive definite (nothing moves).
+__device__ __forceinline__ bool memb_eval(const MembRec& r, const float4 (&p)[3], MembEval& M) {
+  M.bu[1] = r.B[0];
+  M.bu[2] = r.B[2];
+  M.bu[0] = -(r.B[0] + r.B[2]);
+  M.bv[1] = r.B[1];
+  M.bv[2] = r.B[3];
+  M.bv[0] = -(r.B[1] + r.B[3]);
+  const f3 x0 = xyz(p[0]);
+  const f3 d1 = xyz(p[1]) - x0, d2 = xyz(p[2]) - x0;
+  M.fu = d1 * r.B[0] + d2 * r.B[2];
+  M.fv = d1 * r.B[1] + d2 * r.B[3];
+  const float uu = dot(M.fu, M.fu), vv = dot(M.fv, M.fv), uv = dot(M.fu, M.fv);
+  M.C[0] = 0.5f * (uu - 1.f);
+  M.C[1] = 0.5f * (vv - 1.f);
+  M.C[2] = uv;
+  float Wuu = 0.f, Wvv = 0.f, Wuv = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Wuu += p[k].w * M.bu[k] * M.bu[k];
+    Wvv += p[k].w * M.bv[k] * M.bv[k];
+    Wuv += p[k].w * M.bu[k] * M.bv[k];
+  }
+  M.Wuu = Wuu;
+  M.Wvv = Wvv;
+  M.Wuv = Wuv;
+  const float S00 = Wuu * uu + r.a00, S11 = Wvv * vv + r.a11, S01 = Wuv * uv + r.a01;
+  const float S22 = Wuu * vv + 2.f * Wuv * uv + Wvv * uu + r.a22;
+  const float S02 = Wuu * uv + Wuv * uu, S12 = Wuv * vv + Wvv * uv;
+  if (!(S00 > 0.f)) return false;
+  const float i00 = rsqrtf(S00);
+  const float l10 = S01 * i00, l20 = S02 * i00;
+  const float d11 = S11 - l10 * l10;
+  if (!(d11 > 0.f)) return false;
+  const float i11 = rsqrtf(d11);
+  const float l21 = (S12 - l20 * l10) * i11;
+  const float d22 = S22 - l20 * l20 - l21 * l21;
+  if (!(d22 > 0.f)) return false;
+  M.L[0] = i00;
+  M.L[1] = i11;
+  M.L[2] = rsqrtf(d22);
+  M.L[3] = l10;
+  M.L[4] = l20;
+  M.L[5] = l21;
+  return true;
+}
+
+__device__ __forceinline__ void memb_solve(const MembEval& M, const float (&b)[3], float (&x)[3]) {
+  const float y0 = b[0] * M.L[0];
+  const float y1 = (b[1] - M.L[3] * y0) * M.L[1];
+  const float y2 = (b[2] - M.L[4] * y0 - M.L[5] * y1) * M.L[2];
+  x[2] = y2 * M.L[2];
+  x[1] = (y1 - M.L[5] * x[2]) * M.L[1];
+  x[0] = (y0 - M.L[3] * x[1] - M.L[4] * x[2]) * M.L[0];
+}
+
+__device__ __forceinline__ void memb_dlambda(const MembRec& r, const MembEval& M, const float (&lam)[3],
+                                             float (&dl)[3]) {
+  const float rhs[3] = {-M.C[0] - (r.a00 * lam[0] + r.a01 * lam[1]), -M.C[1] - (r.a01 * lam[0] + r.a11 * lam[1]),
+                        -M.C[2] - r.a22 * lam[2]};
+  memb_solve(M, rhs, dl);
+}
+
+template <bool SH = false>
+__device__ __forceinline__ void proj_memb_core(const MembRec& r, float4* __restrict__ P, float (&lam)[3],
+                                               float4* __restrict__ tape3, int ts = 1) {
+  const uint64_t pol = SH ? 0 : vtx_policy();
+  float4 p[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p[k] = vload<SH>(P + r.v[k], pol);
+  if (tape3) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) __stcs(tape3 + k * ts, p[k]);
+  }
+  MembEval M;
+  if (!memb_eval(r, p, M)) return;
+  float dl[3];
+  memb_dlambda(r, M, lam, dl);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lam[k] += dl[k];
+  const f3 Pu = M.fu * dl[0] + M.fv * dl[2], Pv = M.fv * dl[1] + M.fu * dl[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    vstore<SH>(P + r.v[k], with_w(xyz(p[k]) + (Pu * M.bu[k] + Pv * M.bv[k]) * p[k].w, p[k].w), pol);
+}
+
+// Record i's multipliers sit at slots i, i + stride, i + 2 stride (lam_in / lam_out may
+// alias); its tape entries at tape[3i .. 3i+2].
+__device__ __forceinline__ void proj_memb_elem(int i, const MembRec* __restrict__ rec, float4* __restrict__ P,
+                                               const float* lam_in, float* lam_out, int stride,
+                                               float4* __restrict__ tape) {
+  const MembRec r = ld_rec(rec + i);
+  float lam[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lam[k] = lam_in ? ld_stream(lam_in + i + k * stride) : 0.f;
+  proj_memb_core(r, P, lam, tape ? tape + 3 * i : nullptr);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) __stcs(lam_out + i + k * stride, lam[k]);
+}
+
+// Reverse of one membrane update (the 3x3 form of vjp_pair_core):
+//   sbar = lambar' + G W xbar',  q = S^-1 sbar,
+//   Gbar_k = dlambda_k W xbar' - sum_l (q_k dlambda_l + dlambda_k q_l) W g_l,
+//   xbar = xbar' - G^T q + sum_k H_k Gbar_k,  lambar = lambar' - A~ q,
+//   alphabar~ += -q (lambda + dlambda)^T on the entries (00, 11, 01 + 10, 22).
+// With the constant Hessians, sum_k H_k Gbar_k and G^T q both reduce to
+// b_u,i A_u + b_v,i A_v for two vectors A_u, A_v.
+__device__ __forceinline__ void vjp_memb_core(const MembRec& r, const float4 (&p)[3], const float (&lam)[3],
+                                              float (&lb)[3], float (&ab)[4], float4* __restrict__ xbar) {
+  const uint64_t pol = vtx_policy();
+  float4 xb4[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) xb4[k] = vload<false>(xbar + r.v[k], pol);
+  MembEval M;
+  if (!memb_eval(r, p, M)) return;
+  float dl[3];
+  memb_dlambda(r, M, lam, dl);
+  f3 Xu = {0.f, 0.f, 0.f}, Xv = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const f3 x = xyz(xb4[k]) * p[k].w;
+    Xu = Xu + x * M.bu[k];
+    Xv = Xv + x * M.bv[k];
+  }
+  const float sb[3] = {lb[0] + dot(M.fu, Xu), lb[1] + dot(M.fv, Xv), lb[2] + dot(M.fv, Xu) + dot(M.fu, Xv)};
+  float q[3];
+  memb_solve(M, sb, q);
+  const float c00 = 2.f * q[0] * dl[0], c11 = 2.f * q[1] * dl[1], c22 = 2.f * q[2] * dl[2];
+  const float c01 = q[0] * dl[1] + dl[0] * q[1], c02 = q[0] * dl[2] + dl[0] * q[2], c12 = q[1] * dl[2] + dl[1] * q[2];
+  // sum_j b_u,j w_j g_l,j and sum_j b_v,j w_j g_l,j for l = uu, vv, uv
+  const f3 Gu0 = M.fu * M.Wuu, Gu1 = M.fv * M.Wuv, Gu2 = M.fv * M.Wuu + M.fu * M.Wuv;
+  const f3 Gv0 = M.fu * M.Wuv, Gv1 = M.fv * M.Wvv, Gv2 = M.fv * M.Wuv + M.fu * M.Wvv;
+  const f3 P0 = Xu * dl[0] - (Gu0 * c00 + Gu1 * c01 + Gu2 * c02);
+  const f3 P1 = Xv * dl[1] - (Gv0 * c01 + Gv1 * c11 + Gv2 * c12);
+  const f3 Q0 = Xu * dl[2] - (Gu0 * c02 + Gu1 * c12 + Gu2 * c22);
+  const f3 Q1 = Xv * dl[2] - (Gv0 * c02 + Gv1 * c12 + Gv2 * c22);
+  const f3 Au = P0 + Q1 - (M.fu * q[0] + M.fv * q[2]);
+  const f3 Av = P1 + Q0 - (M.fv * q[1] + M.fu * q[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    vstore<false>(xbar + r.v[k], with_w(xyz(xb4[k]) + Au * M.bu[k] + Av * M.bv[k], 0.f), pol);
+  const float m0 = lam[0] + dl[0], m1 = lam[1] + dl[1], m2 = lam[2] + dl[2];
+  ab[0] -= q[0] * m0;
+  ab[1] -= q[1] * m1;
+  ab[2] -= q[0] * m1 + q[1] * m0;
+  ab[3] -= q[2] * m2;
+  lb[0] -= r.a00 * q[0] + r.a01 * q[1];
+  lb[1] -= r.a01 * q[0] + r.a11 * q[1];
+  lb[2] -= r.a22 * q[2];
+}
+
+// Slots i + k stride (k = 0..3) carry (lambar_k, alphabar partial k) within a step and the
+// float64 alphabar accumulators (00, 11, 01, 22) across steps.
+__device__ __forceinline__ void vjp_memb_elem(int i, const MembRec* __restrict__ rec, const float4* __restrict__ tape,
+                                              const float* __restrict__ lam_pre, int stride, float4* __restrict__ xbar,
+                                              float2* __restrict__ lb, double* __restrict__ acc, bool first,
+                                              bool last) {
+  const MembRec r = ld_rec(rec + i);
+  float4 p[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p[k] = ld_stream(tape + 3 * i + k);
+  float lam[3], lbv[3], ab[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lam[k] = lam_pre ? ld_stream(lam_pre + i + k * stride) : 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 l = first ? make_float2(0.f, 0.f) : lb[i + k * stride];
+    if (k < 3) lbv[k] = l.x;
+    ab[k] = l.y;
+  }
+  vjp_memb_core(r, p, lam, lbv, ab, xbar);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) lb_finish(i + k * stride, k < 3 ? lbv[k] : 0.f, ab[k], lb, acc, last);
+}
+
+// alpha~ entries of record i from the caller's (C00, C11, C01, C22) of its triangle:
+// alpha~ = (A K)^-1 / dt^2.  K not positive definite or not finite sets bit 1 of the error
+// word and leaves the record's alpha~ unchanged.
+__device__ __forceinline__ void memb_set_alpha_elem(int i, MembRec* __restrict__ rec, const int* __restrict__ perm,
+                                                    const float* __restrict__ K, float inv_dt2,
+                                                    int* __restrict__ err) {
+  const int t = perm[i];
+  const float c00 = K[4 * t], c11 = K[4 * t + 1], c01 = K[4 * t + 2], c22 = K[4 * t + 3];
+  const float det = c00 * c11 - c01 * c01;
+  if (!(c00 > 0.f) || !(det > 0.f) || !(c22 > 0.f) || isinf(c00) || isinf(c11) || isinf(c22) || isinf(det)) {
+    atomicOr(err, 2);
+    return;
+  }
+  const float s = inv_dt2 / rec[i].A;
+  const float sd = s / det;
+  rec[i].a00 = c11 * sd;
+  rec[i].a11 = c00 * sd;
+  rec[i].a01 = -c01 * sd;
+  rec[i].a22 = s / c22;
+}
+
+// dL/d(C00, C11, C01, C22) of record i's triangle from the float64 accumulated adjoints
+// g = (g00, g11, g01, g22) of its alpha~ entries: with alpha~_2x2 = s K2^-1,
+// Kbar2 = -s K2^-1 Gbar K2^-1 (Gbar = [g00 g01/2; g01/2 g11]), and d alpha~_22 / d C22 =
+// -s / C22^2.  Written (not accumulated) in the caller's triangle order, in float64.
+__device__ __forceinline__ void memb_gradient_elem(int i, const MembRec* __restrict__ rec, const int* __restrict__ perm,
+                                                   const float* __restrict__ K, double inv_dt2,
+                                                   const double* __restrict__ acc, int stride,
+                                                   double* __restrict__ out) {
+  const int t = perm[i];
+  const double c00 = K[4 * t], c11 = K[4 * t + 1], c01 = K[4 * t + 2], c22 = K[4 * t + 3];
+  const double s = inv_dt2 / (double)rec[i].A;
+  const double det = c00 * c11 - c01 * c01;
+  const double i00 = c11 / det, i11 = c00 / det, i01 = -c01 / det;
+  const double g00 = acc[i], g11 = acc[i + stride], g01 = 0.5 * acc[i + 2 * stride], g22 = acc[i + 3 * stride];
+  // M = Gbar K2^-1, Kbar2 = -s K2^-1 M
+  const double m00 = g00 * i00 + g01 * i01, m01 = g00 * i01 + g01 * i11;
+  const double m10 = g01 * i00 + g11 * i01, m11 = g01 * i01 + g11 * i11;
+  const double k00 = -s * (i00 * m00 + i01 * m10), k11 = -s * (i01 * m01 + i11 * m11);
+  const double k01 = -s * (i00 * m01 + i01 * m11);
+  out[4 * t] = k00;
+  out[4 * t + 1] = k11;
+  out[4 * t + 2] = 2.0 * k01;
+  out[4 * t + 3] = -s * g22 / (c22 * c22);
+}
+
 // Reverse of the collision pass.  Plane (inputs p, h; grad_p = e_y, grad_h = -1, H = 0) and
 // sphere (inputs p, c, r; grad_p = n, grad_c = -n, grad_r = -1, H_pp = P/l, H_pc = -P/l;
 // the centre and radius are not moved, so u_c = 0).  Collider adjoints accumulate in the

@@ -115,6 +115,28 @@ void launch_project_tet_pair(const TetRec* rh, const TetRec* rd, int n, float4* 
   if (n > 0) k_proj_tet_pair<<<grid_for(n), kBlock, 0, s>>>(rh, rd, n, P, lam_in, lam_out, doff, tape);
 }
 
+__global__ void k_memb_set_alpha(MembRec* __restrict__ rec, const int* __restrict__ perm, int n,
+                                 const float* __restrict__ K, float inv_dt2, int* __restrict__ err) {
+  XPBD_TID_OR_RETURN(n);
+  memb_set_alpha_elem(i, rec, perm, K, inv_dt2, err);
+}
+
+void launch_memb_set_alpha(MembRec* rec, const int* perm, int n, const float* stiffness, float inv_dt2, int* err,
+                           cudaStream_t s) {
+  if (n > 0) k_memb_set_alpha<<<grid_for(n), kBlock, 0, s>>>(rec, perm, n, stiffness, inv_dt2, err);
+}
+
+__global__ void k_proj_memb(const MembRec* __restrict__ rec, int n, float4* __restrict__ P, const float* lam_in,
+                            float* lam_out, int stride, float4* __restrict__ tape) {
+  XPBD_TID_OR_RETURN(n);
+  proj_memb_elem(i, rec, P, lam_in, lam_out, stride, tape);
+}
+
+void launch_project_memb(const MembRec* rec, int n, float4* P, const float* lam_in, float* lam_out, int stride,
+                         float4* tape, cudaStream_t s) {
+  if (n > 0) k_proj_memb<<<grid_for(n), kBlock, 0, s>>>(rec, n, P, lam_in, lam_out, stride, tape);
+}
+
 __global__ void k_contact(float4* __restrict__ P, const uint8_t* __restrict__ cflags, int V,
                           const float2* lam_in, float2* lam_out, float4* __restrict__ tape, Collide c) {
   XPBD_TID_OR_RETURN(V);
@@ -215,6 +237,31 @@ void launch_vjp_tet_pair(const TetRec* rh, const TetRec* rd, int n, const float4
                          int doff, float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s) {
   if (n > 0)
     k_vjp_tet_pair<<<grid_for(n), kBlock, 0, s>>>(rh, rd, n, tape, lam_pre, doff, xbar, lb, acc, first, last);
+}
+
+__global__ void __launch_bounds__(kBlock, 2)
+k_vjp_memb(const MembRec* __restrict__ rec, int n, const float4* __restrict__ tape, const float* __restrict__ lam_pre,
+           int stride, float4* __restrict__ xbar, float2* __restrict__ lb, double* __restrict__ acc, bool first,
+           bool last) {
+  XPBD_TID_OR_RETURN(n);
+  vjp_memb_elem(i, rec, tape, lam_pre, stride, xbar, lb, acc, first, last);
+}
+
+void launch_vjp_memb(const MembRec* rec, int n, const float4* tape, const float* lam_pre, int stride, float4* xbar,
+                     float2* lb, double* acc, bool first, bool last, cudaStream_t s) {
+  if (n > 0) k_vjp_memb<<<grid_for(n), kBlock, 0, s>>>(rec, n, tape, lam_pre, stride, xbar, lb, acc, first, last);
+}
+
+__global__ void k_memb_gradient(const MembRec* __restrict__ rec, const int* __restrict__ perm, int n,
+                                const float* __restrict__ K, double inv_dt2, const double* __restrict__ acc,
+                                int stride, double* __restrict__ out) {
+  XPBD_TID_OR_RETURN(n);
+  memb_gradient_elem(i, rec, perm, K, inv_dt2, acc, stride, out);
+}
+
+void launch_memb_gradient(const MembRec* rec, const int* perm, int n, const float* stiffness, float inv_dt2,
+                          const double* acc, int stride, double* out, cudaStream_t s) {
+  if (n > 0) k_memb_gradient<<<grid_for(n), kBlock, 0, s>>>(rec, perm, n, stiffness, (double)inv_dt2, acc, stride, out);
 }
 
 __global__ void k_vjp_contact(const float4* __restrict__ tape, const uint8_t* __restrict__ cflags,

@@ -26,7 +26,9 @@ inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
   if (i >= (n)) return
 
 // Types of constraint records (segments of a color).
-enum SegType { SEG_DIST = 0, SEG_BEND = 1, SEG_TETH = 2, SEG_TETD = 3 };
+// SEG_MEMB segments hold membrane records, which sit outside the four per-type arrays
+// (their own record array, multiplier block and tape range).
+enum SegType { SEG_DIST = 0, SEG_BEND = 1, SEG_TETH = 2, SEG_TETD = 3, SEG_MEMB = 4 };
 constexpr int kVerts[4] = {2, 4, 4, 4};
 
 // ---- forward
@@ -58,6 +60,16 @@ void launch_adj_begin(float4* xbar, float4* vbar, float inv_dt, int V, cudaStrea
 // last: the final one (fold the step's alpha-bar into the float64 accumulator)
 void launch_vjp(SegType t, const void* rec, int n, const float4* tape, const float* lam_pre,
                 float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s);
+// Membranes: `stride` separates the per-component multiplier / adjoint slots of one
+// record (slot k of record i at i + k * stride), the tape holds 3 float4 per record.
+void launch_memb_set_alpha(MembRec* rec, const int* perm, int n, const float* stiffness, float inv_dt2, int* err,
+                           cudaStream_t s);
+void launch_project_memb(const MembRec* rec, int n, float4* P, const float* lam_in, float* lam_out, int stride,
+                         float4* tape, cudaStream_t s);
+void launch_vjp_memb(const MembRec* rec, int n, const float4* tape, const float* lam_pre, int stride, float4* xbar,
+                     float2* lb, double* acc, bool first, bool last, cudaStream_t s);
+void launch_memb_gradient(const MembRec* rec, const int* perm, int n, const float* stiffness, float inv_dt2,
+                          const double* acc, int stride, double* out, cudaStream_t s);
 void launch_vjp_tet_pair(const TetRec* rh, const TetRec* rd, int n, const float4* tape, const float* lam_pre,
                          int doff, float4* xbar, float2* lb, double* acc, bool first, bool last, cudaStream_t s);
 void launch_vjp_contact(const float4* tape, const uint8_t* cflags, int V, const float2* lam_pre,

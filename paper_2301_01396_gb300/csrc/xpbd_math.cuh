@@ -98,6 +98,16 @@ struct __align__(16) TetRec {
   float B[9];     // Dm^-1 row-major
   float at, gamma, vol;
 };
+// Orthotropic StVK membrane triangle: vertices, Dm^-1 (2x2, row-major) of the warp/weft
+// rest coordinates, rest area, and the entries of its 3x3 alpha~ = (A K)^-1 / dt^2 that K
+// reaches (00, 11, 01 = 10, 22; the others are 0).
+struct __align__(16) MembRec {
+  int v[3];
+  float B[4];
+  float A;
+  float a00, a11, a01, a22;
+};
+static_assert(sizeof(MembRec) == 48, "MembRec");
 static_assert(sizeof(DistRec) == 16, "DistRec");
 static_assert(sizeof(BendRec) == 32, "BendRec");
 static_assert(sizeof(TetRec) == 64, "TetRec");

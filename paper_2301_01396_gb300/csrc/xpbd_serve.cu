@@ -728,8 +728,8 @@ xpbd_status xpbd_server_submit(xpbd_server s, const xpbd_request* r, uint64_t* t
     return fail(XPBD_ERR_INVALID, "x0/v0/target NULL");
   if (r->params.f_vertex_steps || r->grads.d_f_vertex_steps)
     return fail(XPBD_ERR_INVALID, "per-step per-vertex forces are not served (use xpbd_forward/xpbd_adjoint)");
-  if (r->handle->coupled)
-    return fail(XPBD_ERR_INVALID, "models with coupled tets are not served (use xpbd_forward/xpbd_adjoint)");
+  if (r->handle->coupled || r->handle->nm > 0)
+    return fail(XPBD_ERR_INVALID, "models with coupled tets or membranes are not served (use xpbd_forward/xpbd_adjoint)");
   std::unique_ptr<Request> q(new Request());
   q->r = *r;
   q->h = r->handle;

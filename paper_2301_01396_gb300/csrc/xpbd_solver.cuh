@@ -69,6 +69,15 @@ struct xpbd_solver {
   // Coupled tets: the colors hold C_H segments only, and the C_D records (type 3) are
   // shadows of the C_H records in the same order, updated with them by one 2x2 solve.
   bool coupled = false;
+  // Membranes (segments of type SEG_MEMB): records in color-segment order, record ->
+  // triangle id, and the slot block they use: record i's slot k at mslot + i + k * nm
+  // (k < 3 multipliers; k < 4 adjoint pairs and float64 accumulators); their tape follows
+  // the four types' in each iteration, 3 float4 per record from mtape.
+  int nm = 0;
+  MembRec* d_mrec = nullptr;
+  int* d_mperm = nullptr;
+  int mslot = 0;
+  size_t mtape = 0;
   std::vector<std::vector<Seg>> colors;
   // type arrays in record order; rec_off[t] = offset of type t in the m-long record space
   int n_rec[4] = {0, 0, 0, 0};
@@ -115,7 +124,7 @@ struct xpbd_solver {
   // one iteration's tape: large enough for the per-color layout and the padded phase layout.
   size_t slots = 0, tape_slots = 0;
   size_t tape_per_iter() const {  // float4 entries per iteration, per-color layout
-    return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
+    return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt + (size_t)3 * nm;
   }
 };
 
@@ -145,6 +154,12 @@ inline double unit_bytes(int cls) {
     case XPBD_K_VJP_DIST: return 132;
     case XPBD_K_VJP_BEND: return 244;
     case XPBD_K_VJP_TETH: case XPBD_K_VJP_TETD: return 276;
+    // membrane: record 48 + three multipliers r/w 24 + three vertices r/w 96 (+ tape 48);
+    // reverse: record 48, tape 48, multipliers 12, vertex adjoints r/w 96, four
+    // (lambar, alphabar) pairs r/w 64
+    case XPBD_K_FWD_MEMB: return 168;
+    case XPBD_K_REPLAY_MEMB: return 216;
+    case XPBD_K_VJP_MEMB: return 268;
     default: return 0;
   }
 }
@@ -209,6 +224,7 @@ inline xpbd_status check_params(const xpbd_solver* h, const xpbd_params* p, int 
   if (steps < 0 || iters < 1) return fail(XPBD_ERR_INVALID, "steps must be >= 0 and iters >= 1");
   if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(XPBD_ERR_INVALID, "dt must be positive");
   if (h->m > 0 && !p->compliance) return fail(XPBD_ERR_INVALID, "compliance is NULL");
+  if (h->nm > 0 && !p->memb_stiffness) return fail(XPBD_ERR_INVALID, "memb_stiffness is NULL");
   if (p->collider_flags & ~3) return fail(XPBD_ERR_INVALID, "unknown collider flag");
   if ((p->collider_flags & XPBD_COLLIDE_SPHERE) && !(p->sphere[3] > 0.f))
     return fail(XPBD_ERR_INVALID, "sphere radius must be positive");

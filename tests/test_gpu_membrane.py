@@ -1,0 +1,118 @@
+"""Orthotropic StVK membranes on the GPU (per-color kernels k_proj_memb / k_vjp_memb and
+the stiffness chain rule) against the FP64 oracle, and the entry points that run or
+refuse them."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_01396_gb300 import binding, scenes
+from tests.gpu_common import contact_margin, contact_signs_agree, gpu_adjoint, gpu_forward, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+GRAD_TOL = 1e-3
+KEYS = ("compliance", "x0", "v0", "f_vertex", "memb_stiffness")
+
+
+def _hanging():
+    # 16x16 sheet, two corners pinned, per-triangle stiffness spread 0.3, random start
+    # velocities; float32-rounding floors (oracle emulation): positions 3.7e-7 m,
+    # gradients <= 1.8e-5
+    sc = scenes.membrane_cloth(16, steps=6, iters=8, seed=5)
+    rng = np.random.default_rng(51)
+    v = 0.3 * rng.standard_normal(sc.x0.shape)
+    v[sc.inv_mass == 0] = 0.0
+    sc.v0 = scenes.f32(v)
+    return sc
+
+
+def _on_sphere():
+    # free sheet falling onto a sphere (contacts from step 1); floors <= 1.2e-5
+    sc = scenes.membrane_cloth(16, steps=6, iters=8, seed=6, pins=())
+    sc.x0 = scenes.f32(sc.x0 + np.array([-0.5, 0.0, -0.5]))
+    sc.collider_flags = scenes.COLLIDE_SPHERE
+    sc.sphere = (0.0, -0.3, 0.0, 0.29)
+    sc.v0 = scenes.f32(np.tile([0.0, -0.5, 0.0], (sc.V, 1)))
+    return sc
+
+
+CASES = {"hanging": _hanging, "on_sphere": _on_sphere}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_membrane_forward_and_adjoint_match_oracle(name):
+    sc = CASES[name]()
+    xs_ref, vs_ref, _, _, act = oracle.forward_multipliers(sc)
+    if sc.collider_flags:
+        assert act.any() and contact_margin(sc, xs_ref, vs_ref) > 1e-5
+    solver, p, ck, xs, vs = gpu_forward(sc)
+    assert solver.n_memb == sc.n_memb
+    if sc.collider_flags:
+        assert contact_signs_agree(sc, xs, vs, xs_ref, vs_ref)
+    err = np.abs(xs - xs_ref).max()
+    assert err < POS_TOL, f"max position error {err:.3e}"
+    rng = np.random.default_rng(7)
+    N = sc.steps
+    seeds = {N: scenes.f32(rng.standard_normal((sc.V, 3))), N // 2: scenes.f32(rng.standard_normal((sc.V, 3)))}
+    ref = oracle.adjoint(sc, seeds)
+    gr = solver.adjoint(p, N, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
+                        want=KEYS + (("collider",) if sc.collider_flags else ()))
+    torch.cuda.synchronize()
+    solver.sync_status()
+    for k in KEYS + (("collider",) if sc.collider_flags else ()):
+        e = rel_err(gr[k].cpu().numpy(), ref[k])
+        assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
+
+
+def test_membrane_deterministic_static_and_sparse():
+    """Two runs agree bit for bit; the allocation-free forward and the sparse-checkpoint
+    reverse sweep give the same bits as the allocating forward and the dense sweep."""
+    sc = _hanging()
+    solver = binding.Solver.from_scene(sc)
+    assert solver.exec_info()["phases"] is False
+    p = binding.params_from_scene(sc)
+    x0, v0 = to_dev(sc.x0), to_dev(sc.v0)
+    ck = solver.forward(p, sc.steps, sc.iters, x0, v0)
+    ck2 = solver.forward(p, sc.steps, sc.iters, x0, v0)
+    cks = solver.forward_static(p, sc.steps, sc.iters, x0, v0, solver.new_checkpoints(sc.steps))
+    torch.cuda.synchronize()
+    assert torch.equal(ck, ck2) and torch.equal(ck, cks)
+    seeds = {sc.steps: to_dev(np.random.default_rng(3).standard_normal((sc.V, 3)))}
+    g1 = solver.adjoint(p, sc.steps, sc.iters, ck, seeds, want=KEYS)
+    g2 = solver.adjoint(p, sc.steps, sc.iters, ck, seeds, want=KEYS)
+    ckp = solver.forward_sparse(p, sc.steps, sc.iters, x0, v0, 4)
+    g3 = solver.adjoint(p, sc.steps, sc.iters, ckp, seeds, want=KEYS, stride=4)
+    torch.cuda.synchronize()
+    solver.sync_status()
+    for k in KEYS:
+        assert torch.equal(g1[k], g2[k]) and torch.equal(g1[k], g3[k]), k
+
+
+def test_membrane_invalid_stiffness_is_reported():
+    sc = scenes.membrane_cloth(4, steps=1, iters=1)
+    K = sc.memb_stiffness.copy()
+    K[2, 2] = 2.0 * np.sqrt(K[2, 0] * K[2, 1])        # C01^2 > C00 C11: not positive definite
+    solver = binding.Solver.from_scene(sc)
+    p = binding.params_from_scene(sc.with_(memb_stiffness=K))
+    solver.forward(p, 1, 1, to_dev(sc.x0), to_dev(sc.v0))
+    with pytest.raises(binding.XpbdError) as e:
+        solver.sync_status()
+    assert e.value.status == 5 and "membrane stiffness" in str(e.value)
+
+
+def test_membrane_models_are_refused_by_serving_and_the_implicit_adjoint():
+    sc = scenes.membrane_cloth(4, steps=2, iters=2)
+    solver = binding.Solver.from_scene(sc)
+    p = binding.params_from_scene(sc)
+    x0, v0 = to_dev(sc.x0), to_dev(sc.v0)
+    srv = binding.Server(max_slots=2)
+    with pytest.raises(binding.XpbdError) as e:
+        srv.submit(solver, p, sc.steps, sc.iters, x0, v0, x0)
+    assert "membranes" in str(e.value)
+    srv.close()
+    ck = solver.forward(p, sc.steps, sc.iters, x0, v0)
+    with pytest.raises(binding.XpbdError) as e:
+        solver.adjoint_implicit(p, sc.steps, sc.iters, ck, {sc.steps: x0})
+    assert "membranes" in str(e.value)

@@ -71,3 +71,18 @@ def test_coupled_tet_coloring_rules():
     order = cs.color_order.copy()
     order[0] = sc.n_tet + order[0]
     assert _status(cs.with_(color_order=order)) == 2
+
+
+def test_membrane_model_rules():
+    """A membrane triangle with zero rest area is rejected; so is a coloring that leaves a
+    membrane out or lists an id past the membranes."""
+    sc = scenes.membrane_cloth(4)
+    uv = sc.memb_uv.copy()
+    uv[3, 2] = uv[3, 0]
+    assert _status(sc.with_(memb_uv=uv)) == 1
+    offs = sc.color_offsets.copy()
+    offs[-1] -= 1
+    assert _status(sc.with_(color_offsets=offs)) == 2
+    order = sc.color_order.copy()
+    order[0] = sc.m + sc.n_memb
+    assert _status(sc.with_(color_order=order)) == 2
