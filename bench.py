@@ -63,6 +63,9 @@ def parse():
                     help="time the paper's implicit adjoint next to the discrete one on the 256^2 ground cloth")
     ap.add_argument("--implicit-grid", type=int, default=256)
     ap.add_argument("--cg-tol", type=float, default=1e-6)
+    ap.add_argument("--material", choices=("tets", "tets-coupled", "membrane"), default=None,
+                    help="material-estimation workloads: the 32^3 tet block (one constraint at a time, or each "
+                         "tet's pair by a 2x2 solve) with 100 materials, or a 256^2 orthotropic StVK membrane cloth")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=160)
@@ -590,6 +593,139 @@ def run_implicit(args, local):
     }
 
 
+# ----------------------------------------------------------------------------- material estimation
+
+def material_scene(kind: str):
+    """The material-estimation workloads.  Tets: the 32^3-cell block of 164k tets (35,937
+    vertices) falling onto the ground, 120 steps x 20 iterations at dt = 1/120, inverse
+    moduli log-uniform in 1e-6..1e-3 (each tet's pair by one 2x2 solve for "tets-coupled").
+    Membrane: a 256^2 sheet (65,536 vertices, 130,050 orthotropic StVK triangles and
+    129,540 dihedral bending hinges, tiled coloring with 32^2 blocks) falling flat onto the
+    ground at y = -0.6, 100 steps x 30 iterations at dt = 1/60 (the cloth
+    material-estimation size)."""
+    if kind == "membrane":
+        sc = scenes.membrane_cloth(256, pins=(), steps=100, iters=30, seed=9, coloring="tiled", tile=32)
+        sc.collider_flags = scenes.COLLIDE_PLANE
+        sc.plane_h = -0.6
+        return sc
+    sc = scenes.tet_block(32, steps=120, iters=20)
+    return scenes.couple_tets(sc) if kind == "tets-coupled" else sc
+
+
+def class_roofline(stats: dict, steps: int):
+    """Dominant kernel class by CUDA-event time, its roofline (algorithmic bytes per launch
+    over the mean launch time) and the per-class byte rates."""
+    timed = {k: v for k, v in stats.items() if v["timed_launches"] > 0 and v["alg_bytes"] > 0}
+    dom = max(timed, key=lambda k: timed[k]["ms"])
+    d = timed[dom]
+    avg_ms = d["ms"] / d["timed_launches"]
+    upl = d["units"] / d["launches"]
+    bpl = d["alg_bytes"] / d["launches"]
+    achieved = bpl / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+                "launch_avg_ms": round(avg_ms, 4), "units_per_launch": round(upl),
+                "bytes_per_unit": round(bpl / upl, 2), "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": round(bpl)}
+    class_bytes = {k: {"bytes_per_unit": round(v["alg_bytes"] / v["units"], 2),
+                       "gbs": round(v["alg_bytes"] * v["timed_launches"] / v["launches"] / (v["ms"] / 1e3) / 1e9, 1)}
+                   for k, v in timed.items() if v["units"] > 0}
+    breakdown = {k: round(v["ms"] / steps, 2) for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])
+                 if v["ms"] > 0}
+    return roofline, class_bytes, breakdown
+
+
+def run_material(args, local):
+    """One bench step = forward with per-step checkpoints, the loss at the last step against
+    a target from perturbed parameters, and the reverse sweep with the material gradients:
+    dL/d(a, b) of 100 materials for the tets (mu = a^2, lambda = b^2), dL/d(C00, C11, C01,
+    C22) per triangle and dL/d(bending compliance) for the membrane.  Constraint updates
+    count scalar constraint rows: a tet pair is 2, a membrane triangle 3."""
+    import torch
+    from paper_2301_01396_gb300 import binding
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = material_scene(args.material)
+    N, I = sc.steps, sc.iters
+    solver = binding.Solver.from_scene(sc)
+    x0 = torch.as_tensor(sc.x0.astype(np.float32), device=dev)
+    v0 = torch.as_tensor(sc.v0.astype(np.float32), device=dev)
+    p = binding.params_from_scene(sc, device=dev)
+    rng = np.random.default_rng(12)
+    want = ("compliance", "x0", "v0")
+    tets = args.material != "membrane"
+    if tets:
+        mat, a, b = scenes.tet_materials(sc.n_tet, 100, seed=6)
+        d_mat = torch.as_tensor(mat, device=dev)
+        d_a, d_b = [torch.as_tensor(np.asarray(t, np.float32), device=dev) for t in (a, b)]
+        comp_true = p.compliance.clone()
+        solver.material_compliance(d_mat, d_a * 1.1, d_b * 0.9, comp_true)
+        p_true = binding.Params(**{**p.__dict__, "compliance": comp_true})
+        solver.material_compliance(d_mat, d_a, d_b, p.compliance)
+    else:
+        want = want + ("memb_stiffness",)
+        K_true = p.memb_stiffness * torch.as_tensor(np.exp(0.2 * rng.standard_normal((sc.n_memb, 1))),
+                                                    dtype=torch.float32, device=dev)
+        p_true = binding.Params(**{**p.__dict__, "memb_stiffness": K_true.contiguous()})
+    ck = solver.forward(p_true, N, I, x0, v0)
+    target = solver.read_state(ck, N)[0].clone()
+    grads = {}
+
+    def step():
+        solver.forward(p, N, I, x0, v0, checkpoints=ck)
+        loss, seeds = solver.loss(ck, {N: target})
+        g = solver.adjoint(p, N, I, ck, {N: seeds[0]}, want=want)
+        if tets:
+            g["a"], g["b"] = solver.material_gradient(d_mat, d_a, d_b, g["compliance"])
+        grads.update(g)
+        grads["loss"] = loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    solver.sync_status()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    solver.profile(True)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stats = solver.profile_read()
+    solver.profile(False)
+    solver.sync_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    rows = sc.m + 3 * sc.n_memb
+    units = 2 * rows * I * N
+    roofline, class_bytes, breakdown = class_roofline(stats, args.steps)
+    if tets:
+        wl = (f"tet_block_32: {sc.V} vertices, {sc.n_tet} tets ({sc.m} constraints"
+              f"{', each pair by one 2x2 solve' if sc.tet_coupled else ''}), {N} steps x {I} iterations, dt=1/120, "
+              f"ground plane, 100 materials, gradients for (a, b), compliance, x0, v0")
+    else:
+        wl = (f"membrane_cloth_256: {sc.V} vertices, {sc.n_memb} StVK membrane triangles (3 rows each) + "
+              f"{sc.n_bend} bending, {N} steps x {I} iterations, dt=1/60, ground plane y=-0.6, gradients for "
+              f"(C00, C11, C01, C22) per triangle, bending compliance, x0, v0")
+    return {
+        "metric": METRIC + " (material estimation)", "impl": "ours", "mode": f"material-{args.material}",
+        "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "vs_baseline": None, "dtype": "f32 (f64 gradient reductions)",
+        "data": "synthetic",
+        "config": {"workload": wl, "V": sc.V, "constraint_rows": rows, "colors": sc.n_colors,
+                   "phase_kernels": solver.exec_info()["phases"]},
+        "roofline": roofline, "clocks": clk,
+        "gpu_launches": int(sum(v["launches"] for v in stats.values())),
+        "breakdown_ms_per_step": breakdown, "class_bytes": class_bytes,
+        "loss": float(grads["loss"].item()),
+    }
+
+
 # ----------------------------------------------------------------------------- serving
 
 def run_serving(args):
@@ -756,6 +892,10 @@ def main():
     if args.implicit:
         if rank == 0:
             print(json.dumps(run_implicit(args, local)))
+        return
+    if args.material:
+        if rank == 0:
+            print(json.dumps(run_material(args, local)))
         return
     res = run_ours(args, ws, rank, local)
     if res is not None and rank == 0:

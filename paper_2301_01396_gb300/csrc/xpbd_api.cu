@@ -68,8 +68,11 @@ xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool
     launch(h, XPBD_K_OTHER, cnt[t], s, [&] {
       launch_set_alpha((SegType)t, rec[t], perm + off[t], cnt[t], p->compliance, inv_dt2, h->d_err, s);
     });
-  launch(h, XPBD_K_OTHER, h->nm, s, [&] {
-    launch_memb_set_alpha(h->d_mrec, h->d_mperm, h->nm, p->memb_stiffness, inv_dt2, h->d_err, s);
+  const int nmr = phase ? h->n_prec[SEG_MEMB] : h->nm;
+  launch(h, XPBD_K_OTHER, nmr, s, [&] {
+    launch_memb_set_alpha(phase ? (MembRec*)h->d_prec[SEG_MEMB] : h->d_mrec,
+                          phase ? h->d_pperm + h->pslot_off[SEG_MEMB] : h->d_mperm, nmr, p->memb_stiffness, inv_dt2,
+                          h->d_err, s);
   });
   LAUNCH_CHECK();
   return XPBD_OK;
@@ -288,26 +291,40 @@ TetRec localize(TetRec r, const std::vector<int>& loc) {
   for (int k = 0; k < 4; ++k) r.v[k] = loc[r.v[k]];
   return r;
 }
+template <>
+MembRec localize(MembRec r, const std::vector<int>& loc) {
+  for (int k = 0; k < 3; ++k) r.v[k] = loc[r.v[k]];
+  return r;
+}
 
 xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, const std::vector<DistRec>& rd,
                          const std::vector<BendRec>& rb, const std::vector<TetRec>& rh,
-                         const std::vector<TetRec>& rdv, const std::vector<int>& perm, int min_cut) {
+                         const std::vector<TetRec>& rdv, const std::vector<int>& perm,
+                         const std::vector<MembRec>& rmb, const std::vector<int>& mperm, int min_cut) {
   const int V = h->V, K = h->K;
   if (K == 0 || V == 0) return XPBD_OK;
-  // constraint id -> (type, index in its type's record array)
-  std::vector<int> type_of(h->m), idx_of(h->m);
+  // constraint id (membranes: m + triangle) -> (type, index in its type's record array)
+  std::vector<int> type_of(h->m + h->nm), idx_of(h->m + h->nm);
   for (int t = 0; t < 4; ++t)
     for (int i = 0; i < h->n_rec[t]; ++i) {
       int j = perm[h->rec_off[t] + i];
       type_of[j] = t;
       idx_of[j] = i;
     }
+  for (int i = 0; i < h->nm; ++i) {
+    type_of[h->m + mperm[i]] = SEG_MEMB;
+    idx_of[h->m + mperm[i]] = i;
+  }
   auto verts_of = [&](int j, int* vs) -> int {
     int t = type_of[j], i = idx_of[j];
     if (t == 0) {
       vs[0] = rd[i].a;
       vs[1] = rd[i].b;
       return 2;
+    }
+    if (t == SEG_MEMB) {
+      for (int k = 0; k < 3; ++k) vs[k] = rmb[i].v[k];
+      return 3;
     }
     const int* v = t == 1 ? rb[i].v : (t == 2 ? rh[i].v : rdv[i].v);
     for (int k = 0; k < 4; ++k) vs[k] = v[k];
@@ -419,14 +436,16 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
   std::vector<DistRec> pd;
   std::vector<BendRec> pb;
   std::vector<TetRec> ph, pdv;
-  std::vector<int> pperm_t[4];
+  std::vector<MembRec> pm;
+  std::vector<int> pperm_t[kSegTypes];
   std::vector<PhaseGroup> groups;
   std::vector<PhaseChunk> chunks;
   std::vector<int> pverts;
   std::vector<int> loc(V, -1), comp_of_root(V, -1), group_of_vertex(V, -1);
-  const double rec_bytes[4] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec)};
+  const double rec_bytes[kSegTypes] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec),
+                                       sizeof(MembRec)};
   auto type_size = [&](int t) -> size_t {
-    return t == 0 ? pd.size() : (t == 1 ? pb.size() : (t == 2 ? ph.size() : pdv.size()));
+    return t == 0 ? pd.size() : (t == 1 ? pb.size() : (t == 2 ? ph.size() : (t == 3 ? pdv.size() : pm.size())));
   };
   // a padding record: every vertex is the group's dummy vertex, alpha~ = 0
   auto push_pad = [&](int t, int dummy) {
@@ -436,6 +455,12 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
     } else if (t == 1) {
       BendRec r{{dummy, dummy, dummy, dummy}, 0.f, 0.f, 0.f, 0.f};
       pb.push_back(r);
+    } else if (t == SEG_MEMB) {   // Dm^-1 = 0: S = 0 is not positive definite, so it never moves
+      MembRec r;
+      std::memset(&r, 0, sizeof(r));
+      for (int k = 0; k < 3; ++k) r.v[k] = dummy;
+      r.A = 1.f;
+      pm.push_back(r);
     } else {
       TetRec r;
       std::memset(&r, 0, sizeof(r));
@@ -492,13 +517,13 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
     }
     ph_info.n_groups = (int)groups.size() - ph_info.first_group;
     // bucket the run's constraints by (group, color, type), keeping color order
-    std::vector<std::vector<int>> bucket((size_t)ph_info.n_groups * ncol * 4);
+    std::vector<std::vector<int>> bucket((size_t)ph_info.n_groups * ncol * kSegTypes);
     for (int c = run.first; c < run.second; ++c)
       for (int t = offsets[c]; t < offsets[c + 1]; ++t) {
         int j = order[t], vs[4];
         verts_of(j, vs);
         int g = group_of_vertex[vs[0]] - ph_info.first_group;
-        bucket[((size_t)g * ncol + (c - run.first)) * 4 + type_of[j]].push_back(j);
+        bucket[((size_t)g * ncol + (c - run.first)) * kSegTypes + type_of[j]].push_back(j);
       }
     double vbytes = 0;
     int64_t units = 0;
@@ -510,8 +535,8 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
       vbytes += 36.0 * G.vert_count;   // vertex index + one float4 read + one write
       for (int ci = 0; ci < ncol; ++ci) {
         const size_t color_first = chunks.size();
-        for (int t = 0; t < 4; ++t) {
-          std::vector<int>& b = bucket[((size_t)g * ncol + ci) * 4 + t];
+        for (int t = 0; t < kSegTypes; ++t) {
+          std::vector<int>& b = bucket[((size_t)g * ncol + ci) * kSegTypes + t];
           if (b.empty()) continue;
           int vs0[4], vs1[4];
           std::stable_sort(b.begin(), b.end(), [&](int x, int y) {
@@ -525,8 +550,9 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
             if (t == 0) pd.push_back(localize(rd[i], loc));
             else if (t == 1) pb.push_back(localize(rb[i], loc));
             else if (t == 2) ph.push_back(localize(rh[i], loc));
-            else pdv.push_back(localize(rdv[i], loc));
-            pperm_t[t].push_back(j);
+            else if (t == 3) pdv.push_back(localize(rdv[i], loc));
+            else pm.push_back(localize(rmb[i], loc));
+            pperm_t[t].push_back(t == SEG_MEMB ? j - h->m : j);
           }
           while (type_size(t) % 4) push_pad(t, G.vert_count);
           const int total = (int)type_size(t) - begin;
@@ -540,10 +566,11 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
           }
           ph_info.type_mask |= 1 << t;
           const double n = (double)b.size(), nv = kVerts[t];
+          const double nl = t == SEG_MEMB ? 3.0 : 1.0, na = t == SEG_MEMB ? 4.0 : 1.0;
           units += (int64_t)b.size();
-          rbytes_f += n * (rec_bytes[t] + 8.0);
-          rbytes_r += n * (rec_bytes[t] + 8.0 + 16.0 * nv);
-          rbytes_v += n * (rec_bytes[t] + 16.0 * nv + 4.0 + 16.0);
+          rbytes_f += n * (rec_bytes[t] + 8.0 * nl);
+          rbytes_r += n * (rec_bytes[t] + 8.0 * nl + 16.0 * nv);
+          rbytes_v += n * (rec_bytes[t] + 16.0 * nv + 4.0 * nl + 16.0 * na);
         }
         if (chunks.size() > color_first) {
           chunks[color_first].flags |= kChunkColorFirst;
@@ -570,11 +597,11 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
   // slot space and tape layout of the phase records
   size_t nslots = 0, ntape = 0;
   std::vector<int> pperm;
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < kSegTypes; ++t) {   // membranes last, 4 slots per record
     h->n_prec[t] = (int)type_size(t);
     h->pslot_off[t] = (int)nslots;
     h->ptape_off[t] = ntape;
-    nslots += (size_t)h->n_prec[t];
+    nslots += (size_t)h->n_prec[t] * (t == SEG_MEMB ? 4 : 1);
     ntape += (size_t)h->n_prec[t] * kVerts[t];
     pperm.insert(pperm.end(), pperm_t[t].begin(), pperm_t[t].end());
   }
@@ -590,6 +617,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
   if (e == cudaSuccess) e = up(&h->d_prec[1], pb.data(), pb.size() * sizeof(BendRec));
   if (e == cudaSuccess) e = up(&h->d_prec[2], ph.data(), ph.size() * sizeof(TetRec));
   if (e == cudaSuccess) e = up(&h->d_prec[3], pdv.data(), pdv.size() * sizeof(TetRec));
+  if (e == cudaSuccess) e = up(&h->d_prec[4], pm.data(), pm.size() * sizeof(MembRec));
   if (e == cudaSuccess) e = up((void**)&h->d_pperm, pperm.data(), pperm.size() * sizeof(int));
   if (e == cudaSuccess) e = up((void**)&h->d_groups, groups.data(), groups.size() * sizeof(PhaseGroup));
   if (e == cudaSuccess) e = up((void**)&h->d_chunks, chunks.data(), chunks.size() * sizeof(PhaseChunk));
@@ -610,11 +638,12 @@ PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph) {
   a.groups = h->d_groups + ph.first_group;
   a.chunks = h->d_chunks;
   a.pverts = h->d_pverts;
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < kSegTypes; ++t) {
     a.slot_off[t] = h->pslot_off[t];
     a.prec[t] = h->d_prec[t];
     a.tape_off[t] = h->ptape_off[t];
   }
+  a.memb_stride = h->n_prec[SEG_MEMB];
   a.err = h->d_err;
   a.wait_cycles = 1ll << 31;   // ~1 s at 2 GHz, far beyond any copy
   a.no_issue = 0;
@@ -855,13 +884,13 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     xpbd_destroy(h);
     return fail(XPBD_ERR_INVALID, "exec_mode must be 0, 1 or 2");
   }
-  if (md->exec_mode != 1 && !coupled && nm == 0) {
+  if (md->exec_mode != 1 && !coupled) {
     // Automatic mode: on GB300 the phase plan was faster than per-color launches of the
     // same coloring by 1.7-3.4x where it cut launches per iteration 16x (cloth tiles), and
     // slower (0.5-0.8x) where it cut them 1.8x (row-shaped components serialise many chunks
     // per CTA), so it is used when it needs at most a quarter of the launches.
     const int min_cut = md->exec_mode == 0 ? 4 : 1;
-    xpbd_status pst = build_phases(h, md->color_offsets, md->color_order, rd, rb, rh, rdv, perm, min_cut);
+    xpbd_status pst = build_phases(h, md->color_offsets, md->color_order, rd, rb, rh, rdv, perm, rmb, mperm, min_cut);
     if (pst != XPBD_OK) {
       xpbd_destroy(h);
       return pst;
@@ -881,7 +910,7 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
   if (h->d_mperm) cudaFree(h->d_mperm);
   if (h->d_w) cudaFree(h->d_w);
   if (h->d_err) cudaFree(h->d_err);
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < kSegTypes; ++t)
     if (h->d_prec[t]) cudaFree(h->d_prec[t]);
   void* plan[] = {h->d_pperm, h->d_groups, h->d_chunks, h->d_pverts};
   for (void* q : plan)
@@ -1109,11 +1138,16 @@ xpbd_status adjoint_end(xpbd_solver* h, const xpbd_params* p, const xpbd_grads* 
       });
     }
   }
-  if (out->d_memb_stiffness)
-    launch(h, XPBD_K_ADJ_OTHER, h->nm, s, [&] {
-      launch_memb_gradient(h->d_mrec, h->d_mperm, h->nm, p->memb_stiffness, 1.f / (p->dt * p->dt),
-                           h->acc.as<double>() + h->mslot, h->nm, out->d_memb_stiffness, s);
+  if (out->d_memb_stiffness) {
+    const bool ph = phase_layout;
+    const int nmr = ph ? h->n_prec[SEG_MEMB] : h->nm;
+    launch(h, XPBD_K_ADJ_OTHER, nmr, s, [&] {
+      launch_memb_gradient(ph ? (const MembRec*)h->d_prec[SEG_MEMB] : h->d_mrec,
+                           ph ? h->d_pperm + h->pslot_off[SEG_MEMB] : h->d_mperm, nmr, p->memb_stiffness,
+                           1.f / (p->dt * p->dt), h->acc.as<double>() + (ph ? h->pslot_off[SEG_MEMB] : h->mslot),
+                           nmr, out->d_memb_stiffness, s);
     });
+  }
   LAUNCH_CHECK();
   return XPBD_OK;
 }

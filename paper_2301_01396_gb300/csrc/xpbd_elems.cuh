@@ -848,12 +848,13 @@ __device__ __forceinline__ void proj_memb_elem(int i, const MembRec* __restrict_
 //   alphabar~ += -q (lambda + dlambda)^T on the entries (00, 11, 01 + 10, 22).
 // With the constant Hessians, sum_k H_k Gbar_k and G^T q both reduce to
 // b_u,i A_u + b_v,i A_v for two vectors A_u, A_v.
+template <bool SH = false>
 __device__ __forceinline__ void vjp_memb_core(const MembRec& r, const float4 (&p)[3], const float (&lam)[3],
                                               float (&lb)[3], float (&ab)[4], float4* __restrict__ xbar) {
-  const uint64_t pol = vtx_policy();
+  const uint64_t pol = SH ? 0 : vtx_policy();
   float4 xb4[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) xb4[k] = vload<false>(xbar + r.v[k], pol);
+  for (int k = 0; k < 3; ++k) xb4[k] = vload<SH>(xbar + r.v[k], pol);
   MembEval M;
   if (!memb_eval(r, p, M)) return;
   float dl[3];
@@ -881,7 +882,7 @@ __device__ __forceinline__ void vjp_memb_core(const MembRec& r, const float4 (&p
   const f3 Av = P1 + Q0 - (M.fv * q[1] + M.fu * q[2]);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    vstore<false>(xbar + r.v[k], with_w(xyz(xb4[k]) + Au * M.bu[k] + Av * M.bv[k], 0.f), pol);
+    vstore<SH>(xbar + r.v[k], with_w(xyz(xb4[k]) + Au * M.bu[k] + Av * M.bv[k], 0.f), pol);
   const float m0 = lam[0] + dl[0], m1 = lam[1] + dl[1], m2 = lam[2] + dl[2];
   ab[0] -= q[0] * m0;
   ab[1] -= q[1] * m1;
@@ -923,6 +924,7 @@ __device__ __forceinline__ void memb_set_alpha_elem(int i, MembRec* __restrict__
                                                     const float* __restrict__ K, float inv_dt2,
                                                     int* __restrict__ err) {
   const int t = perm[i];
+  if (t < 0) return;   // padding record of the phase layout (alpha~ stays 0)
   const float c00 = K[4 * t], c11 = K[4 * t + 1], c01 = K[4 * t + 2], c22 = K[4 * t + 3];
   const float det = c00 * c11 - c01 * c01;
   if (!(c00 > 0.f) || !(det > 0.f) || !(c22 > 0.f) || isinf(c00) || isinf(c11) || isinf(c22) || isinf(det)) {
@@ -946,6 +948,7 @@ __device__ __forceinline__ void memb_gradient_elem(int i, const MembRec* __restr
                                                    const double* __restrict__ acc, int stride,
                                                    double* __restrict__ out) {
   const int t = perm[i];
+  if (t < 0) return;
   const double c00 = K[4 * t], c11 = K[4 * t + 1], c01 = K[4 * t + 2], c22 = K[4 * t + 3];
   const double s = inv_dt2 / (double)rec[i].A;
   const double det = c00 * c11 - c01 * c01;

@@ -29,7 +29,8 @@ inline int grid_for(int n) { return (n + kBlock - 1) / kBlock; }
 // SEG_MEMB segments hold membrane records, which sit outside the four per-type arrays
 // (their own record array, multiplier block and tape range).
 enum SegType { SEG_DIST = 0, SEG_BEND = 1, SEG_TETH = 2, SEG_TETD = 3, SEG_MEMB = 4 };
-constexpr int kVerts[4] = {2, 4, 4, 4};
+constexpr int kVerts[5] = {2, 4, 4, 4, 3};
+constexpr int kSegTypes = 5;
 
 // ---- forward
 void launch_init_ckpt(const float* x0, const float* v0, const float* w, float4* ckx, float4* ckv,
@@ -113,9 +114,10 @@ struct PhaseLaunch {
   const PhaseGroup* groups;
   const PhaseChunk* chunks;
   const int* pverts;
-  int slot_off[4];         // offset of each type in the multiplier slot space (multiples of 4)
-  const void* prec[4];     // phase records (vertex indices local to the group)
-  size_t tape_off[4];      // float4 offset of each type within one iteration's tape
+  int slot_off[5];         // offset of each type in the multiplier slot space (multiples of 4)
+  const void* prec[5];     // phase records (vertex indices local to the group)
+  size_t tape_off[5];      // float4 offset of each type within one iteration's tape
+  int memb_stride;         // membranes: slot k of phase record i at slot_off[4] + i + k * memb_stride
   float4* P;               // positions (forward / replay) or vertex adjoints (reverse)
   const float* lam_in;     // multipliers before the iteration (NULL: zero)
   float* lam_out;

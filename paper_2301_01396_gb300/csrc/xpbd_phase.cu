@@ -90,20 +90,27 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 
 __host__ __device__ constexpr unsigned rec_size(int t) {
-  return t == SEG_DIST ? (unsigned)sizeof(DistRec) : (t == SEG_BEND ? (unsigned)sizeof(BendRec) : (unsigned)sizeof(TetRec));
+  return t == SEG_DIST ? (unsigned)sizeof(DistRec)
+                       : (t == SEG_BEND ? (unsigned)sizeof(BendRec)
+                                        : (t == SEG_MEMB ? (unsigned)sizeof(MembRec) : (unsigned)sizeof(TetRec)));
 }
-__host__ __device__ constexpr unsigned nverts(int t) { return t == SEG_DIST ? 2u : 4u; }
+__host__ __device__ constexpr unsigned nverts(int t) { return t == SEG_DIST ? 2u : (t == SEG_MEMB ? 3u : 4u); }
+// multiplier components (a membrane has three) and adjoint slots (four for a membrane:
+// three multiplier adjoints and four alpha~ adjoints in the float2 pairs' two halves)
+__host__ __device__ constexpr unsigned nlam(int t) { return t == SEG_MEMB ? 3u : 1u; }
+__host__ __device__ constexpr unsigned nadj(int t) { return t == SEG_MEMB ? 4u : 1u; }
 
-// Stage layout of a chunk of n constraints of type t: records (n R), multipliers in (4 n),
-// and for the reverse sweep the tape (16 nv n), (lambar, alphabar) (8 n) and the float64
-// accumulators (8 n).  Every part starts on a 16-byte boundary because n is a multiple of 4.
+// Stage layout of a chunk of n constraints of type t: records (n R), multipliers in
+// (4 n per component, component-major), and for the reverse sweep the tape (16 nv n),
+// (lambar, alphabar) pairs (8 n per slot) and the float64 accumulators (8 n per slot).
+// Every part starts on a 16-byte boundary because n is a multiple of 4.
 struct StageLayout {
   unsigned lam, tape, lb, acc;
   __device__ StageLayout(int t, unsigned n) {
     lam = n * rec_size(t);
-    tape = lam + 4 * n;
+    tape = lam + 4 * nlam(t) * n;
     lb = tape + 16 * nverts(t) * n;
-    acc = lb + 8 * n;
+    acc = lb + 8 * nadj(t) * n;
   }
 };
 
@@ -112,18 +119,22 @@ template <bool REVERSE>
 __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChunk& c, unsigned char* st,
                                             uint64_t* b, bool first, bool last) {
   const int t = c.type;
-  const unsigned n = (unsigned)c.count, R = rec_size(t), nv = nverts(t);
+  const unsigned n = (unsigned)c.count, R = rec_size(t), nv = nverts(t), nl = nlam(t), na = nadj(t);
   const StageLayout L(t, n);
   const size_t so = (size_t)a.slot_off[t] + c.begin;
-  unsigned total = n * R + (a.lam_in ? 4 * n : 0);
-  if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * n) + (last ? 8 * n : 0);
+  const size_t cs = t == SEG_MEMB ? (size_t)a.memb_stride : 0;   // component stride in the slot space
+  unsigned total = n * R + (a.lam_in ? 4 * nl * n : 0);
+  if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * na * n) + (last ? 8 * na * n : 0);
   mbar_expect_tx(b, total);
   bulk_g2s(st, (const char*)a.prec[t] + (size_t)c.begin * R, n * R, b);
-  if (a.lam_in) bulk_g2s(st + L.lam, a.lam_in + so, 4 * n, b);
+  if (a.lam_in)
+    for (unsigned k = 0; k < nl; ++k) bulk_g2s(st + L.lam + 4 * n * k, a.lam_in + so + k * cs, 4 * n, b);
   if (REVERSE) {
     bulk_g2s(st + L.tape, a.tape + a.tape_off[t] + (size_t)c.begin * nv, 16 * nv * n, b);
-    if (!first) bulk_g2s(st + L.lb, a.lb + so, 8 * n, b);
-    if (last) bulk_g2s(st + L.acc, a.acc + so, 8 * n, b);
+    for (unsigned k = 0; k < na; ++k) {
+      if (!first) bulk_g2s(st + L.lb + 8 * n * k, a.lb + so + k * cs, 8 * n, b);
+      if (last) bulk_g2s(st + L.acc + 8 * n * k, a.acc + so + k * cs, 8 * n, b);
+    }
   }
 }
 
@@ -148,6 +159,17 @@ __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk
   float4* tp = RECORD ? a.tape + a.tape_off[t] + (size_t)(c.begin + tid) * nverts(t) : nullptr;
   const int ts = 1;
 #endif
+  if (has<TM>(SEG_MEMB) && t == SEG_MEMB) {
+    const float* sl = reinterpret_cast<const float*>(st + L.lam);
+    const int n = c.count;
+    float lm[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lm[k] = a.lam_in ? sl[k * n + tid] : 0.f;
+    proj_memb_core<true>(reinterpret_cast<const MembRec*>(st)[tid], sv, lm, tp, ts);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) __stcs(a.lam_out + gi + (size_t)k * a.memb_stride, lm[k]);
+    return;
+  }
   float lo = lam;
   if (has<TM>(SEG_DIST) && t == SEG_DIST)
     lo = proj_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], sv, lam, tp, ts);
@@ -177,6 +199,32 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
   const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + (size_t)tid * nverts(t);
   const int ts = 1;
 #endif
+  if (has<TM>(SEG_MEMB) && t == SEG_MEMB) {
+    const int n = c.count;
+    const float* sl = reinterpret_cast<const float*>(st + L.lam);
+    const float2* slb = reinterpret_cast<const float2*>(st + L.lb);
+    const double* sacc = reinterpret_cast<const double*>(st + L.acc);
+    float lm[3], lbv[3], ab[4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lm[k] = a.lam_in ? sl[k * n + tid] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 q = first ? make_float2(0.f, 0.f) : slb[k * n + tid];
+      if (k < 3) lbv[k] = q.x;
+      ab[k] = q.y;
+    }
+    const float4 p[3] = {tp[0], tp[ts], tp[2 * ts]};
+    vjp_memb_core<true>(reinterpret_cast<const MembRec*>(st)[tid], p, lm, lbv, ab, sx);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const size_t g = gi + (size_t)k * a.memb_stride;
+      if (last)
+        a.acc[g] = sacc[k * n + tid] + (double)ab[k];
+      else
+        a.lb[g] = make_float2(k < 3 ? lbv[k] : 0.f, ab[k]);
+    }
+    return;
+  }
   if (has<TM>(SEG_DIST) && t == SEG_DIST) {
     l = vjp_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], tp[0], tp[ts], lam, l, sx);
   } else {
@@ -318,17 +366,19 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
 namespace {
 
 // Type sets with their own kernels: cloth (distance + bending), solids (the two tet
-// constraints, with or without distance constraints) and everything.
-constexpr int kMaskCloth = 0x3, kMaskSolid = 0xD, kMaskAll = 0xF;
+// constraints, with or without distance constraints), membrane cloth (membranes with
+// bending and distance constraints) and everything.
+constexpr int kMaskCloth = 0x3, kMaskSolid = 0xD, kMaskMemb = 0x13, kMaskAll = 0x1F;
 
 int kernel_mask(int type_mask) {
   if ((type_mask & ~kMaskCloth) == 0) return kMaskCloth;
   if ((type_mask & ~kMaskSolid) == 0) return kMaskSolid;
+  if ((type_mask & ~kMaskMemb) == 0) return kMaskMemb;
   return kMaskAll;
 }
 
 unsigned elem_stage_bytes(int t, bool rev) {
-  return rec_size(t) + 4 + (rev ? 16 * nverts(t) + 16 : 0);
+  return rec_size(t) + 4 * nlam(t) + (rev ? 16 * nverts(t) + 16 * nadj(t) : 0);
 }
 
 struct Plan {
@@ -344,7 +394,7 @@ Plan stage_plan(const PhaseShape& sh, bool rev) {
   p.vert_bytes = ((sh.max_verts + 1) * 16 + 127) / 128 * 128;
   p.chunk_bytes = (sh.max_chunks * (int)sizeof(PhaseChunk) + 127) / 128 * 128;
   unsigned e = 0;
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < kSegTypes; ++t)
     if ((sh.type_mask >> t) & 1) e = std::max(e, elem_stage_bytes(t, rev));
   p.slot_bytes = (int)(e * kPhaseChunk);
   if (p.slot_bytes == 0) return p;
@@ -387,6 +437,7 @@ void launch_mode(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cud
   switch (kernel_mask(sh.type_mask)) {
     case kMaskCloth: k_phase<MODE, kMaskCloth><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
     case kMaskSolid: k_phase<MODE, kMaskSolid><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
+    case kMaskMemb: k_phase<MODE, kMaskMemb><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
     default: k_phase<MODE, kMaskAll><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last);
   }
 }
@@ -396,6 +447,7 @@ void launch_mode(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cud
 cudaError_t phase_kernel_setup() {
   cudaError_t e = setup_mask<kMaskCloth>();
   if (e == cudaSuccess) e = setup_mask<kMaskSolid>();
+  if (e == cudaSuccess) e = setup_mask<kMaskMemb>();
   if (e == cudaSuccess) e = setup_mask<kMaskAll>();
   return e;
 }

@@ -112,10 +112,11 @@ struct xpbd_solver {
     double bytes_fwd = 0, bytes_replay = 0, bytes_vjp = 0;   // algorithmic bytes per launch
   };
   std::vector<PhaseHost> phases;
-  void* d_prec[4] = {nullptr, nullptr, nullptr, nullptr};     // phase-ordered records (padded)
-  int n_prec[4] = {0, 0, 0, 0};                               // phase records per type
-  int pslot_off[4] = {0, 0, 0, 0};                            // their offsets in the slot space
-  size_t ptape_off[4] = {0, 0, 0, 0};                         // float4 offsets in an iteration's tape
+  // per type (membranes last: 4 slots per record, component-major)
+  void* d_prec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase-ordered records (padded)
+  int n_prec[5] = {0, 0, 0, 0, 0};                                   // phase records per type
+  int pslot_off[5] = {0, 0, 0, 0, 0};                                // their offsets in the slot space
+  size_t ptape_off[5] = {0, 0, 0, 0, 0};                             // float4 offsets in an iteration's tape
   int* d_pperm = nullptr;                                     // phase record -> constraint id (-1: pad)
   PhaseGroup* d_groups = nullptr;
   PhaseChunk* d_chunks = nullptr;

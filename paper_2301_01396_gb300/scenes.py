@@ -346,7 +346,7 @@ def plain_cloth(n: int = 16, *, compliance: float = 1e-7, steps: int = 50, iters
 def membrane_cloth(n: int = 32, size: float = 1.0, *, areal_density: float = 0.2, pins=((0, 0), (-1, 0)),
                    stiffness=(2000.0, 800.0, 300.0, 400.0), spread: float = 0.3, bend: float = 1e-2,
                    bending: bool = True, seed: int = 9, steps: int = 30, iters: int = 10,
-                   dt: float = 1.0 / 60.0) -> Scene:
+                   dt: float = 1.0 / 60.0, coloring: str = "pattern", tile: int = 32) -> Scene:
     """Orthotropic StVK membrane cloth (Sec. "Cloth Material Parameter Estimation"): an
     n x n vertex sheet in the x-z plane, warp u along x and weft v along z (the rest
     positions are the pattern coordinates), two triangles per grid cell, each carrying the
@@ -354,7 +354,10 @@ def membrane_cloth(n: int = 32, size: float = 1.0, *, areal_density: float = 0.2
     base ``stiffness`` with C00, C11, C22 scaled by exp(spread z) (seeded normal z) and
     C01 = nu sqrt(C00 C11) with the base's nu, so every K stays positive definite; plus
     dihedral bending with lognormal compliance around ``bend`` on interior edges.
-    Colors: 8 membrane colors (cell parities x triangle), then the bending colors."""
+    coloring="pattern": 8 membrane colors (cell parities x triangle), then the bending
+    colors.  coloring="tiled": as cloth_grid's, the pattern colors restricted to 4 classes
+    of tile x tile vertex blocks (by the block of each element's first vertex), class by
+    class, so that a class's colors run block by block (the phase plan)."""
     if n < 2:
         raise ValueError("grid needs n >= 2")
     h = size / (n - 1)
@@ -393,6 +396,25 @@ def membrane_cloth(n: int = 32, size: float = 1.0, *, areal_density: float = 0.2
         order.append(np.arange(b0, b0 + c.shape[0]))
         b0 += c.shape[0]
         offsets.append(offsets[-1] + c.shape[0])
+    if coloring == "tiled":
+        if tile < 4:
+            raise ValueError("tile must be >= 4")
+        # first vertex of each colored id: membranes (ids nb + t) then bending (ids 0..nb-1)
+        fv = np.empty(nb + nm, np.int64)
+        fv[nb:] = memb_idx[:, 0]
+        if nb:
+            fv[:nb] = bend_idx[:, 0]
+        cls_of = lambda ids: ((fv[ids] % n) // tile % 2) + 2 * ((fv[ids] // n) // tile % 2)
+        t_order, t_offs = [], [0]
+        for cls in range(4):
+            for ids in order:
+                sel = ids[cls_of(ids) == cls]
+                if sel.shape[0]:
+                    t_order.append(sel)
+                    t_offs.append(t_offs[-1] + sel.shape[0])
+        order, offsets = t_order, t_offs
+    elif coloring != "pattern":
+        raise ValueError("coloring must be 'pattern' or 'tiled'")
     rng = np.random.default_rng(seed)
     c00, c11, c01, c22 = stiffness
     nu = c01 / np.sqrt(c00 * c11)

@@ -70,8 +70,7 @@ def test_membrane_deterministic_static_and_sparse():
     """Two runs agree bit for bit; the allocation-free forward and the sparse-checkpoint
     reverse sweep give the same bits as the allocating forward and the dense sweep."""
     sc = _hanging()
-    solver = binding.Solver.from_scene(sc)
-    assert solver.exec_info()["phases"] is False
+    solver = binding.Solver.from_scene(sc, exec_mode=1)
     p = binding.params_from_scene(sc)
     x0, v0 = to_dev(sc.x0), to_dev(sc.v0)
     ck = solver.forward(p, sc.steps, sc.iters, x0, v0)
@@ -116,3 +115,46 @@ def test_membrane_models_are_refused_by_serving_and_the_implicit_adjoint():
     with pytest.raises(binding.XpbdError) as e:
         solver.adjoint_implicit(p, sc.steps, sc.iters, ck, {sc.steps: x0})
     assert "membranes" in str(e.value)
+
+
+def _tiled():
+    # 64x64 sheet with the tiled coloring (16x16 blocks): the phase plan runs its colors in
+    # multi-color launches; pinned corners, random start velocities
+    sc = scenes.membrane_cloth(64, steps=5, iters=6, seed=8, coloring="tiled", tile=16)
+    rng = np.random.default_rng(52)
+    v = 0.3 * rng.standard_normal(sc.x0.shape)
+    v[sc.inv_mass == 0] = 0.0
+    sc.v0 = scenes.f32(v)
+    return sc
+
+
+def test_membrane_phase_plan_matches_oracle_and_per_color():
+    """Membranes in the multi-color phase kernels (exec_mode 2) against the oracle, and
+    against one launch per color (exec_mode 1) within rounding (FMA contraction differs
+    between the two kernels, as for the other constraint types)."""
+    sc = _tiled()
+    xs_ref, _ = oracle.forward(sc)
+    rng = np.random.default_rng(9)
+    N = sc.steps
+    seeds = {N: scenes.f32(rng.standard_normal((sc.V, 3))), 2: scenes.f32(rng.standard_normal((sc.V, 3)))}
+    ref = oracle.adjoint(sc, seeds)
+    out = {}
+    for mode in (2, 1):
+        solver = binding.Solver.from_scene(sc, exec_mode=mode)
+        info = solver.exec_info()
+        assert info["phases"] == (mode == 2), info
+        if mode == 2:
+            assert info["launches_per_iteration"] < sc.n_colors
+        _, p, ck, xs, _ = gpu_forward(sc, solver=solver)
+        gr = solver.adjoint(p, N, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()}, want=KEYS)
+        torch.cuda.synchronize()
+        solver.sync_status()
+        err = np.abs(xs - xs_ref).max()
+        assert err < POS_TOL, (mode, err)
+        for k in KEYS:
+            e = rel_err(gr[k].cpu().numpy(), ref[k])
+            assert e < GRAD_TOL, (mode, k, e)
+        out[mode] = (xs, {k: gr[k].cpu().numpy() for k in KEYS})
+    assert np.abs(out[2][0] - out[1][0]).max() <= 1e-6
+    for k in KEYS:
+        assert rel_err(out[2][1][k], out[1][1][k]) <= 2e-4, k
