@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--material", choices=("tets", "tets-coupled", "membrane"), default=None,
                     help="material-estimation workloads: the 32^3 tet block (one constraint at a time, or each "
                          "tet's pair by a 2x2 solve) with 100 materials, or a 256^2 orthotropic StVK membrane cloth")
+    ap.add_argument("--material-tile", type=int, default=8, help="tile side of the membrane cloth's coloring")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=160)
@@ -595,16 +596,16 @@ def run_implicit(args, local):
 
 # ----------------------------------------------------------------------------- material estimation
 
-def material_scene(kind: str):
+def material_scene(kind: str, tile: int = 8):
     """The material-estimation workloads.  Tets: the 32^3-cell block of 164k tets (35,937
     vertices) falling onto the ground, 120 steps x 20 iterations at dt = 1/120, inverse
     moduli log-uniform in 1e-6..1e-3 (each tet's pair by one 2x2 solve for "tets-coupled").
     Membrane: a 256^2 sheet (65,536 vertices, 130,050 orthotropic StVK triangles and
-    129,540 dihedral bending hinges, tiled coloring with 32^2 blocks) falling flat onto the
+    129,540 dihedral bending hinges, tiled coloring with tile^2 blocks) falling flat onto the
     ground at y = -0.6, 100 steps x 30 iterations at dt = 1/60 (the cloth
     material-estimation size)."""
     if kind == "membrane":
-        sc = scenes.membrane_cloth(256, pins=(), steps=100, iters=30, seed=9, coloring="tiled", tile=32)
+        sc = scenes.membrane_cloth(256, pins=(), steps=100, iters=30, seed=9, coloring="tiled", tile=tile)
         sc.collider_flags = scenes.COLLIDE_PLANE
         sc.plane_h = -0.6
         return sc
@@ -646,7 +647,7 @@ def run_material(args, local):
     from paper_2301_01396_gb300 import binding
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = material_scene(args.material)
+    sc = material_scene(args.material, args.material_tile)
     N, I = sc.steps, sc.iters
     solver = binding.Solver.from_scene(sc)
     x0 = torch.as_tensor(sc.x0.astype(np.float32), device=dev)

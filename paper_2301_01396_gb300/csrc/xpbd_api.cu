@@ -492,12 +492,14 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
     ph_info.c0 = run.first;
     ph_info.ncolors = ncol;
     // groups: consecutive components packed up to kPhaseGroupVerts vertices (a larger
-    // component is a group of its own)
+    // component is a group of its own).  A small model packs less, down to one component
+    // per group, so that a phase still has about kPhaseTargetGroups CTAs.
     {
+      const int pack = std::max(1, std::min(kPhaseGroupVerts, (int)(tv.size() / kPhaseTargetGroups)));
       int cur = -1, cur_n = 0;
       for (size_t k = 0; k < comps.size(); ++k) {
         int sz = (int)comps[k].size();
-        if (cur < 0 || cur_n + sz > kPhaseGroupVerts) {
+        if (cur < 0 || cur_n + sz > pack) {
           PhaseGroup g;
           g.vert_begin = (int)pverts.size();
           g.vert_count = 0;
@@ -563,6 +565,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
             ck.count = std::min(kPhaseChunk, total - off);
             ck.flags = 0;
             chunks.push_back(ck);
+            ph_info.max_chunk_size = std::max(ph_info.max_chunk_size, ck.count);
           }
           ph_info.type_mask |= 1 << t;
           const double n = (double)b.size(), nv = kVerts[t];

@@ -93,6 +93,7 @@ constexpr int kPhaseChunk = kPhaseBlock;
 constexpr int kPhaseThreads = kPhaseBlock + 32;  // + one producer warp
 constexpr int kPhaseMaxVerts = 6144;             // largest component a phase may hold
 constexpr int kPhaseGroupVerts = 1536;           // small components are packed up to this
+constexpr int kPhaseTargetGroups = 304;          // CTAs a phase should keep (2 per SM) before packing
 constexpr int kPhaseMaxStages = 8;
 constexpr int kPhaseSmemLimit = 226 * 1024;      // dynamic shared memory per CTA (below the 227 KB opt-in
                                                  // maximum, leaving room for static shared memory)
@@ -137,6 +138,7 @@ struct PhaseLaunch {
 // constraint types present (bit t set when type t occurs; selects the kernel).
 struct PhaseShape {
   int n_groups, max_verts, max_chunks, type_mask;
+  int max_chunk_size;   // the largest chunk's constraint count (a stage holds one such chunk)
 };
 cudaError_t phase_kernel_setup();
 // Shared memory a launch of this phase needs (0 if it cannot fit).

@@ -396,7 +396,10 @@ Plan stage_plan(const PhaseShape& sh, bool rev) {
   unsigned e = 0;
   for (int t = 0; t < kSegTypes; ++t)
     if ((sh.type_mask >> t) & 1) e = std::max(e, elem_stage_bytes(t, rev));
-  p.slot_bytes = (int)(e * kPhaseChunk);
+  // a stage holds the phase's largest chunk: phases of small groups (small models) get
+  // stages of their chunk size and so more of them in flight
+  const int csz = sh.max_chunk_size > 0 ? (sh.max_chunk_size + 3) / 4 * 4 : kPhaseChunk;
+  p.slot_bytes = (int)(e * (unsigned)std::min(csz, kPhaseChunk));
   if (p.slot_bytes == 0) return p;
   const int per_sm = 228 * 1024, ctas = rev ? XPBD_PHASE_VJP_MIN_BLOCKS : XPBD_PHASE_FWD_MIN_BLOCKS;
   const int fixed = p.vert_bytes + p.chunk_bytes;

@@ -107,7 +107,8 @@ struct xpbd_solver {
   struct PhaseHost {
     int first_group = 0, n_groups = 0, c0 = 0, ncolors = 0, max_verts = 0, max_chunks = 0;
     int type_mask = 0;                      // bit t: constraint type t occurs
-    PhaseShape shape() const { return PhaseShape{n_groups, max_verts, max_chunks, type_mask}; }
+    int max_chunk_size = 0;
+    PhaseShape shape() const { return PhaseShape{n_groups, max_verts, max_chunks, type_mask, max_chunk_size}; }
     int64_t units = 0;                      // constraints updated by one launch
     double bytes_fwd = 0, bytes_replay = 0, bytes_vjp = 0;   // algorithmic bytes per launch
   };
