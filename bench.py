@@ -648,6 +648,10 @@ def run_material(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc = material_scene(args.material, args.material_tile)
+    if args.sim_steps:
+        sc.steps = args.sim_steps
+    if args.iters:
+        sc.iters = args.iters
     N, I = sc.steps, sc.iters
     solver = binding.Solver.from_scene(sc)
     x0 = torch.as_tensor(sc.x0.astype(np.float32), device=dev)
@@ -719,7 +723,9 @@ def run_material(args, local):
         "ms_per_step": ms, "higher_is_better": True, "vs_baseline": None, "dtype": "f32 (f64 gradient reductions)",
         "data": "synthetic",
         "config": {"workload": wl, "V": sc.V, "constraint_rows": rows, "colors": sc.n_colors,
-                   "phase_kernels": solver.exec_info()["phases"]},
+                   "phase_kernels": solver.exec_info()["phases"],
+                   **({"profiling_override": f"sim_steps={N} iters={I} (not a bench value)"}
+                      if (args.sim_steps or args.iters) else {})},
         "roofline": roofline, "clocks": clk,
         "gpu_launches": int(sum(v["launches"] for v in stats.values())),
         "breakdown_ms_per_step": breakdown, "class_bytes": class_bytes,
