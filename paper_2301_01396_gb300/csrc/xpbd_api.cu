@@ -1396,11 +1396,13 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
   return adjoint_end(h, p, out, s, h->use_phases);
 }
 
-static const char* kClassNames[XPBD_KERNEL_CLASSES] = {
+static const char* kClassNames[] = {
     "fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
     "replay_dist", "replay_bend", "replay_tet_h", "replay_tet_d", "replay_contact",
     "vjp_dist", "vjp_bend", "vjp_tet_h", "vjp_tet_d", "vjp_contact",
-    "predict", "velocity", "adjoint_other", "other", "fwd_phase", "replay_phase", "vjp_phase"};
+    "predict", "velocity", "adjoint_other", "other", "fwd_phase", "replay_phase", "vjp_phase",
+    "fwd_memb", "replay_memb", "vjp_memb"};
+static_assert(sizeof(kClassNames) / sizeof(kClassNames[0]) == XPBD_KERNEL_CLASSES, "one name per kernel class");
 
 const char* xpbd_kernel_class_name(int32_t cls) {
   return (cls >= 0 && cls < XPBD_KERNEL_CLASSES) ? kClassNames[cls] : "";

@@ -45,3 +45,13 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "xpbd_oracle" not in txt, f
+
+
+def test_kernel_class_names_match_the_binding():
+    """xpbd_kernel_class_name names every class the binding's profile table lists, in order."""
+    from paper_2301_01396_gb300 import binding, build
+    lib = ctypes.CDLL(build.build())
+    lib.xpbd_kernel_class_name.restype = ctypes.c_char_p
+    names = [lib.xpbd_kernel_class_name(i).decode() for i in range(len(binding.KERNEL_CLASSES))]
+    assert tuple(names) == binding.KERNEL_CLASSES
+    assert lib.xpbd_kernel_class_name(len(binding.KERNEL_CLASSES)) == b""
