@@ -67,6 +67,7 @@ def parse():
                     help="material-estimation workloads: the 32^3 tet block (one constraint at a time, or each "
                          "tet's pair by a 2x2 solve) with 100 materials, or a 256^2 orthotropic StVK membrane cloth")
     ap.add_argument("--material-tile", type=int, default=8, help="tile side of the membrane cloth's coloring")
+    ap.add_argument("--material-grid", type=int, default=256, help="side of the membrane cloth")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=160)
@@ -596,7 +597,7 @@ def run_implicit(args, local):
 
 # ----------------------------------------------------------------------------- material estimation
 
-def material_scene(kind: str, tile: int = 8):
+def material_scene(kind: str, tile: int = 8, grid: int = 256, steps: int = 100):
     """The material-estimation workloads.  Tets: the 32^3-cell block of 164k tets (35,937
     vertices) falling onto the ground, 120 steps x 20 iterations at dt = 1/120, inverse
     moduli log-uniform in 1e-6..1e-3 (each tet's pair by one 2x2 solve for "tets-coupled").
@@ -605,7 +606,7 @@ def material_scene(kind: str, tile: int = 8):
     ground at y = -0.6, 100 steps x 30 iterations at dt = 1/60 (the cloth
     material-estimation size)."""
     if kind == "membrane":
-        sc = scenes.membrane_cloth(256, pins=(), steps=100, iters=30, seed=9, coloring="tiled", tile=tile)
+        sc = scenes.membrane_cloth(grid, pins=(), steps=steps, iters=30, seed=9, coloring="tiled", tile=tile)
         sc.collider_flags = scenes.COLLIDE_PLANE
         sc.plane_h = -0.6
         return sc
@@ -647,7 +648,7 @@ def run_material(args, local):
     from paper_2301_01396_gb300 import binding
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = material_scene(args.material, args.material_tile)
+    sc = material_scene(args.material, args.material_tile, args.material_grid)
     if args.sim_steps:
         sc.steps = args.sim_steps
     if args.iters:
@@ -714,7 +715,7 @@ def run_material(args, local):
               f"{', each pair by one 2x2 solve' if sc.tet_coupled else ''}), {N} steps x {I} iterations, dt=1/120, "
               f"ground plane, 100 materials, gradients for (a, b), compliance, x0, v0")
     else:
-        wl = (f"membrane_cloth_256: {sc.V} vertices, {sc.n_memb} StVK membrane triangles (3 rows each) + "
+        wl = (f"membrane_cloth_{int(round(sc.V ** 0.5))}: {sc.V} vertices, {sc.n_memb} StVK membrane triangles (3 rows each) + "
               f"{sc.n_bend} bending, {N} steps x {I} iterations, dt=1/60, ground plane y=-0.6, gradients for "
               f"(C00, C11, C01, C22) per triangle, bending compliance, x0, v0")
     return {
