@@ -555,25 +555,34 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
             else if (t == 3) pdv.push_back(localize(rdv[i], loc));
             else pm.push_back(localize(rmb[i], loc));
             pperm_t[t].push_back(t == SEG_MEMB ? j - h->m : j);
+            if (h->coupled && t == SEG_TETH) {   // the C_D shadow at the same phase index
+              pdv.push_back(localize(rdv[i], loc));
+              pperm_t[SEG_TETD].push_back(j + h->nt);
+            }
           }
-          while (type_size(t) % 4) push_pad(t, G.vert_count);
+          while (type_size(t) % 4) {
+            push_pad(t, G.vert_count);
+            if (h->coupled && t == SEG_TETH) push_pad(SEG_TETD, G.vert_count);
+          }
+          const bool pair = h->coupled && t == SEG_TETH;
           const int total = (int)type_size(t) - begin;
           for (int off = 0; off < total; off += kPhaseChunk) {
             PhaseChunk ck;
-            ck.type = t;
+            ck.type = pair ? kChunkPair : t;
             ck.begin = begin + off;
             ck.count = std::min(kPhaseChunk, total - off);
             ck.flags = 0;
             chunks.push_back(ck);
             ph_info.max_chunk_size = std::max(ph_info.max_chunk_size, ck.count);
           }
-          ph_info.type_mask |= 1 << t;
+          ph_info.type_mask |= 1 << (pair ? kChunkPair : t);
           const double n = (double)b.size(), nv = kVerts[t];
-          const double nl = t == SEG_MEMB ? 3.0 : 1.0, na = t == SEG_MEMB ? 4.0 : 1.0;
-          units += (int64_t)b.size();
-          rbytes_f += n * (rec_bytes[t] + 8.0 * nl);
-          rbytes_r += n * (rec_bytes[t] + 8.0 * nl + 16.0 * nv);
-          rbytes_v += n * (rec_bytes[t] + 16.0 * nv + 4.0 * nl + 16.0 * na);
+          const double nl = t == SEG_MEMB ? 3.0 : (pair ? 2.0 : 1.0), na = t == SEG_MEMB ? 4.0 : (pair ? 2.0 : 1.0);
+          const double rb_ = pair ? 2.0 * rec_bytes[t] : rec_bytes[t];
+          units += (int64_t)b.size() * (pair ? 2 : 1);
+          rbytes_f += n * (rb_ + 8.0 * nl);
+          rbytes_r += n * (rb_ + 8.0 * nl + 16.0 * nv);
+          rbytes_v += n * (rb_ + 16.0 * nv + 4.0 * nl + 16.0 * na);
         }
         if (chunks.size() > color_first) {
           chunks[color_first].flags |= kChunkColorFirst;
@@ -887,7 +896,7 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
     xpbd_destroy(h);
     return fail(XPBD_ERR_INVALID, "exec_mode must be 0, 1 or 2");
   }
-  if (md->exec_mode != 1 && !coupled) {
+  if (md->exec_mode != 1) {
     // Automatic mode: on GB300 the phase plan was faster than per-color launches of the
     // same coloring by 1.7-3.4x where it cut launches per iteration 16x (cloth tiles), and
     // slower (0.5-0.8x) where it cut them 1.8x (row-shaped components serialise many chunks

@@ -641,12 +641,13 @@ __device__ __forceinline__ void proj_pair_elem(int i, const TetRec* __restrict__
 //   lambar_k = lambar'_k - alpha~_k q_k,  alphabar~_k += -q_k (lambda_k + dlambda_k).
 // With one constraint this is vjp_quad_core's update (q = s/D).  lh, ld: (lambar, alphabar)
 // of C_H and C_D.
+template <bool SH = false>
 __device__ __forceinline__ void vjp_pair_core(const TetRec& r, float atd, const float4 (&p)[4], float2 lam,
                                               float2& lh, float2& ld, float4* __restrict__ xbar) {
-  const uint64_t pol = vtx_policy();
+  const uint64_t pol = SH ? 0 : vtx_policy();
   float4 xb4[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) xb4[k] = vload<false>(xbar + r.v[k], pol);
+  for (int k = 0; k < 4; ++k) xb4[k] = vload<SH>(xbar + r.v[k], pol);
   TetPair T;
   tet_pair_eval(r, atd, p, T);
   float dlh, dld;
@@ -703,7 +704,7 @@ __device__ __forceinline__ void vjp_pair_core(const TetRec& r, float atd, const 
     ld.x -= atd * qd;
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) vstore<false>(xbar + r.v[k], with_w(out[k], 0.f), pol);
+  for (int k = 0; k < 4; ++k) vstore<SH>(xbar + r.v[k], with_w(out[k], 0.f), pol);
   lh.y += -qh * (lam.x + dlh);
   lh.x -= r.at * qh;
 }

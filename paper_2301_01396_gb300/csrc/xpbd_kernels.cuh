@@ -105,12 +105,15 @@ struct PhaseGroup {   // one CTA: a set of components of one phase
   int chunk_count;
 };
 struct PhaseChunk {   // up to kPhaseChunk constraints of one type and one color of a group
-  int type;
+  int type;           // SegType, or kChunkPair
   int begin;          // first record in the phase record array of its type (multiple of 4)
   int count;          // multiple of 4
   int flags;          // kChunkColorFirst / kChunkColorLast: first / last chunk of its color
 };
 constexpr int kChunkColorFirst = 1, kChunkColorLast = 2;
+// Chunk type of coupled tets: C_H records with their C_D shadows (same phase index in the
+// type-3 array, multipliers in the type-3 slots), updated by one 2x2 solve each.
+constexpr int kChunkPair = 5;
 struct PhaseLaunch {
   const PhaseGroup* groups;
   const PhaseChunk* chunks;

@@ -89,16 +89,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Record bytes staged per constraint (a coupled pair stages its C_H and its C_D record).
 __host__ __device__ constexpr unsigned rec_size(int t) {
   return t == SEG_DIST ? (unsigned)sizeof(DistRec)
                        : (t == SEG_BEND ? (unsigned)sizeof(BendRec)
-                                        : (t == SEG_MEMB ? (unsigned)sizeof(MembRec) : (unsigned)sizeof(TetRec)));
+                                        : (t == SEG_MEMB ? (unsigned)sizeof(MembRec)
+                                                         : (t == kChunkPair ? 2u : 1u) * (unsigned)sizeof(TetRec)));
 }
 __host__ __device__ constexpr unsigned nverts(int t) { return t == SEG_DIST ? 2u : (t == SEG_MEMB ? 3u : 4u); }
-// multiplier components (a membrane has three) and adjoint slots (four for a membrane:
-// three multiplier adjoints and four alpha~ adjoints in the float2 pairs' two halves)
-__host__ __device__ constexpr unsigned nlam(int t) { return t == SEG_MEMB ? 3u : 1u; }
-__host__ __device__ constexpr unsigned nadj(int t) { return t == SEG_MEMB ? 4u : 1u; }
+// multiplier components (a membrane has three, a pair two) and adjoint slots (four for a
+// membrane: three multiplier adjoints and four alpha~ adjoints in the float2 pairs' halves)
+__host__ __device__ constexpr unsigned nlam(int t) { return t == SEG_MEMB ? 3u : (t == kChunkPair ? 2u : 1u); }
+__host__ __device__ constexpr unsigned nadj(int t) { return t == SEG_MEMB ? 4u : (t == kChunkPair ? 2u : 1u); }
+// The record array, slot block and tape range a chunk type uses (pairs: the C_H ones).
+__host__ __device__ constexpr int home(int t) { return t == kChunkPair ? (int)SEG_TETH : t; }
 
 // Stage layout of a chunk of n constraints of type t: records (n R), multipliers in
 // (4 n per component, component-major), and for the reverse sweep the tape (16 nv n),
@@ -118,19 +122,27 @@ struct StageLayout {
 template <bool REVERSE>
 __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChunk& c, unsigned char* st,
                                             uint64_t* b, bool first, bool last) {
-  const int t = c.type;
+  const int t = c.type, h = home(t);
   const unsigned n = (unsigned)c.count, R = rec_size(t), nv = nverts(t), nl = nlam(t), na = nadj(t);
   const StageLayout L(t, n);
-  const size_t so = (size_t)a.slot_off[t] + c.begin;
-  const size_t cs = t == SEG_MEMB ? (size_t)a.memb_stride : 0;   // component stride in the slot space
+  const size_t so = (size_t)a.slot_off[h] + c.begin;
+  // component stride in the slot space: membrane blocks, or C_H -> C_D slots of a pair
+  const size_t cs = t == SEG_MEMB ? (size_t)a.memb_stride
+                                  : (t == kChunkPair ? (size_t)(a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]) : 0);
   unsigned total = n * R + (a.lam_in ? 4 * nl * n : 0);
   if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * na * n) + (last ? 8 * na * n : 0);
   mbar_expect_tx(b, total);
-  bulk_g2s(st, (const char*)a.prec[t] + (size_t)c.begin * R, n * R, b);
+  if (t == kChunkPair) {
+    const unsigned R1 = (unsigned)sizeof(TetRec);
+    bulk_g2s(st, (const char*)a.prec[SEG_TETH] + (size_t)c.begin * R1, n * R1, b);
+    bulk_g2s(st + n * R1, (const char*)a.prec[SEG_TETD] + (size_t)c.begin * R1, n * R1, b);
+  } else {
+    bulk_g2s(st, (const char*)a.prec[h] + (size_t)c.begin * R, n * R, b);
+  }
   if (a.lam_in)
     for (unsigned k = 0; k < nl; ++k) bulk_g2s(st + L.lam + 4 * n * k, a.lam_in + so + k * cs, 4 * n, b);
   if (REVERSE) {
-    bulk_g2s(st + L.tape, a.tape + a.tape_off[t] + (size_t)c.begin * nv, 16 * nv * n, b);
+    bulk_g2s(st + L.tape, a.tape + a.tape_off[h] + (size_t)c.begin * nv, 16 * nv * n, b);
     for (unsigned k = 0; k < na; ++k) {
       if (!first) bulk_g2s(st + L.lb + 8 * n * k, a.lb + so + k * cs, 8 * n, b);
       if (last) bulk_g2s(st + L.acc + 8 * n * k, a.acc + so + k * cs, 8 * n, b);
@@ -151,14 +163,24 @@ __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk
   if (tid >= c.count) return;
   const StageLayout L(t, (unsigned)c.count);
   const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
-  const size_t gi = (size_t)a.slot_off[t] + c.begin + tid;
+  const size_t gi = (size_t)a.slot_off[home(t)] + c.begin + tid;
 #if XPBD_PHASE_TAPE_SOA
-  float4* tp = RECORD ? a.tape + a.tape_off[t] + (size_t)c.begin * nverts(t) + tid : nullptr;
+  float4* tp = RECORD ? a.tape + a.tape_off[home(t)] + (size_t)c.begin * nverts(t) + tid : nullptr;
   const int ts = c.count;
 #else
-  float4* tp = RECORD ? a.tape + a.tape_off[t] + (size_t)(c.begin + tid) * nverts(t) : nullptr;
+  float4* tp = RECORD ? a.tape + a.tape_off[home(t)] + (size_t)(c.begin + tid) * nverts(t) : nullptr;
   const int ts = 1;
 #endif
+  if (has<TM>(kChunkPair) && t == kChunkPair) {
+    const int n = c.count;
+    const float* sl = reinterpret_cast<const float*>(st + L.lam);
+    const float atd = reinterpret_cast<const TetRec*>(st + (size_t)n * sizeof(TetRec))[tid].at;
+    const float2 l2 = a.lam_in ? make_float2(sl[tid], sl[n + tid]) : make_float2(0.f, 0.f);
+    const float2 lo2 = proj_pair_core<true>(reinterpret_cast<const TetRec*>(st)[tid], atd, sv, l2, tp, ts);
+    __stcs(a.lam_out + gi, lo2.x);
+    __stcs(a.lam_out + gi + (a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]), lo2.y);
+    return;
+  }
   if (has<TM>(SEG_MEMB) && t == SEG_MEMB) {
     const float* sl = reinterpret_cast<const float*>(st + L.lam);
     const int n = c.count;
@@ -191,7 +213,7 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
   const StageLayout L(t, (unsigned)c.count);
   const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
   float2 l = first ? make_float2(0.f, 0.f) : reinterpret_cast<const float2*>(st + L.lb)[tid];
-  const size_t gi = (size_t)a.slot_off[t] + c.begin + tid;
+  const size_t gi = (size_t)a.slot_off[home(t)] + c.begin + tid;
 #if XPBD_PHASE_TAPE_SOA
   const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + tid;
   const int ts = c.count;
@@ -199,6 +221,27 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
   const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + (size_t)tid * nverts(t);
   const int ts = 1;
 #endif
+  if (has<TM>(kChunkPair) && t == kChunkPair) {
+    const int n = c.count;
+    const float* sl = reinterpret_cast<const float*>(st + L.lam);
+    const float2* slb = reinterpret_cast<const float2*>(st + L.lb);
+    const double* sacc = reinterpret_cast<const double*>(st + L.acc);
+    const float atd = reinterpret_cast<const TetRec*>(st + (size_t)n * sizeof(TetRec))[tid].at;
+    const float2 l2 = a.lam_in ? make_float2(sl[tid], sl[n + tid]) : make_float2(0.f, 0.f);
+    float2 lh = first ? make_float2(0.f, 0.f) : slb[tid];
+    float2 ld = first ? make_float2(0.f, 0.f) : slb[n + tid];
+    const float4 p[4] = {tp[0], tp[ts], tp[2 * ts], tp[3 * ts]};
+    vjp_pair_core<true>(reinterpret_cast<const TetRec*>(st)[tid], atd, p, l2, lh, ld, sx);
+    const size_t gd = gi + (a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]);
+    if (last) {
+      a.acc[gi] = sacc[tid] + (double)lh.y;
+      a.acc[gd] = sacc[n + tid] + (double)ld.y;
+    } else {
+      a.lb[gi] = lh;
+      a.lb[gd] = ld;
+    }
+    return;
+  }
   if (has<TM>(SEG_MEMB) && t == SEG_MEMB) {
     const int n = c.count;
     const float* sl = reinterpret_cast<const float*>(st + L.lam);
@@ -368,12 +411,15 @@ namespace {
 // Type sets with their own kernels: cloth (distance + bending), solids (the two tet
 // constraints, with or without distance constraints), membrane cloth (membranes with
 // bending and distance constraints) and everything.
-constexpr int kMaskCloth = 0x3, kMaskSolid = 0xD, kMaskMemb = 0x13, kMaskAll = 0x1F;
+// Coupled tets (pair chunks, bit kChunkPair) have a kernel of their own (with distance
+// constraints); they never share a model with one-at-a-time tets.
+constexpr int kMaskCloth = 0x3, kMaskSolid = 0xD, kMaskMemb = 0x13, kMaskPair = 0x21, kMaskAll = 0x3F;
 
 int kernel_mask(int type_mask) {
   if ((type_mask & ~kMaskCloth) == 0) return kMaskCloth;
   if ((type_mask & ~kMaskSolid) == 0) return kMaskSolid;
   if ((type_mask & ~kMaskMemb) == 0) return kMaskMemb;
+  if ((type_mask & ~kMaskPair) == 0) return kMaskPair;
   return kMaskAll;
 }
 
@@ -394,7 +440,7 @@ Plan stage_plan(const PhaseShape& sh, bool rev) {
   p.vert_bytes = ((sh.max_verts + 1) * 16 + 127) / 128 * 128;
   p.chunk_bytes = (sh.max_chunks * (int)sizeof(PhaseChunk) + 127) / 128 * 128;
   unsigned e = 0;
-  for (int t = 0; t < kSegTypes; ++t)
+  for (int t = 0; t <= kChunkPair; ++t)
     if ((sh.type_mask >> t) & 1) e = std::max(e, elem_stage_bytes(t, rev));
   // a stage holds the phase's largest chunk: phases of small groups (small models) get
   // stages of their chunk size and so more of them in flight
@@ -441,6 +487,7 @@ void launch_mode(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cud
     case kMaskCloth: k_phase<MODE, kMaskCloth><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
     case kMaskSolid: k_phase<MODE, kMaskSolid><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
     case kMaskMemb: k_phase<MODE, kMaskMemb><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
+    case kMaskPair: k_phase<MODE, kMaskPair><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
     default: k_phase<MODE, kMaskAll><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last);
   }
 }
@@ -451,6 +498,7 @@ cudaError_t phase_kernel_setup() {
   cudaError_t e = setup_mask<kMaskCloth>();
   if (e == cudaSuccess) e = setup_mask<kMaskSolid>();
   if (e == cudaSuccess) e = setup_mask<kMaskMemb>();
+  if (e == cudaSuccess) e = setup_mask<kMaskPair>();
   if (e == cudaSuccess) e = setup_mask<kMaskAll>();
   return e;
 }

@@ -53,15 +53,32 @@ def test_coupled_differs_from_one_at_a_time():
     assert np.abs(xu - oracle.forward(un)[0]).max() < POS_TOL
 
 
-def test_coupled_runs_per_color_in_every_mode():
+def test_coupled_phase_plan_matches_per_color_and_oracle():
+    """Pairs in the multi-color phase kernels (exec_mode 2; each chunk stages the C_H records
+    with their C_D shadows) against one launch per color (within rounding: FMA contraction
+    differs between the kernels) and against the oracle."""
     sc = _block()
-    outs = []
-    for mode in (0, 1, 2):
+    rng = np.random.default_rng(19)
+    seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3)))}
+    ref = oracle.adjoint(sc, seeds)
+    xs_ref, _ = oracle.forward(sc)
+    out = {}
+    for mode in (2, 1):
         solver = binding.Solver.from_scene(sc, exec_mode=mode)
-        assert solver.exec_info()["phases"] is False
-        _, _, ck, _, _ = gpu_forward(sc, solver=solver)
-        outs.append(ck)
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+        info = solver.exec_info()
+        assert info["phases"] == (mode == 2), info
+        _, p, ck, xs, _ = gpu_forward(sc, solver=solver)
+        gr = solver.adjoint(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
+                            want=("compliance", "x0", "v0", "f_vertex"))
+        torch.cuda.synchronize()
+        solver.sync_status()
+        assert np.abs(xs - xs_ref).max() < POS_TOL, mode
+        out[mode] = (xs, {k: v.cpu().numpy() for k, v in gr.items()})
+        for k, v in out[mode][1].items():
+            assert rel_err(v, ref[k]) < GRAD_TOL, (mode, k)
+    assert np.abs(out[2][0] - out[1][0]).max() <= 1e-6
+    for k in out[2][1]:
+        assert rel_err(out[2][1][k], out[1][1][k]) <= 2e-4, k
 
 
 def test_serving_refuses_coupled_models():

@@ -252,9 +252,8 @@ def test_phase_plan_matches_per_color_launches(name, cases):
     for mode in (2, 1):   # 2: the phase plan whenever the coloring allows one
         solver = binding.Solver.from_scene(sc, exec_mode=mode)
         info = solver.exec_info()
-        # coupled tets run one launch per color in every mode
-        assert info["phases"] == (mode == 2 and not sc.tet_coupled), info
-        if mode == 2 and not sc.tet_coupled:
+        assert info["phases"] == (mode == 2), info
+        if mode == 2:
             assert info["launches_per_iteration"] < sc.n_colors
         p = binding.params_from_scene(sc)
         ck = solver.forward(p, sc.steps, sc.iters, to_dev(sc.x0), to_dev(sc.v0))

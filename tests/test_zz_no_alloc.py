@@ -52,7 +52,7 @@ def test_static_forward_tet_block_with_contacts():
 
 def test_static_forward_coupled_tets():
     sc = scenes.couple_tets(helpers.small_tets(4, steps=5, iters=6, y0=0.004, v_scale=0.05))
-    solver = binding.Solver.from_scene(sc)
+    solver = binding.Solver.from_scene(sc, exec_mode=1)
     p = binding.params_from_scene(sc)
     x0, v0 = to_dev(sc.x0), to_dev(sc.v0)
     ref = solver.forward(p, sc.steps, sc.iters, x0, v0)
