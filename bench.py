@@ -118,6 +118,13 @@ def max_over_ranks(ws, v: float) -> float:
     return float(t.item())
 
 
+def replica_rate(ws: int, units_per_rank: float, ms_local: float):
+    """Whole-job rate of N independent replicas: every rank processed `units_per_rank`
+    units and the job took as long as its slowest rank.  Returns (units/s, ms)."""
+    ms_max = max_over_ranks(ws, ms_local)
+    return ws * units_per_rank / (ms_max / 1e3), ms_max
+
+
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -346,9 +353,8 @@ def run_ours(args, ws, rank, local):
     solver.profile(False)
     solver.sync_status()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = max_over_ranks(ws, ms)
     units = 2 * sc.m * I * N
-    value = ws * units / (ms_max / 1e3)
+    value, ms_max = replica_rate(ws, units, ms)
 
     # dominant kernel class and its roofline: algorithmic bytes per launch (the library's
     # byte model: records, multipliers, tapes, one read and one write per vertex per launch)
