@@ -184,3 +184,39 @@ def test_sphere_cloth_2950_adjoint_window(big_cloth):
     print(f"2950^2 window: compliance-gradient error {err:.3e}, float32 rounding floor {floor:.3e}")
     assert err < max(GRAD_TOL, 4.0 * floor), (err, floor)
     assert rel_err(got["f_global"].cpu().numpy()[:1], ref["f_global"]) < GRAD_TOL
+
+
+def test_membrane_cloth_256_full_size():
+    """The material-estimation membrane workload at its full size (65,536 vertices, 130,050
+    StVK triangles + 129,540 hinges, 8x8-tile coloring, 30 iterations) in the phase
+    kernels bench.py times, over one step, with a smooth start velocity field (0.3 m/s, one
+    wavelength across the sheet) so that the sheet strains and every gradient group is
+    nonzero (the bench's flat fall keeps it strain-free for 20 steps).  The stiff
+    membranes (K ~ 1e3 N/m on 4 mm triangles) amplify float32 rounding in the reverse
+    sweep to ~9e-4, so the gradient bound is max(1e-3, 4 x floor) with the floor measured
+    by the oracle's float32 emulation."""
+    sc = scenes.membrane_cloth(256, pins=(), steps=1, iters=30, seed=9, coloring="tiled", tile=8)
+    sc.collider_flags = scenes.COLLIDE_PLANE
+    sc.plane_h = -0.6
+    x, z = sc.x0[:, 0], sc.x0[:, 2]
+    sc.v0 = scenes.f32(0.3 * np.stack([np.sin(2 * np.pi * z + 0.3), np.sin(2 * np.pi * (x + z)),
+                                        np.cos(2 * np.pi * x - 0.7)], axis=1))
+    solver = binding.Solver.from_scene(sc)
+    assert solver.exec_info()["phases"]
+    rng = np.random.default_rng(42)
+    seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3)))}
+    keys = ("compliance", "x0", "v0", "f_vertex", "memb_stiffness")
+    xs_ref, _ = oracle.forward(sc)
+    ref = oracle.adjoint(sc, seeds)
+    with oracle.fp32_rounding():
+        ref32 = oracle.adjoint(sc, seeds)
+    _, p, ck, xs, _ = gpu_forward(sc, solver=solver)
+    assert np.abs(xs - xs_ref).max() < POS_TOL
+    got = solver.adjoint(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()}, want=keys)
+    torch.cuda.synchronize()
+    for k in keys:
+        assert np.abs(ref[k]).max() > 0, k
+        floor = rel_err(ref32[k], ref[k])
+        e = rel_err(got[k].cpu().numpy().reshape(ref[k].shape), ref[k])
+        print(f"membrane 256^2 {k}: error {e:.3e}, float32 floor {floor:.3e}")
+        assert e < max(GRAD_TOL, 4.0 * floor), (k, e, floor)
