@@ -185,6 +185,21 @@ def forward_multipliers(scene, steps: Optional[int] = None, iters: Optional[int]
     return xs, vs, lam, lamc, act.astype(bool)
 
 
+def forward_memb_multipliers(scene, steps: Optional[int] = None, iters: Optional[int] = None, *, x0=None, v0=None,
+                             memb_stiffness=None) -> np.ndarray:
+    """The membranes' multipliers (E_uu, E_vv, 2 E_uv rows) each step ended with:
+    [steps, n_memb, 3]."""
+    steps = scene.steps if steps is None else steps
+    iters = scene.iters if iters is None else iters
+    a = _Args(scene, None, None, None, None, None, steps, None, memb_stiffness)
+    x0a, x0p = _d(scene.x0 if x0 is None else x0)
+    v0a, v0p = _d(scene.v0 if v0 is None else v0)
+    out = np.zeros((steps, scene.n_memb, 3))
+    lib().oracle_forward_memb_multipliers(C.byref(a.model), C.byref(a.params), steps, iters, x0p, v0p,
+                                          out.ctypes.data_as(_dp))
+    return out
+
+
 def adjoint(scene, seeds: dict, steps: Optional[int] = None, iters: Optional[int] = None, *,
             seed_dv_T=None, x0=None, v0=None, compliance=None, f_global=None, f_vertex=None,
             plane_h=None, sphere=None, f_vertex_steps=None, memb_stiffness=None) -> dict:

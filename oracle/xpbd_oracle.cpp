@@ -653,7 +653,7 @@ template <class T>
 void forward(const Model& M, const Params<T>& P, int steps, int iters, const std::vector<T>& x0,
              const std::vector<T>& v0, std::vector<T>& xs, std::vector<T>& vs,
              std::vector<T>* lam_steps = nullptr, std::vector<T>* lamc_steps = nullptr,
-             std::vector<uint8_t>* active_steps = nullptr) {
+             std::vector<uint8_t>* active_steps = nullptr, std::vector<T>* lam_m_steps = nullptr) {
   size_t V3n = (size_t)M.V * 3;
   xs.assign(V3n * (steps + 1), T(0.0));
   vs.assign(V3n * (steps + 1), T(0.0));
@@ -679,6 +679,7 @@ void forward(const Model& M, const Params<T>& P, int steps, int iters, const std
     if (lam_steps) lam_steps->insert(lam_steps->end(), W.lam.begin(), W.lam.end());
     if (lamc_steps) lamc_steps->insert(lamc_steps->end(), W.lam_c.begin(), W.lam_c.end());
     if (active_steps) active_steps->insert(active_steps->end(), W.active.begin(), W.active.end());
+    if (lam_m_steps) lam_m_steps->insert(lam_m_steps->end(), W.lam_m.begin(), W.lam_m.end());
     for (size_t i = 0; i < V3n; ++i) {
       xs[V3n * (n + 1) + i] = W.p[i];
       vs[V3n * (n + 1) + i] = (W.p[i] - x[i]) / P.dt;
@@ -1198,6 +1199,17 @@ int oracle_forward_multipliers(const om_model* in, const om_params* pin, int32_t
   if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
   if (lamc_out) std::copy(lamc.begin(), lamc.end(), lamc_out);
   if (active_out) std::copy(act.begin(), act.end(), active_out);
+  return 0;
+}
+
+// The membranes' multipliers each step ended with: lam_m_out [steps*n_memb*3].
+int oracle_forward_memb_multipliers(const om_model* in, const om_params* pin, int32_t steps, int32_t iters,
+                                    const double* x0, const double* v0, double* lam_m_out) {
+  Model M = make_model(in);
+  Params<double> P = make_params<double>(M, pin, steps);
+  std::vector<double> x(x0, x0 + 3 * (size_t)M.V), v(v0, v0 + 3 * (size_t)M.V), xs, vs, lm;
+  forward<double>(M, P, steps, iters, x, v, xs, vs, nullptr, nullptr, nullptr, &lm);
+  std::copy(lm.begin(), lm.end(), lam_m_out);
   return 0;
 }
 
