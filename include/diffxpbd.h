@@ -111,9 +111,8 @@ typedef struct {
                                    warp/weft rest coordinates; compliance block (A K)^-1
                                    with A the rest area and K = [C00 C01 0; C01 C11 0;
                                    0 0 C22] (xpbd_params.memb_stiffness); its three
-                                   multipliers are solved together.  Models with membranes
-                                   run one launch per color; the serving entry points and
-                                   the implicit adjoint refuse them.                        */
+                                   multipliers are solved together.  The serving entry
+                                   points refuse models with membranes.                     */
   const int32_t* memb_idx;      /* [n_memb*3] vertices of each triangle                     */
   const float* memb_uv;         /* [n_memb*6] (u, v) rest coordinates of each triangle's
                                    three vertices (u warp, v weft); a triangle whose rest
@@ -253,7 +252,9 @@ xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t ste
    free vertices by block-Jacobi preconditioned conjugate gradients, pinned vertices
    filtered out (Sec. "Linear System Filtering"); then pbar = M y (free), pbar = b - A y
    (pinned), alphabar~_j += -(lambda_j / alpha~_j) grad C_j . y, and the prediction adjoint
-   as in xpbd_adjoint.  The gradient differs from xpbd_adjoint's by design: XPBD's
+   as in xpbd_adjoint.  A membrane is one block, G^T alpha~^-1 G - sum_k lambda_k hess C_k
+   over its three rows, with alphabar~ += -(alpha~^-1 G y) lambda^T (then dL/dK in
+   d_memb_stiffness).  The gradient differs from xpbd_adjoint's by design: XPBD's
    iterations leave the primal residual M (x - p) - grad C^T lambda nonzero, so this is the
    derivative of the exactly solved step at XPBD's end state. */
 typedef struct {

@@ -354,12 +354,13 @@ class Solver:
         keys = sorted(seeds)
         sd = torch.stack([seeds[k] for k in keys]).contiguous() if keys else None
         shapes = dict(compliance=(self.m,), x0=(self.V, 3), v0=(self.V, 3), f_global=(max(steps, 1), 3),
-                      f_vertex=(self.V, 3), f_vertex_steps=(max(steps, 1), self.V, 3))
+                      f_vertex=(self.V, 3), f_vertex_steps=(max(steps, 1), self.V, 3), memb_stiffness=(self.n_memb, 4))
         out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
         g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
                       d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
                       d_f_vertex=_ptr(out.get("f_vertex")), d_collider=None,
-                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")))
+                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")),
+                      d_memb_stiffness=_ptr(out.get("memb_stiffness")))
         its = (C.c_int32 * max(steps, 1))()
         o = XpbdImplicitOpts(cg_tol=float(cg_tol), cg_max_iters=int(cg_max_iters), pd_project=int(bool(pd_project)),
                              cg_iters_out=C.cast(its, _ip))

@@ -1275,7 +1275,6 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   if (out->d_collider)
     return fail(XPBD_ERR_INVALID, "the implicit adjoint forms no collider-parameter gradient (d_collider must be NULL)");
   if (!(o->cg_tol > 0.0) || o->cg_max_iters < 1) return fail(XPBD_ERR_INVALID, "cg_tol must be > 0 and cg_max_iters >= 1");
-  if (h->nm > 0) return fail(XPBD_ERR_INVALID, "the implicit adjoint does not take membranes");
   cudaStream_t s = (cudaStream_t)stream;
   AdjointSweep A;
   st = adjoint_begin(h, p, steps, iters, n_seeds, seed_steps, seed_dx, seed_dv_T, out, s, A);
@@ -1287,7 +1286,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   const int V = h->V;
   const size_t V3 = 3 * (size_t)V;
   const int64_t nq = (int64_t)h->n_rec[1] + h->n_rec[2] + h->n_rec[3];
-  CU_TRY(h->imp_blocks.ensure(sizeof(double) * 45 * (size_t)std::max<int64_t>(nq, 1)));
+  CU_TRY(h->imp_blocks.ensure(sizeof(double) * (45 * (size_t)nq + 21 * (size_t)h->nm + 1)));
   CU_TRY(h->imp_vec.ensure(sizeof(double) * 6 * std::max<size_t>(V3, 1)));
   CU_TRY(h->imp_dinv.ensure(sizeof(double) * 9 * (size_t)std::max(V, 1)));
   CU_TRY(h->imp_sc.ensure(sizeof(double) * 8));
@@ -1297,6 +1296,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   double* sc = h->imp_sc.as<double>();
   double* partials = h->partials.as<double>();
   double* blocks = h->imp_blocks.as<double>();
+  double* mblocks = blocks + 45 * (size_t)nq;   // membranes: 21 per record
   const int64_t boff[4] = {0, 0, h->n_rec[1], (int64_t)h->n_rec[1] + h->n_rec[2]};
   const float* lam = h->lam.as<float>();
   const Collide c = make_collide(p);
@@ -1313,6 +1313,12 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
       for (int col = 0; col < h->K; ++col)
         for (const Seg& cg : h->colors[col])
           for_each_record_seg(h, cg, [&](const Seg& g) {
+            if (g.type == SEG_MEMB) {
+              launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+                launch_apply_memb(h->d_mrec + g.begin, g.count, mblocks + 21 * (size_t)g.begin, pin, qout, s);
+              });
+              return;
+            }
             const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
             launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
               launch_apply_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
@@ -1329,10 +1335,19 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
         launch_quad_blocks((SegType)t, h->d_rec[t], h->n_rec[t], X, lam + h->rec_off[t],
                            blocks + 45 * (size_t)boff[t], pd, s);
       });
+    launch(h, XPBD_K_ADJ_OTHER, h->nm, s, [&] {
+      launch_memb_blocks(h->d_mrec, h->nm, X, lam + h->mslot, h->nm, mblocks, pd, s);
+    });
     launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_mass_contacts(X, cf, lamc, c, pd, dinv, V, s); });
     for (int col = 0; col < h->K; ++col)
       for (const Seg& cg : h->colors[col])
         for_each_record_seg(h, cg, [&](const Seg& g) {
+          if (g.type == SEG_MEMB) {
+            launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+              launch_diag_memb(h->d_mrec + g.begin, g.count, mblocks + 21 * (size_t)g.begin, dinv, s);
+            });
+            return;
+          }
           const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
           launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
             launch_diag_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
@@ -1378,6 +1393,9 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
         launch_abar((SegType)t, h->d_rec[t], h->n_rec[t], X, lam + h->rec_off[t], y,
                     h->acc.as<double>() + h->rec_off[t], s);
       });
+    launch(h, XPBD_K_ADJ_OTHER, h->nm, s, [&] {
+      launch_abar_memb(h->d_mrec, h->nm, X, lam + h->mslot, h->nm, y, h->acc.as<double>() + h->mslot, s);
+    });
     LAUNCH_CHECK();
     st = adjoint_predict(h, p, n, ck_x(ck, V, n), A, s);
     if (st != XPBD_OK) return st;

@@ -30,52 +30,58 @@ __device__ __forceinline__ int pk9(int i, int j) {   // packed upper triangle of
   return i * 9 - (i * (i - 1)) / 2 + (j - i);
 }
 
-// Positive semi-definite part of a symmetric 9x9 matrix (row-major in a), by cyclic
+__device__ __forceinline__ int pk6(int i, int j) {   // packed upper triangle of a 6x6
+  if (i > j) { int t = i; i = j; j = t; }
+  return i * 6 - (i * (i - 1)) / 2 + (j - i);
+}
+
+// Positive semi-definite part of a symmetric N x N matrix (row-major in a), by cyclic
 // Jacobi rotations: a = V D V^T, then sum over max(d_i, 0) v_i v_i^T.  In float64: the
 // projected block must stay semi-definite to well below a vertex mass, which float32
 // round-off of a stiff bending block (entries ~1e3) does not guarantee.
-__device__ void psd_part9(double* a) {
-  double v[81];
-  for (int i = 0; i < 81; ++i) v[i] = (i % 10 == 0) ? 1.0 : 0.0;
+template <int N>
+__device__ void psd_part(double* a) {
+  double v[N * N];
+  for (int i = 0; i < N * N; ++i) v[i] = (i % (N + 1) == 0) ? 1.0 : 0.0;
   double scale = 0.0;
-  for (int i = 0; i < 81; ++i) scale = fmax(scale, fabs(a[i]));
+  for (int i = 0; i < N * N; ++i) scale = fmax(scale, fabs(a[i]));
   if (scale == 0.0) return;
   for (int sweep = 0; sweep < 20; ++sweep) {
     double off = 0.0;
-    for (int p = 0; p < 9; ++p)
-      for (int q = p + 1; q < 9; ++q) off += a[p * 9 + q] * a[p * 9 + q];
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) off += a[p * N + q] * a[p * N + q];
     if (off <= 1e-28 * scale * scale) break;
-    for (int p = 0; p < 9; ++p)
-      for (int q = p + 1; q < 9; ++q) {
-        const double apq = a[p * 9 + q];
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        const double apq = a[p * N + q];
         if (fabs(apq) <= 1e-30 * scale) continue;
-        const double theta = (a[q * 9 + q] - a[p * 9 + p]) / (2.0 * apq);
+        const double theta = (a[q * N + q] - a[p * N + p]) / (2.0 * apq);
         const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
         const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < 9; ++k) {   // columns p, q
-          const double akp = a[k * 9 + p], akq = a[k * 9 + q];
-          a[k * 9 + p] = c * akp - s * akq;
-          a[k * 9 + q] = s * akp + c * akq;
+        for (int k = 0; k < N; ++k) {   // columns p, q
+          const double akp = a[k * N + p], akq = a[k * N + q];
+          a[k * N + p] = c * akp - s * akq;
+          a[k * N + q] = s * akp + c * akq;
         }
-        for (int k = 0; k < 9; ++k) {   // rows p, q
-          const double apk = a[p * 9 + k], aqk = a[q * 9 + k];
-          a[p * 9 + k] = c * apk - s * aqk;
-          a[q * 9 + k] = s * apk + c * aqk;
+        for (int k = 0; k < N; ++k) {   // rows p, q
+          const double apk = a[p * N + k], aqk = a[q * N + k];
+          a[p * N + k] = c * apk - s * aqk;
+          a[q * N + k] = s * apk + c * aqk;
         }
-        for (int k = 0; k < 9; ++k) {
-          const double vkp = v[k * 9 + p], vkq = v[k * 9 + q];
-          v[k * 9 + p] = c * vkp - s * vkq;
-          v[k * 9 + q] = s * vkp + c * vkq;
+        for (int k = 0; k < N; ++k) {
+          const double vkp = v[k * N + p], vkq = v[k * N + q];
+          v[k * N + p] = c * vkp - s * vkq;
+          v[k * N + q] = s * vkp + c * vkq;
         }
       }
   }
-  double d[9];
-  for (int i = 0; i < 9; ++i) d[i] = fmax(a[i * 9 + i], 0.0);
-  for (int i = 0; i < 9; ++i)
-    for (int j = 0; j < 9; ++j) {
+  double d[N];
+  for (int i = 0; i < N; ++i) d[i] = fmax(a[i * N + i], 0.0);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
       double s = 0.0;
-      for (int k = 0; k < 9; ++k) s += v[i * 9 + k] * d[k] * v[j * 9 + k];
-      a[i * 9 + j] = s;
+      for (int k = 0; k < N; ++k) s += v[i * N + k] * d[k] * v[j * N + k];
+      a[i * N + j] = s;
     }
 }
 
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_quad_blocks(const typename Quad<KIND
       a[row * 9 + col] = b;
       a[col * 9 + row] = b;
     }
-  if (pd) psd_part9(a);
+  if (pd) psd_part<9>(a);
   for (int row = 0; row < 9; ++row)
     for (int col = row; col < 9; ++col) out[pk9(row, col)] = a[row * 9 + col];
 }
@@ -444,7 +450,168 @@ __global__ void __launch_bounds__(kBlock) k_abar_quad(const typename Quad<KIND>:
   acc[i] += -((double)lam[i] / (double)r.at) * gy;
 }
 
+// ---- membranes (three rows, 3x3 compliance block), in relative coordinates of vertices 1, 2
+// (e_a = x_a - x_0): the rows' gradients are b_u,a f_u | b_v,a f_v | b_u,a f_v + b_v,a f_u
+// per vertex a, their Hessians (b b^T) (x) I3 with the per-vertex weights b of f_u, f_v.
+struct MembRows {
+  double G[3][6];       // row k, relative coordinate 3 (a-1) + c
+  double Ai[3][3];      // alpha~^-1
+  double bu[2], bv[2];  // weights of vertices 1, 2
+  bool ok;
+  __device__ MembRows(const MembRec& r, const float4* X) {
+    const double det2 = (double)r.a00 * r.a11 - (double)r.a01 * r.a01;
+    ok = r.a00 > 0.f && r.a22 > 0.f && det2 > 0.0;
+    const float4 p0 = X[r.v[0]], p1 = X[r.v[1]], p2 = X[r.v[2]];
+    const double d1[3] = {(double)p1.x - p0.x, (double)p1.y - p0.y, (double)p1.z - p0.z};
+    const double d2[3] = {(double)p2.x - p0.x, (double)p2.y - p0.y, (double)p2.z - p0.z};
+    bu[0] = r.B[0];
+    bu[1] = r.B[2];
+    bv[0] = r.B[1];
+    bv[1] = r.B[3];
+    double fu[3], fv[3];
+    for (int c = 0; c < 3; ++c) {
+      fu[c] = d1[c] * bu[0] + d2[c] * bu[1];
+      fv[c] = d1[c] * bv[0] + d2[c] * bv[1];
+    }
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < 3; ++c) {
+        G[0][3 * a + c] = bu[a] * fu[c];
+        G[1][3 * a + c] = bv[a] * fv[c];
+        G[2][3 * a + c] = bu[a] * fv[c] + bv[a] * fu[c];
+      }
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) Ai[k][l] = 0.0;
+    if (ok) {
+      Ai[0][0] = r.a11 / det2;
+      Ai[1][1] = r.a00 / det2;
+      Ai[0][1] = Ai[1][0] = -r.a01 / det2;
+      Ai[2][2] = 1.0 / r.a22;
+    }
+  }
+};
+
+// B_rel = G^T alpha~^-1 G - (lambda_0 b_u b_u^T + lambda_1 b_v b_v^T + lambda_2 (b_u b_v^T + b_v b_u^T)) (x) I3,
+// projected when pd, stored packed (21 float64).
+__global__ void __launch_bounds__(kBlock) k_memb_blocks(const MembRec* __restrict__ rec, int n, const float4* __restrict__ X,
+                                                        const float* __restrict__ lam, int stride,
+                                                        double* __restrict__ blocks, bool pd) {
+  XPBD_TID_OR_RETURN(n);
+  const MembRec r = rec[i];
+  double* out = blocks + 21 * (size_t)i;
+  const MembRows M(r, X);
+  if (!M.ok) {
+    for (int k = 0; k < 21; ++k) out[k] = 0.0;
+    return;
+  }
+  const double l0 = lam[i], l1 = lam[i + stride], l2 = lam[i + 2 * stride];
+  double a[36];
+  for (int row = 0; row < 6; ++row)
+    for (int col = 0; col < 6; ++col) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) s += M.G[k][row] * M.Ai[k][l] * M.G[l][col];
+      if (row % 3 == col % 3) {
+        const int va = row / 3, vb = col / 3;
+        s -= l0 * M.bu[va] * M.bu[vb] + l1 * M.bv[va] * M.bv[vb] + l2 * (M.bu[va] * M.bv[vb] + M.bv[va] * M.bu[vb]);
+      }
+      a[row * 6 + col] = s;
+    }
+  for (int row = 0; row < 6; ++row)
+    for (int col = row + 1; col < 6; ++col) {
+      const double h = 0.5 * (a[row * 6 + col] + a[col * 6 + row]);
+      a[row * 6 + col] = a[col * 6 + row] = h;
+    }
+  if (pd) psd_part<6>(a);
+  for (int row = 0; row < 6; ++row)
+    for (int col = row; col < 6; ++col) out[pk6(row, col)] = a[row * 6 + col];
+}
+
+__global__ void __launch_bounds__(kBlock) k_apply_memb(const MembRec* __restrict__ rec, int n, const double* __restrict__ blocks,
+                                                       const double* __restrict__ p, double* __restrict__ q) {
+  XPBD_TID_OR_RETURN(n);
+  const MembRec r = rec[i];
+  const double* B = blocks + 21 * (size_t)i;
+  const D3 p0 = ld3(p, r.v[0]);
+  double u[6];
+  for (int k = 0; k < 2; ++k) {
+    const D3 pk = ld3(p, r.v[k + 1]);
+    u[3 * k] = pk.x - p0.x;
+    u[3 * k + 1] = pk.y - p0.y;
+    u[3 * k + 2] = pk.z - p0.z;
+  }
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int row = 0; row < 6; ++row) {
+    double t = 0.0;
+    for (int col = 0; col < 6; ++col) t += B[pk6(row, col)] * u[col];
+    q[3 * r.v[row / 3 + 1] + row % 3] += t;
+    s[row % 3] += t;
+  }
+  add3(q, r.v[0], -s[0], -s[1], -s[2]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_diag_memb(const MembRec* __restrict__ rec, int n, const double* __restrict__ blocks,
+                                                      double* __restrict__ dg) {
+  XPBD_TID_OR_RETURN(n);
+  const MembRec r = rec[i];
+  const double* B = blocks + 21 * (size_t)i;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s0 = 0.0;
+      for (int k = 0; k < 2; ++k) {
+        for (int l = 0; l < 2; ++l) s0 += B[pk6(3 * k + a, 3 * l + b)];
+        dg[9 * r.v[k + 1] + 3 * a + b] += B[pk6(3 * k + a, 3 * k + b)];
+      }
+      dg[9 * r.v[0] + 3 * a + b] += s0;
+    }
+}
+
+// alphabar~ += -(alpha~^-1 G y) lambda^T on the entries (00, 11, 01 + 10, 22).
+__global__ void __launch_bounds__(kBlock) k_abar_memb(const MembRec* __restrict__ rec, int n, const float4* __restrict__ X,
+                                                      const float* __restrict__ lam, int stride, const double* __restrict__ y,
+                                                      double* __restrict__ acc) {
+  XPBD_TID_OR_RETURN(n);
+  const MembRec r = rec[i];
+  const MembRows M(r, X);
+  if (!M.ok) return;
+  const D3 y0 = ld3(y, r.v[0]);
+  double u[6];
+  for (int k = 0; k < 2; ++k) {
+    const D3 yk = ld3(y, r.v[k + 1]);
+    u[3 * k] = yk.x - y0.x;
+    u[3 * k + 1] = yk.y - y0.y;
+    u[3 * k + 2] = yk.z - y0.z;
+  }
+  double gy[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 6; ++c) gy[k] += M.G[k][c] * u[c];
+  double z[3];
+  for (int k = 0; k < 3; ++k) z[k] = M.Ai[k][0] * gy[0] + M.Ai[k][1] * gy[1] + M.Ai[k][2] * gy[2];
+  const double l0 = lam[i], l1 = lam[i + stride], l2 = lam[i + 2 * stride];
+  acc[i] += -z[0] * l0;
+  acc[i + stride] += -z[1] * l1;
+  acc[i + 2 * stride] += -(z[0] * l1 + z[1] * l0);
+  acc[i + 3 * stride] += -z[2] * l2;
+}
+
 }  // namespace
+
+void launch_memb_blocks(const MembRec* rec, int n, const float4* X, const float* lam, int stride, double* blocks, bool pd,
+                        cudaStream_t s) {
+  if (n > 0) k_memb_blocks<<<grid_for(n), kBlock, 0, s>>>(rec, n, X, lam, stride, blocks, pd);
+}
+
+void launch_apply_memb(const MembRec* rec, int n, const double* blocks, const double* p, double* q, cudaStream_t s) {
+  if (n > 0) k_apply_memb<<<grid_for(n), kBlock, 0, s>>>(rec, n, blocks, p, q);
+}
+
+void launch_diag_memb(const MembRec* rec, int n, const double* blocks, double* dg, cudaStream_t s) {
+  if (n > 0) k_diag_memb<<<grid_for(n), kBlock, 0, s>>>(rec, n, blocks, dg);
+}
+
+void launch_abar_memb(const MembRec* rec, int n, const float4* X, const float* lam, int stride, const double* y,
+                      double* acc, cudaStream_t s) {
+  if (n > 0) k_abar_memb<<<grid_for(n), kBlock, 0, s>>>(rec, n, X, lam, stride, y, acc);
+}
 
 void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, double* blocks, bool pd,
                         cudaStream_t s) {

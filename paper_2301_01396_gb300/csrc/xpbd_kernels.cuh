@@ -152,6 +152,14 @@ void launch_phase_vjp(PhaseLaunch a, const PhaseShape& sh, bool first, bool last
 // ---- implicit adjoint (xpbd_implicit.cu): blocks, matrix-free products, PCG pieces
 void launch_quad_blocks(SegType t, const void* rec, int n, const float4* X, const float* lam, double* blocks, bool pd,
                         cudaStream_t s);
+// membranes: 21 packed float64 per block (6x6 in the relative coordinates of vertices 1, 2);
+// multiplier and accumulator slots k of record i at i + k * stride
+void launch_memb_blocks(const MembRec* rec, int n, const float4* X, const float* lam, int stride, double* blocks, bool pd,
+                        cudaStream_t s);
+void launch_apply_memb(const MembRec* rec, int n, const double* blocks, const double* p, double* q, cudaStream_t s);
+void launch_diag_memb(const MembRec* rec, int n, const double* blocks, double* dg, cudaStream_t s);
+void launch_abar_memb(const MembRec* rec, int n, const float4* X, const float* lam, int stride, const double* y,
+                      double* acc, cudaStream_t s);
 void launch_apply_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
                                 const double* p, double* q, int V, cudaStream_t s);
 void launch_apply_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* blocks,

@@ -28,10 +28,21 @@ def _cases():
         "tets": helpers.small_tets(2, steps=3, iters=6, y0=0.05, plane=False, v_scale=0.05),
         "tets_coupled": scenes.couple_tets(helpers.small_tets(2, steps=3, iters=6, y0=0.05, plane=False,
                                                               v_scale=0.05)),
+        "membrane": _membrane(),
     }
 
 
-@pytest.mark.parametrize("name", ["pinned_cloth", "ground_cloth", "tets", "tets_coupled"])
+def _membrane():
+    # a pinned 8x8 orthotropic StVK sheet with bending, random start velocities
+    sc = scenes.membrane_cloth(8, steps=3, iters=6, seed=8, pins=((0, 0),), stiffness=(60.0, 30.0, 10.0, 20.0))
+    rng = np.random.default_rng(9)
+    v = 0.3 * rng.standard_normal(sc.x0.shape)
+    v[sc.inv_mass == 0] = 0.0
+    sc.v0 = scenes.f32(v)
+    return sc
+
+
+@pytest.mark.parametrize("name", ["pinned_cloth", "ground_cloth", "tets", "tets_coupled", "membrane"])
 @pytest.mark.parametrize("pd", [True, False])
 def test_implicit_adjoint_matches_oracle(name, pd):
     sc = _cases()[name]
@@ -43,12 +54,13 @@ def test_implicit_adjoint_matches_oracle(name, pd):
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3))), 1: scenes.f32(rng.standard_normal((sc.V, 3)))}
     ref = implicit.adjoint(sc, seeds, pd=pd)
     solver, p, ck, xs, _ = gpu_forward(sc)
+    keys = KEYS + ("f_vertex_steps",) + (("memb_stiffness",) if sc.n_memb else ())
     got, its = solver.adjoint_implicit(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
-                                       want=KEYS + ("f_vertex_steps",), pd_project=pd)
+                                       want=keys, pd_project=pd)
     torch.cuda.synchronize()
     solver.sync_status()
     assert all(0 < n < 5000 for n in its), its
-    for k in KEYS + ("f_vertex_steps",):
+    for k in keys:
         e = rel_err(got[k].cpu().numpy().reshape(ref[k].shape), ref[k])
         assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
 
