@@ -220,5 +220,9 @@ def test_membrane_coloring(oracle_mod):
     sc = scenes.membrane_cloth(7)
     scenes.validate_coloring(sc)
     assert sc.n_memb == 2 * 6 * 6 and sc.n_colored == sc.m + sc.n_memb
+    tiled = scenes.membrane_cloth(40, coloring="tiled", tile=8)
+    scenes.validate_coloring(tiled)                      # vertex-disjoint colors, every id once
+    assert tiled.n_colors == 4 * 16
+    assert np.array_equal(np.sort(tiled.color_order), np.sort(scenes.membrane_cloth(40).color_order))
     K = sc.memb_stiffness.astype(np.float64)
     assert np.all(K[:, 0] * K[:, 1] - K[:, 2] ** 2 > 0) and np.all(K[:, 3] > 0)
