@@ -104,35 +104,60 @@ __host__ __device__ constexpr unsigned nadj(int t) { return t == SEG_MEMB ? 4u :
 // The record array, slot block and tape range a chunk type uses (pairs: the C_H ones).
 __host__ __device__ constexpr int home(int t) { return t == kChunkPair ? (int)SEG_TETH : t; }
 
+template <int TM>
+__device__ __forceinline__ constexpr bool has(int t) {
+  return (TM >> t) & 1;
+}
+
+// The same sizes in a kernel of type set TM: the types it cannot meet fold away, so a
+// cloth kernel computes its stage layout exactly as if membranes and pairs did not exist.
+template <int TM>
+struct TypeSet {
+  static __device__ __forceinline__ bool memb(int t) { return has<TM>(SEG_MEMB) && t == SEG_MEMB; }
+  static __device__ __forceinline__ bool pair(int t) { return has<TM>(kChunkPair) && t == kChunkPair; }
+  static __device__ __forceinline__ unsigned rec(int t) {
+    if (memb(t)) return (unsigned)sizeof(MembRec);
+    if (pair(t)) return 2u * (unsigned)sizeof(TetRec);
+    return t == SEG_DIST ? (unsigned)sizeof(DistRec) : (t == SEG_BEND ? (unsigned)sizeof(BendRec) : (unsigned)sizeof(TetRec));
+  }
+  static __device__ __forceinline__ unsigned nv(int t) { return memb(t) ? 3u : (t == SEG_DIST ? 2u : 4u); }
+  static __device__ __forceinline__ unsigned nl(int t) { return memb(t) ? 3u : (pair(t) ? 2u : 1u); }
+  static __device__ __forceinline__ unsigned na(int t) { return memb(t) ? 4u : (pair(t) ? 2u : 1u); }
+  static __device__ __forceinline__ int home(int t) { return pair(t) ? (int)SEG_TETH : t; }
+};
+
 // Stage layout of a chunk of n constraints of type t: records (n R), multipliers in
 // (4 n per component, component-major), and for the reverse sweep the tape (16 nv n),
 // (lambar, alphabar) pairs (8 n per slot) and the float64 accumulators (8 n per slot).
 // Every part starts on a 16-byte boundary because n is a multiple of 4.
+template <int TM>
 struct StageLayout {
   unsigned lam, tape, lb, acc;
   __device__ StageLayout(int t, unsigned n) {
-    lam = n * rec_size(t);
-    tape = lam + 4 * nlam(t) * n;
-    lb = tape + 16 * nverts(t) * n;
-    acc = lb + 8 * nadj(t) * n;
+    using TS = TypeSet<TM>;
+    lam = n * TS::rec(t);
+    tape = lam + 4 * TS::nl(t) * n;
+    lb = tape + 16 * TS::nv(t) * n;
+    acc = lb + 8 * TS::na(t) * n;
   }
 };
 
 // Issued by the producer: copies of chunk c's streams into stage `st`, counted on barrier b.
-template <bool REVERSE>
+template <bool REVERSE, int TM>
 __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChunk& c, unsigned char* st,
                                             uint64_t* b, bool first, bool last) {
-  const int t = c.type, h = home(t);
-  const unsigned n = (unsigned)c.count, R = rec_size(t), nv = nverts(t), nl = nlam(t), na = nadj(t);
-  const StageLayout L(t, n);
+  using TS = TypeSet<TM>;
+  const int t = c.type, h = TS::home(t);
+  const unsigned n = (unsigned)c.count, R = TS::rec(t), nv = TS::nv(t), nl = TS::nl(t), na = TS::na(t);
+  const StageLayout<TM> L(t, n);
   const size_t so = (size_t)a.slot_off[h] + c.begin;
   // component stride in the slot space: membrane blocks, or C_H -> C_D slots of a pair
-  const size_t cs = t == SEG_MEMB ? (size_t)a.memb_stride
-                                  : (t == kChunkPair ? (size_t)(a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]) : 0);
+  const size_t cs = TS::memb(t) ? (size_t)a.memb_stride
+                                 : (TS::pair(t) ? (size_t)(a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]) : 0);
   unsigned total = n * R + (a.lam_in ? 4 * nl * n : 0);
   if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * na * n) + (last ? 8 * na * n : 0);
   mbar_expect_tx(b, total);
-  if (t == kChunkPair) {
+  if (TS::pair(t)) {
     const unsigned R1 = (unsigned)sizeof(TetRec);
     bulk_g2s(st, (const char*)a.prec[SEG_TETH] + (size_t)c.begin * R1, n * R1, b);
     bulk_g2s(st + n * R1, (const char*)a.prec[SEG_TETD] + (size_t)c.begin * R1, n * R1, b);
@@ -150,25 +175,21 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
   }
 }
 
-template <int TM>
-__device__ __forceinline__ constexpr bool has(int t) {
-  return (TM >> t) & 1;
-}
-
 // Forward / replay update of constraint `tid` of chunk c from stage st.
 template <bool RECORD, int TM>
 __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk& c, const unsigned char* st,
                                           float4* sv) {
+  using TS = TypeSet<TM>;
   const int t = c.type, tid = threadIdx.x;
   if (tid >= c.count) return;
-  const StageLayout L(t, (unsigned)c.count);
+  const StageLayout<TM> L(t, (unsigned)c.count);
   const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
-  const size_t gi = (size_t)a.slot_off[home(t)] + c.begin + tid;
+  const size_t gi = (size_t)a.slot_off[TS::home(t)] + c.begin + tid;
 #if XPBD_PHASE_TAPE_SOA
-  float4* tp = RECORD ? a.tape + a.tape_off[home(t)] + (size_t)c.begin * nverts(t) + tid : nullptr;
+  float4* tp = RECORD ? a.tape + a.tape_off[TS::home(t)] + (size_t)c.begin * TS::nv(t) + tid : nullptr;
   const int ts = c.count;
 #else
-  float4* tp = RECORD ? a.tape + a.tape_off[home(t)] + (size_t)(c.begin + tid) * nverts(t) : nullptr;
+  float4* tp = RECORD ? a.tape + a.tape_off[TS::home(t)] + (size_t)(c.begin + tid) * TS::nv(t) : nullptr;
   const int ts = 1;
 #endif
   if (has<TM>(kChunkPair) && t == kChunkPair) {
@@ -208,17 +229,18 @@ __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk
 template <int TM>
 __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk& c, const unsigned char* st,
                                           float4* sx, bool first, bool last) {
+  using TS = TypeSet<TM>;
   const int t = c.type, tid = threadIdx.x;
   if (tid >= c.count) return;
-  const StageLayout L(t, (unsigned)c.count);
+  const StageLayout<TM> L(t, (unsigned)c.count);
   const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
   float2 l = first ? make_float2(0.f, 0.f) : reinterpret_cast<const float2*>(st + L.lb)[tid];
-  const size_t gi = (size_t)a.slot_off[home(t)] + c.begin + tid;
+  const size_t gi = (size_t)a.slot_off[TS::home(t)] + c.begin + tid;
 #if XPBD_PHASE_TAPE_SOA
   const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + tid;
   const int ts = c.count;
 #else
-  const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + (size_t)tid * nverts(t);
+  const float4* tp = reinterpret_cast<const float4*>(st + L.tape) + (size_t)tid * TS::nv(t);
   const int ts = 1;
 #endif
   if (has<TM>(kChunkPair) && t == kChunkPair) {
@@ -361,7 +383,7 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
   // the table to shared memory and gathers the vertices meanwhile
   if (threadIdx.x == kPhaseBlock && !a.no_issue)
     for (int k = 0; k < S && k < nch; ++k)
-      issue_chunk<REV>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &full[k], first, last);
+      issue_chunk<REV, TM>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &full[k], first, last);
   for (int i = threadIdx.x; i < nch; i += blockDim.x) sch[i] = ch[i];
   gather_vertices(a.P, a.pverts + G.vert_begin, G.vert_count, sv);
   __syncthreads();
@@ -371,7 +393,7 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
       for (; q < nch; ++q) {
         const int s = q % S;
         if (!mbar_wait(&empty[s], (unsigned)(q / S - 1) & 1u, a.wait_cycles)) break;   // the consumers stopped
-        issue_chunk<REV>(a, sch[REV ? nch - 1 - q : q], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
+        issue_chunk<REV, TM>(a, sch[REV ? nch - 1 - q : q], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
       }
       if (q < nch)   // gave up: let the copies in flight land before the CTA ends
         for (int j = q - S; j < q; ++j)
