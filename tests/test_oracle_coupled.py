@@ -146,3 +146,20 @@ def test_coupled_sweep_sensitivity_on_stiff_tets(oracle_mod):
     assert growth((1e-5, 1e-3), True) > 30.0
     assert growth((1e-5, 1e-3), False) < 1.0
     assert growth((1e-4, 1e-2), True) < 1.0
+
+
+def test_coupled_update_falls_back_to_c_h_when_c_d_is_degenerate(oracle_mod):
+    """A tet collapsed to a point has F = 0, so C_D = |F| has no gradient: the pair update
+    is then the single C_H update (which moves nothing either, cof F = 0, but builds
+    lambda_H against alpha~_H), and lambda_D is left alone."""
+    rng = np.random.default_rng(24)
+    r = _tet(rng)
+    q = np.tile(rng.standard_normal(3), 4)
+    w = np.ones(4)
+    at = np.array([0.2, 0.3])
+    lam = np.array([0.1, -0.4])
+    q2, lam2 = oracle_mod.project_pair(q, w, r, lam, at)
+    q1, lh = oracle_mod.project_one("tet_h", q, w, r, lam[0], at[0])
+    assert np.array_equal(q2, q1) and lam2[0] == lh and lam2[1] == lam[1]
+    CH = oracle_mod.constraint("tet_h", q, r)[0]
+    assert abs(lh - (lam[0] + (-CH - at[0] * lam[0]) / at[0])) < 1e-12
