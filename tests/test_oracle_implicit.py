@@ -172,3 +172,27 @@ def test_membrane_projected_block_is_psd_with_translations_in_its_null_space():
         assert np.linalg.eigvalsh(B).min() > -1e-10 * max(1.0, np.abs(B).max())
         t = np.tile(rng.standard_normal(3), 3)
         assert np.abs(B @ t).max() < 1e-9 * max(1.0, np.abs(B).max())
+
+
+def test_membrane_alpha_is_the_inverse_scaled_stiffness():
+    """The implicit oracle's membrane compliance: alpha~ (A K dt^2) = I for the printed
+    inverse-compliance matrix A [C00 C01; C01 C11; C22], and its stiffness gradient is the
+    chain rule through it (central differences of <G, alpha~(K)>)."""
+    K, A, dt = np.array([50.0, 20.0, 5.0, 10.0]), 0.4, 0.05
+    Km = np.array([[K[0], K[2], 0.0], [K[2], K[1], 0.0], [0.0, 0.0, K[3]]])
+    at = implicit._memb_alpha(K, A, dt)
+    assert np.allclose(at @ (A * Km * dt * dt), np.eye(3), atol=1e-12)
+    sc = scenes.membrane_cloth(2)
+    sc.memb_stiffness = np.array([K, K * 1.5])
+    Gbar = np.random.default_rng(3).standard_normal((2, 3, 3))
+    g = implicit._memb_alpha_grad(sc, Gbar, None, dt)
+    areas = [a for _, a in implicit._memb_rest(sc)]
+    for t in range(2):
+        for p in range(4):
+            h = 1e-6 * sc.memb_stiffness[t, p]
+            kp, km = sc.memb_stiffness[t].copy(), sc.memb_stiffness[t].copy()
+            kp[p] += h
+            km[p] -= h
+            fd = (np.sum(Gbar[t] * implicit._memb_alpha(kp, areas[t], dt))
+                  - np.sum(Gbar[t] * implicit._memb_alpha(km, areas[t], dt))) / (2 * h)
+            assert abs(fd - g[t, p]) <= 1e-6 * abs(g[t, p]) + 1e-12

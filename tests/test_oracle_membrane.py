@@ -226,3 +226,40 @@ def test_membrane_coloring(oracle_mod):
     assert np.array_equal(np.sort(tiled.color_order), np.sort(scenes.membrane_cloth(40).color_order))
     K = sc.memb_stiffness.astype(np.float64)
     assert np.all(K[:, 0] * K[:, 1] - K[:, 2] ** 2 > 0) and np.all(K[:, 3] > 0)
+
+
+def _one_triangle(K, w, vx, dt):
+    """Unit right triangle in the x-z plane, (u, v) = (x, z), vertices 0 and 2 pinned,
+    vertex 1 moving along the warp."""
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    return scenes.Scene(rest_x=x, inv_mass=np.array([0.0, w, 0.0]), dist_idx=np.zeros((0, 2), np.int32),
+                        bend_idx=np.zeros((0, 4), np.int32), tet_idx=np.zeros((0, 4), np.int32), tet_gamma=np.zeros(0),
+                        color_offsets=np.array([0, 1], np.int32), color_order=np.array([0], np.int32), x0=x.copy(),
+                        v0=np.array([[0.0, 0.0, 0.0], [vx, 0.0, 0.0], [0.0, 0.0, 0.0]]), compliance=np.zeros(0),
+                        dt=dt, gravity=(0.0, 0.0, 0.0), steps=1, iters=1,
+                        memb_idx=np.array([[0, 1, 2]], np.int32), memb_uv=x[:, [0, 2]][None],
+                        memb_stiffness=np.array([K], np.float64))
+
+
+def test_scene_level_membrane_update_closed_form(oracle_mod):
+    """One step, one iteration of a scene with one triangle: the rest area (1/2), the
+    map K -> alpha~ = (A K)^-1 / dt^2 with C01 != 0 and the warp/weft assignment all enter
+    the closed form.  At the free vertex only E_uu and the shear row have gradients
+    (s e_x and e_z); the shear row has no residual, so S reduces to the 2x2 of (E_uu, E_vv)
+    rows [[w s^2 + a00, a01], [a01, a11]] against (-C_uu, 0): the E_vv multiplier is
+    -a01 dlambda_uu / a11 (its sign follows alpha~'s off-diagonal)."""
+    K = (800.0, 300.0, 200.0, 150.0)
+    w, vx, dt = 2.0, 3.0, 0.05
+    sc = _one_triangle(K, w, vx, dt)
+    xs, _ = oracle_mod.forward(sc)
+    lam = oracle_mod.forward_memb_multipliers(sc)[0, 0]
+    Km = np.array([[K[0], K[2], 0.0], [K[2], K[1], 0.0], [0.0, 0.0, K[3]]])
+    at = np.linalg.inv(0.5 * Km) / dt ** 2
+    s = 1.0 + vx * dt
+    C = 0.5 * (s * s - 1.0)
+    S2 = np.array([[w * s * s + at[0, 0], at[0, 1]], [at[0, 1], at[1, 1]]])
+    dl = np.linalg.solve(S2, [-C, 0.0])
+    assert abs(xs[1, 1, 0] - (s + w * s * dl[0])) < 1e-13
+    assert np.abs(xs[1, 1, 1:]).max() < 1e-15 and np.allclose(xs[1, [0, 2]], sc.x0[[0, 2]])
+    assert np.allclose(lam, [dl[0], dl[1], 0.0], rtol=1e-12, atol=1e-15)
+    assert abs(dl[1]) > 1e-6 * abs(dl[0])                 # the off-diagonal is exercised
