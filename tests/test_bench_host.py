@@ -35,3 +35,19 @@ def test_material_workload_sizes(kind, V, rows):
     if kind == "membrane":
         assert sc.collider_flags == scenes.COLLIDE_PLANE and sc.plane_h == -0.6
         assert np.all(sc.inv_mass > 0)
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the oracle on the host cores) prints one line with the keys the
+    driver reads; its e2e moves no bytes and its cpu_baseline describes the same run."""
+    class Args:
+        cpu_window, warmup, steps = 8, 0, 1
+
+    d = bench.run_reference(Args, 1, 0)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert bench.run_reference(Args, 2, 1) is None
