@@ -294,8 +294,9 @@ xpbd_status xpbd_material_gradient(xpbd_handle h, int32_t n_materials, const int
                                    void* stream);
 
 /* Synchronise `stream` and report (then clear) the device error word of the handle:
-   XPBD_ERR_TIMEOUT if, since the last check, a bounded wait of a phase kernel gave up;
-   XPBD_ERR_NONFINITE if a call was given a negative or non-finite compliance or a step
+   XPBD_ERR_TIMEOUT if, since the last check, a bounded wait of a phase kernel gave up (the
+   message says whether that kernel also gave up waiting for its own copies in flight before
+   returning, after which the CUDA context may be unusable); XPBD_ERR_NONFINITE if a call was given a negative or non-finite compliance or a step
    produced a non-finite state. */
 xpbd_status xpbd_sync_status(xpbd_handle h, void* stream);
 
@@ -317,17 +318,22 @@ xpbd_status xpbd_selftest_wait_timeout(xpbd_handle h, void* stream);
    handle's constraint records) and afterwards calls this instead of xpbd_forward, which
    allocates its working state on first use.
 
-   Same arguments, steps and results as xpbd_forward.  The working state (predicted
-   positions, multipliers, contact state) lives in one fixed device array inside the
-   library, sized for at most XPBD_STATIC_MAX_VERTICES vertices and
-   XPBD_STATIC_MAX_CONSTRAINTS constraints (about 3.1 MiB, held by every GPU that loads
-   the library until the process exits); larger models get XPBD_ERR_BOUNDS before any GPU
-   work.  The call allocates nothing: no cudaMalloc, cudaFree or allocating library call.
-   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
-   with that device current; make that first call before any stream capture.  Each device
-   has one copy of the array, shared by every call on that device and keeping what the last
-   call left in it: calls whose GPU work overlaps in time on one device (different streams,
-   or different handles) race on it and give wrong results, so serialise them. */
+   Same arguments, steps and results as xpbd_forward (it always runs one launch per color;
+   with a handle in the multi-color phase mode the results agree with xpbd_forward's to
+   float32 rounding).  The working state (predicted positions, multipliers, contact state)
+   lives in one fixed device array inside the library, sized for at most
+   XPBD_STATIC_MAX_VERTICES vertices and XPBD_STATIC_MAX_CONSTRAINTS multiplier slots (one
+   per constraint, four per membrane; about 3.1 MiB, held by every GPU that loads the
+   library until the process exits); larger models get XPBD_ERR_BOUNDS before any GPU work.
+   The call allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Set-up
+   happens in xpbd_create: with the handle's device current, it looks up the array's device
+   address (cudaGetSymbolAddress, which under CUDA's lazy module loading is also when the
+   array's memory is taken) and stores it in the handle.  Each device has one copy of the
+   array, shared by every call on that device and keeping what the last call left in it
+   (nothing in it needs clearing: each step overwrites the positions and contact flags, and
+   each step's first iteration reads no multiplier); calls whose GPU work overlaps in time
+   on one device (different streams, or different handles) race on it and give wrong
+   results, so serialise them. */
 #define XPBD_STATIC_MAX_VERTICES 65536
 #define XPBD_STATIC_MAX_CONSTRAINTS 393216
 xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,

@@ -290,7 +290,8 @@ class Solver:
                        checkpoints: torch.Tensor, stream=None) -> torch.Tensor:
         """xpbd_forward_static: the forward simulation without any device allocation by the
         library, for callers that cannot allocate while they simulate (the checkpoint buffer
-        is the caller's).  Limited to STATIC_MAX_VERTICES / STATIC_MAX_CONSTRAINTS; calls
+        is the caller's).  Limited to STATIC_MAX_VERTICES vertices and STATIC_MAX_CONSTRAINTS
+        multiplier slots (one per constraint, four per membrane); calls
         whose GPU work overlaps on one device race on the library's shared working array."""
         p = params.c_struct()
         _check(lib().xpbd_forward_static(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),

@@ -753,7 +753,7 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   h->coupled = coupled;
   h->nm = nm;
   h->mslot = (int)(((size_t)std::max(m, 1) + 3) / 4 * 4);
-  h->slots = (size_t)h->mslot + ((size_t)4 * nm + 3) / 4 * 4;
+  h->slots = h->color_slots();
   h->mtape = (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt;
   h->tape_slots = h->tape_per_iter();
   h->n_rec[0] = nd; h->n_rec[1] = nb; h->n_rec[2] = nt; h->n_rec[3] = nt;
@@ -907,6 +907,15 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
       xpbd_destroy(h);
       return pst;
     }
+  }
+  // The allocation-free forward's working array lives in this file's device module.  With
+  // CUDA's lazy module loading that module (and the array's memory) is loaded on first use,
+  // so it is looked up here, at set-up, where allocating is allowed: xpbd_forward_static
+  // then only reads the stored address.
+  xpbd_status sst = static_scratch_address(&h->static_base);
+  if (sst != XPBD_OK) {
+    xpbd_destroy(h);
+    return sst;
   }
   *out = h;
   return XPBD_OK;
@@ -1478,16 +1487,18 @@ xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t ste
   g_err.clear();
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
-  if (h->V > XPBD_STATIC_MAX_VERTICES || h->slots > (size_t)XPBD_STATIC_MAX_CONSTRAINTS)
+  // the one-launch-per-color sweep this entry point runs needs one multiplier slot per
+  // constraint and four per membrane (rounded up to a multiple of 4 per block)
+  const size_t need = h->color_slots();
+  if (h->V > XPBD_STATIC_MAX_VERTICES || need > (size_t)XPBD_STATIC_MAX_CONSTRAINTS)
     return fail(XPBD_ERR_BOUNDS, "xpbd_forward_static supports at most " + std::to_string(XPBD_STATIC_MAX_VERTICES) +
                                      " vertices and " + std::to_string(XPBD_STATIC_MAX_CONSTRAINTS) +
-                                     " constraints; this model has " + std::to_string(h->V) + " and " +
-                                     std::to_string(h->m));
+                                     " multiplier slots (one per constraint, four per membrane); this model has " +
+                                     std::to_string(h->V) + " vertices and needs " + std::to_string(need) + " slots");
   if (h->V > 0 && (!x0 || !v0 || !ck)) return fail(XPBD_ERR_INVALID, "x0/v0/checkpoints NULL");
   if (h->V == 0) return XPBD_OK;
-  void* base = nullptr;
-  st = static_scratch_address(&base);
-  if (st != XPBD_OK) return st;
+  void* base = h->static_base;
+  if (!base) return fail(XPBD_ERR_CUDA, "the fixed working array has no device address");
   float4* P = reinterpret_cast<float4*>(base);
   float* lam = reinterpret_cast<float*>(static_cast<char*>(base) + kStaticPosBytes);
   float2* lamc = reinterpret_cast<float2*>(static_cast<char*>(base) + kStaticPosBytes + kStaticLamBytes);
@@ -1589,6 +1600,9 @@ xpbd_status xpbd_sync_status(xpbd_handle h, void* stream) {
   int err = 0;
   CU_TRY(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CU_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+  if (err & 16)
+    return fail(XPBD_ERR_TIMEOUT, "a phase kernel gave up waiting for its own copies in flight before it returned; "
+                                  "the CUDA context may be unusable");
   if (err & 4) return fail(XPBD_ERR_TIMEOUT, "a phase kernel gave up waiting for its staged copies");
   if (err & 8) return fail(XPBD_ERR_INVALID, "a tet material id is out of range");
   if (err & 2)

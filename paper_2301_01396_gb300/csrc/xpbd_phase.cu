@@ -389,15 +389,21 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
   __syncthreads();
   if (threadIdx.x >= kPhaseBlock) {   // producer warp
     if (threadIdx.x == kPhaseBlock && !a.no_issue) {
-      int q = S;
-      for (; q < nch; ++q) {
-        const int s = q % S;
-        if (!mbar_wait(&empty[s], (unsigned)(q / S - 1) & 1u, a.wait_cycles)) break;   // the consumers stopped
-        issue_chunk<REV, TM>(a, sch[REV ? nch - 1 - q : q], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
+      int issued = S < nch ? S : nch;
+      for (; issued < nch; ++issued) {
+        const int s = issued % S;
+        if (!mbar_wait(&empty[s], (unsigned)(issued / S - 1) & 1u, a.wait_cycles)) break;   // the consumers stopped
+        issue_chunk<REV, TM>(a, sch[REV ? nch - 1 - issued : issued], stage + (size_t)s * a.slot_bytes, &full[s],
+                             first, last);
       }
-      if (q < nch)   // gave up: let the copies in flight land before the CTA ends
-        for (int j = q - S; j < q; ++j)
-          if (j >= 0) mbar_wait(&full[j % S], (unsigned)(j / S) & 1u, a.wait_cycles);
+      // Whether it issued every chunk or gave up, the CTA must not end while a copy into its
+      // shared memory is in flight (the consumers may have stopped early): wait for the last
+      // stages issued.  A drain that runs out latches bit 5: the context may be unusable.
+      for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+        if (!mbar_wait(&full[j % S], (unsigned)(j / S) & 1u, a.wait_cycles)) {
+          atomicOr(a.err, 16);
+          break;
+        }
     }
     return;
   }

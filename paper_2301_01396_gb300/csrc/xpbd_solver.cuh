@@ -125,6 +125,11 @@ struct xpbd_solver {
   // Per-constraint slot space of the multiplier / adjoint buffers and float4 entries of
   // one iteration's tape: large enough for the per-color layout and the padded phase layout.
   size_t slots = 0, tape_slots = 0;
+  // Multiplier slots of the one-launch-per-color layout alone (no phase padding).
+  size_t color_slots() const { return (size_t)mslot + ((size_t)4 * nm + 3) / 4 * 4; }
+  // Device address of the allocation-free forward's fixed working array on the device this
+  // handle was created on (looked up by xpbd_create).
+  void* static_base = nullptr;
   size_t tape_per_iter() const {  // float4 entries per iteration, per-color layout
     return (size_t)2 * nd + (size_t)4 * nb + (size_t)8 * nt + (size_t)3 * nm;
   }

@@ -40,6 +40,56 @@ def rel_err(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
+# Element-wise gradient bound.  Every entry j of a gradient group must satisfy
+#   |g_j - r_j| <= ELEM_TOL * (|r_j| + ELEM_FLOOR * max_i |r_i|),
+# i.e. 1 % relative error for entries within three decades of the group's largest, and an
+# absolute 1e-5 * max|r| below that.  The group-norm bound (1e-3) can hide a wrong
+# gradient on a few boundary hinges, pinned-vertex springs or contact vertices under large
+# entries; a wrong update there is O(1) relative, 100x this bound.  Entries far below the
+# group's scale carry float32 cancellation of large terms (their absolute error is set by
+# the group's scale, not their own), hence the floor.
+ELEM_TOL = 1e-2
+ELEM_FLOOR = 1e-3
+
+
+def elem_err(a, b, floor=ELEM_FLOOR):
+    """max_j |a_j - b_j| / (|b_j| + floor * max|b|): the worst entry's error relative to its
+    own size, floored at `floor` times the group's largest entry."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    if a.size == 0:
+        return 0.0
+    s = np.abs(b).max()
+    if s == 0:
+        return float(np.abs(a).max())
+    return float(np.max(np.abs(a - b) / (np.abs(b) + floor * s)))
+
+
+# Where float32 state rounding alone moves a gradient past the bounds above (stiff or
+# near-resolution strains), the bounds become these multiples of the "floor": the same
+# errors of the oracle's own float32-rounding emulation (oracle.fp32_rounding).
+FLOOR_FACTOR = 1.25
+ELEM_FLOOR_FACTOR = 2.0
+
+
+def check_grad(tag, got, ref, tol=1e-3, elem_tol=ELEM_TOL, ref32=None):
+    """Assert a gradient group against the oracle's: relative L2 error below `tol` and every
+    entry within the element-wise bound (with `ref32`, the oracle's float32-rounding run,
+    both bounds are at least FLOOR_FACTOR / ELEM_FLOOR_FACTOR times its errors).  Prints
+    the errors (one PARITY line per group)."""
+    got = np.asarray(got, np.float64).reshape(np.shape(ref))
+    e, ee = rel_err(got, ref), elem_err(got, ref)
+    msg = f"PARITY {tag}: rel {e:.3e} elem {ee:.3e}"
+    if ref32 is not None:
+        f, fe = rel_err(ref32, ref), elem_err(ref32, ref)
+        tol, elem_tol = max(tol, FLOOR_FACTOR * f), max(elem_tol, ELEM_FLOOR_FACTOR * fe)
+        msg += f" (float32 floor: rel {f:.3e} elem {fe:.3e})"
+    print(msg)
+    assert e < tol, f"{tag}: relative error {e:.3e} (bound {tol:.3e})"
+    assert ee < elem_tol, f"{tag}: element-wise error {ee:.3e} (bound {elem_tol:.3e})"
+    return e, ee
+
+
 def _contact_values(sc, xs, vs):
     out = []
     g = np.asarray(sc.gravity)

@@ -74,6 +74,40 @@ def small_sphere_cloth(n=6, *, steps=4, iters=3, seed=4):
     return sc
 
 
+def grid_window(full, n, i0, j0, w):
+    """The sub-scene of an n x n grid scene on vertices i0 <= i < i0+w, j0 <= j < j0+w,
+    keeping every constraint whose vertices all lie inside, in the same color order."""
+    ii = np.arange(full.V) % n
+    jj = np.arange(full.V) // n
+    inside = (ii >= i0) & (ii < i0 + w) & (jj >= j0) & (jj < j0 + w)
+    local = np.full(full.V, -1, np.int64)
+    local[inside] = (jj[inside] - j0) * w + (ii[inside] - i0)
+    keep_d = inside[full.dist_idx].all(1)
+    keep_b = inside[full.bend_idx].all(1)
+    nd, nb = int(keep_d.sum()), int(keep_b.sum())
+    new_id = np.full(full.m, -1, np.int64)
+    new_id[:full.n_dist][keep_d] = np.arange(nd)
+    new_id[full.n_dist:][keep_b] = nd + np.arange(nb)
+    offs = [0]
+    order = []
+    for c in range(full.n_colors):
+        ids = full.color_order[full.color_offsets[c]:full.color_offsets[c + 1]]
+        ids = new_id[ids]
+        ids = ids[ids >= 0]
+        order.append(ids)
+        offs.append(offs[-1] + ids.shape[0])
+    sel = np.nonzero(inside)[0][np.argsort(local[inside])]
+    comp = np.concatenate([full.compliance[:full.n_dist][keep_d], full.compliance[full.n_dist:][keep_b]])
+    sub = full.with_(rest_x=full.rest_x[sel], inv_mass=full.inv_mass[sel],
+                     dist_idx=local[full.dist_idx[keep_d]].astype(np.int32),
+                     bend_idx=local[full.bend_idx[keep_b]].astype(np.int32),
+                     color_offsets=np.asarray(offs, np.int32),
+                     color_order=np.concatenate(order).astype(np.int32),
+                     x0=full.x0[sel], v0=full.v0[sel], compliance=comp,
+                     f_vertex=None if full.f_vertex is None else full.f_vertex[sel])
+    return sub, sel, np.nonzero(keep_d)[0], full.n_dist + np.nonzero(keep_b)[0]
+
+
 def rel(a, b):
     a = np.asarray(a, np.float64).ravel()
     b = np.asarray(b, np.float64).ravel()

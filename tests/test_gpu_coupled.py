@@ -7,7 +7,7 @@ import torch
 import oracle
 from paper_2301_01396_gb300 import binding, scenes
 from tests import helpers
-from tests.gpu_common import gpu_adjoint, gpu_forward, rel_err, to_dev
+from tests.gpu_common import check_grad, gpu_adjoint, gpu_forward, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -38,8 +38,7 @@ def test_coupled_block_matches_oracle():
     ref = oracle.adjoint(sc, seeds)
     got, _ = gpu_adjoint(sc, seeds)
     for k in ("compliance", "x0", "v0", "f_vertex"):
-        e = rel_err(got[k], ref[k])
-        assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
+        check_grad(f"coupled_block {k}", got[k], ref[k], GRAD_TOL)
 
 
 def test_coupled_differs_from_one_at_a_time():
@@ -75,7 +74,7 @@ def test_coupled_phase_plan_matches_per_color_and_oracle():
         assert np.abs(xs - xs_ref).max() < POS_TOL, mode
         out[mode] = (xs, {k: v.cpu().numpy() for k, v in gr.items()})
         for k, v in out[mode][1].items():
-            assert rel_err(v, ref[k]) < GRAD_TOL, (mode, k)
+            check_grad(f"coupled_mode{mode} {k}", v, ref[k], GRAD_TOL)
     assert np.abs(out[2][0] - out[1][0]).max() <= 1e-6
     for k in out[2][1]:
         assert rel_err(out[2][1][k], out[1][1][k]) <= 2e-4, k

@@ -9,7 +9,7 @@ import oracle
 from oracle import implicit
 from paper_2301_01396_gb300 import binding, scenes
 from tests import helpers
-from tests.gpu_common import contact_margin, gpu_forward, rel_err, to_dev
+from tests.gpu_common import check_grad, contact_margin, gpu_forward, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -61,8 +61,7 @@ def test_implicit_adjoint_matches_oracle(name, pd):
     solver.sync_status()
     assert all(0 < n < 5000 for n in its), its
     for k in keys:
-        e = rel_err(got[k].cpu().numpy().reshape(ref[k].shape), ref[k])
-        assert e < GRAD_TOL, f"{k}: relative error {e:.3e}"
+        check_grad(f"implicit {name} pd{int(pd)} {k}", got[k].cpu().numpy(), ref[k], GRAD_TOL)
 
 
 def test_phase_plan_handle_gives_the_same_gradient():

@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2301_01396_gb300 import binding, scenes
 from tests import helpers
-from tests.gpu_common import rel_err, to_dev
+from tests.gpu_common import check_grad, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -96,7 +96,7 @@ def test_matches_oracle():
     assert abs(got["loss"][0] - 0.5 * np.sum(seed ** 2)) <= 1e-4 * got["loss"][0]
     ref = oracle.adjoint(sc, {sc.steps: scenes.f32(seed)})
     for k in ("compliance", "x0", "v0", "f_vertex"):
-        assert rel_err(got[k], ref[k]) < GRAD_TOL, k
+        check_grad(f"serving {k}", got[k], ref[k], GRAD_TOL)
 
 
 def test_admission_waits_for_memory():
