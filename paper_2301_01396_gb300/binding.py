@@ -128,13 +128,20 @@ def _stream(stream=None) -> C.c_void_p:
     return C.c_void_p(s.cuda_stream)
 
 
-def _ptr(t: Optional[torch.Tensor]):
+F32, F64, I32 = torch.float32, torch.float64, torch.int32
+
+
+def _ptr(t: Optional[torch.Tensor], dtype: Optional[torch.dtype] = None):
+    """Device pointer of a contiguous CUDA tensor (of `dtype`, when given: the C ABI reads
+    raw memory, so a tensor of another type would be misread, not converted)."""
     if t is None:
         return None
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected a {dtype} tensor, got {t.dtype}")
     return C.c_void_p(t.data_ptr())
 
 
@@ -159,11 +166,11 @@ class Params:
             if t is not None and t.dtype != torch.float32:
                 raise ValueError("params tensors must be float32")
         return XpbdParams(dt=self.dt, gravity=(C.c_float * 3)(*self.gravity),
-                          compliance=_ptr(self.compliance), f_global=_ptr(self.f_global),
-                          f_vertex=_ptr(self.f_vertex), collider_flags=int(self.collider_flags),
+                          compliance=_ptr(self.compliance, F32), f_global=_ptr(self.f_global, F32),
+                          f_vertex=_ptr(self.f_vertex, F32), collider_flags=int(self.collider_flags),
                           plane_h=float(self.plane_h), sphere=(C.c_float * 4)(*[float(v) for v in self.sphere]),
                           contact_compliance=float(self.contact_compliance), thickness=float(self.thickness),
-                          f_vertex_steps=_ptr(self.f_vertex_steps), memb_stiffness=_ptr(self.memb_stiffness))
+                          f_vertex_steps=_ptr(self.f_vertex_steps, F32), memb_stiffness=_ptr(self.memb_stiffness, F32))
 
 
 def sparse_slots(steps: int, stride: int) -> int:
@@ -268,8 +275,8 @@ class Solver:
                 checkpoints: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         ck = self.new_checkpoints(steps, x0.device) if checkpoints is None else checkpoints
         p = params.c_struct()
-        _check(lib().xpbd_forward(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
-                                  _ptr(ck), _stream(stream)))
+        _check(lib().xpbd_forward(self._h, C.byref(p), int(steps), int(iters), _ptr(x0, F32), _ptr(v0, F32),
+                                  _ptr(ck, F32), _stream(stream)))
         return ck
 
     def forward_sparse(self, params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
@@ -282,8 +289,8 @@ class Solver:
         ck = (torch.empty((n, 2, self.V, 4), dtype=torch.float32, device=x0.device)
               if checkpoints is None else checkpoints)
         p = params.c_struct()
-        _check(lib().xpbd_forward_sparse(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
-                                         int(stride), _ptr(ck), _stream(stream)))
+        _check(lib().xpbd_forward_sparse(self._h, C.byref(p), int(steps), int(iters), _ptr(x0, F32), _ptr(v0, F32),
+                                         int(stride), _ptr(ck, F32), _stream(stream)))
         return ck
 
     def forward_static(self, params: Params, steps: int, iters: int, x0: torch.Tensor, v0: torch.Tensor,
@@ -294,14 +301,14 @@ class Solver:
         multiplier slots (one per constraint, four per membrane); calls
         whose GPU work overlaps on one device race on the library's shared working array."""
         p = params.c_struct()
-        _check(lib().xpbd_forward_static(self._h, C.byref(p), int(steps), int(iters), _ptr(x0), _ptr(v0),
-                                         _ptr(checkpoints), _stream(stream)))
+        _check(lib().xpbd_forward_static(self._h, C.byref(p), int(steps), int(iters), _ptr(x0, F32), _ptr(v0, F32),
+                                         _ptr(checkpoints, F32), _stream(stream)))
         return checkpoints
 
     def read_state(self, checkpoints: torch.Tensor, step: int, stream=None):
         x = torch.empty((self.V, 3), dtype=torch.float32, device=checkpoints.device)
         v = torch.empty_like(x)
-        _check(lib().xpbd_read_state(self._h, _ptr(checkpoints), int(step), _ptr(x), _ptr(v), _stream(stream)))
+        _check(lib().xpbd_read_state(self._h, _ptr(checkpoints, F32), int(step), _ptr(x, F32), _ptr(v, F32), _stream(stream)))
         return x, v
 
     def loss(self, checkpoints: torch.Tensor, targets: dict, stream=None):
@@ -311,8 +318,8 @@ class Solver:
         seeds = torch.empty_like(tg)
         out = torch.empty(1, dtype=torch.float64, device=checkpoints.device)
         ks = (C.c_int32 * len(keys))(*keys)
-        _check(lib().xpbd_loss(self._h, _ptr(checkpoints), len(keys), ks, _ptr(tg), _ptr(out),
-                               _ptr(seeds), _stream(stream)))
+        _check(lib().xpbd_loss(self._h, _ptr(checkpoints, F32), len(keys), ks, _ptr(tg, F32), _ptr(out, F64),
+                               _ptr(seeds, F32), _stream(stream)))
         return out, seeds
 
     def adjoint(self, params: Params, steps: int, iters: int, checkpoints: torch.Tensor, seeds: dict,
@@ -329,19 +336,19 @@ class Solver:
                       memb_stiffness=(self.n_memb, 4))
         if out is None:
             out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
-        g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
-                      d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
-                      d_f_vertex=_ptr(out.get("f_vertex")), d_collider=_ptr(out.get("collider")),
-                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")),
-                      d_memb_stiffness=_ptr(out.get("memb_stiffness")))
+        g = XpbdGrads(d_compliance=_ptr(out.get("compliance"), F64), d_x0=_ptr(out.get("x0"), F64),
+                      d_v0=_ptr(out.get("v0"), F64), d_f_global=_ptr(out.get("f_global"), F64),
+                      d_f_vertex=_ptr(out.get("f_vertex"), F64), d_collider=_ptr(out.get("collider"), F64),
+                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps"), F64),
+                      d_memb_stiffness=_ptr(out.get("memb_stiffness"), F64))
         p = params.c_struct()
         ks = (C.c_int32 * max(len(keys), 1))(*keys)
         if stride is None:
-            _check(lib().xpbd_adjoint(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
-                                      len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), _stream(stream)))
+            _check(lib().xpbd_adjoint(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints, F32),
+                                      len(keys), ks, _ptr(sd, F32), _ptr(seed_dv_T, F32), C.byref(g), _stream(stream)))
         else:
-            _check(lib().xpbd_adjoint_sparse(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
-                                             int(stride), len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g),
+            _check(lib().xpbd_adjoint_sparse(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints, F32),
+                                             int(stride), len(keys), ks, _ptr(sd, F32), _ptr(seed_dv_T, F32), C.byref(g),
                                              _stream(stream)))
         return out
 
@@ -357,18 +364,18 @@ class Solver:
         shapes = dict(compliance=(self.m,), x0=(self.V, 3), v0=(self.V, 3), f_global=(max(steps, 1), 3),
                       f_vertex=(self.V, 3), f_vertex_steps=(max(steps, 1), self.V, 3), memb_stiffness=(self.n_memb, 4))
         out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
-        g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")),
-                      d_v0=_ptr(out.get("v0")), d_f_global=_ptr(out.get("f_global")),
-                      d_f_vertex=_ptr(out.get("f_vertex")), d_collider=None,
-                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps")),
-                      d_memb_stiffness=_ptr(out.get("memb_stiffness")))
+        g = XpbdGrads(d_compliance=_ptr(out.get("compliance"), F64), d_x0=_ptr(out.get("x0"), F64),
+                      d_v0=_ptr(out.get("v0"), F64), d_f_global=_ptr(out.get("f_global"), F64),
+                      d_f_vertex=_ptr(out.get("f_vertex"), F64), d_collider=None,
+                      d_f_vertex_steps=_ptr(out.get("f_vertex_steps"), F64),
+                      d_memb_stiffness=_ptr(out.get("memb_stiffness"), F64))
         its = (C.c_int32 * max(steps, 1))()
         o = XpbdImplicitOpts(cg_tol=float(cg_tol), cg_max_iters=int(cg_max_iters), pd_project=int(bool(pd_project)),
                              cg_iters_out=C.cast(its, _ip))
         p = params.c_struct()
         ks = (C.c_int32 * max(len(keys), 1))(*keys)
-        _check(lib().xpbd_adjoint_implicit(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints),
-                                           len(keys), ks, _ptr(sd), _ptr(seed_dv_T), C.byref(g), C.byref(o),
+        _check(lib().xpbd_adjoint_implicit(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints, F32),
+                                           len(keys), ks, _ptr(sd, F32), _ptr(seed_dv_T, F32), C.byref(g), C.byref(o),
                                            _stream(stream)))
         return out, list(its)[:steps]
 
@@ -376,8 +383,8 @@ class Solver:
                             compliance: torch.Tensor, stream=None) -> torch.Tensor:
         """Writes the tet entries of `compliance` from materials mu = a^2, lambda = b^2
         (xpbd_material_compliance); returns `compliance`."""
-        _check(lib().xpbd_material_compliance(self._h, int(a.numel()), _ptr(tet_material), _ptr(a), _ptr(b),
-                                              _ptr(compliance), _stream(stream)))
+        _check(lib().xpbd_material_compliance(self._h, int(a.numel()), _ptr(tet_material, I32), _ptr(a, F32), _ptr(b, F32),
+                                              _ptr(compliance, F32), _stream(stream)))
         return compliance
 
     def material_gradient(self, tet_material: torch.Tensor, a: torch.Tensor, b: torch.Tensor,
@@ -385,8 +392,8 @@ class Solver:
         """(dL/da, dL/db) float64 from a compliance gradient (xpbd_material_gradient)."""
         da = torch.empty(a.numel(), dtype=torch.float64, device=a.device)
         db = torch.empty_like(da)
-        _check(lib().xpbd_material_gradient(self._h, int(a.numel()), _ptr(tet_material), _ptr(a), _ptr(b),
-                                            _ptr(d_compliance), _ptr(da), _ptr(db), _stream(stream)))
+        _check(lib().xpbd_material_gradient(self._h, int(a.numel()), _ptr(tet_material, I32), _ptr(a, F32), _ptr(b, F32),
+                                            _ptr(d_compliance, F64), _ptr(da, F64), _ptr(db, F64), _stream(stream)))
         return da, db
 
     def sync_status(self, stream=None):
@@ -508,11 +515,11 @@ class Server:
                       f_vertex=(solver.V, 3), collider=(5,))
         out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
         out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
-        g = XpbdGrads(d_compliance=_ptr(out.get("compliance")), d_x0=_ptr(out.get("x0")), d_v0=_ptr(out.get("v0")),
-                      d_f_global=_ptr(out.get("f_global")), d_f_vertex=_ptr(out.get("f_vertex")),
-                      d_collider=_ptr(out.get("collider")))
+        g = XpbdGrads(d_compliance=_ptr(out.get("compliance"), F64), d_x0=_ptr(out.get("x0"), F64), d_v0=_ptr(out.get("v0"), F64),
+                      d_f_global=_ptr(out.get("f_global"), F64), d_f_vertex=_ptr(out.get("f_vertex"), F64),
+                      d_collider=_ptr(out.get("collider"), F64))
         req = XpbdRequest(handle=solver.handle, params=params.c_struct(), steps=int(steps), iters=int(iters),
-                          x0=_ptr(x0), v0=_ptr(v0), target=_ptr(target), loss_out=_ptr(out["loss"]), grads=g)
+                          x0=_ptr(x0, F32), v0=_ptr(v0, F32), target=_ptr(target, F32), loss_out=_ptr(out["loss"], F64), grads=g)
         t = C.c_uint64()
         _check(lib().xpbd_server_submit(self._s, C.byref(req), C.byref(t)))
         self._live[t.value] = (solver, params, x0, v0, target, out)

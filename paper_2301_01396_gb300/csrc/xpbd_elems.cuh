@@ -280,6 +280,11 @@ struct Quad<1> {
                              const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
     bend_grad_rel<df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), g1, g2, g3);
   }
+  // H u alone (relative rows 1..3), in closed form
+  __device__ static void hvp_f(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
+                               const f3& du2, const f3& du3, f3& h1, f3& h2, f3& h3) {
+    bend_hvp_rel(e1, e2, e3, du1, du2, du3, h1, h2, h3);
+  }
 };
 
 template <bool HYDRO>
@@ -295,6 +300,14 @@ struct TetQuad {
                              const f3& du2, const f3& du3, d3& g1, d3& g2, d3& g3) {
     tet_grad_rel<HYDRO, df>(mkd3(e1, du1), mkd3(e2, du2), mkd3(e3, du3), r.B, g1, g2, g3, nullptr,
                             r.gamma);
+  }
+  __device__ static void hvp_f(const Rec& r, const f3& e1, const f3& e2, const f3& e3, const f3& du1,
+                               const f3& du2, const f3& du3, f3& h1, f3& h2, f3& h3) {
+    d3 g1, g2, g3;
+    hvp(r, e1, e2, e3, du1, du2, du3, g1, g2, g3);
+    h1 = dpart(g1);
+    h2 = dpart(g2);
+    h3 = dpart(g3);
   }
 };
 template <> struct Quad<2> : TetQuad<true> {};
@@ -500,9 +513,8 @@ __device__ __forceinline__ float2 vjp_quad_core(const typename Quad<KIND>::Rec& 
       const f3 du1 = (xb1 * dl - g1 * c2) * w1 - u0;
       const f3 du2 = (xb2 * dl - g2 * c2) * w2 - u0;
       const f3 du3 = (xb3 * dl - g3 * c2) * w3 - u0;
-      d3 h1, h2, h3;
-      Quad<KIND>::hvp(r, e1, e2, e3, du1, du2, du3, h1, h2, h3);
-      const f3 hu1 = dpart(h1), hu2 = dpart(h2), hu3 = dpart(h3);
+      f3 hu1, hu2, hu3;
+      Quad<KIND>::hvp_f(r, e1, e2, e3, du1, du2, du3, hu1, hu2, hu3);
       const f3 hu0 = -(hu1 + hu2 + hu3);
       vstore<SH>(xbar + r.v[0], with_w(xb0 - g0 * sD + hu0, 0.f), pol);
       vstore<SH>(xbar + r.v[1], with_w(xb1 - g1 * sD + hu1, 0.f), pol);

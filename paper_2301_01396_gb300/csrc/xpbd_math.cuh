@@ -1,8 +1,9 @@
 // Per-constraint math of the XPBD step and of its reverse, in float32.
 //
 // Every function is __host__ __device__ so the same code runs in the kernels.  Gradients
-// are analytic; Hessian-vector products (needed by the reverse of one update) come from
-// one forward-mode dual evaluation of the analytic gradient (distance: closed form).
+// are analytic; Hessian-vector products (needed by the reverse of one update) are written
+// out in closed form for the distance and bending constraints, and come from one
+// forward-mode dual evaluation of the analytic gradient for tets.
 //
 // Constraint functions (Sec. 4.6, Sec. 5.1, Sec. 5.2 of DiffXPBD):
 //   distance  C = |x_a - x_b| - L
@@ -152,6 +153,35 @@ XHD void bend_grad_rel(const v3<S>& e, const v3<S>& a, const v3<S>& b, v3<S>& g1
   g2 = -(le * qA);
   g3 = -(le * qB);
   g1 = (dot(a, e) * ile) * qA + (dot(b, e) * ile) * qB;
+}
+
+// Hessian-vector product of the signed dihedral angle in the same relative coordinates:
+// the directional derivative of (g1, g2, g3) = bend_grad_rel(e, a, b) along (de, da, db),
+// written out by the chain rule (no dual numbers).  With nA = e x a, nB = b x e,
+// qA = nA/|nA|^2, cA = (a.e)/|e| (likewise B):
+//   dnA = de x a + e x da,              dnB = db x e + b x de
+//   dqA = dnA/|nA|^2 - 2 (qA.dnA) qA,   d|e| = (e.de)/|e|
+//   dcA = ((da.e) + (a.de) - cA d|e|)/|e|
+//   dg1 = dcA qA + cA dqA + dcB qB + cB dqB,   dg2 = -(d|e| qA + |e| dqA),   dg3 likewise.
+XHD void bend_hvp_rel(const f3& e, const f3& a, const f3& b, const f3& de, const f3& da, const f3& db, f3& h1,
+                      f3& h2, f3& h3) {
+  const f3 nA = cross(e, a);
+  const f3 nB = cross(b, e);
+  const float iA = 1.f / dot(nA, nA), iB = 1.f / dot(nB, nB);
+  const f3 qA = nA * iA, qB = nB * iB;
+  const float le = sqrtf(dot(e, e));
+  const float ile = 1.f / le;
+  const float cA = dot(a, e) * ile, cB = dot(b, e) * ile;
+  const f3 dnA = cross(de, a) + cross(e, da);
+  const f3 dnB = cross(db, e) + cross(b, de);
+  const f3 dqA = dnA * iA - qA * (2.f * dot(qA, dnA));
+  const f3 dqB = dnB * iB - qB * (2.f * dot(qB, dnB));
+  const float dle = dot(e, de) * ile;
+  const float dcA = (dot(da, e) + dot(a, de) - cA * dle) * ile;
+  const float dcB = (dot(db, e) + dot(b, de) - cB * dle) * ile;
+  h1 = qA * dcA + dqA * cA + qB * dcB + dqB * cB;
+  h2 = -(qA * dle + dqA * le);
+  h3 = -(qB * dle + dqB * le);
 }
 
 XHD bool bend_degenerate_rel(const f3& e, const f3& a, const f3& b) {

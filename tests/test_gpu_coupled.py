@@ -7,7 +7,7 @@ import torch
 import oracle
 from paper_2301_01396_gb300 import binding, scenes
 from tests import helpers
-from tests.gpu_common import check_grad, gpu_adjoint, gpu_forward, rel_err, to_dev
+from tests.gpu_common import check_grad, gpu_adjoint, gpu_forward, oracle_adjoint_floor, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -35,10 +35,10 @@ def test_coupled_block_matches_oracle():
     assert err < POS_TOL, f"max position error {err:.3e}"
     rng = np.random.default_rng(17)
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3))), 2: scenes.f32(rng.standard_normal((sc.V, 3)))}
-    ref = oracle.adjoint(sc, seeds)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds)
     got, _ = gpu_adjoint(sc, seeds)
     for k in ("compliance", "x0", "v0", "f_vertex"):
-        check_grad(f"coupled_block {k}", got[k], ref[k], GRAD_TOL)
+        check_grad(f"coupled_block {k}", got[k], ref[k], GRAD_TOL, ref32=ref32[k])
 
 
 def test_coupled_differs_from_one_at_a_time():
@@ -59,7 +59,7 @@ def test_coupled_phase_plan_matches_per_color_and_oracle():
     sc = _block()
     rng = np.random.default_rng(19)
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3)))}
-    ref = oracle.adjoint(sc, seeds)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds)
     xs_ref, _ = oracle.forward(sc)
     out = {}
     for mode in (2, 1):
@@ -74,7 +74,7 @@ def test_coupled_phase_plan_matches_per_color_and_oracle():
         assert np.abs(xs - xs_ref).max() < POS_TOL, mode
         out[mode] = (xs, {k: v.cpu().numpy() for k, v in gr.items()})
         for k, v in out[mode][1].items():
-            check_grad(f"coupled_mode{mode} {k}", v, ref[k], GRAD_TOL)
+            check_grad(f"coupled_mode{mode} {k}", v, ref[k], GRAD_TOL, ref32=ref32[k])
     assert np.abs(out[2][0] - out[1][0]).max() <= 1e-6
     for k in out[2][1]:
         assert rel_err(out[2][1][k], out[1][1][k]) <= 2e-4, k

@@ -53,6 +53,8 @@ def test_implicit_adjoint_matches_oracle(name, pd):
     rng = np.random.default_rng(8)
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3))), 1: scenes.f32(rng.standard_normal((sc.V, 3)))}
     ref = implicit.adjoint(sc, seeds, pd=pd)
+    with oracle.fp32_rounding():
+        ref32 = implicit.adjoint(sc, seeds, pd=pd)
     solver, p, ck, xs, _ = gpu_forward(sc)
     keys = KEYS + ("f_vertex_steps",) + (("memb_stiffness",) if sc.n_memb else ())
     got, its = solver.adjoint_implicit(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
@@ -61,7 +63,7 @@ def test_implicit_adjoint_matches_oracle(name, pd):
     solver.sync_status()
     assert all(0 < n < 5000 for n in its), its
     for k in keys:
-        check_grad(f"implicit {name} pd{int(pd)} {k}", got[k].cpu().numpy(), ref[k], GRAD_TOL)
+        check_grad(f"implicit {name} pd{int(pd)} {k}", got[k].cpu().numpy(), ref[k], GRAD_TOL, ref32=ref32[k])
 
 
 def test_phase_plan_handle_gives_the_same_gradient():

@@ -1,8 +1,10 @@
 """GPU (sm_103a, through the C ABI) versus the FP64 oracle, element by element.
 
 Tolerances: positions within 1e-5 m (relative to the 1 m scenes) over the horizon; each
-gradient group within 1e-3 relative L2 error, with the same FP32-rounded seed dL/dx fed to
-both sides."""
+gradient group within 1e-3 relative L2 error and each of its entries within 2 % of its own
+size (floored at 1e-3 of the group's largest entry), with the same FP32-rounded seed dL/dx
+fed to both sides; where the oracle's own float32-rounding emulation already moves a group
+further, the bounds are twice that floor (tests/gpu_common.py)."""
 import numpy as np
 import pytest
 import torch
@@ -11,7 +13,7 @@ import oracle
 from paper_2301_01396_gb300 import binding, scenes
 from tests import helpers
 from tests.gpu_common import (GRAD_KEYS, check_grad, contact_margin, contact_signs_agree, gpu_adjoint,
-                              gpu_forward, rel_err, to_dev)
+                              gpu_forward, oracle_adjoint_floor, rel_err, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -75,7 +77,7 @@ def test_adjoint_matches_oracle(name, cases):
     rng = np.random.default_rng(7)
     N = sc.steps
     seeds = {N: scenes.f32(rng.standard_normal((sc.V, 3))), N // 2: scenes.f32(rng.standard_normal((sc.V, 3)))}
-    ref = oracle.adjoint(sc, seeds)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds)
     got, _ = gpu_adjoint(sc, seeds)
     for k in GRAD_KEYS:
         if k == "f_global" and sc.f_global is None and np.abs(ref[k]).max() == 0:
@@ -83,13 +85,13 @@ def test_adjoint_matches_oracle(name, cases):
         if k == "collider" and not sc.collider_flags:
             assert np.all(got[k] == 0)
             continue
-        r = ref[k]
+        r, r32 = ref[k], ref32[k]
         g = got[k].reshape(r.shape) if k != "f_global" else got[k][:N]
         if k == "collider":
             sel = [0] if sc.collider_flags == scenes.COLLIDE_PLANE else \
                   [1, 2, 3, 4] if sc.collider_flags == scenes.COLLIDE_SPHERE else [0, 1, 2, 3, 4]
-            r, g = r[sel], g[sel]
-        check_grad(f"{name} {k}", g, r, GRAD_TOL)
+            r, g, r32 = r[sel], g[sel], r32[sel]
+        check_grad(f"{name} {k}", g, r, GRAD_TOL, ref32=r32)
 
 
 def _keyframe_force_scene():
@@ -111,12 +113,12 @@ def test_per_step_vertex_forces_match_oracle():
     assert np.abs(xs - xs_ref).max() < POS_TOL
     rng = np.random.default_rng(32)
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3))), 2: scenes.f32(rng.standard_normal((sc.V, 3)))}
-    ref = oracle.adjoint(sc, seeds)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds)
     got = solver.adjoint(p, sc.steps, sc.iters, ck, {k: to_dev(v) for k, v in seeds.items()},
                          want=GRAD_KEYS + ("f_vertex_steps",))
     torch.cuda.synchronize()
     for k in ("compliance", "x0", "v0", "f_global", "f_vertex", "f_vertex_steps"):
-        check_grad(f"keyframe_forces {k}", got[k].cpu().numpy(), ref[k], GRAD_TOL)
+        check_grad(f"keyframe_forces {k}", got[k].cpu().numpy(), ref[k], GRAD_TOL, ref32=ref32[k])
     fvs = got["f_vertex_steps"].cpu().numpy()
     assert np.allclose(fvs.sum(0), got["f_vertex"].cpu().numpy(), rtol=1e-12, atol=0)
 
@@ -159,10 +161,10 @@ def test_mixed_type_colors_and_greedy_order():
     assert np.abs(xs - xs_ref).max() < POS_TOL
     rng = np.random.default_rng(2)
     seeds = {sc.steps: scenes.f32(rng.standard_normal((sc.V, 3)))}
-    ref = oracle.adjoint(sc, seeds)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds)
     got, _ = gpu_adjoint(sc, seeds)
     for k in ("compliance", "x0", "v0"):
-        check_grad(f"greedy_order {k}", got[k], ref[k], GRAD_TOL)
+        check_grad(f"greedy_order {k}", got[k], ref[k], GRAD_TOL, ref32=ref32[k])
 
 
 def test_zero_steps_and_single_iteration():
@@ -176,10 +178,10 @@ def test_zero_steps_and_single_iteration():
     _, _, _, xs, _ = gpu_forward(sc, 3, 1)
     assert np.abs(xs - xs_ref).max() < POS_TOL
     seeds = {3: seed}
-    ref = oracle.adjoint(sc, seeds, 3, 1)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds, 3, 1)
     got, _ = gpu_adjoint(sc, seeds, 3, 1)
     for k in ("compliance", "x0", "v0"):
-        check_grad(f"single_iteration {k}", got[k], ref[k], GRAD_TOL)
+        check_grad(f"single_iteration {k}", got[k], ref[k], GRAD_TOL, ref32=ref32[k])
 
 
 def test_no_constraints_is_ballistic():
@@ -213,13 +215,11 @@ def test_autograd_function_matches_adjoint():
     loss = 0.5 * ((xT - target) ** 2).sum()
     loss.backward()
     seeds = {sc.steps: scenes.f32((xT - target).detach().cpu().numpy())}
-    ref = oracle.adjoint(sc, seeds)
-    check_grad("autograd compliance", comp.grad.cpu().numpy(), ref["compliance"], GRAD_TOL)
-    check_grad("autograd x0", x0.grad.cpu().numpy(), ref["x0"], GRAD_TOL)
-    check_grad("autograd v0", v0.grad.cpu().numpy(), ref["v0"], GRAD_TOL)
-    check_grad("autograd f_global", fg.grad.cpu().numpy(), ref["f_global"], GRAD_TOL)
-    check_grad("autograd f_vertex", fv.grad.cpu().numpy(), ref["f_vertex"], GRAD_TOL)
-    check_grad("autograd sphere", col.grad.numpy()[1:], ref["collider"][1:], GRAD_TOL)
+    ref, ref32 = oracle_adjoint_floor(sc, seeds)
+    grads = {"compliance": comp.grad, "x0": x0.grad, "v0": v0.grad, "f_global": fg.grad, "f_vertex": fv.grad}
+    for k, g in grads.items():
+        check_grad(f"autograd {k}", g.cpu().numpy(), ref[k], GRAD_TOL, ref32=ref32[k])
+    check_grad("autograd sphere", col.grad.numpy()[1:], ref["collider"][1:], GRAD_TOL, ref32=ref32["collider"][1:])
 
 
 def test_nonfinite_state_is_reported():
@@ -264,3 +264,44 @@ def test_phase_plan_matches_per_color_launches(name, cases):
     assert np.abs(x0 - x1).max() <= 1e-6
     for k in g0:
         assert rel_err(g0[k], g1[k]) <= 2e-4, k
+
+
+def test_config1_workload_loss_and_gradients():
+    """Config 1 on its own workload over the well-conditioned 10-step horizon: the 16 x 16
+    stiff cloth (930 springs, compliance 1e-7, 20 iterations), the loss 1/2 |x_T - x*|^2
+    against a target made (by the oracle) with seeded lognormal(0, 0.5) compliances, and
+    its gradient with respect to all 930 compliances and v0.
+
+    The target differs from the simulated cloth by at most ~4e-7 m (stiff springs stretch by
+    m g alpha ~ 1e-8 m), the size of float32 position rounding: the loss and the end-to-end
+    gradient are not resolvable in float32 (the oracle's own float32-rounding emulation
+    moves the seed by ~66 % and the gradients by 20-50 %).  So the gradient is compared
+    element by element with the same float32-rounded seed fed to both sides, and the GPU's
+    own loss and seed are checked against twice that float32 floor."""
+    sc = scenes.plain_cloth(16, steps=10)
+    T = sc.steps
+    xt, _ = oracle.forward(scenes.plain_cloth(16, steps=10, target=True))
+    target = scenes.f32(xt[T])
+    xs_ref, _ = oracle.forward(sc)
+    with oracle.fp32_rounding():
+        xs32, _ = oracle.forward(sc)
+    solver, p, ck, xs, _ = gpu_forward(sc)
+    assert np.abs(xs - xs_ref).max() < POS_TOL
+    loss, seeds = solver.loss(ck, {T: to_dev(target)})
+    torch.cuda.synchronize()
+    seed_ref = xs_ref[T] - target
+    loss_ref = 0.5 * float(np.sum(seed_ref ** 2))
+    loss32 = 0.5 * float(np.sum((xs32[T] - target) ** 2))
+    floor = abs(loss32 - loss_ref) / loss_ref
+    err = abs(loss.item() - loss_ref) / loss_ref
+    print(f"PARITY config1 loss: rel {err:.3e} (float32 floor {floor:.3e})")
+    assert err < max(1e-3, 2.0 * floor)
+    assert rel_err(seeds[0].cpu().numpy(), seed_ref) < max(1e-3, 2.0 * rel_err(xs32[T] - target, seed_ref))
+    # the gradient of the workload's loss, same seed on both sides
+    seed = scenes.f32(seed_ref)
+    ref, ref32 = oracle_adjoint_floor(sc, {T: seed})
+    got = solver.adjoint(p, T, sc.iters, ck, {T: to_dev(seed)}, want=("compliance", "v0"))
+    torch.cuda.synchronize()
+    assert got["compliance"].shape == (930,)
+    for k in ("compliance", "v0"):
+        check_grad(f"config1 {k}", got[k].cpu().numpy(), ref[k], GRAD_TOL, ref32=ref32[k])
