@@ -606,6 +606,34 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
       comp_of_root[find(v)] = -1;
     }
   }
+  // padded per-group vertex lists and chunk tables (fixed strides per phase), so a CTA
+  // addresses its own from its index alone; chunk tables in forward and reverse order
+  std::vector<int> pv_pad;
+  std::vector<PhaseChunk> ch_pad, ch_rev;
+  for (auto& ph : h->phases) {
+    ph.vstride = ph.max_verts;
+    ph.cstride = std::max(ph.max_chunks, 1);
+    ph.vbase = (int64_t)pv_pad.size();
+    ph.cbase = (int64_t)ch_pad.size();
+    pv_pad.resize(pv_pad.size() + (size_t)ph.n_groups * ph.vstride, -1);
+    PhaseChunk empty;
+    std::memset(&empty, 0, sizeof(empty));
+    ch_pad.resize(ch_pad.size() + (size_t)ph.n_groups * ph.cstride, empty);
+    ch_rev.resize(ch_pad.size(), empty);
+    for (int g = 0; g < ph.n_groups; ++g) {
+      PhaseGroup& G = groups[ph.first_group + g];
+      const int64_t vb = ph.vbase + (int64_t)g * ph.vstride, cb = ph.cbase + (int64_t)g * ph.cstride;
+      std::copy(pverts.begin() + G.vert_begin, pverts.begin() + G.vert_begin + G.vert_count, pv_pad.begin() + vb);
+      for (int k = 0; k < G.chunk_count; ++k) {
+        ch_pad[cb + k] = chunks[G.chunk_begin + k];
+        ch_rev[cb + k] = chunks[G.chunk_begin + G.chunk_count - 1 - k];
+      }
+      G.vert_begin = (int)vb;
+      G.chunk_begin = (int)cb;
+    }
+  }
+  pverts.swap(pv_pad);
+  chunks.swap(ch_pad);
   // slot space and tape layout of the phase records
   size_t nslots = 0, ntape = 0;
   std::vector<int> pperm;
@@ -633,6 +661,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
   if (e == cudaSuccess) e = up((void**)&h->d_pperm, pperm.data(), pperm.size() * sizeof(int));
   if (e == cudaSuccess) e = up((void**)&h->d_groups, groups.data(), groups.size() * sizeof(PhaseGroup));
   if (e == cudaSuccess) e = up((void**)&h->d_chunks, chunks.data(), chunks.size() * sizeof(PhaseChunk));
+  if (e == cudaSuccess) e = up((void**)&h->d_chunks_rev, ch_rev.data(), ch_rev.size() * sizeof(PhaseChunk));
   if (e == cudaSuccess) e = up((void**)&h->d_pverts, pverts.data(), pverts.size() * sizeof(int));
   if (e == cudaSuccess) e = phase_kernel_setup();
   if (e != cudaSuccess)
@@ -648,8 +677,11 @@ PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph) {
   PhaseLaunch a;
   std::memset(&a, 0, sizeof(a));
   a.groups = h->d_groups + ph.first_group;
-  a.chunks = h->d_chunks;
-  a.pverts = h->d_pverts;
+  a.chunks = h->d_chunks + ph.cbase;
+  a.chunks_rev = h->d_chunks_rev + ph.cbase;
+  a.pverts = h->d_pverts + ph.vbase;
+  a.vstride = ph.vstride;
+  a.cstride = ph.cstride;
   for (int t = 0; t < kSegTypes; ++t) {
     a.slot_off[t] = h->pslot_off[t];
     a.prec[t] = h->d_prec[t];
@@ -933,7 +965,7 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
   if (h->d_err) cudaFree(h->d_err);
   for (int t = 0; t < kSegTypes; ++t)
     if (h->d_prec[t]) cudaFree(h->d_prec[t]);
-  void* plan[] = {h->d_pperm, h->d_groups, h->d_chunks, h->d_pverts};
+  void* plan[] = {h->d_pperm, h->d_groups, h->d_chunks, h->d_chunks_rev, h->d_pverts};
   for (void* q : plan)
     if (q) cudaFree(q);
   DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,

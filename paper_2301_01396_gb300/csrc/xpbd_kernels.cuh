@@ -116,8 +116,13 @@ constexpr int kChunkColorFirst = 1, kChunkColorLast = 2;
 constexpr int kChunkPair = 5;
 struct PhaseLaunch {
   const PhaseGroup* groups;
+  // CTA b's vertex list at pverts + b * vstride (padded with -1) and its chunks at
+  // chunks + b * cstride in execution order (chunks_rev: reverse order; padded with empty
+  // chunks), so a CTA finds them without first reading its PhaseGroup
   const PhaseChunk* chunks;
+  const PhaseChunk* chunks_rev;
   const int* pverts;
+  int vstride, cstride;
   int slot_off[5];         // offset of each type in the multiplier slot space (multiples of 4)
   const void* prec[5];     // phase records (vertex indices local to the group)
   size_t tape_off[5];      // float4 offset of each type within one iteration's tape
@@ -131,7 +136,8 @@ struct PhaseLaunch {
   int* err;                // device error word (bit 4: a bounded wait gave up)
   long long wait_cycles;   // limit of every wait (SM clock cycles)
   int no_issue;            // self-test of the bounded waits: the producer issues no copies
-  // shared-memory layout, filled by the launcher: vertices, chunk table, stage ring
+  // shared-memory layout, filled by the launcher: vertices (float4, then their global
+  // indices), chunk table, stage ring
   int vert_bytes;
   int chunk_bytes;
   int slot_bytes;          // bytes of one stage

@@ -157,6 +157,7 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
   unsigned total = n * R + (a.lam_in ? 4 * nl * n : 0);
   if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * na * n) + (last ? 8 * na * n : 0);
   mbar_expect_tx(b, total);
+  if (n == 0) return;   // a padding entry of the chunk table: the arrival completes the stage
   if (TS::pair(t)) {
     const unsigned R1 = (unsigned)sizeof(TetRec);
     bulk_g2s(st, (const char*)a.prec[SEG_TETH] + (size_t)c.begin * R1, n * R1, b);
@@ -318,18 +319,20 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
 #define XPBD_PHASE_VJP_MIN_BLOCKS 2
 #endif
 
-// Gathers the group's vertices (or vertex adjoints) into shared memory, 8 independent
-// loads in flight per thread, and zeroes the dummy vertex.
-__device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, const int* __restrict__ vlist, int n,
-                                                float4* sv) {
-  constexpr int U = 8;
-  for (int v0 = threadIdx.x; v0 < n; v0 += U * blockDim.x) {
+// Gathers the group's vertices (or vertex adjoints) into shared memory, 6 independent
+// loads in flight per thread, and keeps their global indices there for the write-back.
+// The list is the group's padded one (`stride` entries, -1 past the group's vertices), so
+// this needs nothing from the group's record.
+__device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, const int* __restrict__ vlist,
+                                                int stride, float4* sv, int* svl) {
+  constexpr int U = 6;
+  for (int v0 = threadIdx.x; v0 < stride; v0 += U * blockDim.x) {
     int idx[U];
     float4 val[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int v = v0 + u * (int)blockDim.x;
-      idx[u] = v < n ? vlist[v] : -1;
+      idx[u] = v < stride ? __ldg(vlist + v) : -1;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -337,10 +340,12 @@ __device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, co
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int v = v0 + u * (int)blockDim.x;
-      if (v < n) sv[v] = val[u];
+      if (idx[u] >= 0) {
+        sv[v] = val[u];
+        svl[v] = idx[u];
+      }
     }
   }
-  if (threadIdx.x == 0) sv[n] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
@@ -365,11 +370,13 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
   __shared__ uint64_t full[kPhaseMaxStages], empty[kPhaseMaxStages];
   __shared__ int abort_run;
   float4* sv = reinterpret_cast<float4*>(smem);
+  int* svl = reinterpret_cast<int*>(smem + (size_t)(a.vstride + 1) * sizeof(float4));
   PhaseChunk* sch = reinterpret_cast<PhaseChunk*>(smem + a.vert_bytes);
   unsigned char* stage = smem + a.vert_bytes + a.chunk_bytes;
-  const PhaseGroup G = a.groups[blockIdx.x];
-  const PhaseChunk* ch = a.chunks + G.chunk_begin;
-  const int nch = G.chunk_count, S = a.stages;
+  // the chunk table (in execution order) and vertex list of this CTA, and its record, are
+  // read at once: none of the three addresses depends on another load
+  const PhaseChunk* ch = (REV ? a.chunks_rev : a.chunks) + (size_t)blockIdx.x * a.cstride;
+  const int S = a.stages;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -379,22 +386,25 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     mbar_fence_init();
   }
   __syncthreads();
-  // the producer starts the first stages from the global chunk table; everyone else copies
-  // the table to shared memory and gathers the vertices meanwhile
-  if (threadIdx.x == kPhaseBlock && !a.no_issue)
-    for (int k = 0; k < S && k < nch; ++k)
-      issue_chunk<REV, TM>(a, ch[REV ? nch - 1 - k : k], stage + (size_t)k * a.slot_bytes, &full[k], first, last);
-  for (int i = threadIdx.x; i < nch; i += blockDim.x) sch[i] = ch[i];
-  gather_vertices(a.P, a.pverts + G.vert_begin, G.vert_count, sv);
+  // lanes of the producer warp start the first stages (one chunk each, empty padding chunks
+  // only arrive); everyone else copies the table to shared memory and gathers the vertices
+  const int lane_p = (int)threadIdx.x - kPhaseBlock;
+  if (lane_p >= 0 && lane_p < S && lane_p < a.cstride && !a.no_issue)
+    issue_chunk<REV, TM>(a, ch[lane_p], stage + (size_t)lane_p * a.slot_bytes, &full[lane_p], first, last);
+  for (int i = threadIdx.x; i < a.cstride; i += blockDim.x) sch[i] = ch[i];
+  const PhaseGroup G = a.groups[blockIdx.x];
+  gather_vertices(a.P, a.pverts + (size_t)blockIdx.x * a.vstride, a.vstride, sv, svl);
+  if (threadIdx.x == 0) sv[G.vert_count] = make_float4(0.f, 0.f, 0.f, 0.f);   // the dummy vertex
+  const int nch = G.chunk_count;
   __syncthreads();
   if (threadIdx.x >= kPhaseBlock) {   // producer warp
     if (threadIdx.x == kPhaseBlock && !a.no_issue) {
-      int issued = S < nch ? S : nch;
+      // stages [0, S) were issued above (chunks past nch are empty); refill from chunk S on
+      int issued = S < a.cstride ? S : a.cstride;
       for (; issued < nch; ++issued) {
         const int s = issued % S;
         if (!mbar_wait(&empty[s], (unsigned)(issued / S - 1) & 1u, a.wait_cycles)) break;   // the consumers stopped
-        issue_chunk<REV, TM>(a, sch[REV ? nch - 1 - issued : issued], stage + (size_t)s * a.slot_bytes, &full[s],
-                             first, last);
+        issue_chunk<REV, TM>(a, sch[issued], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
       }
       // Whether it issued every chunk or gave up, the CTA must not end while a copy into its
       // shared memory is in flight (the consumers may have stopped early): wait for the last
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
   for (int k = 0; k < nch; ++k) {
     const int s = k % S;
     const unsigned char* st = stage + (size_t)s * a.slot_bytes;
-    const PhaseChunk c = sch[REV ? nch - 1 - k : k];
+    const PhaseChunk c = sch[k];
     if (mbar_wait(&full[s], (unsigned)(k / S) & 1u, a.wait_cycles)) {
       if (REV)
         vjp_chunk<TM>(a, c, st, sv, first, last);
@@ -430,8 +440,7 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
       }
     }
   }
-  const int* vlist = a.pverts + G.vert_begin;
-  for (int v = threadIdx.x; v < G.vert_count; v += kPhaseBlock) a.P[vlist[v]] = sv[v];
+  for (int v = threadIdx.x; v < G.vert_count; v += kPhaseBlock) a.P[svl[v]] = sv[v];
 }
 
 namespace {
@@ -465,8 +474,8 @@ struct Plan {
 // (reverse) resident CTAs per SM.
 Plan stage_plan(const PhaseShape& sh, bool rev) {
   Plan p;
-  p.vert_bytes = ((sh.max_verts + 1) * 16 + 127) / 128 * 128;
-  p.chunk_bytes = (sh.max_chunks * (int)sizeof(PhaseChunk) + 127) / 128 * 128;
+  p.vert_bytes = ((sh.max_verts + 1) * 16 + (sh.max_verts + 1) * 4 + 127) / 128 * 128;
+  p.chunk_bytes = (std::max(sh.max_chunks, 1) * (int)sizeof(PhaseChunk) + 127) / 128 * 128;
   unsigned e = 0;
   for (int t = 0; t <= kChunkPair; ++t)
     if ((sh.type_mask >> t) & 1) e = std::max(e, elem_stage_bytes(t, rev));

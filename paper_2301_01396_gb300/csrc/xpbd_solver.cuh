@@ -108,6 +108,10 @@ struct xpbd_solver {
     int first_group = 0, n_groups = 0, c0 = 0, ncolors = 0, max_verts = 0, max_chunks = 0;
     int type_mask = 0;                      // bit t: constraint type t occurs
     int max_chunk_size = 0;
+    // padded per-group tables: group g's vertex list at vbase + g * vstride (padding -1),
+    // its chunks at cbase + g * cstride (padding: empty chunks), forward and reverse order
+    int64_t vbase = 0, cbase = 0;
+    int vstride = 0, cstride = 0;
     PhaseShape shape() const { return PhaseShape{n_groups, max_verts, max_chunks, type_mask, max_chunk_size}; }
     int64_t units = 0;                      // constraints updated by one launch
     double bytes_fwd = 0, bytes_replay = 0, bytes_vjp = 0;   // algorithmic bytes per launch
@@ -121,6 +125,7 @@ struct xpbd_solver {
   int* d_pperm = nullptr;                                     // phase record -> constraint id (-1: pad)
   PhaseGroup* d_groups = nullptr;
   PhaseChunk* d_chunks = nullptr;
+  PhaseChunk* d_chunks_rev = nullptr;
   int* d_pverts = nullptr;
   // Per-constraint slot space of the multiplier / adjoint buffers and float4 entries of
   // one iteration's tape: large enough for the per-color layout and the padded phase layout.
