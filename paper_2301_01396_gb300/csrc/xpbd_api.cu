@@ -297,6 +297,26 @@ MembRec localize(MembRec r, const std::vector<int>& loc) {
   return r;
 }
 
+// Local order of a group's vertices in shared memory.  A run of consecutive vertex ids (a
+// grid row) is stored as its even offsets followed by its odd offsets.  A color's
+// constraints are sorted by the local index of their first vertex, so a grid color whose
+// constraints step by two columns (one parity class) then touches consecutive local
+// vertices instead of every other one: the 128-bit accesses of 8 threads cover 128
+// contiguous bytes, free of shared-memory bank conflicts.
+std::vector<int> shared_memory_order(const std::vector<int>& list) {
+  std::vector<int> out;
+  out.reserve(list.size());
+  size_t i = 0;
+  while (i < list.size()) {
+    size_t j = i;
+    while (j + 1 < list.size() && list[j + 1] == list[j] + 1) ++j;
+    for (size_t k = i; k <= j; k += 2) out.push_back(list[k]);
+    for (size_t k = i + 1; k <= j; k += 2) out.push_back(list[k]);
+    i = j + 1;
+  }
+  return out;
+}
+
 xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, const std::vector<DistRec>& rd,
                          const std::vector<BendRec>& rb, const std::vector<TetRec>& rh,
                          const std::vector<TetRec>& rdv, const std::vector<int>& perm,
@@ -494,27 +514,36 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
     // groups: consecutive components packed up to kPhaseGroupVerts vertices (a larger
     // component is a group of its own).  A small model packs less, down to one component
     // per group, so that a phase still has about kPhaseTargetGroups CTAs.
+    std::vector<int> real_verts;   // per group of this phase: vertices without padding
     {
       const int pack = std::max(1, std::min(kPhaseGroupVerts, (int)(tv.size() / kPhaseTargetGroups)));
-      int cur = -1, cur_n = 0;
+      std::vector<std::vector<int>> gv;
+      int cur_n = 0;
       for (size_t k = 0; k < comps.size(); ++k) {
         int sz = (int)comps[k].size();
-        if (cur < 0 || cur_n + sz > pack) {
-          PhaseGroup g;
-          g.vert_begin = (int)pverts.size();
-          g.vert_count = 0;
-          g.chunk_begin = 0;
-          g.chunk_count = 0;
-          groups.push_back(g);
-          cur = (int)groups.size() - 1;
+        if (gv.empty() || cur_n + sz > pack) {
+          gv.emplace_back();
           cur_n = 0;
         }
-        for (int v : comps[k]) {
-          loc[v] = groups[cur].vert_count++;
-          group_of_vertex[v] = cur;
-          pverts.push_back(v);
-        }
+        gv.back().insert(gv.back().end(), comps[k].begin(), comps[k].end());
         cur_n += sz;
+      }
+      for (const std::vector<int>& list : gv) {
+        PhaseGroup g;
+        g.vert_begin = (int)pverts.size();
+        g.chunk_begin = 0;
+        g.chunk_count = 0;
+        const std::vector<int> order = shared_memory_order(list);
+        g.vert_count = (int)order.size();
+        groups.push_back(g);
+        const int cur = (int)groups.size() - 1;
+        for (int k = 0; k < (int)order.size(); ++k) {
+          pverts.push_back(order[k]);
+          if (order[k] < 0) continue;
+          loc[order[k]] = k;
+          group_of_vertex[order[k]] = cur;
+        }
+        real_verts.push_back((int)list.size());
       }
     }
     ph_info.n_groups = (int)groups.size() - ph_info.first_group;
@@ -534,7 +563,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
       PhaseGroup& G = groups[ph_info.first_group + g];
       G.chunk_begin = (int)chunks.size();
       ph_info.max_verts = std::max(ph_info.max_verts, G.vert_count);
-      vbytes += 36.0 * G.vert_count;   // vertex index + one float4 read + one write
+      vbytes += 36.0 * real_verts[g];   // vertex index + one float4 read + one write
       for (int ci = 0; ci < ncol; ++ci) {
         const size_t color_first = chunks.size();
         for (int t = 0; t < kSegTypes; ++t) {

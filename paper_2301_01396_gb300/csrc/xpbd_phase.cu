@@ -127,18 +127,19 @@ struct TypeSet {
 };
 
 // Stage layout of a chunk of n constraints of type t: records (n R), multipliers in
-// (4 n per component, component-major), and for the reverse sweep the tape (16 nv n),
-// (lambar, alphabar) pairs (8 n per slot) and the float64 accumulators (8 n per slot).
-// Every part starts on a 16-byte boundary because n is a multiple of 4.
+// (4 n per component, component-major), and for the reverse sweep the tape (16 nv n) and
+// (lambar, alphabar) pairs (8 n per slot).  Every part starts on a 16-byte boundary because
+// n is a multiple of 4.  The last reverse iteration of a step folds alphabar into the float64
+// accumulators with one atomic add per slot (fire and forget; a slot is added to once per
+// launch, so the sums are deterministic).
 template <int TM>
 struct StageLayout {
-  unsigned lam, tape, lb, acc;
+  unsigned lam, tape, lb;
   __device__ StageLayout(int t, unsigned n) {
     using TS = TypeSet<TM>;
     lam = n * TS::rec(t);
     tape = lam + 4 * TS::nl(t) * n;
     lb = tape + 16 * TS::nv(t) * n;
-    acc = lb + 8 * TS::na(t) * n;
   }
 };
 
@@ -155,7 +156,7 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
   const size_t cs = TS::memb(t) ? (size_t)a.memb_stride
                                  : (TS::pair(t) ? (size_t)(a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]) : 0);
   unsigned total = n * R + (a.lam_in ? 4 * nl * n : 0);
-  if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * na * n) + (last ? 8 * na * n : 0);
+  if (REVERSE) total += 16 * nv * n + (first ? 0 : 8 * na * n);
   mbar_expect_tx(b, total);
   if (n == 0) return;   // a padding entry of the chunk table: the arrival completes the stage
   if (TS::pair(t)) {
@@ -171,7 +172,6 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
     bulk_g2s(st + L.tape, a.tape + a.tape_off[h] + (size_t)c.begin * nv, 16 * nv * n, b);
     for (unsigned k = 0; k < na; ++k) {
       if (!first) bulk_g2s(st + L.lb + 8 * n * k, a.lb + so + k * cs, 8 * n, b);
-      if (last) bulk_g2s(st + L.acc + 8 * n * k, a.acc + so + k * cs, 8 * n, b);
     }
   }
 }
@@ -248,7 +248,6 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
     const int n = c.count;
     const float* sl = reinterpret_cast<const float*>(st + L.lam);
     const float2* slb = reinterpret_cast<const float2*>(st + L.lb);
-    const double* sacc = reinterpret_cast<const double*>(st + L.acc);
     const float atd = reinterpret_cast<const TetRec*>(st + (size_t)n * sizeof(TetRec))[tid].at;
     const float2 l2 = a.lam_in ? make_float2(sl[tid], sl[n + tid]) : make_float2(0.f, 0.f);
     float2 lh = first ? make_float2(0.f, 0.f) : slb[tid];
@@ -257,8 +256,8 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
     vjp_pair_core<true>(reinterpret_cast<const TetRec*>(st)[tid], atd, p, l2, lh, ld, sx);
     const size_t gd = gi + (a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]);
     if (last) {
-      a.acc[gi] = sacc[tid] + (double)lh.y;
-      a.acc[gd] = sacc[n + tid] + (double)ld.y;
+      atomicAdd(a.acc + gi, (double)lh.y);
+      atomicAdd(a.acc + gd, (double)ld.y);
     } else {
       a.lb[gi] = lh;
       a.lb[gd] = ld;
@@ -269,7 +268,6 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
     const int n = c.count;
     const float* sl = reinterpret_cast<const float*>(st + L.lam);
     const float2* slb = reinterpret_cast<const float2*>(st + L.lb);
-    const double* sacc = reinterpret_cast<const double*>(st + L.acc);
     float lm[3], lbv[3], ab[4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) lm[k] = a.lam_in ? sl[k * n + tid] : 0.f;
@@ -285,7 +283,7 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
     for (int k = 0; k < 4; ++k) {
       const size_t g = gi + (size_t)k * a.memb_stride;
       if (last)
-        a.acc[g] = sacc[k * n + tid] + (double)ab[k];
+        atomicAdd(a.acc + g, (double)ab[k]);
       else
         a.lb[g] = make_float2(k < 3 ? lbv[k] : 0.f, ab[k]);
     }
@@ -303,7 +301,7 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
       l = vjp_quad_core<3, true>(reinterpret_cast<const TetRec*>(st)[tid], p, lam, l, sx);
   }
   if (last)
-    a.acc[gi] = reinterpret_cast<const double*>(st + L.acc)[tid] + (double)l.y;
+    atomicAdd(a.acc + gi, (double)l.y);
   else
     a.lb[gi] = l;
 }
@@ -320,9 +318,10 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
 #endif
 
 // Gathers the group's vertices (or vertex adjoints) into shared memory, 6 independent
-// loads in flight per thread, and keeps their global indices there for the write-back.
-// The list is the group's padded one (`stride` entries, -1 past the group's vertices), so
-// this needs nothing from the group's record.
+// loads in flight per thread, and (svl not NULL) keeps their global indices there for the
+// write-back.  The list is the group's padded one (`stride` entries, -1 for the padding
+// between row halves and past the group's vertices), so this needs nothing from the
+// group's record.
 __device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, const int* __restrict__ vlist,
                                                 int stride, float4* sv, int* svl) {
   constexpr int U = 6;
@@ -340,10 +339,8 @@ __device__ __forceinline__ void gather_vertices(const float4* __restrict__ P, co
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int v = v0 + u * (int)blockDim.x;
-      if (idx[u] >= 0) {
-        sv[v] = val[u];
-        svl[v] = idx[u];
-      }
+      if (idx[u] >= 0) sv[v] = val[u];
+      if (svl && v < stride) svl[v] = idx[u];
     }
   }
 }
@@ -370,7 +367,9 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
   __shared__ uint64_t full[kPhaseMaxStages], empty[kPhaseMaxStages];
   __shared__ int abort_run;
   float4* sv = reinterpret_cast<float4*>(smem);
-  int* svl = reinterpret_cast<int*>(smem + (size_t)(a.vstride + 1) * sizeof(float4));
+  // the reverse keeps the vertex indices in shared memory for its write-back; the forward
+  // re-reads them (still in L2) and spends that shared memory on another stage
+  int* svl = REV ? reinterpret_cast<int*>(smem + (size_t)(a.vstride + 1) * sizeof(float4)) : nullptr;
   PhaseChunk* sch = reinterpret_cast<PhaseChunk*>(smem + a.vert_bytes);
   unsigned char* stage = smem + a.vert_bytes + a.chunk_bytes;
   // the chunk table (in execution order) and vertex list of this CTA, and its record, are
@@ -440,7 +439,11 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
       }
     }
   }
-  for (int v = threadIdx.x; v < G.vert_count; v += kPhaseBlock) a.P[svl[v]] = sv[v];
+  const int* vlist = a.pverts + (size_t)blockIdx.x * a.vstride;
+  for (int v = threadIdx.x; v < G.vert_count; v += kPhaseBlock) {
+    const int gv = REV ? svl[v] : __ldg(vlist + v);
+    if (gv >= 0) a.P[gv] = sv[v];
+  }
 }
 
 namespace {
@@ -461,7 +464,7 @@ int kernel_mask(int type_mask) {
 }
 
 unsigned elem_stage_bytes(int t, bool rev) {
-  return rec_size(t) + 4 * nlam(t) + (rev ? 16 * nverts(t) + 16 * nadj(t) : 0);
+  return rec_size(t) + 4 * nlam(t) + (rev ? 16 * nverts(t) + 8 * nadj(t) : 0);
 }
 
 struct Plan {
@@ -474,7 +477,7 @@ struct Plan {
 // (reverse) resident CTAs per SM.
 Plan stage_plan(const PhaseShape& sh, bool rev) {
   Plan p;
-  p.vert_bytes = ((sh.max_verts + 1) * 16 + (sh.max_verts + 1) * 4 + 127) / 128 * 128;
+  p.vert_bytes = ((sh.max_verts + 1) * (rev ? 20 : 16) + 127) / 128 * 128;
   p.chunk_bytes = (std::max(sh.max_chunks, 1) * (int)sizeof(PhaseChunk) + 127) / 128 * 128;
   unsigned e = 0;
   for (int t = 0; t <= kChunkPair; ++t)
