@@ -222,6 +222,23 @@ __device__ __forceinline__ void predict_elem(int i, const float4* __restrict__ c
 }
 
 // ---- distance: C = |x_a - x_b| - L, grad_a = n = (x_a - x_b)/l, grad_b = -n.
+// One update on values in registers: returns false (nothing changes) for a degenerate
+// constraint, else updates pa, pb and lam.
+__device__ __forceinline__ bool dist_step(const DistRec& r, float4& pa, float4& pb, float& lam) {
+  f3 d = xyz(pa) - xyz(pb);
+  float l2 = dot(d, d);
+  float D = pa.w + pb.w + r.at;
+  if (!(l2 >= XPBD_DEGEN2 && D > 0.f)) return false;
+  float il = rsqrtf(l2);
+  float l = l2 * il;
+  f3 nrm = d * il;
+  float dl = (-(l - r.L) - r.at * lam) / D;
+  lam += dl;
+  pa = with_w(xyz(pa) + nrm * (pa.w * dl), pa.w);
+  pb = with_w(xyz(pb) - nrm * (pb.w * dl), pb.w);
+  return true;
+}
+
 // lam_in and lam_out may alias (in-place forward), so they are not __restrict__.
 template <bool SH = false>
 __device__ __forceinline__ float proj_dist_core(const DistRec& r, float4* __restrict__ P, float lam,
@@ -233,19 +250,9 @@ __device__ __forceinline__ float proj_dist_core(const DistRec& r, float4* __rest
     __stcs(tape2, pa);
     __stcs(tape2 + ts, pb);
   }
-  f3 d = xyz(pa) - xyz(pb);
-  float l2 = dot(d, d);
-  float D = pa.w + pb.w + r.at;
-  if (l2 >= XPBD_DEGEN2 && D > 0.f) {
-    float il = rsqrtf(l2);
-    float l = l2 * il;
-    f3 nrm = d * il;
-    float dl = (-(l - r.L) - r.at * lam) / D;
-    lam += dl;
-    f3 a = xyz(pa) + nrm * (pa.w * dl);
-    f3 b = xyz(pb) - nrm * (pb.w * dl);
-    vstore<SH>(P + r.a, with_w(a, pa.w), pol);
-    vstore<SH>(P + r.b, with_w(b, pb.w), pol);
+  if (dist_step(r, pa, pb, lam)) {
+    vstore<SH>(P + r.a, pa, pol);
+    vstore<SH>(P + r.b, pb, pol);
   }
   return lam;
 }

@@ -176,57 +176,97 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
   }
 }
 
-// Forward / replay update of constraint `tid` of chunk c from stage st.
-template <bool RECORD, int TM>
+// Forward / replay update of constraint `tid` of chunk c from stage st.  `release` hands the
+// stage back to the producer (every thread of the warp calls it once).  In the cloth kernel
+// a thread first reads what its update needs from the stage into registers and releases
+// before the arithmetic, so the next copy into the stage overlaps it.
+template <bool RECORD, int TM, class Release>
 __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk& c, const unsigned char* st,
-                                          float4* sv) {
+                                          float4* sv, Release&& release) {
   using TS = TypeSet<TM>;
-  const int t = c.type, tid = threadIdx.x;
-  if (tid >= c.count) return;
-  const StageLayout<TM> L(t, (unsigned)c.count);
-  const float lam = a.lam_in ? reinterpret_cast<const float*>(st + L.lam)[tid] : 0.f;
+  const int t = c.type, tid = threadIdx.x, n = c.count;
+  const bool act = tid < n;
+  const StageLayout<TM> L(t, (unsigned)n);
+  const float* sl = reinterpret_cast<const float*>(st + L.lam);
   const size_t gi = (size_t)a.slot_off[TS::home(t)] + c.begin + tid;
 #if XPBD_PHASE_TAPE_SOA
   float4* tp = RECORD ? a.tape + a.tape_off[TS::home(t)] + (size_t)c.begin * TS::nv(t) + tid : nullptr;
-  const int ts = c.count;
+  const int ts = n;
 #else
   float4* tp = RECORD ? a.tape + a.tape_off[TS::home(t)] + (size_t)(c.begin + tid) * TS::nv(t) : nullptr;
   const int ts = 1;
 #endif
+  // coupled pairs, membranes and tets read the stage as they go and release it at the end
+  // (holding their larger records in registers across the release spills them)
   if (has<TM>(kChunkPair) && t == kChunkPair) {
-    const int n = c.count;
-    const float* sl = reinterpret_cast<const float*>(st + L.lam);
-    const float atd = reinterpret_cast<const TetRec*>(st + (size_t)n * sizeof(TetRec))[tid].at;
-    const float2 l2 = a.lam_in ? make_float2(sl[tid], sl[n + tid]) : make_float2(0.f, 0.f);
-    const float2 lo2 = proj_pair_core<true>(reinterpret_cast<const TetRec*>(st)[tid], atd, sv, l2, tp, ts);
-    __stcs(a.lam_out + gi, lo2.x);
-    __stcs(a.lam_out + gi + (a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]), lo2.y);
+    if (act) {
+      const float atd = reinterpret_cast<const TetRec*>(st + (size_t)n * sizeof(TetRec))[tid].at;
+      const float2 l2 = a.lam_in ? make_float2(sl[tid], sl[n + tid]) : make_float2(0.f, 0.f);
+      const float2 lo2 = proj_pair_core<true>(reinterpret_cast<const TetRec*>(st)[tid], atd, sv, l2, tp, ts);
+      __stcs(a.lam_out + gi, lo2.x);
+      __stcs(a.lam_out + gi + (a.slot_off[SEG_TETD] - a.slot_off[SEG_TETH]), lo2.y);
+    }
+    release();
     return;
   }
   if (has<TM>(SEG_MEMB) && t == SEG_MEMB) {
-    const float* sl = reinterpret_cast<const float*>(st + L.lam);
-    const int n = c.count;
-    float lm[3];
+    if (act) {
+      float lm[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) lm[k] = a.lam_in ? sl[k * n + tid] : 0.f;
-    proj_memb_core<true>(reinterpret_cast<const MembRec*>(st)[tid], sv, lm, tp, ts);
+      for (int k = 0; k < 3; ++k) lm[k] = a.lam_in ? sl[k * n + tid] : 0.f;
+      proj_memb_core<true>(reinterpret_cast<const MembRec*>(st)[tid], sv, lm, tp, ts);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) __stcs(a.lam_out + gi + (size_t)k * a.memb_stride, lm[k]);
+      for (int k = 0; k < 3; ++k) __stcs(a.lam_out + gi + (size_t)k * a.memb_stride, lm[k]);
+    }
+    release();
     return;
   }
+  const float lam = act && a.lam_in ? sl[tid] : 0.f;
   float lo = lam;
-  if (has<TM>(SEG_DIST) && t == SEG_DIST)
-    lo = proj_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], sv, lam, tp, ts);
-  else if (has<TM>(SEG_BEND) && t == SEG_BEND)
-    lo = proj_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], sv, lam, tp, ts);
-  else if (has<TM>(SEG_TETH) && t == SEG_TETH)
-    lo = proj_quad_core<2, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp, ts);
-  else if (has<TM>(SEG_TETD) && t == SEG_TETD)
-    lo = proj_quad_core<3, true>(reinterpret_cast<const TetRec*>(st)[tid], sv, lam, tp, ts);
+  // the cloth kernel (distance and bending only) releases before its arithmetic; kernels
+  // that also carry tets or membranes keep their registers for those and release after
+  constexpr bool early = TM == 0x3;
+  if (has<TM>(SEG_DIST) && t == SEG_DIST) {
+    if constexpr (early) {
+      DistRec r;
+      if (act) r = reinterpret_cast<const DistRec*>(st)[tid];
+      release();
+      if (!act) return;
+      lo = proj_dist_core<true>(r, sv, lam, tp, ts);
+    } else {
+      if (act) lo = proj_dist_core<true>(reinterpret_cast<const DistRec*>(st)[tid], sv, lam, tp, ts);
+      release();
+      if (!act) return;
+    }
+  } else if (has<TM>(SEG_BEND) && t == SEG_BEND) {
+    if constexpr (early) {
+      BendRec r;
+      if (act) r = reinterpret_cast<const BendRec*>(st)[tid];
+      release();
+      if (!act) return;
+      lo = proj_quad_core<1, true>(r, sv, lam, tp, ts);
+    } else {
+      if (act) lo = proj_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], sv, lam, tp, ts);
+      release();
+      if (!act) return;
+    }
+  } else if ((has<TM>(SEG_TETH) && t == SEG_TETH) || (has<TM>(SEG_TETD) && t == SEG_TETD)) {
+    if (act) {
+      const TetRec* r = reinterpret_cast<const TetRec*>(st) + tid;
+      lo = t == SEG_TETH ? proj_quad_core<2, true>(*r, sv, lam, tp, ts) : proj_quad_core<3, true>(*r, sv, lam, tp, ts);
+    }
+    release();
+    if (!act) return;
+  } else {
+    release();
+    return;
+  }
   __stcs(a.lam_out + gi, lo);
 }
 
-// Reverse update of constraint `tid` of chunk c from stage st.
+// Reverse update of constraint `tid` of chunk c from stage st.  The reverse holds more
+// state per update (tape, adjoint slots); it reads the stage as it goes and the caller
+// releases the stage afterwards.
 template <int TM>
 __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk& c, const unsigned char* st,
                                           float4* sx, bool first, bool last) {
@@ -421,16 +461,23 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     const int s = k % S;
     const unsigned char* st = stage + (size_t)s * a.slot_bytes;
     const PhaseChunk c = sch[k];
+    // a warp hands the stage back once all its threads have read what they need from it
+    uint64_t* const emp = &empty[s];
+    auto release = [emp, lane]() {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(emp);
+    };
     if (mbar_wait(&full[s], (unsigned)(k / S) & 1u, a.wait_cycles)) {
-      if (REV)
+      if (REV) {
         vjp_chunk<TM>(a, c, st, sv, first, last);
-      else
-        fwd_chunk<MODE == 1, TM>(a, c, st, sv);
+        release();
+      } else {
+        fwd_chunk<MODE == 1, TM>(a, c, st, sv, release);
+      }
     } else {
       abort_run = 1;
+      release();
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
     if ((c.flags & (REV ? kChunkColorFirst : kChunkColorLast)) || k + 1 == nch) {
       consumer_sync();
       if (abort_run) {
