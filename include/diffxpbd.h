@@ -344,9 +344,12 @@ xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t ste
    `steps` steps of `iters` iterations from (x0, v0), the loss L = 1/2 |x_steps - target|^2
    (Sec. 4.1 with one keyframe at the last step), and the full reverse sweep.  The server
    keeps every admitted request's state, checkpoints and tapes resident and advances all
-   of them together: each launch of its dispatch kernel runs the next pass (a color of a
-   forward or reverse iteration, a contact pass, a prediction, ...) of every resident
-   request, reading a concatenated table of those passes.  Requests submitted while others
+   of them together: each tick runs the next pass (a color of a forward or reverse
+   iteration, a contact pass, a prediction, ...) of every resident request, reading a
+   concatenated table of those passes; one cooperative launch of the dispatch kernel runs
+   a batch of ticks, its blocks meeting at a grid-wide barrier between ticks (every wait
+   bounded: one that runs out is reported as XPBD_ERR_TIMEOUT by a later
+   xpbd_server_run, and that batch's results are invalid).  Requests submitted while others
    run are admitted at the next xpbd_server_run call, in submission order, as soon as a
    slot is free and their workspace fits in the memory budget; their passes then share the
    GPU with the requests already running.  Every request computes exactly the values it
@@ -375,7 +378,7 @@ typedef struct {
   int64_t submitted, admitted, completed;
   int32_t pending, active;  /* waiting for admission / resident on the GPU                 */
   size_t bytes_in_use, budget;
-  int64_t ticks;            /* dispatch-kernel launches so far                             */
+  int64_t ticks;            /* ticks dispatched so far (one cooperative launch per batch)  */
   int64_t items;            /* passes executed by them                                     */
 } xpbd_server_stats;
 
@@ -395,10 +398,11 @@ xpbd_status xpbd_server_destroy(xpbd_server s);
    budget; XPBD_ERR_INVALID for bad arguments.  Returns a ticket. */
 xpbd_status xpbd_server_submit(xpbd_server s, const xpbd_request* r, uint64_t* ticket);
 
-/* Retire finished requests, admit queued ones that fit, and queue up to `max_ticks`
-   dispatch launches on the server's stream (fewer if every resident request finishes).
-   Returns without waiting for the GPU; at most two batches of launches are in flight.
-   *active_out (may be NULL) receives the number of resident requests afterwards. */
+/* Retire finished requests, admit queued ones that fit, and queue a batch of up to
+   `max_ticks` ticks (at most 256; fewer if every resident request finishes) as one
+   cooperative launch on the server's stream.  Returns without waiting for the GPU; at most
+   two batches are in flight.  XPBD_ERR_TIMEOUT if a grid barrier of an earlier batch gave
+   up.  *active_out (may be NULL) receives the number of resident requests afterwards. */
 xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_out);
 
 /* *done = 1 once every pass of the request has finished on the GPU (its outputs are then

@@ -1,14 +1,17 @@
 // Batched serving runtime: continuous batching of forward + gradient requests on one GPU.
 //
 // Every admitted request is a fixed program of passes (the same sequence xpbd_forward,
-// xpbd_loss and xpbd_adjoint launch for it).  One launch of k_tick runs the next pass of
-// every resident request: its grid is the concatenation of those passes' blocks, and each
-// block looks up its pass in a table built on the host (a batch of tables is copied in one
-// transfer).  Consecutive passes of one request are ordered by the launch boundaries;
-// passes of different requests touch disjoint memory, so they share a launch freely.
-// Each element of a pass runs the element function of xpbd_elems.cuh that the one-request
-// kernels run, and a pass is split into blocks the same way whatever shares its launch, so
-// a request's results do not depend on the mix.
+// xpbd_loss and xpbd_adjoint launch for it).  A tick runs the next pass of every resident
+// request: its blocks are the concatenation of those passes' blocks, and each block looks
+// up its pass in a table built on the host.  A batch of up to kMaxTicksPerRun ticks is one
+// cooperative launch of k_ticks (a grid no larger than the GPU holds at once): its blocks
+// walk the first tick's blocks, meet at a grid-wide barrier, walk the next tick's, and so
+// on.  Consecutive passes of one request are ordered by those barriers; passes of
+// different requests touch disjoint memory, so they share a tick freely.  Each element of
+// a pass runs the element function of xpbd_elems.cuh that the one-request kernels run,
+// and a pass is split into blocks the same way whatever shares its tick, so a request's
+// results do not depend on the mix.  The barrier's waits are bounded: a wait that runs out
+// latches an error and every block leaves the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,12 +66,16 @@ __host__ __device__ inline int item_blocks(const TickItem& it) {
   return it.kind == IK_REDUCE ? 1 : (it.n + kBlock - 1) / kBlock;
 }
 
-// The dispatch kernel: block b runs block (b - block0) of the pass whose block range holds b.
-__global__ void __launch_bounds__(kBlock, 3) k_tick(const TickItem* __restrict__ items, int n_items) {
-  __shared__ TickItem it;
+// The ticks of one batch: tick t's passes are items [first, first + count) of the batch
+// table, and its blocks number `blocks`.
+struct __align__(16) TickHead {
+  int32_t first, count, blocks, pad;
+};
+
+// Block b of a tick: runs block (b - block0) of the pass whose block range holds b.
+__device__ __forceinline__ void tick_block(const TickItem* __restrict__ items, int n_items, int b, TickItem& it) {
   if (threadIdx.x == 0) {
     int lo = 0, hi = n_items - 1;
-    const int b = blockIdx.x;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
       if (items[mid].block0 <= b)
@@ -79,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_tick(const TickItem* __restrict__
     it = items[lo];
   }
   __syncthreads();
-  const int lb = blockIdx.x - it.block0;
+  const int lb = b - it.block0;
   const int i = lb * kBlock + threadIdx.x;
   const bool ok = i < it.n;
   const bool first = (it.flags & 1) != 0, last = (it.flags & 2) != 0;
@@ -188,6 +195,67 @@ __global__ void __launch_bounds__(kBlock, 3) k_tick(const TickItem* __restrict__
       break;
     default:
       break;
+  }
+  __syncthreads();   // `it` is rewritten by the next block this thread block runs
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is the
+// generation.  The last block to arrive resets the count and advances the generation
+// (release); the others wait for the generation to change (acquire), at most `limit`
+// cycles, after which they latch bit 0 of *err and return false.  Writes of every block
+// before the barrier are visible to every block after it (release / acquire at GPU scope,
+// ordered within a block by __syncthreads).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long limit, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire_gpu(bar + 1);
+    ok = 1;
+    if (atom_add_acq_rel_gpu(bar, 1u) == nblocks - 1) {
+      st_relaxed_gpu(bar, 0u);
+      st_release_gpu(bar + 1, g + 1);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_gpu(bar + 1) == g) {
+        if (clock64() - t0 > limit) {
+          atomicOr(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// One batch of ticks in one cooperative launch (gridDim.x blocks, all resident at once).
+__global__ void __launch_bounds__(kBlock, 3)
+    k_ticks(const TickItem* __restrict__ items, const TickHead* __restrict__ heads, int n_ticks, unsigned* bar,
+            long long limit, int* err) {
+  __shared__ TickItem it;
+  for (int t = 0; t < n_ticks; ++t) {
+    const TickHead h = heads[t];
+    for (int b = blockIdx.x; b < h.blocks; b += gridDim.x) tick_block(items + h.first, h.count, b, it);
+    if (t + 1 < n_ticks && !grid_barrier(bar, gridDim.x, limit, err)) return;
   }
 }
 
@@ -599,12 +667,18 @@ struct xpbd_server_t {
   std::deque<Request*> queued;
   std::vector<Request*> resident;                       // admission order
   std::map<uint64_t, std::unique_ptr<Request>> all;
-  // double-buffered dispatch tables
+  // double-buffered dispatch tables: pass items, then the batch's tick heads
   size_t cap_items = 0;
-  TickItem* host_tab[2] = {nullptr, nullptr};
-  TickItem* dev_tab[2] = {nullptr, nullptr};
+  char* host_tab[2] = {nullptr, nullptr};
+  char* dev_tab[2] = {nullptr, nullptr};
   cudaEvent_t tab_ev[2] = {nullptr, nullptr};
   bool tab_used[2] = {false, false};
+  // the batch kernel's grid barrier (arrival count, generation) and error word; the error
+  // word is copied to pinned memory after every batch and checked when its buffer is reused
+  unsigned* d_bar = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;   // [2], pinned
+  int grid = 1;           // blocks of a batch launch (all resident at once)
   int run_count = 0;
   xpbd_server_stats stats{};
 };
@@ -691,11 +765,27 @@ xpbd_status xpbd_server_create(size_t hbm_budget, int32_t max_slots, void* strea
   }
   s->budget = hbm_budget;
   s->cap_items = (size_t)kMaxTicksPerRun * (size_t)max_slots;
+  const size_t tab_bytes = s->cap_items * sizeof(TickItem) + kMaxTicksPerRun * sizeof(TickHead);
   for (int b = 0; b < 2; ++b) {
-    CU_TRY(cudaHostAlloc((void**)&s->host_tab[b], s->cap_items * sizeof(TickItem), cudaHostAllocDefault));
-    CU_TRY(cudaMalloc((void**)&s->dev_tab[b], s->cap_items * sizeof(TickItem)));
+    CU_TRY(cudaHostAlloc((void**)&s->host_tab[b], tab_bytes, cudaHostAllocDefault));
+    CU_TRY(cudaMalloc((void**)&s->dev_tab[b], tab_bytes));
     CU_TRY(cudaEventCreateWithFlags(&s->tab_ev[b], cudaEventDisableTiming));
   }
+  CU_TRY(cudaMalloc((void**)&s->d_bar, 2 * sizeof(unsigned)));
+  CU_TRY(cudaMemset(s->d_bar, 0, 2 * sizeof(unsigned)));
+  CU_TRY(cudaMalloc((void**)&s->d_err, sizeof(int)));
+  CU_TRY(cudaMemset(s->d_err, 0, sizeof(int)));
+  CU_TRY(cudaHostAlloc((void**)&s->h_err, 2 * sizeof(int), cudaHostAllocDefault));
+  s->h_err[0] = s->h_err[1] = 0;
+  // a cooperative launch must fit on the GPU at once: the grid is the number of k_ticks
+  // blocks every SM holds together
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  CU_TRY(cudaGetDevice(&dev));
+  CU_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  CU_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ticks, kBlock, 0));
+  if (!coop || per_sm < 1) return fail(XPBD_ERR_CUDA, "the device cannot run the cooperative serving kernel");
+  s->grid = sms * per_sm;
   s->stats.budget = s->budget;
   *out = s.release();
   return XPBD_OK;
@@ -715,6 +805,9 @@ xpbd_status xpbd_server_destroy(xpbd_server s) {
     if (s->dev_tab[b]) cudaFree(s->dev_tab[b]);
     if (s->tab_ev[b]) cudaEventDestroy(s->tab_ev[b]);
   }
+  if (s->d_bar) cudaFree(s->d_bar);
+  if (s->d_err) cudaFree(s->d_err);
+  if (s->h_err) cudaFreeHost(s->h_err);
   delete s;
   return XPBD_OK;
 }
@@ -758,13 +851,17 @@ xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_ou
   if (st != XPBD_OK) return st;
   const int T = std::max(1, std::min<int>(max_ticks, kMaxTicksPerRun));
   const int b = s->run_count & 1;
-  if (s->tab_used[b]) CU_TRY(cudaEventSynchronize(s->tab_ev[b]));   // at most two batches in flight
-  TickItem* tab = s->host_tab[b];
-  std::vector<std::pair<int, int>> ticks;            // (first item, item count) per tick
-  std::vector<int> blocks;                           // grid size per tick
-  std::vector<std::vector<Request*>> finish_at(T);   // programs whose last pass is in tick t
-  std::vector<Request*> finish_now;                  // programs that ended in an earlier batch
-  for (Request* q : s->resident) q->last_tick = -1;
+  if (s->tab_used[b]) {   // at most two batches in flight
+    CU_TRY(cudaEventSynchronize(s->tab_ev[b]));
+    if (s->h_err[b]) {
+      s->h_err[b] = 0;
+      return fail(XPBD_ERR_TIMEOUT, "a grid barrier of the serving kernel gave up waiting");
+    }
+  }
+  TickItem* tab = reinterpret_cast<TickItem*>(s->host_tab[b]);
+  TickHead* heads = reinterpret_cast<TickHead*>(s->host_tab[b] + s->cap_items * sizeof(TickItem));
+  int n_ticks = 0, max_blocks = 0;
+  std::vector<Request*> finished;   // programs whose last pass is in this batch (or earlier)
   size_t used = 0;
   for (int t = 0; t < T; ++t) {
     const size_t first = used;
@@ -776,36 +873,36 @@ xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_ou
         it.block0 = nb;
         nb += item_blocks(it);
         ++used;
-        q->last_tick = t;
       } else {
         q->state = RQ_ALL_QUEUED;
-        if (q->last_tick >= 0)
-          finish_at[q->last_tick].push_back(q);
-        else
-          finish_now.push_back(q);
+        finished.push_back(q);
       }
     }
     if (used == first) break;
-    ticks.push_back({(int)first, (int)(used - first)});
-    blocks.push_back(nb);
+    heads[n_ticks++] = TickHead{(int)first, (int)(used - first), nb, 0};
+    max_blocks = std::max(max_blocks, nb);
   }
-  for (Request* q : finish_now) {
+  if (n_ticks > 0) {
+    char* dev = s->dev_tab[b];
+    const TickItem* d_items = reinterpret_cast<const TickItem*>(dev);
+    const TickHead* d_heads = reinterpret_cast<const TickHead*>(dev + s->cap_items * sizeof(TickItem));
+    CU_TRY(cudaMemcpyAsync(dev, tab, used * sizeof(TickItem), cudaMemcpyHostToDevice, s->stream));
+    CU_TRY(cudaMemcpyAsync((void*)d_heads, heads, n_ticks * sizeof(TickHead), cudaMemcpyHostToDevice, s->stream));
+    CU_TRY(cudaMemsetAsync(s->d_bar, 0, sizeof(unsigned), s->stream));   // arrival count
+    int grid = std::min(s->grid, max_blocks);
+    long long limit = 1ll << 31;   // ~1 s at 2 GHz, far beyond any tick
+    int nt = n_ticks;
+    void* args[] = {(void*)&d_items, (void*)&d_heads, (void*)&nt, (void*)&s->d_bar, (void*)&limit, (void*)&s->d_err};
+    CU_TRY(cudaLaunchCooperativeKernel((const void*)k_ticks, dim3(grid), dim3(kBlock), args, 0, s->stream));
+    s->stats.ticks += n_ticks;
+    s->stats.items += (int64_t)used;
+  }
+  for (Request* q : finished) {
     CU_TRY(cudaEventRecord(q->ev, s->stream));
     q->ev_recorded = true;
   }
-  if (!ticks.empty()) {
-    CU_TRY(cudaMemcpyAsync(s->dev_tab[b], tab, used * sizeof(TickItem), cudaMemcpyHostToDevice, s->stream));
-    for (size_t t = 0; t < ticks.size(); ++t) {
-      k_tick<<<blocks[t], kBlock, 0, s->stream>>>(s->dev_tab[b] + ticks[t].first, ticks[t].second);
-      LAUNCH_CHECK();
-      for (Request* q : finish_at[t]) {
-        CU_TRY(cudaEventRecord(q->ev, s->stream));
-        q->ev_recorded = true;
-      }
-      s->stats.ticks += 1;
-      s->stats.items += ticks[t].second;
-    }
-  }
+  CU_TRY(cudaMemcpyAsync(&s->h_err[b], s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CU_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
   CU_TRY(cudaEventRecord(s->tab_ev[b], s->stream));
   s->tab_used[b] = true;
   s->run_count += 1;
