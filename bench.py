@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--serving-load", type=float, default=1.0,
                     help="arrival rate as a multiple of the one-at-a-time service rate")
     ap.add_argument("--serving-slots", type=int, default=64)
+    ap.add_argument("--serving-ticks", type=int, default=32, help="ticks per server batch (one launch)")
     return ap.parse_args()
 
 
@@ -802,6 +803,7 @@ def run_serving(args):
     live = {}
     nxt = 0
     max_active = 0
+    t_run = t_poll = 0.0
     t0 = time.perf_counter()
     while nxt < len(items) or live:
         now = time.perf_counter() - t0
@@ -815,11 +817,15 @@ def run_serving(args):
         if not live:
             time.sleep(min(max(arrivals[nxt] - now, 0.0), 0.002))
             continue
-        max_active = max(max_active, srv.run(32))
+        r0 = time.perf_counter()
+        max_active = max(max_active, srv.run(args.serving_ticks))
+        r1 = time.perf_counter()
         for t in list(live):
             if srv.poll(t):
                 k = live.pop(t)
                 lat_b[k] = time.perf_counter() - t0 - arrivals[k]
+        t_run += r1 - r0
+        t_poll += time.perf_counter() - r1
     span_b = time.perf_counter() - t0
     st = srv.stats()
     worst = 0.0
@@ -846,7 +852,10 @@ def run_serving(args):
                    "requests": len(items), "slots": args.serving_slots, "mean_service_s": round(mean_service, 4)},
         "batched": {"p50_s": round(pb[0], 4), "p99_s": round(pb[1], 4), "makespan_s": round(span_b, 3),
                     "steps_per_s": round(sim_steps / span_b, 1), "updates_per_s": updates / span_b,
-                    "max_resident": max_active, "dispatch_launches": st["ticks"], "passes": st["items"]},
+                    "max_resident": max_active, "ticks": st["ticks"], "batch_launches": st["batches"],
+                    "passes": st["items"], "host_wait_s": round(st["host_wait_s"], 3),
+                    "host_build_s": round(st["host_build_s"], 3), "host_run_call_s": round(t_run, 3),
+                    "host_poll_s": round(t_poll, 3)},
         "one_at_a_time": {"p50_s": round(pa[0], 4), "p99_s": round(pa[1], 4), "makespan_s": round(span_a, 3),
                           "steps_per_s": round(sim_steps / span_a, 1), "updates_per_s": updates / span_a},
         "speedup_steps_per_s": round(span_a / span_b, 3),

@@ -380,6 +380,10 @@ typedef struct {
   size_t bytes_in_use, budget;
   int64_t ticks;            /* ticks dispatched so far (one cooperative launch per batch)  */
   int64_t items;            /* passes executed by them                                     */
+  int64_t batches;          /* cooperative launches so far                                 */
+  double host_wait_s;       /* host time xpbd_server_run spent waiting for the GPU (a batch
+                               table still in use)                                         */
+  double host_build_s;      /* host time spent building batch tables and launching         */
 } xpbd_server_stats;
 
 /* Device bytes a request allocates at admission (checkpoints, tapes, gradient state). */

@@ -79,7 +79,8 @@ class XpbdRequest(C.Structure):
 class XpbdServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("pending", C.c_int32), ("active", C.c_int32), ("bytes_in_use", C.c_size_t),
-                ("budget", C.c_size_t), ("ticks", C.c_int64), ("items", C.c_int64)]
+                ("budget", C.c_size_t), ("ticks", C.c_int64), ("items", C.c_int64), ("batches", C.c_int64),
+                ("host_wait_s", C.c_double), ("host_build_s", C.c_double)]
 
 
 class XpbdError(RuntimeError):

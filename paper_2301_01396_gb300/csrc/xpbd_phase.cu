@@ -440,10 +440,17 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     if (threadIdx.x == kPhaseBlock && !a.no_issue) {
       // stages [0, S) were issued above (chunks past nch are empty); refill from chunk S on
       int issued = S < a.cstride ? S : a.cstride;
+      // stage s = issued mod S and the parity of its previous use, kept as counters (a
+      // division by the runtime S per chunk costs more than the rest of this loop)
+      int s = 0;
+      unsigned par = 0;
       for (; issued < nch; ++issued) {
-        const int s = issued % S;
-        if (!mbar_wait(&empty[s], (unsigned)(issued / S - 1) & 1u, a.wait_cycles)) break;   // the consumers stopped
+        if (!mbar_wait(&empty[s], par, a.wait_cycles)) break;   // the consumers stopped
         issue_chunk<REV, TM>(a, sch[issued], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
+        if (++s == S) {
+          s = 0;
+          par ^= 1u;
+        }
       }
       // Whether it issued every chunk or gave up, the CTA must not end while a copy into its
       // shared memory is in flight (the consumers may have stopped early): wait for the last
@@ -457,8 +464,14 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     return;
   }
   const int lane = threadIdx.x & 31;
+  // stage s = k mod S and par = (k / S) & 1, the phase of stage s that chunk k fills: kept as
+  // counters in the reverse (two divisions by the runtime S per chunk cost more than they
+  // save registers there); the forward kernels, at their register limit, divide
+  int sc = 0;
+  unsigned pc = 0;
   for (int k = 0; k < nch; ++k) {
-    const int s = k % S;
+    const int s = REV ? sc : k % S;
+    const unsigned par = REV ? pc : (unsigned)(k / S) & 1u;
     const unsigned char* st = stage + (size_t)s * a.slot_bytes;
     const PhaseChunk c = sch[k];
     // a warp hands the stage back once all its threads have read what they need from it
@@ -467,7 +480,7 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
       __syncwarp();
       if (lane == 0) mbar_arrive(emp);
     };
-    if (mbar_wait(&full[s], (unsigned)(k / S) & 1u, a.wait_cycles)) {
+    if (mbar_wait(&full[s], par, a.wait_cycles)) {
       if (REV) {
         vjp_chunk<TM>(a, c, st, sv, first, last);
         release();
@@ -477,6 +490,10 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     } else {
       abort_run = 1;
       release();
+    }
+    if (REV && ++sc == S) {
+      sc = 0;
+      pc ^= 1u;
     }
     if ((c.flags & (REV ? kChunkColorFirst : kChunkColorLast)) || k + 1 == nch) {
       consumer_sync();

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -851,13 +852,17 @@ xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_ou
   if (st != XPBD_OK) return st;
   const int T = std::max(1, std::min<int>(max_ticks, kMaxTicksPerRun));
   const int b = s->run_count & 1;
+  using clk = std::chrono::steady_clock;
+  const auto t_wait = clk::now();
   if (s->tab_used[b]) {   // at most two batches in flight
     CU_TRY(cudaEventSynchronize(s->tab_ev[b]));
+    s->stats.host_wait_s += std::chrono::duration<double>(clk::now() - t_wait).count();
     if (s->h_err[b]) {
       s->h_err[b] = 0;
       return fail(XPBD_ERR_TIMEOUT, "a grid barrier of the serving kernel gave up waiting");
     }
   }
+  const auto t_build = clk::now();
   TickItem* tab = reinterpret_cast<TickItem*>(s->host_tab[b]);
   TickHead* heads = reinterpret_cast<TickHead*>(s->host_tab[b] + s->cap_items * sizeof(TickItem));
   int n_ticks = 0, max_blocks = 0;
@@ -896,6 +901,7 @@ xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_ou
     CU_TRY(cudaLaunchCooperativeKernel((const void*)k_ticks, dim3(grid), dim3(kBlock), args, 0, s->stream));
     s->stats.ticks += n_ticks;
     s->stats.items += (int64_t)used;
+    s->stats.batches += 1;
   }
   for (Request* q : finished) {
     CU_TRY(cudaEventRecord(q->ev, s->stream));
@@ -906,6 +912,7 @@ xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_ou
   CU_TRY(cudaEventRecord(s->tab_ev[b], s->stream));
   s->tab_used[b] = true;
   s->run_count += 1;
+  s->stats.host_build_s += std::chrono::duration<double>(clk::now() - t_build).count();
   if (active_out) *active_out = (int)s->resident.size();
   return XPBD_OK;
 }
