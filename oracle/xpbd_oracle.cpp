@@ -636,7 +636,7 @@ void solve_iteration(const Model& M, const Params<T>& P, Work<T>& W) {
   for (int c = 0; c < M.K; ++c) {
     int b = M.offsets[c], e = M.offsets[c + 1];
     // constraints of one color share no vertex: they are independent
-#pragma omp parallel for schedule(static) if (e - b > 4096)
+#pragma omp parallel for schedule(static) if (e - b >= 1024)
     for (int t = b; t < e; ++t) project_constraint(M, P, M.order[t], W);
   }
   if (P.flags) {

@@ -50,6 +50,22 @@ def test_ground_cloth_256_forward_first_steps():
     assert np.abs(xs - xs_ref).max() < POS_TOL
 
 
+def test_ground_cloth_256_error_vs_step_full_horizon():
+    """Config 2 over its full horizon (100 steps of 30 iterations): the largest position
+    error against the oracle at every step (printed every 10 steps).  The oracle's own
+    float32-rounding emulation stays within 1.1e-6 m of it over the 100 steps, so a float32
+    implementation can stay within the 1e-5 m position tolerance; the bound asserted over
+    the whole horizon is that tolerance.  (Over 100 steps the cloth lies on the ground, and
+    a contact whose predicted position is within float32 rounding of the plane could be
+    decided differently by float32 and float64; none is on this trajectory.)"""
+    sc = scenes.ground_cloth(256)
+    xs_ref, _ = oracle.forward(sc)
+    _, _, _, xs, _ = gpu_forward(sc)
+    err = np.abs(xs - xs_ref).max(axis=(1, 2))
+    print("PARITY config2 error vs step: " + " ".join(f"{n}:{err[n]:.1e}" for n in range(0, sc.steps + 1, 10)))
+    assert err.max() < POS_TOL, err.max()
+
+
 def test_ground_cloth_256_contact_regime():
     """From the oracle state of step 15, when the tilted cloth's low edge reaches the
     ground: forward over steps 15-18 and the reverse sweep over steps 16-18.  Over this
@@ -76,7 +92,9 @@ def test_tet_block_32_forward_to_contact():
     assert contact_margin(sc, xs_ref, vs_ref) > 1e-6
     _, _, _, xs, vs = gpu_forward(sc)
     assert contact_signs_agree(sc, xs, vs, xs_ref, vs_ref)
-    assert np.abs(xs - xs_ref).max() < POS_TOL
+    err = np.abs(xs - xs_ref).max(axis=(1, 2))
+    print("PARITY config3 error vs step: " + " ".join(f"{n}:{err[n]:.1e}" for n in range(sc.steps + 1)))
+    assert err.max() < POS_TOL
 
 
 def test_tet_block_32_adjoint_in_contact():
