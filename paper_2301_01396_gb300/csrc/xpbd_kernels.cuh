@@ -142,6 +142,8 @@ struct PhaseLaunch {
   int chunk_bytes;
   int slot_bytes;          // bytes of one stage
   int stages;              // stages in flight
+  unsigned stage_magic;    // ceil(2^32 / stages): k / stages = __umulhi(k, stage_magic) for the
+                           // chunk counts of a group (exact for k < 2^32 / stages)
 };
 // Sizes of one phase: its groups, the largest group's vertex and chunk counts and the
 // constraint types present (bit t set when type t occurs; selects the kernel).

@@ -440,17 +440,13 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     if (threadIdx.x == kPhaseBlock && !a.no_issue) {
       // stages [0, S) were issued above (chunks past nch are empty); refill from chunk S on
       int issued = S < a.cstride ? S : a.cstride;
-      // stage s = issued mod S and the parity of its previous use, kept as counters (a
-      // division by the runtime S per chunk costs more than the rest of this loop)
-      int s = 0;
-      unsigned par = 0;
       for (; issued < nch; ++issued) {
-        if (!mbar_wait(&empty[s], par, a.wait_cycles)) break;   // the consumers stopped
+        // stage issued mod S, whose previous use was phase (issued / S - 1) mod 2; the
+        // quotient by multiplication (a division by the runtime S costs ~20 instructions)
+        const unsigned q = __umulhi((unsigned)issued, a.stage_magic);
+        const int s = issued - (int)q * S;
+        if (!mbar_wait(&empty[s], (q - 1u) & 1u, a.wait_cycles)) break;   // the consumers stopped
         issue_chunk<REV, TM>(a, sch[issued], stage + (size_t)s * a.slot_bytes, &full[s], first, last);
-        if (++s == S) {
-          s = 0;
-          par ^= 1u;
-        }
       }
       // Whether it issued every chunk or gave up, the CTA must not end while a copy into its
       // shared memory is in flight (the consumers may have stopped early): wait for the last
@@ -464,14 +460,12 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     return;
   }
   const int lane = threadIdx.x & 31;
-  // stage s = k mod S and par = (k / S) & 1, the phase of stage s that chunk k fills: kept as
-  // counters in the reverse (two divisions by the runtime S per chunk cost more than they
-  // save registers there); the forward kernels, at their register limit, divide
-  int sc = 0;
-  unsigned pc = 0;
   for (int k = 0; k < nch; ++k) {
-    const int s = REV ? sc : k % S;
-    const unsigned par = REV ? pc : (unsigned)(k / S) & 1u;
+    // stage s = k mod S and par = (k / S) mod 2, the phase of stage s that chunk k fills
+    // (the quotient by multiplication, as in the producer)
+    const unsigned q = __umulhi((unsigned)k, a.stage_magic);
+    const int s = k - (int)q * S;
+    const unsigned par = q & 1u;
     const unsigned char* st = stage + (size_t)s * a.slot_bytes;
     const PhaseChunk c = sch[k];
     // a warp hands the stage back once all its threads have read what they need from it
@@ -490,10 +484,6 @@ __global__ void __launch_bounds__(kPhaseThreads, MODE == 2 ? XPBD_PHASE_VJP_MIN_
     } else {
       abort_run = 1;
       release();
-    }
-    if (REV && ++sc == S) {
-      sc = 0;
-      pc ^= 1u;
     }
     if ((c.flags & (REV ? kChunkColorFirst : kChunkColorLast)) || k + 1 == nch) {
       consumer_sync();
@@ -586,6 +576,7 @@ void launch_mode(PhaseLaunch a, const PhaseShape& sh, bool first, bool last, cud
   a.chunk_bytes = p.chunk_bytes;
   a.slot_bytes = p.slot_bytes;
   a.stages = p.stages;
+  a.stage_magic = p.stages > 0 ? (unsigned)((0x100000000ull + (unsigned)p.stages - 1) / (unsigned)p.stages) : 0u;
   const size_t smem = p.smem();
   switch (kernel_mask(sh.type_mask)) {
     case kMaskCloth: k_phase<MODE, kMaskCloth><<<sh.n_groups, kPhaseThreads, smem, s>>>(a, first, last); break;
