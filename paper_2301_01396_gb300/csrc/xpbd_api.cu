@@ -731,6 +731,7 @@ const char* xpbd_last_error(void) { return g_err.c_str(); }
 
 xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_create");
   if (!md || !out) return fail(XPBD_ERR_INVALID, "null argument");
   *out = nullptr;
   const int V = md->n_vertices, nd = md->n_dist, nb = md->n_bend, nt = md->n_tet, K = md->n_colors;
@@ -1033,6 +1034,7 @@ size_t xpbd_workspace_bytes(xpbd_handle h, int32_t iters) {
 xpbd_status xpbd_forward(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
                          const float* x0, const float* v0, float* ck, void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_forward");
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
   if (h->V > 0 && (!x0 || !v0 || !ck)) return fail(XPBD_ERR_INVALID, "x0/v0/checkpoints NULL");
@@ -1065,6 +1067,7 @@ xpbd_status xpbd_read_state(xpbd_handle h, const float* ck, int32_t step, float*
 xpbd_status xpbd_loss(xpbd_handle h, const float* ck, int32_t n_keys, const int32_t* key_steps,
                       const float* targets, double* loss_out, float* seeds_out, void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_loss");
   if (!h || !ck || n_keys < 0 || (n_keys > 0 && (!key_steps || !targets)))
     return fail(XPBD_ERR_INVALID, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1265,6 +1268,7 @@ int32_t xpbd_sparse_slot(int32_t steps, int32_t stride, int32_t step) {
 xpbd_status xpbd_forward_sparse(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
                                 const float* x0, const float* v0, int32_t stride, float* ck, void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_forward_sparse");
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
   if (stride < 1) return fail(XPBD_ERR_INVALID, "stride must be >= 1");
@@ -1297,6 +1301,7 @@ xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t ste
                                 const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
                                 void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_adjoint_sparse");
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
   if (stride < 1) return fail(XPBD_ERR_INVALID, "stride must be >= 1");
@@ -1338,6 +1343,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
                                   const float* seed_dv_T, const xpbd_grads* out, const xpbd_implicit_opts* o,
                                   void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_adjoint_implicit");
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
   if (!ck || !out || !o || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
@@ -1478,6 +1484,7 @@ xpbd_status xpbd_adjoint(xpbd_handle h, const xpbd_params* p, int32_t steps, int
                          const float* seed_dx, const float* seed_dv_T, const xpbd_grads* out,
                          void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_adjoint");
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
   if (!ck || !out || n_seeds < 0 || (n_seeds > 0 && (!seed_steps || !seed_dx)))
@@ -1546,6 +1553,7 @@ xpbd_status xpbd_profile_read(xpbd_handle h, xpbd_kernel_stat* out) {
 xpbd_status xpbd_forward_static(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
                                 const float* x0, const float* v0, float* ck, void* stream) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_forward_static");
   xpbd_status st = check_params(h, p, steps, iters);
   if (st != XPBD_OK) return st;
   // the one-launch-per-color sweep this entry point runs needs one multiplier slot per

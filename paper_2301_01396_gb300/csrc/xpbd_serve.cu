@@ -845,6 +845,7 @@ xpbd_status xpbd_server_submit(xpbd_server s, const xpbd_request* r, uint64_t* t
 
 xpbd_status xpbd_server_run(xpbd_server s, int32_t max_ticks, int32_t* active_out) {
   g_err.clear();
+  NvtxRange nvtx_range("xpbd_server_run");
   if (!s) return fail(XPBD_ERR_INVALID, "null server");
   xpbd_status st = sweep(s);
   if (st != XPBD_OK) return st;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdint>
@@ -16,6 +17,15 @@
 using namespace xpbd;
 
 inline thread_local std::string g_err;
+
+// A named NVTX range around an entry point's host work (what it enqueues shows up under it
+// in a timeline profiler; without a profiler attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 inline xpbd_status fail(xpbd_status st, const std::string& msg) {
   g_err = msg;
