@@ -775,10 +775,16 @@ def run_serving(args):
         torch.cuda.synchronize()
         return g
 
+    def done_one(it):
+        # the next request runs on another handle: give this one's tapes back (thousands of
+        # handles each keeping its largest workspace would not fit in device memory)
+        it["solver"].release_workspace()
+
     n_cal = min(6, len(items))
     t0 = time.perf_counter()
     for it in items[:n_cal]:
         serve_one(it)
+        done_one(it)
     mean_service = (time.perf_counter() - t0) / n_cal
     rng = np.random.default_rng(55)
     gaps = rng.exponential(mean_service / args.serving_load, len(items))
@@ -794,6 +800,8 @@ def run_serving(args):
         g = serve_one(it)
         lat_a.append(time.perf_counter() - t0 - arrivals[k])
         ref.append({kk: v.cpu() for kk, v in g.items()})
+        del g
+        done_one(it)
     span_a = time.perf_counter() - t0
 
     # (b) continuous batching: arrivals are admitted while earlier requests run

@@ -174,8 +174,14 @@ size_t xpbd_checkpoint_bytes(xpbd_handle h, int32_t steps);
 
 /* Device bytes the handle allocates for a forward or adjoint call with `iters`
    iterations (working state, multiplier and position tapes, gradient scratch); the
-   library allocates them on first use and keeps them until xpbd_destroy. */
+   library allocates them on first use and keeps them until xpbd_destroy or
+   xpbd_release_workspace. */
 size_t xpbd_workspace_bytes(xpbd_handle h, int32_t iters);
+
+/* Free the handle's workspace (synchronises the device first); the next call that needs it
+   allocates it again.  For a process that keeps many handles and runs them one at a time.
+   The constraint records and the execution plan stay. */
+xpbd_status xpbd_release_workspace(xpbd_handle h);
 
 /* Forward simulation of `steps` steps (Sec. 3.1).  x0, v0: DEVICE [V*3].  Writes
    checkpoints 0..steps (checkpoint 0 = x0, v0).  Pinned vertices should start with

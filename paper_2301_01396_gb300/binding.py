@@ -106,7 +106,7 @@ def lib():
                      "xpbd_server_poll", "xpbd_server_get_stats", "xpbd_exec_info",
                      "xpbd_selftest_wait_timeout", "xpbd_forward_sparse", "xpbd_adjoint_sparse",
                      "xpbd_sparse_slots", "xpbd_sparse_slot", "xpbd_adjoint_implicit",
-                     "xpbd_material_compliance", "xpbd_material_gradient"):
+                     "xpbd_material_compliance", "xpbd_material_gradient", "xpbd_release_workspace"):
             getattr(L, name).restype = C.c_int
         L.xpbd_checkpoint_bytes.restype = C.c_size_t
         L.xpbd_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int32]
@@ -266,6 +266,10 @@ class Solver:
 
     def workspace_bytes(self, iters: int) -> int:
         return int(lib().xpbd_workspace_bytes(self._h, iters))
+
+    def release_workspace(self):
+        """xpbd_release_workspace: free the handle's working buffers until its next call."""
+        _check(lib().xpbd_release_workspace(self._h))
 
     def new_checkpoints(self, steps: int, device="cuda") -> torch.Tensor:
         """[(steps+1), 2, V, 4] float32: per step (x,y,z,w) positions then velocities."""

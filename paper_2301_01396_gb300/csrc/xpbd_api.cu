@@ -66,7 +66,10 @@ xpbd_status set_alpha(xpbd_solver* h, const xpbd_params* p, cudaStream_t s, bool
   const int* cnt = phase ? h->n_prec : h->n_rec;
   for (int t = 0; t < 4; ++t)
     launch(h, XPBD_K_OTHER, cnt[t], s, [&] {
-      launch_set_alpha((SegType)t, rec[t], perm + off[t], cnt[t], p->compliance, inv_dt2, h->d_err, s);
+      if (phase && t == SEG_BEND)
+        launch_set_alpha_btail(h->d_prec_btail, perm + off[t], cnt[t], p->compliance, inv_dt2, h->d_err, s);
+      else
+        launch_set_alpha((SegType)t, rec[t], perm + off[t], cnt[t], p->compliance, inv_dt2, h->d_err, s);
     });
   const int nmr = phase ? h->n_prec[SEG_MEMB] : h->nm;
   launch(h, XPBD_K_OTHER, nmr, s, [&] {
@@ -267,6 +270,15 @@ xpbd_status static_scratch_address(void** out) {
   return XPBD_OK;
 }
 
+// Frees every growable workspace buffer of a handle (the caller has synchronised).
+void release_workspace(xpbd_solver* h) {
+  DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
+                    &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
+                    &h->partials, &h->roll, &h->seg, &h->imp_blocks, &h->imp_vec, &h->imp_dinv,
+                    &h->imp_sc};
+  for (DevBuf* b : bufs) b->release();
+}
+
 // ---------------------------------------------------------------- phase plan
 // Runs of consecutive colors whose constraints, taken together, split into connected
 // components of at most kPhaseMaxVerts vertices are launched as one phase kernel
@@ -462,7 +474,7 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
   std::vector<PhaseChunk> chunks;
   std::vector<int> pverts;
   std::vector<int> loc(V, -1), comp_of_root(V, -1), group_of_vertex(V, -1);
-  const double rec_bytes[kSegTypes] = {sizeof(DistRec), sizeof(BendRec), sizeof(TetRec), sizeof(TetRec),
+  const double rec_bytes[kSegTypes] = {sizeof(DistRec), sizeof(int4) + sizeof(BendTail), sizeof(TetRec), sizeof(TetRec),
                                        sizeof(MembRec)};
   auto type_size = [&](int t) -> size_t {
     return t == 0 ? pd.size() : (t == 1 ? pb.size() : (t == 2 ? ph.size() : (t == 3 ? pdv.size() : pm.size())));
@@ -683,7 +695,16 @@ xpbd_status build_phases(xpbd_solver* h, const int* offsets, const int* order, c
     return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   };
   cudaError_t e = up(&h->d_prec[0], pd.data(), pd.size() * sizeof(DistRec));
-  if (e == cudaSuccess) e = up(&h->d_prec[1], pb.data(), pb.size() * sizeof(BendRec));
+  {   // bending records as vertex indices and tails
+    std::vector<int4> bv(pb.size());
+    std::vector<BendTail> bt(pb.size());
+    for (size_t i = 0; i < pb.size(); ++i) {
+      bv[i] = make_int4(pb[i].v[0], pb[i].v[1], pb[i].v[2], pb[i].v[3]);
+      bt[i] = BendTail{pb[i].theta0, pb[i].at};
+    }
+    if (e == cudaSuccess) e = up(&h->d_prec[1], bv.data(), bv.size() * sizeof(int4));
+    if (e == cudaSuccess) e = up((void**)&h->d_prec_btail, bt.data(), bt.size() * sizeof(BendTail));
+  }
   if (e == cudaSuccess) e = up(&h->d_prec[2], ph.data(), ph.size() * sizeof(TetRec));
   if (e == cudaSuccess) e = up(&h->d_prec[3], pdv.data(), pdv.size() * sizeof(TetRec));
   if (e == cudaSuccess) e = up(&h->d_prec[4], pm.data(), pm.size() * sizeof(MembRec));
@@ -716,6 +737,7 @@ PhaseLaunch phase_args(const xpbd_solver* h, const xpbd_solver::PhaseHost& ph) {
     a.prec[t] = h->d_prec[t];
     a.tape_off[t] = h->ptape_off[t];
   }
+  a.prec_btail = h->d_prec_btail;
   a.memb_stride = h->n_prec[SEG_MEMB];
   a.err = h->d_err;
   a.wait_cycles = 1ll << 31;   // ~1 s at 2 GHz, far beyond any copy
@@ -983,6 +1005,13 @@ xpbd_status xpbd_create(const xpbd_model* md, xpbd_handle* out) {
   return XPBD_OK;
 }
 
+xpbd_status xpbd_release_workspace(xpbd_handle h) {
+  if (!h) return fail(XPBD_ERR_INVALID, "null handle");
+  CU_TRY(cudaDeviceSynchronize());
+  release_workspace(h);
+  return XPBD_OK;
+}
+
 xpbd_status xpbd_destroy(xpbd_handle h) {
   if (!h) return XPBD_OK;
   cudaDeviceSynchronize();
@@ -995,14 +1024,11 @@ xpbd_status xpbd_destroy(xpbd_handle h) {
   if (h->d_err) cudaFree(h->d_err);
   for (int t = 0; t < kSegTypes; ++t)
     if (h->d_prec[t]) cudaFree(h->d_prec[t]);
+  if (h->d_prec_btail) cudaFree(h->d_prec_btail);
   void* plan[] = {h->d_pperm, h->d_groups, h->d_chunks, h->d_chunks_rev, h->d_pverts};
   for (void* q : plan)
     if (q) cudaFree(q);
-  DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
-                    &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
-                    &h->partials, &h->roll, &h->seg, &h->imp_blocks, &h->imp_vec, &h->imp_dinv,
-                    &h->imp_sc};
-  for (DevBuf* b : bufs) b->release();
+  release_workspace(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return XPBD_OK;

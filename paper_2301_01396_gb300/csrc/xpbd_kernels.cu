@@ -37,6 +37,12 @@ __global__ void k_set_alpha(Rec* __restrict__ rec, const int* __restrict__ perm,
   set_alpha_elem<Rec, VOL>(i, rec, perm, compliance, inv_dt2, err);
 }
 
+void launch_set_alpha_btail(BendTail* tail, const int* perm, int n, const float* compliance, float inv_dt2, int* err,
+                            cudaStream_t s) {
+  if (n <= 0) return;
+  k_set_alpha<BendTail, false><<<grid_for(n), kBlock, 0, s>>>(tail, perm, n, compliance, inv_dt2, err);
+}
+
 void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float* compliance,
                       float inv_dt2, int* err, cudaStream_t s) {
   if (n <= 0) return;

@@ -37,6 +37,9 @@ void launch_init_ckpt(const float* x0, const float* v0, const float* w, float4* 
                       int V, cudaStream_t s);
 void launch_set_alpha(SegType t, void* rec, const int* perm, int n, const float* compliance,
                       float inv_dt2, int* err, cudaStream_t s);
+// alpha~ of the phase bending records' tails (BendTail array)
+void launch_set_alpha_btail(BendTail* tail, const int* perm, int n, const float* compliance, float inv_dt2, int* err,
+                            cudaStream_t s);
 void launch_predict(const float4* ckx, const float4* ckv, float4* P, const float* fg_n,
                     const float* fv, const float* fvs_n, float dt, float gx, float gy, float gz, Collide c,
                     uint8_t* cflags, int V, cudaStream_t s);
@@ -124,7 +127,9 @@ struct PhaseLaunch {
   const int* pverts;
   int vstride, cstride;
   int slot_off[5];         // offset of each type in the multiplier slot space (multiples of 4)
-  const void* prec[5];     // phase records (vertex indices local to the group)
+  const void* prec[5];     // phase records (vertex indices local to the group); bending:
+                           // the int4 vertex indices, with their tails in prec_btail
+  const BendTail* prec_btail;
   size_t tape_off[5];      // float4 offset of each type within one iteration's tape
   int memb_stride;         // membranes: slot k of phase record i at slot_off[4] + i + k * memb_stride
   float4* P;               // positions (forward / replay) or vertex adjoints (reverse)

@@ -108,6 +108,12 @@ struct __align__(16) MembRec {
   float A;
   float a00, a11, a01, a22;
 };
+// The phase kernels keep their bending records as two arrays: the four vertex indices
+// (int4) and this tail (rest angle, alpha~), 24 bytes per record instead of 32, staged as
+// two contiguous blocks (16-byte and 8-byte reads per thread, free of bank conflicts).
+struct __align__(8) BendTail {
+  float theta0, at;
+};
 static_assert(sizeof(MembRec) == 48, "MembRec");
 static_assert(sizeof(DistRec) == 16, "DistRec");
 static_assert(sizeof(BendRec) == 32, "BendRec");

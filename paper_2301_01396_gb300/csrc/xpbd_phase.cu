@@ -92,7 +92,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // Record bytes staged per constraint (a coupled pair stages its C_H and its C_D record).
 __host__ __device__ constexpr unsigned rec_size(int t) {
   return t == SEG_DIST ? (unsigned)sizeof(DistRec)
-                       : (t == SEG_BEND ? (unsigned)sizeof(BendRec)
+                       : (t == SEG_BEND ? (unsigned)(sizeof(int4) + sizeof(BendTail))
                                         : (t == SEG_MEMB ? (unsigned)sizeof(MembRec)
                                                          : (t == kChunkPair ? 2u : 1u) * (unsigned)sizeof(TetRec)));
 }
@@ -118,7 +118,8 @@ struct TypeSet {
   static __device__ __forceinline__ unsigned rec(int t) {
     if (memb(t)) return (unsigned)sizeof(MembRec);
     if (pair(t)) return 2u * (unsigned)sizeof(TetRec);
-    return t == SEG_DIST ? (unsigned)sizeof(DistRec) : (t == SEG_BEND ? (unsigned)sizeof(BendRec) : (unsigned)sizeof(TetRec));
+    return t == SEG_DIST ? (unsigned)sizeof(DistRec)
+                         : (t == SEG_BEND ? (unsigned)(sizeof(int4) + sizeof(BendTail)) : (unsigned)sizeof(TetRec));
   }
   static __device__ __forceinline__ unsigned nv(int t) { return memb(t) ? 3u : (t == SEG_DIST ? 2u : 4u); }
   static __device__ __forceinline__ unsigned nl(int t) { return memb(t) ? 3u : (pair(t) ? 2u : 1u); }
@@ -163,6 +164,9 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
     const unsigned R1 = (unsigned)sizeof(TetRec);
     bulk_g2s(st, (const char*)a.prec[SEG_TETH] + (size_t)c.begin * R1, n * R1, b);
     bulk_g2s(st + n * R1, (const char*)a.prec[SEG_TETD] + (size_t)c.begin * R1, n * R1, b);
+  } else if (t == SEG_BEND) {   // vertex indices, then the tails
+    bulk_g2s(st, (const int4*)a.prec[SEG_BEND] + c.begin, n * (unsigned)sizeof(int4), b);
+    bulk_g2s(st + n * sizeof(int4), a.prec_btail + c.begin, n * (unsigned)sizeof(BendTail), b);
   } else {
     bulk_g2s(st, (const char*)a.prec[h] + (size_t)c.begin * R, n * R, b);
   }
@@ -174,6 +178,21 @@ __device__ __forceinline__ void issue_chunk(const PhaseLaunch& a, const PhaseChu
       if (!first) bulk_g2s(st + L.lb + 8 * n * k, a.lb + so + k * cs, 8 * n, b);
     }
   }
+}
+
+// Bending record i of a stage holding n of them (vertex indices, then tails).
+__device__ __forceinline__ BendRec staged_bend(const unsigned char* st, int n, int i) {
+  const int4 v = reinterpret_cast<const int4*>(st)[i];
+  const BendTail tl = reinterpret_cast<const BendTail*>(st + (size_t)n * sizeof(int4))[i];
+  BendRec r;
+  r.v[0] = v.x;
+  r.v[1] = v.y;
+  r.v[2] = v.z;
+  r.v[3] = v.w;
+  r.theta0 = tl.theta0;
+  r.at = tl.at;
+  r.pad0 = r.pad1 = 0.f;
+  return r;
 }
 
 // Forward / replay update of constraint `tid` of chunk c from stage st.  `release` hands the
@@ -241,12 +260,12 @@ __device__ __forceinline__ void fwd_chunk(const PhaseLaunch& a, const PhaseChunk
   } else if (has<TM>(SEG_BEND) && t == SEG_BEND) {
     if constexpr (early) {
       BendRec r;
-      if (act) r = reinterpret_cast<const BendRec*>(st)[tid];
+      if (act) r = staged_bend(st, n, tid);
       release();
       if (!act) return;
       lo = proj_quad_core<1, true>(r, sv, lam, tp, ts);
     } else {
-      if (act) lo = proj_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], sv, lam, tp, ts);
+      if (act) lo = proj_quad_core<1, true>(staged_bend(st, n, tid), sv, lam, tp, ts);
       release();
       if (!act) return;
     }
@@ -334,7 +353,7 @@ __device__ __forceinline__ void vjp_chunk(const PhaseLaunch& a, const PhaseChunk
   } else {
     const float4 p[4] = {tp[0], tp[ts], tp[2 * ts], tp[3 * ts]};
     if (has<TM>(SEG_BEND) && t == SEG_BEND)
-      l = vjp_quad_core<1, true>(reinterpret_cast<const BendRec*>(st)[tid], p, lam, l, sx);
+      l = vjp_quad_core<1, true>(staged_bend(st, c.count, tid), p, lam, l, sx);
     else if (has<TM>(SEG_TETH) && t == SEG_TETH)
       l = vjp_quad_core<2, true>(reinterpret_cast<const TetRec*>(st)[tid], p, lam, l, sx);
     else if (has<TM>(SEG_TETD) && t == SEG_TETD)

@@ -128,7 +128,9 @@ struct xpbd_solver {
   };
   std::vector<PhaseHost> phases;
   // per type (membranes last: 4 slots per record, component-major)
-  void* d_prec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase-ordered records (padded)
+  void* d_prec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase-ordered records (padded);
+                                                                     // bending: int4 vertex indices
+  BendTail* d_prec_btail = nullptr;                                  // bending: (theta0, alpha~)
   int n_prec[5] = {0, 0, 0, 0, 0};                                   // phase records per type
   int pslot_off[5] = {0, 0, 0, 0, 0};                                // their offsets in the slot space
   size_t ptape_off[5] = {0, 0, 0, 0, 0};                             // float4 offsets in an iteration's tape
