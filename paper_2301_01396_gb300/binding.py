@@ -55,7 +55,8 @@ class XpbdGrads(C.Structure):
 
 class XpbdImplicitOpts(C.Structure):
     _fields_ = [("cg_tol", C.c_double), ("cg_max_iters", C.c_int32), ("pd_project", C.c_int32),
-                ("cg_iters_out", _ip)]
+                ("cg_iters_out", _ip), ("mg_nx", C.c_int32), ("mg_ny", C.c_int32), ("mg_lines", C.c_int32),
+                ("mg_sweeps", C.c_int32)]
 
 
 KERNEL_CLASSES = ("fwd_dist", "fwd_bend", "fwd_tet_h", "fwd_tet_d", "fwd_contact",
@@ -360,9 +361,10 @@ class Solver:
     def adjoint_implicit(self, params: Params, steps: int, iters: int, checkpoints: torch.Tensor, seeds: dict,
                          seed_dv_T: Optional[torch.Tensor] = None,
                          want=("compliance", "x0", "v0", "f_global", "f_vertex"), cg_tol: float = 1e-10,
-                         cg_max_iters: int = 5000, pd_project: bool = True, stream=None):
+                         cg_max_iters: int = 5000, pd_project: bool = True, multigrid=None, stream=None):
         """The paper's implicit adjoint (xpbd_adjoint_implicit).  Returns (float64 gradients,
-        conjugate-gradient iterations per step)."""
+        conjugate-gradient iterations per step).  `multigrid` = (nx, ny[, lines[, sweeps]])
+        preconditions the solve with the grid multigrid V-cycle (block Jacobi when None)."""
         dev = checkpoints.device
         keys = sorted(seeds)
         sd = torch.stack([seeds[k] for k in keys]).contiguous() if keys else None
@@ -375,8 +377,10 @@ class Solver:
                       d_f_vertex_steps=_ptr(out.get("f_vertex_steps"), F64),
                       d_memb_stiffness=_ptr(out.get("memb_stiffness"), F64))
         its = (C.c_int32 * max(steps, 1))()
+        mg = tuple(multigrid) + (0, 0) if multigrid else (0, 0, 0, 0)
         o = XpbdImplicitOpts(cg_tol=float(cg_tol), cg_max_iters=int(cg_max_iters), pd_project=int(bool(pd_project)),
-                             cg_iters_out=C.cast(its, _ip))
+                             cg_iters_out=C.cast(its, _ip), mg_nx=int(mg[0]), mg_ny=int(mg[1]), mg_lines=int(mg[2]),
+                             mg_sweeps=int(mg[3]))
         p = params.c_struct()
         ks = (C.c_int32 * max(len(keys), 1))(*keys)
         _check(lib().xpbd_adjoint_implicit(self._h, C.byref(p), int(steps), int(iters), _ptr(checkpoints, F32),

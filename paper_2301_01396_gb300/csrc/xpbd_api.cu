@@ -17,6 +17,7 @@
 
 #include "../../include/diffxpbd.h"
 #include "xpbd_kernels.cuh"
+#include "xpbd_multigrid.cuh"
 #include "xpbd_solver.cuh"
 
 using namespace xpbd;
@@ -275,7 +276,7 @@ void release_workspace(xpbd_solver* h) {
   DevBuf* bufs[] = {&h->P, &h->lam, &h->cflags, &h->lamc, &h->tape, &h->lam_tape, &h->tape_c,
                     &h->lamc_tape, &h->xbar, &h->vbar, &h->lb, &h->acc, &h->lbc, &h->cgrad,
                     &h->partials, &h->roll, &h->seg, &h->imp_blocks, &h->imp_vec, &h->imp_dinv,
-                    &h->imp_sc};
+                    &h->imp_sc, &h->imp_mg};
   for (DevBuf* b : bufs) b->release();
 }
 
@@ -1364,6 +1365,48 @@ xpbd_status xpbd_adjoint_sparse(xpbd_handle h, const xpbd_params* p, int32_t ste
   return adjoint_end(h, p, out, s, h->use_phases);
 }
 
+// z = V-cycle(r) of the grid multigrid preconditioner (xpbd_multigrid.cuh); X is the
+// level-0 pin mask.  Level 0's right-hand side and correction are r and z themselves.
+static void mg_vcycle(xpbd_solver* h, const MgPlan& g, const float4* X, const double* r, double* z, cudaStream_t s) {
+  const int L = g.levels;
+  auto rhs = [&](int l) { return l == 0 ? r : (const double*)g.lv[l].b; };
+  auto sol = [&](int l) { return l == 0 ? z : g.lv[l].x; };
+  auto smooth = [&](int l, bool forward) {
+    const MgLevel& lv = g.lv[l];
+    const int n = lv.nx * lv.ny;
+    for (int sweep = 0; sweep < g.sweeps; ++sweep) {
+      if (l == 0 && g.line_dir) {
+        for (int k = 0; k < 5; ++k) {
+          const int col = forward ? k : 4 - k;
+          launch(h, XPBD_K_ADJ_OTHER, n, s, [&] { launch_mg_line_resid(lv, X, rhs(l), sol(l), lv.r, g.line_dir, col, s); });
+          launch(h, XPBD_K_ADJ_OTHER, n, s, [&] { launch_mg_line_solve(lv, g.lfac, lv.r, sol(l), g.line_dir, col, s); });
+        }
+      } else {
+        for (int k = 0; k < 9; ++k) {
+          const int col = forward ? k : 8 - k;
+          launch(h, XPBD_K_ADJ_OTHER, n, s, [&] { launch_mg_point_gs(lv, rhs(l), sol(l), col, s); });
+        }
+      }
+    }
+  };
+  for (int l = 0; l + 1 < L; ++l) {
+    const MgLevel& lv = g.lv[l];
+    const int n = lv.nx * lv.ny;
+    cudaMemsetAsync(sol(l), 0, sizeof(double) * 3 * (size_t)n, s);
+    smooth(l, true);
+    launch(h, XPBD_K_ADJ_OTHER, n, s, [&] { launch_mg_resid(lv, l == 0 ? X : nullptr, rhs(l), sol(l), lv.r, s); });
+    launch(h, XPBD_K_ADJ_OTHER, n, s, [&] { launch_mg_restrict(lv, lv.r, g.lv[l + 1], g.lv[l + 1].b, s); });
+  }
+  const MgLevel& lc = g.lv[L - 1];
+  launch(h, XPBD_K_ADJ_OTHER, lc.nx * lc.ny, s, [&] { launch_mg_coarse_solve(lc, g.cinv, rhs(L - 1), sol(L - 1), s); });
+  for (int l = L - 2; l >= 0; --l) {
+    const MgLevel& lv = g.lv[l];
+    launch(h, XPBD_K_ADJ_OTHER, lv.nx * lv.ny, s,
+           [&] { launch_mg_prolong(g.lv[l + 1], g.lv[l + 1].x, lv, l == 0 ? X : nullptr, sol(l), s); });
+    smooth(l, false);
+  }
+}
+
 xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
                                   const float* ck, int32_t n_seeds, const int32_t* seed_steps, const float* seed_dx,
                                   const float* seed_dv_T, const xpbd_grads* out, const xpbd_implicit_opts* o,
@@ -1377,6 +1420,11 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   if (out->d_collider)
     return fail(XPBD_ERR_INVALID, "the implicit adjoint forms no collider-parameter gradient (d_collider must be NULL)");
   if (!(o->cg_tol > 0.0) || o->cg_max_iters < 1) return fail(XPBD_ERR_INVALID, "cg_tol must be > 0 and cg_max_iters >= 1");
+  const bool use_mg = o->mg_nx != 0 || o->mg_ny != 0;
+  if (use_mg && (o->mg_nx < 1 || o->mg_ny < 1 || (int64_t)o->mg_nx * o->mg_ny != h->V))
+    return fail(XPBD_ERR_INVALID, "multigrid: mg_nx * mg_ny must equal the vertex count");
+  if (use_mg && (o->mg_lines < -1 || o->mg_lines > 1 || o->mg_sweeps < 0))
+    return fail(XPBD_ERR_INVALID, "multigrid: mg_lines must be -1, 0 or 1 and mg_sweeps >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   AdjointSweep A;
   st = adjoint_begin(h, p, steps, iters, n_seeds, seed_steps, seed_dx, seed_dv_T, out, s, A);
@@ -1392,6 +1440,11 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   CU_TRY(h->imp_vec.ensure(sizeof(double) * 6 * std::max<size_t>(V3, 1)));
   CU_TRY(h->imp_dinv.ensure(sizeof(double) * 9 * (size_t)std::max(V, 1)));
   CU_TRY(h->imp_sc.ensure(sizeof(double) * 8));
+  MgPlan mg;
+  if (use_mg) {
+    CU_TRY(h->imp_mg.ensure(sizeof(double) * mg_workspace_doubles(o->mg_nx, o->mg_ny, o->mg_lines != 0)));
+    mg_carve(mg, h->imp_mg.as<double>(), o->mg_nx, o->mg_ny, o->mg_lines, std::max(o->mg_sweeps, 1));
+  }
   double* vb = h->imp_vec.as<double>();
   double *b = vb, *y = vb + V3, *r = vb + 2 * V3, *z = vb + 3 * V3, *pd_dir = vb + 4 * V3, *q = vb + 5 * V3;
   double* dinv = h->imp_dinv.as<double>();
@@ -1440,31 +1493,73 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
     launch(h, XPBD_K_ADJ_OTHER, h->nm, s, [&] {
       launch_memb_blocks(h->d_mrec, h->nm, X, lam + h->mslot, h->nm, mblocks, pd, s);
     });
-    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_mass_contacts(X, cf, lamc, c, pd, dinv, V, s); });
-    for (int col = 0; col < h->K; ++col)
-      for (const Seg& cg : h->colors[col])
-        for_each_record_seg(h, cg, [&](const Seg& g) {
-          if (g.type == SEG_MEMB) {
+    if (use_mg) {   // level-0 stencil, colour by colour, then the coarse levels
+      double* A0 = mg.lv[0].A;
+      CU_TRY(cudaMemsetAsync(A0, 0, sizeof(double) * kMgBlock * (size_t)V, s));
+      CU_TRY(cudaMemsetAsync(sc + 6, 0, sizeof(double), s));
+      launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_mg_asm_mass_contacts(X, cf, lamc, c, pd, A0, V, s); });
+      for (int col = 0; col < h->K; ++col)
+        for (const Seg& cg : h->colors[col])
+          for_each_record_seg(h, cg, [&](const Seg& g) {
+            if (g.type == SEG_MEMB) {
+              launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+                launch_mg_asm_memb(h->d_mrec + g.begin, g.count, mblocks + 21 * (size_t)g.begin, A0, o->mg_nx, V,
+                                   sc + 6, s);
+              });
+              return;
+            }
+            const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
             launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
-              launch_diag_memb(h->d_mrec + g.begin, g.count, mblocks + 21 * (size_t)g.begin, dinv, s);
+              launch_mg_asm_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
+                                  blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, A0, o->mg_nx, V, sc + 6, s);
             });
-            return;
-          }
-          const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
-          launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
-            launch_diag_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
-                              blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, dinv, s);
           });
-        });
-    launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_invert(X, dinv, V, s); });
+      for (int l = 0; l + 1 < mg.levels; ++l)
+        launch(h, XPBD_K_ADJ_OTHER, (int64_t)mg.lv[l + 1].nx * mg.lv[l + 1].ny * kMgSlots, s,
+               [&] { launch_mg_rap(mg.lv[l], mg.lv[l + 1], l == 0 ? X : nullptr, s); });
+      for (int l = 0; l < mg.levels; ++l)
+        launch(h, XPBD_K_ADJ_OTHER, (int64_t)mg.lv[l].nx * mg.lv[l].ny, s,
+               [&] { launch_mg_dinv(mg.lv[l], l == 0 ? X : nullptr, s); });
+      const MgLevel& lc = mg.lv[mg.levels - 1];
+      launch(h, XPBD_K_ADJ_OTHER, lc.nx * lc.ny, s,
+             [&] { launch_mg_coarse_inverse(lc, mg.levels == 1 ? X : nullptr, mg.cinv, s); });
+      if (mg.line_dir)
+        launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_mg_line_factor(mg.lv[0], X, mg.line_dir, mg.lfac, s); });
+    } else {
+      launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_mass_contacts(X, cf, lamc, c, pd, dinv, V, s); });
+      for (int col = 0; col < h->K; ++col)
+        for (const Seg& cg : h->colors[col])
+          for_each_record_seg(h, cg, [&](const Seg& g) {
+            if (g.type == SEG_MEMB) {
+              launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+                launch_diag_memb(h->d_mrec + g.begin, g.count, mblocks + 21 * (size_t)g.begin, dinv, s);
+              });
+              return;
+            }
+            const size_t ro = (size_t)h->rec_off[g.type] + g.begin;
+            launch(h, XPBD_K_ADJ_OTHER, g.count, s, [&] {
+              launch_diag_block(g.type, rec_ptr(h, g.type, g.begin), g.count, X, lam + ro,
+                                blocks + 45 * (size_t)(boff[g.type] + g.begin), pd, dinv, s);
+            });
+          });
+      launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_diag_invert(X, dinv, V, s); });
+    }
     LAUNCH_CHECK();
     // preconditioned conjugate gradients on the free vertices
     const int pb = partial_blocks(V);
-    launch_cg_start(X, b, dinv, y, r, z, pd_dir, partials, V, s);
+    if (use_mg) {
+      launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_cg_init(X, b, y, r, V, s); });
+      mg_vcycle(h, mg, X, r, z, s);
+      launch_cg_rz(r, z, pd_dir, partials, 3, V, s);
+    } else {
+      launch_cg_start(X, b, dinv, y, r, z, pd_dir, partials, V, s);
+    }
     launch_reduce_partials(partials, pb, 3, sc + 1, false, s);
-    double host[2];
-    CU_TRY(cudaMemcpyAsync(host, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    double host[4];
+    CU_TRY(cudaMemcpyAsync(host, sc + 3, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU_TRY(cudaStreamSynchronize(s));
+    if (use_mg && host[3] != 0.0)
+      return fail(XPBD_ERR_INVALID, "multigrid: a constraint couples vertices more than two grid cells apart");
     const double bb = host[0];
     int used = 0;
     if (bb > 0.0) {
@@ -1473,7 +1568,13 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
         spmv(pd_dir, q);
         launch_cg_pq(X, pd_dir, q, partials, V, s);
         launch_reduce_partials(partials, pb, 1, sc, false, s);
-        launch_cg_step(sc, old_slot, pd_dir, q, dinv, y, r, z, partials, V, s);
+        if (use_mg) {
+          launch_cg_update(sc, old_slot, pd_dir, q, y, r, V, s);
+          mg_vcycle(h, mg, X, r, z, s);
+          launch_cg_rz(r, z, nullptr, partials, 2, V, s);
+        } else {
+          launch_cg_step(sc, old_slot, pd_dir, q, dinv, y, r, z, partials, V, s);
+        }
         launch_reduce_partials(partials, pb, 2, sc + new_slot, false, s);
         launch_cg_dir(sc, old_slot, new_slot, z, pd_dir, V, s);
         used = it + 1;

@@ -20,6 +20,7 @@
 // Matrix-vector products run color by color (a color's constraints share no vertex), so
 // every sum has a fixed order and the solve is deterministic.
 #include "xpbd_elems.cuh"
+#include "xpbd_multigrid.cuh"
 
 namespace xpbd {
 
@@ -696,6 +697,663 @@ void launch_abar(SegType t, const void* rec, int n, const float4* X, const float
     case SEG_TETH: k_abar_quad<2><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, X, lam, y, acc); break;
     default: k_abar_quad<3><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, X, lam, y, acc);
   }
+}
+
+// ============================================================================ multigrid
+// Grid multigrid preconditioner (declared in xpbd_multigrid.cuh, which states the method).
+
+namespace {
+
+__device__ __forceinline__ bool mg_inv3(const double* m, double* o) {
+  const double a = m[0], b = m[1], c = m[2], d = m[3], e = m[4], f = m[5], g = m[6], h = m[7], k = m[8];
+  const double A = e * k - f * h, B = -(d * k - f * g), Cc = d * h - e * g;
+  const double det = a * A + b * B + c * Cc;
+  if (!(fabs(det) > 0.0) || !isfinite(det)) {
+    for (int t = 0; t < 9; ++t) o[t] = 0.0;
+    return false;
+  }
+  const double id = 1.0 / det;
+  o[0] = A * id;
+  o[1] = -(b * k - c * h) * id;
+  o[2] = (b * f - c * e) * id;
+  o[3] = B * id;
+  o[4] = (a * k - c * g) * id;
+  o[5] = -(a * f - c * d) * id;
+  o[6] = Cc * id;
+  o[7] = -(a * h - b * g) * id;
+  o[8] = (a * e - b * d) * id;
+  return true;
+}
+
+// o = a b (3x3), o = a b^T, o -= a b^T
+__device__ __forceinline__ void mm3(const double* a, const double* b, double* o) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) o[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+__device__ __forceinline__ void mm3_sub_bt(const double* a, const double* b, double* o) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) o[3 * i + j] -= a[3 * i] * b[3 * j] + a[3 * i + 1] * b[3 * j + 1] + a[3 * i + 2] * b[3 * j + 2];
+}
+
+// Bilinear prolongation weight of coarse index X for fine index x (nc coarse points).
+__device__ __forceinline__ double mg_w(int x, int X, int nc) {
+  const int d = x - 2 * X;
+  if (d == 0) return 1.0;
+  if (d == 1) return X + 1 < nc ? 0.5 : 1.0;
+  if (d == -1) return 0.5;
+  return 0.0;
+}
+
+__device__ __forceinline__ bool mg_pinned(const float4* X, int v) { return X && !(X[v].w > 0.f); }
+
+// out += (A x)_v over the 5 x 5 stencil.
+__device__ __forceinline__ void mg_row_apply(const double* __restrict__ A, const double* __restrict__ x, int v, int nx,
+                                             int ny, double out[3]) {
+  const int vx = v % nx, vy = v / nx;
+  const double* a = A + (size_t)v * kMgBlock;
+#pragma unroll 5
+  for (int sl = 0; sl < kMgSlots; ++sl) {
+    const int xx = vx + sl % 5 - 2, yy = vy + sl / 5 - 2;
+    if (xx < 0 || xx >= nx || yy < 0 || yy >= ny) continue;
+    const double* xj = x + 3 * ((size_t)yy * nx + xx);
+    const double x0 = xj[0], x1 = xj[1], x2 = xj[2];
+    const double* m = a + 9 * sl;
+    out[0] += m[0] * x0 + m[1] * x1 + m[2] * x2;
+    out[1] += m[3] * x0 + m[4] * x1 + m[5] * x2;
+    out[2] += m[6] * x0 + m[7] * x1 + m[8] * x2;
+  }
+}
+
+__device__ __forceinline__ void mg_add(double* A0, int vi, int vj, int nx, int V, const double* B, double* flag) {
+  if (vi < 0 || vj < 0 || vi >= V || vj >= V) {
+    *flag = 1.0;
+    return;
+  }
+  const int dx = vj % nx - vi % nx, dy = vj / nx - vi / nx;
+  if (dx < -2 || dx > 2 || dy < -2 || dy > 2) {
+    *flag = 1.0;
+    return;
+  }
+  double* a = A0 + (size_t)vi * kMgBlock + 9 * ((dy + 2) * 5 + dx + 2);
+  for (int k = 0; k < 9; ++k) a[k] += B[k];
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_mass_contacts(const float4* __restrict__ X, const uint8_t* __restrict__ cflags,
+                                                             const float2* __restrict__ lamc, Collide c, bool pd,
+                                                             double* __restrict__ A0, int V) {
+  XPBD_TID_OR_RETURN(V);
+  const float w = X[i].w;
+  const double m = w > 0.f ? 1.0 / (double)w : 0.0;
+  float B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const uint8_t f = cflags ? cflags[i] : 0;
+  if (f) contact_block(i, X, f, lamc[i], c, pd, B);
+  double* a = A0 + (size_t)i * kMgBlock + 9 * 12;
+  for (int k = 0; k < 9; ++k) a[k] += (double)B[k] + (k % 4 == 0 ? m : 0.0);
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_asm_dist(const DistRec* __restrict__ rec, int n, const float4* __restrict__ X,
+                                                        const float* __restrict__ lam, bool pd, double* __restrict__ A0,
+                                                        int nx, int V, double* flag) {
+  XPBD_TID_OR_RETURN(n);
+  const DistRec r = rec[i];
+  const DistBlock B(r, X, lam[i], pd);
+  if (!B.ok) return;
+  const float nn[3] = {B.nx, B.ny, B.nz};
+  double P[9], N[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      P[3 * a + b] = (double)nn[a] * nn[b] * ((double)B.inv_at - (double)B.c) + (a == b ? (double)B.c : 0.0);
+      N[3 * a + b] = -P[3 * a + b];
+    }
+  mg_add(A0, r.a, r.a, nx, V, P, flag);
+  mg_add(A0, r.b, r.b, nx, V, P, flag);
+  mg_add(A0, r.a, r.b, nx, V, N, flag);
+  mg_add(A0, r.b, r.a, nx, V, N, flag);
+}
+
+// A block stored in the relative coordinates of vertices 1..NR (packed upper triangle of
+// a (3 NR)^2 matrix), scattered into the vertex-pair blocks T^T B T.
+template <int NR>
+__device__ __forceinline__ double rel_entry(const double* B, int row, int col) {
+  return NR == 3 ? B[pk9(row, col)] : B[pk6(row, col)];
+}
+
+template <int NR>
+__device__ void mg_scatter_rel(const int* v, const double* __restrict__ B, double* __restrict__ A0, int nx, int V,
+                               double* flag) {
+  for (int a = 0; a <= NR; ++a)
+    for (int b = 0; b <= NR; ++b) {
+      double M[9];
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          double s = 0.0;
+          if (a > 0 && b > 0) {
+            s = rel_entry<NR>(B, 3 * (a - 1) + al, 3 * (b - 1) + be);
+          } else if (a > 0) {
+            for (int l = 0; l < NR; ++l) s -= rel_entry<NR>(B, 3 * (a - 1) + al, 3 * l + be);
+          } else if (b > 0) {
+            for (int k = 0; k < NR; ++k) s -= rel_entry<NR>(B, 3 * k + al, 3 * (b - 1) + be);
+          } else {
+            for (int k = 0; k < NR; ++k)
+              for (int l = 0; l < NR; ++l) s += rel_entry<NR>(B, 3 * k + al, 3 * l + be);
+          }
+          M[3 * al + be] = s;
+        }
+      mg_add(A0, v[a], v[b], nx, V, M, flag);
+    }
+}
+
+template <class Rec>
+__global__ void __launch_bounds__(kBlock) k_mg_asm_quad(const Rec* __restrict__ rec, int n, const double* __restrict__ blocks,
+                                                        double* __restrict__ A0, int nx, int V, double* flag) {
+  XPBD_TID_OR_RETURN(n);
+  const Rec r = rec[i];
+  const int v[4] = {r.v[0], r.v[1], r.v[2], r.v[3]};
+  mg_scatter_rel<3>(v, blocks + 45 * (size_t)i, A0, nx, V, flag);
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_asm_memb(const MembRec* __restrict__ rec, int n, const double* __restrict__ blocks,
+                                                        double* __restrict__ A0, int nx, int V, double* flag) {
+  XPBD_TID_OR_RETURN(n);
+  const MembRec r = rec[i];
+  const int v[3] = {r.v[0], r.v[1], r.v[2]};
+  mg_scatter_rel<2>(v, blocks + 21 * (size_t)i, A0, nx, V, flag);
+}
+
+// Galerkin coarse operator: one thread per (coarse vertex, stencil offset).
+__global__ void __launch_bounds__(kBlock) k_mg_rap(const double* __restrict__ Af, int nxf, int nyf,
+                                                   const float4* __restrict__ X, double* __restrict__ Ac, int nxc,
+                                                   int nyc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nxc * nyc * kMgSlots) return;
+  const int I = t / kMgSlots, sl = t % kMgSlots;
+  const int IX = I % nxc, IY = I / nxc;
+  const int JX = IX + sl % 5 - 2, JY = IY + sl / 5 - 2;
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (JX >= 0 && JX < nxc && JY >= 0 && JY < nyc) {
+    for (int iy = max(2 * IY - 1, 0); iy <= min(2 * IY + 1, nyf - 1); ++iy) {
+      const double wy = mg_w(iy, IY, nyc);
+      if (wy == 0.0) continue;
+      for (int ix = max(2 * IX - 1, 0); ix <= min(2 * IX + 1, nxf - 1); ++ix) {
+        const double wi = wy * mg_w(ix, IX, nxc);
+        const int i = iy * nxf + ix;
+        if (wi == 0.0 || mg_pinned(X, i)) continue;
+        const double* ai = Af + (size_t)i * kMgBlock;
+        for (int jy = max(2 * JY - 1, max(iy - 2, 0)); jy <= min(2 * JY + 1, min(iy + 2, nyf - 1)); ++jy) {
+          const double wjy = mg_w(jy, JY, nyc);
+          if (wjy == 0.0) continue;
+          for (int jx = max(2 * JX - 1, max(ix - 2, 0)); jx <= min(2 * JX + 1, min(ix + 2, nxf - 1)); ++jx) {
+            const double w = wi * wjy * mg_w(jx, JX, nxc);
+            if (w == 0.0 || mg_pinned(X, jy * nxf + jx)) continue;
+            const double* m = ai + 9 * ((jy - iy + 2) * 5 + (jx - ix + 2));
+            for (int k = 0; k < 9; ++k) acc[k] += w * m[k];
+          }
+        }
+      }
+    }
+  }
+  double* o = Ac + (size_t)t * 9;
+  for (int k = 0; k < 9; ++k) o[k] = acc[k];
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_dinv(const double* __restrict__ A, const float4* __restrict__ X,
+                                                    double* __restrict__ dinv, int n) {
+  XPBD_TID_OR_RETURN(n);
+  double* o = dinv + 9 * (size_t)i;
+  if (mg_pinned(X, i)) {
+    for (int k = 0; k < 9; ++k) o[k] = 0.0;
+    return;
+  }
+  mg_inv3(A + (size_t)i * kMgBlock + 9 * 12, o);
+}
+
+// Dense inverse of the coarsest level by in-place Gauss-Jordan elimination (the matrix is
+// symmetric positive definite on its nonempty rows; empty rows get a unit diagonal).
+__global__ void __launch_bounds__(256) k_mg_coarse_inverse(const double* __restrict__ A, const float4* __restrict__ X,
+                                                           int nx, int ny, double* __restrict__ cinv) {
+  constexpr int NM = 3 * kMgCoarseMax;
+  __shared__ double M[NM * NM];
+  __shared__ double col[NM];
+  const int n = nx * ny, N = 3 * n;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) M[t] = 0.0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * kMgSlots; t += blockDim.x) {
+    const int v = t / kMgSlots, sl = t % kMgSlots;
+    const int xx = v % nx + sl % 5 - 2, yy = v / nx + sl / 5 - 2;
+    if (xx < 0 || xx >= nx || yy < 0 || yy >= ny) continue;
+    const int j = yy * nx + xx;
+    if (mg_pinned(X, v) || mg_pinned(X, j)) continue;
+    const double* m = A + (size_t)v * kMgBlock + 9 * sl;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) M[(3 * v + a) * N + 3 * j + b] = m[3 * a + b];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += blockDim.x)
+    if (M[t * N + t] == 0.0) M[t * N + t] = 1.0;
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) col[t] = M[t * N + k];
+    __syncthreads();
+    double p = col[k];
+    if (!(fabs(p) > 0.0)) p = 1.0;
+    const double ip = 1.0 / p;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) M[k * N + j] = (j == k ? 1.0 : M[k * N + j]) * ip;
+    __syncthreads();
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+      const int i = t / N, j = t % N;
+      if (i == k) continue;
+      M[t] = (j == k ? 0.0 : M[t]) - col[i] * M[k * N + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) cinv[t] = M[t];
+}
+
+__global__ void __launch_bounds__(256) k_mg_coarse_solve(const double* __restrict__ cinv, const double* __restrict__ b,
+                                                         double* __restrict__ x, int N) {
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) s += cinv[(size_t)r * N + j] * b[j];
+    x[r] = s;
+  }
+}
+
+// Lines of direction dir (+1: x - y = const, -1: x + y = const), numbered 0 .. nx + ny - 2;
+// point k of line l is (x0 + dir k, y0 + k).
+__device__ __forceinline__ int mg_line(int l, int nx, int ny, int dir, int& x0, int& y0) {
+  if (dir > 0) {
+    const int c = l - (ny - 1);
+    y0 = c < 0 ? -c : 0;
+    x0 = y0 + c;
+    return min(ny - y0, nx - x0);
+  }
+  y0 = l > nx - 1 ? l - (nx - 1) : 0;
+  x0 = l - y0;
+  return min(ny - y0, x0 + 1);
+}
+
+// Block LDL^T of every line's pentadiagonal block matrix (its vertices' couplings along the
+// line); pinned vertices are left out (zero inverse pivot, no coupling).  Per vertex:
+// [L(k, k-1) | L(k, k-2) | D_k^-1].
+__global__ void __launch_bounds__(kBlock) k_mg_line_factor(const double* __restrict__ A, const float4* __restrict__ X,
+                                                           int nx, int ny, int dir, double* __restrict__ F) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nx + ny - 1) return;
+  int x0, y0;
+  const int len = mg_line(l, nx, ny, dir, x0, y0);
+  const int s1 = 5 + (2 - dir), s2 = 2 - 2 * dir;   // in-line offsets -1 and -2
+  double Dm1[9], Dm2[9], L2m1[9];
+  for (int k = 0; k < 9; ++k) Dm1[k] = Dm2[k] = L2m1[k] = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int v = (y0 + k) * nx + x0 + dir * k;
+    double* f = F + (size_t)v * kMgLineFactor;
+    double L1[9], L2[9], D[9], W1[9], W2[9];
+    if (mg_pinned(X, v)) {
+      for (int t = 0; t < 27; ++t) f[t] = 0.0;
+      for (int t = 0; t < 9; ++t) {
+        Dm2[t] = Dm1[t];
+        Dm1[t] = 0.0;
+        L2m1[t] = 0.0;
+      }
+      continue;
+    }
+    const double* a = A + (size_t)v * kMgBlock;
+    for (int t = 0; t < 9; ++t) {
+      W2[t] = k >= 2 ? a[9 * s2 + t] : 0.0;
+      W1[t] = k >= 1 ? a[9 * s1 + t] : 0.0;
+      D[t] = a[9 * 12 + t];
+    }
+    mm3(W2, Dm2, L2);          // L(k, k-2) = W2 D_{k-2}^-1
+    mm3_sub_bt(W2, L2m1, W1);  // W1 = A(k, k-1) - W2 L(k-1, k-2)^T
+    mm3(W1, Dm1, L1);          // L(k, k-1) = W1 D_{k-1}^-1
+    mm3_sub_bt(W2, L2, D);     // D_k = A(k, k) - W2 L2^T - W1 L1^T
+    mm3_sub_bt(W1, L1, D);
+    double Di[9];
+    mg_inv3(D, Di);
+    for (int t = 0; t < 9; ++t) {
+      f[t] = L1[t];
+      f[9 + t] = L2[t];
+      f[18 + t] = Di[t];
+      Dm2[t] = Dm1[t];
+      Dm1[t] = Di[t];
+      L2m1[t] = L2[t];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_line_resid(const double* __restrict__ A, const float4* __restrict__ X,
+                                                          const double* __restrict__ b, const double* __restrict__ x,
+                                                          double* __restrict__ r, int nx, int ny, int dir, int color) {
+  XPBD_TID_OR_RETURN(nx * ny);
+  const int vx = i % nx, vy = i / nx;
+  const int l = dir > 0 ? vx - vy + ny - 1 : vx + vy;
+  if (l % 5 != color) return;
+  double o[3] = {0.0, 0.0, 0.0};
+  if (!mg_pinned(X, i)) {
+    mg_row_apply(A, x, i, nx, ny, o);
+    for (int a = 0; a < 3; ++a) o[a] = b[3 * i + a] - o[a];
+  }
+  for (int a = 0; a < 3; ++a) r[3 * i + a] = o[a];
+}
+
+// One block per line of the colour: solve the line's block system for the residual in r
+// and add the solution to x.  The recurrences are sequential along the line, so the block
+// stages the line's factors in chunks into shared memory and one thread runs them there
+// (forward substitution writes z over r; backward substitution adds u to x).
+constexpr int kLineChunk = 128;
+
+__global__ void __launch_bounds__(64) k_mg_line_solve(const double* __restrict__ F, double* __restrict__ r,
+                                                      double* __restrict__ x, int nx, int ny, int dir, int color) {
+  __shared__ double sf[kLineChunk * kMgLineFactor];
+  __shared__ double sv[kLineChunk * 3];
+  const int l = color + 5 * blockIdx.x;
+  if (l >= nx + ny - 1) return;
+  int x0, y0;
+  const int len = mg_line(l, nx, ny, dir, x0, y0);
+  auto vert = [&](int k) { return (y0 + k) * nx + x0 + dir * k; };
+  double z1[3] = {0, 0, 0}, z2[3] = {0, 0, 0};
+  for (int c0 = 0; c0 < len; c0 += kLineChunk) {   // forward: z_k = r_k - L(k,k-1) z_{k-1} - L(k,k-2) z_{k-2}
+    const int cn = min(kLineChunk, len - c0);
+    for (int t = threadIdx.x; t < cn * 18; t += blockDim.x)
+      sf[(t / 18) * kMgLineFactor + t % 18] = F[(size_t)vert(c0 + t / 18) * kMgLineFactor + t % 18];
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = r[3 * (size_t)vert(c0 + t / 3) + t % 3];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < cn; ++k) {
+        const double* f = sf + k * kMgLineFactor;
+        double z[3];
+        for (int a = 0; a < 3; ++a)
+          z[a] = sv[3 * k + a] - (f[3 * a] * z1[0] + f[3 * a + 1] * z1[1] + f[3 * a + 2] * z1[2]) -
+                 (f[9 + 3 * a] * z2[0] + f[9 + 3 * a + 1] * z2[1] + f[9 + 3 * a + 2] * z2[2]);
+        for (int a = 0; a < 3; ++a) {
+          sv[3 * k + a] = z[a];
+          z2[a] = z1[a];
+          z1[a] = z[a];
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) r[3 * (size_t)vert(c0 + t / 3) + t % 3] = sv[t];
+    __syncthreads();
+  }
+  // backward: u_k = D_k^-1 z_k - L(k+1,k)^T u_{k+1} - L(k+2,k)^T u_{k+2}
+  double u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
+  double L1n[9], L2n[9], L2nn[9];   // L(k+1, k), L(k+1, k-1), L(k+2, k)
+  for (int t = 0; t < 9; ++t) L1n[t] = L2n[t] = L2nn[t] = 0.0;
+  for (int c1 = len; c1 > 0; c1 -= kLineChunk) {
+    const int c0 = max(0, c1 - kLineChunk), cn = c1 - c0;
+    for (int t = threadIdx.x; t < cn * kMgLineFactor; t += blockDim.x)
+      sf[t] = F[(size_t)vert(c0 + t / kMgLineFactor) * kMgLineFactor + t % kMgLineFactor];
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = r[3 * (size_t)vert(c0 + t / 3) + t % 3];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = cn - 1; k >= 0; --k) {
+        const double* f = sf + k * kMgLineFactor;
+        double u[3];
+        for (int a = 0; a < 3; ++a) {
+          const double w = f[18 + 3 * a] * sv[3 * k] + f[18 + 3 * a + 1] * sv[3 * k + 1] + f[18 + 3 * a + 2] * sv[3 * k + 2];
+          u[a] = w - (L1n[a] * u1[0] + L1n[3 + a] * u1[1] + L1n[6 + a] * u1[2]) -
+                 (L2nn[a] * u2[0] + L2nn[3 + a] * u2[1] + L2nn[6 + a] * u2[2]);
+        }
+        for (int a = 0; a < 3; ++a) {
+          sv[3 * k + a] = u[a];
+          u2[a] = u1[a];
+          u1[a] = u[a];
+        }
+        for (int t = 0; t < 9; ++t) {
+          L2nn[t] = L2n[t];
+          L1n[t] = f[t];
+          L2n[t] = f[9 + t];
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) x[3 * (size_t)vert(c0 + t / 3) + t % 3] += sv[t];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_point_gs(const double* __restrict__ A, const double* __restrict__ dinv,
+                                                        const double* __restrict__ b, double* __restrict__ x, int nx,
+                                                        int ny, int cx, int cy) {
+  const int nxs = (nx - cx + 2) / 3, nys = (ny - cy + 2) / 3;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nxs * nys) return;
+  const int v = (cy + 3 * (t / nxs)) * nx + cx + 3 * (t % nxs);
+  double o[3] = {0.0, 0.0, 0.0};
+  mg_row_apply(A, x, v, nx, ny, o);
+  double r[3];
+  for (int a = 0; a < 3; ++a) r[a] = b[3 * v + a] - o[a];
+  const double* m = dinv + 9 * (size_t)v;
+  for (int a = 0; a < 3; ++a) x[3 * v + a] += m[3 * a] * r[0] + m[3 * a + 1] * r[1] + m[3 * a + 2] * r[2];
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_resid(const double* __restrict__ A, const float4* __restrict__ X,
+                                                     const double* __restrict__ b, const double* __restrict__ x,
+                                                     double* __restrict__ r, int nx, int ny) {
+  XPBD_TID_OR_RETURN(nx * ny);
+  double o[3] = {0.0, 0.0, 0.0};
+  if (!mg_pinned(X, i)) {
+    mg_row_apply(A, x, i, nx, ny, o);
+    for (int a = 0; a < 3; ++a) o[a] = b[3 * i + a] - o[a];
+  }
+  for (int a = 0; a < 3; ++a) r[3 * i + a] = o[a];
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_restrict(const double* __restrict__ r, int nxf, int nyf,
+                                                        double* __restrict__ bc, int nxc, int nyc) {
+  XPBD_TID_OR_RETURN(nxc * nyc);
+  const int IX = i % nxc, IY = i / nxc;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int iy = max(2 * IY - 1, 0); iy <= min(2 * IY + 1, nyf - 1); ++iy) {
+    const double wy = mg_w(iy, IY, nyc);
+    for (int ix = max(2 * IX - 1, 0); ix <= min(2 * IX + 1, nxf - 1); ++ix) {
+      const double w = wy * mg_w(ix, IX, nxc);
+      const double* rf = r + 3 * ((size_t)iy * nxf + ix);
+      for (int a = 0; a < 3; ++a) s[a] += w * rf[a];
+    }
+  }
+  for (int a = 0; a < 3; ++a) bc[3 * i + a] = s[a];
+}
+
+__global__ void __launch_bounds__(kBlock) k_mg_prolong(const double* __restrict__ xc, int nxc, int nyc,
+                                                       const float4* __restrict__ X, double* __restrict__ x, int nxf,
+                                                       int nyf) {
+  XPBD_TID_OR_RETURN(nxf * nyf);
+  if (mg_pinned(X, i)) return;
+  const int ix = i % nxf, iy = i / nxf;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int Y = (iy - 1) / 2; Y <= min((iy + 1) / 2, nyc - 1); ++Y) {
+    const double wy = mg_w(iy, Y, nyc);
+    for (int Xc = (ix - 1) / 2; Xc <= min((ix + 1) / 2, nxc - 1); ++Xc) {
+      const double w = wy * mg_w(ix, Xc, nxc);
+      const double* c = xc + 3 * ((size_t)Y * nxc + Xc);
+      for (int a = 0; a < 3; ++a) s[a] += w * c[a];
+    }
+  }
+  for (int a = 0; a < 3; ++a) x[3 * i + a] += s[a];
+}
+
+// CG with an external preconditioner.
+__global__ void __launch_bounds__(kBlock) k_cg_init(const float4* __restrict__ X, const double* __restrict__ b,
+                                                    double* __restrict__ y, double* __restrict__ r, int V) {
+  XPBD_TID_OR_RETURN(V);
+  const bool fr = X[i].w > 0.f;
+  for (int a = 0; a < 3; ++a) {
+    y[3 * i + a] = 0.0;
+    r[3 * i + a] = fr ? b[3 * i + a] : 0.0;
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_cg_rz(const double* __restrict__ r, const double* __restrict__ z,
+                                                  double* __restrict__ p, double* __restrict__ partials, int V) {
+  double acc[NC];
+  for (int k = 0; k < NC; ++k) acc[k] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    for (int a = 0; a < 3; ++a) {
+      const double rr = r[3 * i + a], zz = z[3 * i + a];
+      if (p) p[3 * i + a] = zz;
+      acc[0] += rr * zz;
+      acc[1] += rr * rr;
+      if (NC == 3) acc[NC - 1] += rr * rr;
+    }
+  }
+  block_sum_store<NC>(acc, partials + NC * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kBlock) k_cg_update(const double* __restrict__ sc, int rz_slot, const double* __restrict__ p,
+                                                      const double* __restrict__ q, double* __restrict__ y,
+                                                      double* __restrict__ r, int V) {
+  const double pq = sc[0];
+  const double alpha = pq != 0.0 ? sc[rz_slot] / pq : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * V; i += gridDim.x * blockDim.x) {
+    y[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+}  // namespace
+
+size_t mg_workspace_doubles(int nx, int ny, bool lines) {
+  size_t tot = 0;
+  int x = nx, y = ny, levels = 0;
+  while (true) {
+    const size_t n = (size_t)x * y;
+    tot += n * (kMgBlock + 9 + 9);   // A, dinv, x, b, r
+    ++levels;
+    if ((x <= 4 && y <= 4) || levels == kMgMaxLevels) break;
+    x = (x + 1) / 2;
+    y = (y + 1) / 2;
+  }
+  const size_t nc3 = 3 * (size_t)x * y;
+  tot += nc3 * nc3;
+  if (lines) tot += (size_t)nx * ny * kMgLineFactor;
+  return tot;
+}
+
+void mg_carve(MgPlan& g, double* base, int nx, int ny, int line_dir, int sweeps) {
+  g = MgPlan();
+  g.line_dir = line_dir;
+  g.sweeps = sweeps;
+  int x = nx, y = ny;
+  double* p = base;
+  while (true) {
+    MgLevel& L = g.lv[g.levels++];
+    const size_t n = (size_t)x * y;
+    L.nx = x;
+    L.ny = y;
+    L.A = p;
+    p += n * kMgBlock;
+    L.dinv = p;
+    p += 9 * n;
+    L.x = p;
+    p += 3 * n;
+    L.b = p;
+    p += 3 * n;
+    L.r = p;
+    p += 3 * n;
+    if ((x <= 4 && y <= 4) || g.levels == kMgMaxLevels) break;
+    x = (x + 1) / 2;
+    y = (y + 1) / 2;
+  }
+  g.cinv = p;
+  p += 9 * (size_t)x * y * x * y;
+  g.lfac = line_dir ? p : nullptr;
+}
+
+void launch_mg_asm_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
+                                 double* A0, int V, cudaStream_t s) {
+  if (V > 0) k_mg_mass_contacts<<<grid_for(V), kBlock, 0, s>>>(X, cflags, lamc, c, pd, A0, V);
+}
+
+void launch_mg_asm_block(SegType t, const void* rec, int n, const float4* X, const float* lam, const double* blocks,
+                         bool pd, double* A0, int nx, int V, double* flag, cudaStream_t s) {
+  if (n <= 0) return;
+  if (t == SEG_DIST)
+    k_mg_asm_dist<<<grid_for(n), kBlock, 0, s>>>((const DistRec*)rec, n, X, lam, pd, A0, nx, V, flag);
+  else if (t == SEG_BEND)
+    k_mg_asm_quad<BendRec><<<grid_for(n), kBlock, 0, s>>>((const BendRec*)rec, n, blocks, A0, nx, V, flag);
+  else
+    k_mg_asm_quad<TetRec><<<grid_for(n), kBlock, 0, s>>>((const TetRec*)rec, n, blocks, A0, nx, V, flag);
+}
+
+void launch_mg_asm_memb(const MembRec* rec, int n, const double* blocks, double* A0, int nx, int V, double* flag,
+                        cudaStream_t s) {
+  if (n > 0) k_mg_asm_memb<<<grid_for(n), kBlock, 0, s>>>(rec, n, blocks, A0, nx, V, flag);
+}
+
+void launch_mg_rap(const MgLevel& f, const MgLevel& c, const float4* X, cudaStream_t s) {
+  const int n = c.nx * c.ny * kMgSlots;
+  k_mg_rap<<<grid_for(n), kBlock, 0, s>>>(f.A, f.nx, f.ny, X, c.A, c.nx, c.ny);
+}
+
+void launch_mg_dinv(const MgLevel& l, const float4* X, cudaStream_t s) {
+  const int n = l.nx * l.ny;
+  k_mg_dinv<<<grid_for(n), kBlock, 0, s>>>(l.A, X, l.dinv, n);
+}
+
+void launch_mg_coarse_inverse(const MgLevel& l, const float4* X, double* cinv, cudaStream_t s) {
+  k_mg_coarse_inverse<<<1, 256, 0, s>>>(l.A, X, l.nx, l.ny, cinv);
+}
+
+void launch_mg_line_factor(const MgLevel& l, const float4* X, int dir, double* lfac, cudaStream_t s) {
+  const int lines = l.nx + l.ny - 1;
+  k_mg_line_factor<<<grid_for(lines), kBlock, 0, s>>>(l.A, X, l.nx, l.ny, dir, lfac);
+}
+
+void launch_mg_point_gs(const MgLevel& l, const double* b, double* x, int color, cudaStream_t s) {
+  const int cx = color % 3, cy = color / 3;
+  const int n = ((l.nx - cx + 2) / 3) * ((l.ny - cy + 2) / 3);
+  if (n > 0) k_mg_point_gs<<<grid_for(n), kBlock, 0, s>>>(l.A, l.dinv, b, x, l.nx, l.ny, cx, cy);
+}
+
+void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, int dir,
+                          int color, cudaStream_t s) {
+  const int n = l.nx * l.ny;
+  k_mg_line_resid<<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny, dir, color);
+}
+
+void launch_mg_line_solve(const MgLevel& l, const double* lfac, double* r, double* x, int dir, int color,
+                          cudaStream_t s) {
+  const int lines = (l.nx + l.ny - 1 - color + 4) / 5;
+  if (lines > 0) k_mg_line_solve<<<lines, 64, 0, s>>>(lfac, r, x, l.nx, l.ny, dir, color);
+}
+
+void launch_mg_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, cudaStream_t s) {
+  const int n = l.nx * l.ny;
+  k_mg_resid<<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny);
+}
+
+void launch_mg_restrict(const MgLevel& f, const double* r, const MgLevel& c, double* bc, cudaStream_t s) {
+  const int n = c.nx * c.ny;
+  k_mg_restrict<<<grid_for(n), kBlock, 0, s>>>(r, f.nx, f.ny, bc, c.nx, c.ny);
+}
+
+void launch_mg_prolong(const MgLevel& c, const double* xc, const MgLevel& f, const float4* X, double* x,
+                       cudaStream_t s) {
+  const int n = f.nx * f.ny;
+  k_mg_prolong<<<grid_for(n), kBlock, 0, s>>>(xc, c.nx, c.ny, X, x, f.nx, f.ny);
+}
+
+void launch_mg_coarse_solve(const MgLevel& l, const double* cinv, const double* b, double* x, cudaStream_t s) {
+  k_mg_coarse_solve<<<1, 256, 0, s>>>(cinv, b, x, 3 * l.nx * l.ny);
+}
+
+void launch_cg_init(const float4* X, const double* b, double* y, double* r, int V, cudaStream_t s) {
+  if (V > 0) k_cg_init<<<grid_for(V), kBlock, 0, s>>>(X, b, y, r, V);
+}
+
+void launch_cg_rz(const double* r, const double* z, double* p, double* partials, int ncomp, int V, cudaStream_t s) {
+  if (ncomp == 3)
+    k_cg_rz<3><<<partial_blocks(V), kBlock, 0, s>>>(r, z, p, partials, V);
+  else
+    k_cg_rz<2><<<partial_blocks(V), kBlock, 0, s>>>(r, z, p, partials, V);
+}
+
+void launch_cg_update(const double* sc, int rz_slot, const double* p, const double* q, double* y, double* r, int V,
+                      cudaStream_t s) {
+  k_cg_update<<<partial_blocks(V), kBlock, 0, s>>>(sc, rz_slot, p, q, y, r, V);
 }
 
 }  // namespace xpbd

@@ -102,6 +102,7 @@ struct xpbd_solver {
   DevBuf xbar, vbar, lb, acc, lbc, cgrad, partials;  // reverse
   DevBuf roll, seg;                                  // sparse checkpoints: rolling / segment states
   DevBuf imp_blocks, imp_vec, imp_dinv, imp_sc;      // implicit adjoint: blocks, CG vectors, scalars
+  DevBuf imp_mg;                                     // implicit adjoint: multigrid levels
   // launch statistics per kernel class (always counted; timed with CUDA events on the
   // launching stream while profiling is enabled)
   bool prof_on = false;
