@@ -1407,6 +1407,68 @@ static void mg_vcycle(xpbd_solver* h, const MgPlan& g, const float4* X, const do
   }
 }
 
+// The V-cycle's launches are the same in every CG iteration of a call (same buffers; the
+// level-0 pin mask reads only the inverse masses, which every checkpointed state holds),
+// so they are captured once per call into a CUDA graph and replayed: the ~135 small
+// launches of a V-cycle otherwise cost more in launch overhead than in work.  Capture
+// runs on a private stream (the caller's may be the legacy default stream, which cannot
+// capture); the replay is ordered on the caller's stream.  If capture fails the V-cycle
+// is launched directly.
+struct VcycleGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  cudaStream_t cs = nullptr;
+  int64_t launches = 0, units = 0;
+  double bytes = 0.0;
+  VcycleGraph() = default;
+  VcycleGraph(const VcycleGraph&) = delete;
+  VcycleGraph& operator=(const VcycleGraph&) = delete;
+  ~VcycleGraph() {
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+  }
+  bool capture(xpbd_solver* h, const MgPlan& mg, const float4* X, const double* r, double* z) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      cs = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    const int k = XPBD_K_ADJ_OTHER;
+    const bool prof = h->prof_on;
+    const int64_t l0 = h->launches[k], u0 = h->units[k];
+    const double b0 = h->alg_bytes[k];
+    h->prof_on = false;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      mg_vcycle(h, mg, X, r, z, cs);
+      ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g != nullptr;
+    }
+    h->prof_on = prof;
+    launches = h->launches[k] - l0;
+    units = h->units[k] - u0;
+    bytes = h->alg_bytes[k] - b0;
+    h->launches[k] = l0;
+    h->units[k] = u0;
+    h->alg_bytes[k] = b0;
+    if (ok) ok = cudaGraphInstantiate(&e, g, 0) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+      e = nullptr;
+      g = nullptr;
+    }
+    return ok;
+  }
+  cudaError_t run(xpbd_solver* h, cudaStream_t s) const {
+    h->launches[XPBD_K_ADJ_OTHER] += launches;
+    h->units[XPBD_K_ADJ_OTHER] += units;
+    h->alg_bytes[XPBD_K_ADJ_OTHER] += bytes;
+    return cudaGraphLaunch(e, s);
+  }
+};
+
 xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t steps, int32_t iters,
                                   const float* ck, int32_t n_seeds, const int32_t* seed_steps, const float* seed_dx,
                                   const float* seed_dv_T, const xpbd_grads* out, const xpbd_implicit_opts* o,
@@ -1440,11 +1502,6 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   CU_TRY(h->imp_vec.ensure(sizeof(double) * 6 * std::max<size_t>(V3, 1)));
   CU_TRY(h->imp_dinv.ensure(sizeof(double) * 9 * (size_t)std::max(V, 1)));
   CU_TRY(h->imp_sc.ensure(sizeof(double) * 8));
-  MgPlan mg;
-  if (use_mg) {
-    CU_TRY(h->imp_mg.ensure(sizeof(double) * mg_workspace_doubles(o->mg_nx, o->mg_ny, o->mg_lines != 0)));
-    mg_carve(mg, h->imp_mg.as<double>(), o->mg_nx, o->mg_ny, o->mg_lines, std::max(o->mg_sweeps, 1));
-  }
   double* vb = h->imp_vec.as<double>();
   double *b = vb, *y = vb + V3, *r = vb + 2 * V3, *z = vb + 3 * V3, *pd_dir = vb + 4 * V3, *q = vb + 5 * V3;
   double* dinv = h->imp_dinv.as<double>();
@@ -1452,6 +1509,19 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
   double* partials = h->partials.as<double>();
   double* blocks = h->imp_blocks.as<double>();
   double* mblocks = blocks + 45 * (size_t)nq;   // membranes: 21 per record
+  MgPlan mg;
+  VcycleGraph vgraph;
+  bool use_graph = false;
+  if (use_mg) {
+    CU_TRY(h->imp_mg.ensure(sizeof(double) * mg_workspace_doubles(o->mg_nx, o->mg_ny, o->mg_lines != 0)));
+    mg_carve(mg, h->imp_mg.as<double>(), o->mg_nx, o->mg_ny, o->mg_lines, std::max(o->mg_sweeps, 1));
+    use_graph = vgraph.capture(h, mg, ck_x(ck, V, 0), vb + 2 * V3, vb + 3 * V3);   // r -> z
+  }
+  auto vcycle = [&](const float4* Xm) -> cudaError_t {
+    if (use_graph) return vgraph.run(h, s);
+    mg_vcycle(h, mg, Xm, r, z, s);
+    return cudaSuccess;
+  };
   const int64_t boff[4] = {0, 0, h->n_rec[1], (int64_t)h->n_rec[1] + h->n_rec[2]};
   const float* lam = h->lam.as<float>();
   const Collide c = make_collide(p);
@@ -1549,7 +1619,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
     const int pb = partial_blocks(V);
     if (use_mg) {
       launch(h, XPBD_K_ADJ_OTHER, V, s, [&] { launch_cg_init(X, b, y, r, V, s); });
-      mg_vcycle(h, mg, X, r, z, s);
+      CU_TRY(vcycle(X));
       launch_cg_rz(r, z, pd_dir, partials, 3, V, s);
     } else {
       launch_cg_start(X, b, dinv, y, r, z, pd_dir, partials, V, s);
@@ -1570,7 +1640,7 @@ xpbd_status xpbd_adjoint_implicit(xpbd_handle h, const xpbd_params* p, int32_t s
         launch_reduce_partials(partials, pb, 1, sc, false, s);
         if (use_mg) {
           launch_cg_update(sc, old_slot, pd_dir, q, y, r, V, s);
-          mg_vcycle(h, mg, X, r, z, s);
+          CU_TRY(vcycle(X));
           launch_cg_rz(r, z, nullptr, partials, 2, V, s);
         } else {
           launch_cg_step(sc, old_slot, pd_dir, q, dinv, y, r, z, partials, V, s);

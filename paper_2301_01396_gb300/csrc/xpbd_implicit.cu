@@ -976,7 +976,7 @@ __device__ __forceinline__ int mg_line(int l, int nx, int ny, int dir, int& x0, 
 // line); pinned vertices are left out (zero inverse pivot, no coupling).  Per vertex:
 // [L(k, k-1) | L(k, k-2) | D_k^-1].
 __global__ void __launch_bounds__(kBlock) k_mg_line_factor(const double* __restrict__ A, const float4* __restrict__ X,
-                                                           int nx, int ny, int dir, double* __restrict__ F) {
+                                                           int nx, int ny, int dir, float* __restrict__ F) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nx + ny - 1) return;
   int x0, y0;
@@ -986,10 +986,10 @@ __global__ void __launch_bounds__(kBlock) k_mg_line_factor(const double* __restr
   for (int k = 0; k < 9; ++k) Dm1[k] = Dm2[k] = L2m1[k] = 0.0;
   for (int k = 0; k < len; ++k) {
     const int v = (y0 + k) * nx + x0 + dir * k;
-    double* f = F + (size_t)v * kMgLineFactor;
+    float* f = F + (size_t)v * kMgLineFactor;
     double L1[9], L2[9], D[9], W1[9], W2[9];
     if (mg_pinned(X, v)) {
-      for (int t = 0; t < 27; ++t) f[t] = 0.0;
+      for (int t = 0; t < 27; ++t) f[t] = 0.f;
       for (int t = 0; t < 9; ++t) {
         Dm2[t] = Dm1[t];
         Dm1[t] = 0.0;
@@ -1011,9 +1011,9 @@ __global__ void __launch_bounds__(kBlock) k_mg_line_factor(const double* __restr
     double Di[9];
     mg_inv3(D, Di);
     for (int t = 0; t < 9; ++t) {
-      f[t] = L1[t];
-      f[9 + t] = L2[t];
-      f[18 + t] = Di[t];
+      f[t] = (float)L1[t];
+      f[9 + t] = (float)L2[t];
+      f[18 + t] = (float)Di[t];
       Dm2[t] = Dm1[t];
       Dm1[t] = Di[t];
       L2m1[t] = L2[t];
@@ -1039,29 +1039,32 @@ __global__ void __launch_bounds__(kBlock) k_mg_line_resid(const double* __restri
 // One block per line of the colour: solve the line's block system for the residual in r
 // and add the solution to x.  The recurrences are sequential along the line, so the block
 // stages the line's factors in chunks into shared memory and one thread runs them there
-// (forward substitution writes z over r; backward substitution adds u to x).
+// (forward substitution writes z over r; backward substitution adds u to x).  The factors
+// and the substitutions are float32: a dependent float64 chain costs ~1.6 us per line
+// vertex on this GPU (float64 issues at 1/64 of the float32 rate), and a smoother needs no
+// more than float32 accuracy; residuals, corrections and the CG stay float64.
 constexpr int kLineChunk = 128;
 
-__global__ void __launch_bounds__(64) k_mg_line_solve(const double* __restrict__ F, double* __restrict__ r,
+__global__ void __launch_bounds__(64) k_mg_line_solve(const float* __restrict__ F, double* __restrict__ r,
                                                       double* __restrict__ x, int nx, int ny, int dir, int color) {
-  __shared__ double sf[kLineChunk * kMgLineFactor];
-  __shared__ double sv[kLineChunk * 3];
+  __shared__ float sf[kLineChunk * kMgLineFactor];
+  __shared__ float sv[kLineChunk * 3];
   const int l = color + 5 * blockIdx.x;
   if (l >= nx + ny - 1) return;
   int x0, y0;
   const int len = mg_line(l, nx, ny, dir, x0, y0);
   auto vert = [&](int k) { return (y0 + k) * nx + x0 + dir * k; };
-  double z1[3] = {0, 0, 0}, z2[3] = {0, 0, 0};
+  float z1[3] = {0.f, 0.f, 0.f}, z2[3] = {0.f, 0.f, 0.f};
   for (int c0 = 0; c0 < len; c0 += kLineChunk) {   // forward: z_k = r_k - L(k,k-1) z_{k-1} - L(k,k-2) z_{k-2}
     const int cn = min(kLineChunk, len - c0);
     for (int t = threadIdx.x; t < cn * 18; t += blockDim.x)
       sf[(t / 18) * kMgLineFactor + t % 18] = F[(size_t)vert(c0 + t / 18) * kMgLineFactor + t % 18];
-    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = r[3 * (size_t)vert(c0 + t / 3) + t % 3];
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = (float)r[3 * (size_t)vert(c0 + t / 3) + t % 3];
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int k = 0; k < cn; ++k) {
-        const double* f = sf + k * kMgLineFactor;
-        double z[3];
+        const float* f = sf + k * kMgLineFactor;
+        float z[3];
         for (int a = 0; a < 3; ++a)
           z[a] = sv[3 * k + a] - (f[3 * a] * z1[0] + f[3 * a + 1] * z1[1] + f[3 * a + 2] * z1[2]) -
                  (f[9 + 3 * a] * z2[0] + f[9 + 3 * a + 1] * z2[1] + f[9 + 3 * a + 2] * z2[2]);
@@ -1073,25 +1076,25 @@ __global__ void __launch_bounds__(64) k_mg_line_solve(const double* __restrict__
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) r[3 * (size_t)vert(c0 + t / 3) + t % 3] = sv[t];
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) r[3 * (size_t)vert(c0 + t / 3) + t % 3] = (double)sv[t];
     __syncthreads();
   }
   // backward: u_k = D_k^-1 z_k - L(k+1,k)^T u_{k+1} - L(k+2,k)^T u_{k+2}
-  double u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
-  double L1n[9], L2n[9], L2nn[9];   // L(k+1, k), L(k+1, k-1), L(k+2, k)
-  for (int t = 0; t < 9; ++t) L1n[t] = L2n[t] = L2nn[t] = 0.0;
+  float u1[3] = {0.f, 0.f, 0.f}, u2[3] = {0.f, 0.f, 0.f};
+  float L1n[9], L2n[9], L2nn[9];   // L(k+1, k), L(k+1, k-1), L(k+2, k)
+  for (int t = 0; t < 9; ++t) L1n[t] = L2n[t] = L2nn[t] = 0.f;
   for (int c1 = len; c1 > 0; c1 -= kLineChunk) {
     const int c0 = max(0, c1 - kLineChunk), cn = c1 - c0;
     for (int t = threadIdx.x; t < cn * kMgLineFactor; t += blockDim.x)
       sf[t] = F[(size_t)vert(c0 + t / kMgLineFactor) * kMgLineFactor + t % kMgLineFactor];
-    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = r[3 * (size_t)vert(c0 + t / 3) + t % 3];
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = (float)r[3 * (size_t)vert(c0 + t / 3) + t % 3];
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int k = cn - 1; k >= 0; --k) {
-        const double* f = sf + k * kMgLineFactor;
-        double u[3];
+        const float* f = sf + k * kMgLineFactor;
+        float u[3];
         for (int a = 0; a < 3; ++a) {
-          const double w = f[18 + 3 * a] * sv[3 * k] + f[18 + 3 * a + 1] * sv[3 * k + 1] + f[18 + 3 * a + 2] * sv[3 * k + 2];
+          const float w = f[18 + 3 * a] * sv[3 * k] + f[18 + 3 * a + 1] * sv[3 * k + 1] + f[18 + 3 * a + 2] * sv[3 * k + 2];
           u[a] = w - (L1n[a] * u1[0] + L1n[3 + a] * u1[1] + L1n[6 + a] * u1[2]) -
                  (L2nn[a] * u2[0] + L2nn[3 + a] * u2[1] + L2nn[6 + a] * u2[2]);
         }
@@ -1108,7 +1111,7 @@ __global__ void __launch_bounds__(64) k_mg_line_solve(const double* __restrict__
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) x[3 * (size_t)vert(c0 + t / 3) + t % 3] += sv[t];
+    for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) x[3 * (size_t)vert(c0 + t / 3) + t % 3] += (double)sv[t];
     __syncthreads();
   }
 }
@@ -1228,7 +1231,7 @@ size_t mg_workspace_doubles(int nx, int ny, bool lines) {
   }
   const size_t nc3 = 3 * (size_t)x * y;
   tot += nc3 * nc3;
-  if (lines) tot += (size_t)nx * ny * kMgLineFactor;
+  if (lines) tot += ((size_t)nx * ny * kMgLineFactor + 1) / 2;   // float32 factors
   return tot;
 }
 
@@ -1259,7 +1262,7 @@ void mg_carve(MgPlan& g, double* base, int nx, int ny, int line_dir, int sweeps)
   }
   g.cinv = p;
   p += 9 * (size_t)x * y * x * y;
-  g.lfac = line_dir ? p : nullptr;
+  g.lfac = line_dir ? reinterpret_cast<float*>(p) : nullptr;
 }
 
 void launch_mg_asm_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
@@ -1297,7 +1300,7 @@ void launch_mg_coarse_inverse(const MgLevel& l, const float4* X, double* cinv, c
   k_mg_coarse_inverse<<<1, 256, 0, s>>>(l.A, X, l.nx, l.ny, cinv);
 }
 
-void launch_mg_line_factor(const MgLevel& l, const float4* X, int dir, double* lfac, cudaStream_t s) {
+void launch_mg_line_factor(const MgLevel& l, const float4* X, int dir, float* lfac, cudaStream_t s) {
   const int lines = l.nx + l.ny - 1;
   k_mg_line_factor<<<grid_for(lines), kBlock, 0, s>>>(l.A, X, l.nx, l.ny, dir, lfac);
 }
@@ -1314,7 +1317,7 @@ void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, co
   k_mg_line_resid<<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny, dir, color);
 }
 
-void launch_mg_line_solve(const MgLevel& l, const double* lfac, double* r, double* x, int dir, int color,
+void launch_mg_line_solve(const MgLevel& l, const float* lfac, double* r, double* x, int dir, int color,
                           cudaStream_t s) {
   const int lines = (l.nx + l.ny - 1 - color + 4) / 5;
   if (lines > 0) k_mg_line_solve<<<lines, 64, 0, s>>>(lfac, r, x, l.nx, l.ny, dir, color);

@@ -32,7 +32,7 @@ namespace xpbd {
 
 constexpr int kMgSlots = 25;            // 5 x 5 stencil offsets
 constexpr int kMgBlock = kMgSlots * 9;  // float64 per vertex of a level matrix
-constexpr int kMgLineFactor = 27;       // per vertex: two sub-diagonal blocks and an inverse pivot
+constexpr int kMgLineFactor = 27;       // float32 per vertex: two sub-diagonal blocks, an inverse pivot
 constexpr int kMgMaxLevels = 32;        // halving any int side reaches <= 4 within 31 levels
 constexpr int kMgCoarseMax = 16;        // vertices of the densely inverted level
 
@@ -49,7 +49,7 @@ struct MgPlan {
   int levels = 0;
   MgLevel lv[kMgMaxLevels];
   double* cinv = nullptr;   // dense inverse of the coarsest level, (3 n_c)^2
-  double* lfac = nullptr;   // level-0 line factors [n0][27], or null without line smoothing
+  float* lfac = nullptr;    // level-0 line factors [n0][27] float32, or null without line smoothing
   int line_dir = 0;         // 0: point smoothing on level 0; +1: lines x - y = c; -1: lines x + y = c
   int sweeps = 1;
 };
@@ -73,13 +73,13 @@ void launch_mg_asm_memb(const MembRec* rec, int n, const double* blocks, double*
 void launch_mg_rap(const MgLevel& f, const MgLevel& c, const float4* X, cudaStream_t s);
 void launch_mg_dinv(const MgLevel& l, const float4* X, cudaStream_t s);
 void launch_mg_coarse_inverse(const MgLevel& l, const float4* X, double* cinv, cudaStream_t s);
-void launch_mg_line_factor(const MgLevel& l, const float4* X, int dir, double* lfac, cudaStream_t s);
+void launch_mg_line_factor(const MgLevel& l, const float4* X, int dir, float* lfac, cudaStream_t s);
 
 // V-cycle pieces.
 void launch_mg_point_gs(const MgLevel& l, const double* b, double* x, int color, cudaStream_t s);
 void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, int dir,
                           int color, cudaStream_t s);
-void launch_mg_line_solve(const MgLevel& l, const double* lfac, double* r, double* x, int dir, int color,
+void launch_mg_line_solve(const MgLevel& l, const float* lfac, double* r, double* x, int dir, int color,
                           cudaStream_t s);
 void launch_mg_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, cudaStream_t s);
 void launch_mg_restrict(const MgLevel& f, const double* r, const MgLevel& c, double* bc, cudaStream_t s);
