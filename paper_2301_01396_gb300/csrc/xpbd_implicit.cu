@@ -764,6 +764,52 @@ __device__ __forceinline__ void mg_row_apply(const double* __restrict__ A, const
   }
 }
 
+// The same product with a warp per row: lane s < 25 takes stencil slot s, and the three
+// sums are reduced over the warp in a fixed order (every lane gets them).  float64 issues
+// at 1/64 of the float32 rate on this GPU, so a thread that sums a whole row (225
+// multiply-adds) costs ~7 us however few rows a launch has; a warp per row costs ~1 us.
+__device__ __forceinline__ void mg_row_apply_warp(const double* __restrict__ A, const double* __restrict__ x, int v,
+                                                  int nx, int ny, double out[3]) {
+  const int lane = threadIdx.x & 31;
+  double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+  if (lane < kMgSlots) {
+    const int xx = v % nx + lane % 5 - 2, yy = v / nx + lane / 5 - 2;
+    if (xx >= 0 && xx < nx && yy >= 0 && yy < ny) {
+      const double* xj = x + 3 * ((size_t)yy * nx + xx);
+      const double x0 = xj[0], x1 = xj[1], x2 = xj[2];
+      const double* m = A + (size_t)v * kMgBlock + 9 * lane;
+      o0 = m[0] * x0 + m[1] * x1 + m[2] * x2;
+      o1 = m[3] * x0 + m[4] * x1 + m[5] * x2;
+      o2 = m[6] * x0 + m[7] * x1 + m[8] * x2;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    o0 += __shfl_xor_sync(0xffffffffu, o0, off);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, off);
+    o2 += __shfl_xor_sync(0xffffffffu, o2, off);
+  }
+  out[0] += o0;
+  out[1] += o1;
+  out[2] += o2;
+}
+
+// Item (row) index of this thread (WARP = false) or of this thread's warp (WARP = true);
+// with WARP every lane of a warp gets the same item, so early returns are warp-uniform.
+template <bool WARP>
+__device__ __forceinline__ int mg_item() {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  return WARP ? (t >> 5) : t;
+}
+
+template <bool WARP>
+__device__ __forceinline__ void mg_apply(const double* __restrict__ A, const double* __restrict__ x, int v, int nx, int ny,
+                                         double out[3]) {
+  if (WARP)
+    mg_row_apply_warp(A, x, v, nx, ny, out);
+  else
+    mg_row_apply(A, x, v, nx, ny, out);
+}
+
 __device__ __forceinline__ void mg_add(double* A0, int vi, int vj, int nx, int V, const double* B, double* flag) {
   if (vi < 0 || vj < 0 || vi >= V || vj >= V) {
     *flag = 1.0;
@@ -1021,19 +1067,26 @@ __global__ void __launch_bounds__(kBlock) k_mg_line_factor(const double* __restr
   }
 }
 
+// Residual of the colour's line vertices: item t is point t % L of the colour's line
+// t / L (L = min(nx, ny) bounds every line's length).
+template <bool WARP>
 __global__ void __launch_bounds__(kBlock) k_mg_line_resid(const double* __restrict__ A, const float4* __restrict__ X,
                                                           const double* __restrict__ b, const double* __restrict__ x,
-                                                          double* __restrict__ r, int nx, int ny, int dir, int color) {
-  XPBD_TID_OR_RETURN(nx * ny);
-  const int vx = i % nx, vy = i / nx;
-  const int l = dir > 0 ? vx - vy + ny - 1 : vx + vy;
-  if (l % 5 != color) return;
+                                                          double* __restrict__ r, int nx, int ny, int dir, int color,
+                                                          int items) {
+  const int t = mg_item<WARP>();
+  if (t >= items) return;
+  const int L = min(nx, ny);
+  const int l = color + 5 * (t / L), k = t % L;
+  if (l >= nx + ny - 1) return;
+  int x0, y0;
+  if (k >= mg_line(l, nx, ny, dir, x0, y0)) return;
+  const int i = (y0 + k) * nx + x0 + dir * k;
   double o[3] = {0.0, 0.0, 0.0};
-  if (!mg_pinned(X, i)) {
-    mg_row_apply(A, x, i, nx, ny, o);
-    for (int a = 0; a < 3; ++a) o[a] = b[3 * i + a] - o[a];
-  }
-  for (int a = 0; a < 3; ++a) r[3 * i + a] = o[a];
+  const bool pin = mg_pinned(X, i);
+  if (!pin) mg_apply<WARP>(A, x, i, nx, ny, o);
+  if (WARP && (threadIdx.x & 31) != 0) return;
+  for (int a = 0; a < 3; ++a) r[3 * i + a] = pin ? 0.0 : b[3 * i + a] - o[a];
 }
 
 // One block per line of the colour: solve the line's block system for the residual in r
@@ -1116,31 +1169,34 @@ __global__ void __launch_bounds__(64) k_mg_line_solve(const float* __restrict__ 
   }
 }
 
+template <bool WARP>
 __global__ void __launch_bounds__(kBlock) k_mg_point_gs(const double* __restrict__ A, const double* __restrict__ dinv,
                                                         const double* __restrict__ b, double* __restrict__ x, int nx,
                                                         int ny, int cx, int cy) {
   const int nxs = (nx - cx + 2) / 3, nys = (ny - cy + 2) / 3;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = mg_item<WARP>();
   if (t >= nxs * nys) return;
   const int v = (cy + 3 * (t / nxs)) * nx + cx + 3 * (t % nxs);
   double o[3] = {0.0, 0.0, 0.0};
-  mg_row_apply(A, x, v, nx, ny, o);
+  mg_apply<WARP>(A, x, v, nx, ny, o);
+  if (WARP && (threadIdx.x & 31) != 0) return;
   double r[3];
   for (int a = 0; a < 3; ++a) r[a] = b[3 * v + a] - o[a];
   const double* m = dinv + 9 * (size_t)v;
   for (int a = 0; a < 3; ++a) x[3 * v + a] += m[3 * a] * r[0] + m[3 * a + 1] * r[1] + m[3 * a + 2] * r[2];
 }
 
+template <bool WARP>
 __global__ void __launch_bounds__(kBlock) k_mg_resid(const double* __restrict__ A, const float4* __restrict__ X,
                                                      const double* __restrict__ b, const double* __restrict__ x,
                                                      double* __restrict__ r, int nx, int ny) {
-  XPBD_TID_OR_RETURN(nx * ny);
+  const int i = mg_item<WARP>();
+  if (i >= nx * ny) return;
   double o[3] = {0.0, 0.0, 0.0};
-  if (!mg_pinned(X, i)) {
-    mg_row_apply(A, x, i, nx, ny, o);
-    for (int a = 0; a < 3; ++a) o[a] = b[3 * i + a] - o[a];
-  }
-  for (int a = 0; a < 3; ++a) r[3 * i + a] = o[a];
+  const bool pin = mg_pinned(X, i);
+  if (!pin) mg_apply<WARP>(A, x, i, nx, ny, o);
+  if (WARP && (threadIdx.x & 31) != 0) return;
+  for (int a = 0; a < 3; ++a) r[3 * i + a] = pin ? 0.0 : b[3 * i + a] - o[a];
 }
 
 __global__ void __launch_bounds__(kBlock) k_mg_restrict(const double* __restrict__ r, int nxf, int nyf,
@@ -1305,16 +1361,30 @@ void launch_mg_line_factor(const MgLevel& l, const float4* X, int dir, float* lf
   k_mg_line_factor<<<grid_for(lines), kBlock, 0, s>>>(l.A, X, l.nx, l.ny, dir, lfac);
 }
 
+// Rows per launch up to which a warp per row beats a thread per row (one warp per row
+// keeps at most ~7 warps per SM sub-partition busy; beyond that the thread form's fewer
+// instructions win).
+constexpr int kMgWarpRows = 4096;
+
 void launch_mg_point_gs(const MgLevel& l, const double* b, double* x, int color, cudaStream_t s) {
   const int cx = color % 3, cy = color / 3;
   const int n = ((l.nx - cx + 2) / 3) * ((l.ny - cy + 2) / 3);
-  if (n > 0) k_mg_point_gs<<<grid_for(n), kBlock, 0, s>>>(l.A, l.dinv, b, x, l.nx, l.ny, cx, cy);
+  if (n <= 0) return;
+  if (n <= kMgWarpRows)
+    k_mg_point_gs<true><<<(n * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(l.A, l.dinv, b, x, l.nx, l.ny, cx, cy);
+  else
+    k_mg_point_gs<false><<<grid_for(n), kBlock, 0, s>>>(l.A, l.dinv, b, x, l.nx, l.ny, cx, cy);
 }
 
 void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, int dir,
                           int color, cudaStream_t s) {
-  const int n = l.nx * l.ny;
-  k_mg_line_resid<<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny, dir, color);
+  const int lines = (l.nx + l.ny - 1 - color + 4) / 5;
+  const int n = lines * std::min(l.nx, l.ny);
+  if (n <= 0) return;
+  if (n <= kMgWarpRows)
+    k_mg_line_resid<true><<<(n * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny, dir, color, n);
+  else
+    k_mg_line_resid<false><<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny, dir, color, n);
 }
 
 void launch_mg_line_solve(const MgLevel& l, const float* lfac, double* r, double* x, int dir, int color,
@@ -1325,7 +1395,10 @@ void launch_mg_line_solve(const MgLevel& l, const float* lfac, double* r, double
 
 void launch_mg_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, cudaStream_t s) {
   const int n = l.nx * l.ny;
-  k_mg_resid<<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny);
+  if (n <= kMgWarpRows)
+    k_mg_resid<true><<<(n * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny);
+  else
+    k_mg_resid<false><<<grid_for(n), kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny);
 }
 
 void launch_mg_restrict(const MgLevel& f, const double* r, const MgLevel& c, double* bc, cudaStream_t s) {
