@@ -1098,7 +1098,7 @@ __global__ void __launch_bounds__(kBlock) k_mg_line_resid(const double* __restri
 // more than float32 accuracy; residuals, corrections and the CG stay float64.
 constexpr int kLineChunk = 128;
 
-__global__ void __launch_bounds__(64) k_mg_line_solve(const float* __restrict__ F, double* __restrict__ r,
+__global__ void __launch_bounds__(256) k_mg_line_solve(const float* __restrict__ F, double* __restrict__ r,
                                                       double* __restrict__ x, int nx, int ny, int dir, int color) {
   __shared__ float sf[kLineChunk * kMgLineFactor];
   __shared__ float sv[kLineChunk * 3];
@@ -1115,6 +1115,7 @@ __global__ void __launch_bounds__(64) k_mg_line_solve(const float* __restrict__ 
     for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = (float)r[3 * (size_t)vert(c0 + t / 3) + t % 3];
     __syncthreads();
     if (threadIdx.x == 0) {
+#pragma unroll 4
       for (int k = 0; k < cn; ++k) {
         const float* f = sf + k * kMgLineFactor;
         float z[3];
@@ -1143,6 +1144,7 @@ __global__ void __launch_bounds__(64) k_mg_line_solve(const float* __restrict__ 
     for (int t = threadIdx.x; t < cn * 3; t += blockDim.x) sv[t] = (float)r[3 * (size_t)vert(c0 + t / 3) + t % 3];
     __syncthreads();
     if (threadIdx.x == 0) {
+#pragma unroll 4
       for (int k = cn - 1; k >= 0; --k) {
         const float* f = sf + k * kMgLineFactor;
         float u[3];
@@ -1390,7 +1392,7 @@ void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, co
 void launch_mg_line_solve(const MgLevel& l, const float* lfac, double* r, double* x, int dir, int color,
                           cudaStream_t s) {
   const int lines = (l.nx + l.ny - 1 - color + 4) / 5;
-  if (lines > 0) k_mg_line_solve<<<lines, 64, 0, s>>>(lfac, r, x, l.nx, l.ny, dir, color);
+  if (lines > 0) k_mg_line_solve<<<lines, 256, 0, s>>>(lfac, r, x, l.nx, l.ny, dir, color);
 }
 
 void launch_mg_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, cudaStream_t s) {
