@@ -276,7 +276,7 @@ typedef struct {
      3x3 float64 blocks, Galerkin coarse operators with bilinear prolongation down to at
      most 4x4 vertices (inverted densely), symmetric Gauss-Seidel smoothing.  The V-cycle is
      symmetric positive definite when A is (pd_project = 1 guarantees it).  Workspace:
-     about 2.4 KB of device memory per vertex (+216 B with line smoothing).             */
+     about 2.6 KB of device memory per vertex (+108 B with line smoothing).             */
   int32_t mg_nx, mg_ny;
   int32_t mg_lines;             /* level-0 smoother: 0 point Gauss-Seidel (9 colours);
                                    +1 / -1 exact solves along the grid diagonals
