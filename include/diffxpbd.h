@@ -275,7 +275,9 @@ typedef struct {
      grid direction; otherwise the call returns XPBD_ERR_INVALID.  Levels: 5x5 stencils of
      3x3 float64 blocks, Galerkin coarse operators with bilinear prolongation down to at
      most 4x4 vertices (inverted densely), symmetric Gauss-Seidel smoothing.  The V-cycle is
-     symmetric positive definite when A is (pd_project = 1 guarantees it).  Workspace:
+     symmetric positive definite when A is (pd_project = 1 guarantees it).  Each call
+     captures its V-cycle once into a CUDA graph on a private stream and replays it on
+     `stream` (launched directly if capture fails).  Workspace:
      about 2.6 KB of device memory per vertex (+108 B with line smoothing).             */
   int32_t mg_nx, mg_ny;
   int32_t mg_lines;             /* level-0 smoother: 0 point Gauss-Seidel (9 colours);
