@@ -735,15 +735,6 @@ __device__ __forceinline__ void mm3_sub_bt(const double* a, const double* b, dou
     for (int j = 0; j < 3; ++j) o[3 * i + j] -= a[3 * i] * b[3 * j] + a[3 * i + 1] * b[3 * j + 1] + a[3 * i + 2] * b[3 * j + 2];
 }
 
-// Bilinear prolongation weight of coarse index X for fine index x (nc coarse points).
-__device__ __forceinline__ double mg_w(int x, int X, int nc) {
-  const int d = x - 2 * X;
-  if (d == 0) return 1.0;
-  if (d == 1) return X + 1 < nc ? 0.5 : 1.0;
-  if (d == -1) return 0.5;
-  return 0.0;
-}
-
 __device__ __forceinline__ bool mg_pinned(const float4* X, int v) { return X && !(X[v].w > 0.f); }
 
 // out += (A x)_v over the 5 x 5 stencil.
@@ -1004,20 +995,6 @@ __global__ void __launch_bounds__(256) k_mg_coarse_solve(const double* __restric
   }
 }
 
-// Lines of direction dir (+1: x - y = const, -1: x + y = const), numbered 0 .. nx + ny - 2;
-// point k of line l is (x0 + dir k, y0 + k).
-__device__ __forceinline__ int mg_line(int l, int nx, int ny, int dir, int& x0, int& y0) {
-  if (dir > 0) {
-    const int c = l - (ny - 1);
-    y0 = c < 0 ? -c : 0;
-    x0 = y0 + c;
-    return min(ny - y0, nx - x0);
-  }
-  y0 = l > nx - 1 ? l - (nx - 1) : 0;
-  x0 = l - y0;
-  return min(ny - y0, x0 + 1);
-}
-
 // Block LDL^T of every line's pentadiagonal block matrix (its vertices' couplings along the
 // line); pinned vertices are left out (zero inverse pivot, no coupling).  Per vertex:
 // [L(k, k-1) | L(k, k-2) | D_k^-1].
@@ -1067,21 +1044,15 @@ __global__ void __launch_bounds__(kBlock) k_mg_line_factor(const double* __restr
   }
 }
 
-// Residual of the colour's line vertices: item t is point t % L of the colour's line
-// t / L (L = min(nx, ny) bounds every line's length).
+// Residual of the colour's line vertices (items as mg_line_item numbers them).
 template <bool WARP>
 __global__ void __launch_bounds__(kBlock) k_mg_line_resid(const double* __restrict__ A, const float4* __restrict__ X,
                                                           const double* __restrict__ b, const double* __restrict__ x,
                                                           double* __restrict__ r, int nx, int ny, int dir, int color,
                                                           int items) {
   const int t = mg_item<WARP>();
-  if (t >= items) return;
-  const int L = min(nx, ny);
-  const int l = color + 5 * (t / L), k = t % L;
-  if (l >= nx + ny - 1) return;
-  int x0, y0;
-  if (k >= mg_line(l, nx, ny, dir, x0, y0)) return;
-  const int i = (y0 + k) * nx + x0 + dir * k;
+  int i;
+  if (t >= items || !mg_line_item(t, nx, ny, dir, color, i)) return;
   double o[3] = {0.0, 0.0, 0.0};
   const bool pin = mg_pinned(X, i);
   if (!pin) mg_apply<WARP>(A, x, i, nx, ny, o);
@@ -1175,10 +1146,9 @@ template <bool WARP>
 __global__ void __launch_bounds__(kBlock) k_mg_point_gs(const double* __restrict__ A, const double* __restrict__ dinv,
                                                         const double* __restrict__ b, double* __restrict__ x, int nx,
                                                         int ny, int cx, int cy) {
-  const int nxs = (nx - cx + 2) / 3, nys = (ny - cy + 2) / 3;
   const int t = mg_item<WARP>();
-  if (t >= nxs * nys) return;
-  const int v = (cy + 3 * (t / nxs)) * nx + cx + 3 * (t % nxs);
+  if (t >= mg_color_points(nx, ny, 3 * cy + cx)) return;
+  const int v = mg_color_point(t, nx, 3 * cy + cx);
   double o[3] = {0.0, 0.0, 0.0};
   mg_apply<WARP>(A, x, v, nx, ny, o);
   if (WARP && (threadIdx.x & 31) != 0) return;
@@ -1276,53 +1246,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(const double* __restrict__
 
 }  // namespace
 
-size_t mg_workspace_doubles(int nx, int ny, bool lines) {
-  size_t tot = 0;
-  int x = nx, y = ny, levels = 0;
-  while (true) {
-    const size_t n = (size_t)x * y;
-    tot += n * (kMgBlock + 9 + 9);   // A, dinv, x, b, r
-    ++levels;
-    if ((x <= 4 && y <= 4) || levels == kMgMaxLevels) break;
-    x = (x + 1) / 2;
-    y = (y + 1) / 2;
-  }
-  const size_t nc3 = 3 * (size_t)x * y;
-  tot += nc3 * nc3;
-  if (lines) tot += ((size_t)nx * ny * kMgLineFactor + 1) / 2;   // float32 factors
-  return tot;
-}
-
-void mg_carve(MgPlan& g, double* base, int nx, int ny, int line_dir, int sweeps) {
-  g = MgPlan();
-  g.line_dir = line_dir;
-  g.sweeps = sweeps;
-  int x = nx, y = ny;
-  double* p = base;
-  while (true) {
-    MgLevel& L = g.lv[g.levels++];
-    const size_t n = (size_t)x * y;
-    L.nx = x;
-    L.ny = y;
-    L.A = p;
-    p += n * kMgBlock;
-    L.dinv = p;
-    p += 9 * n;
-    L.x = p;
-    p += 3 * n;
-    L.b = p;
-    p += 3 * n;
-    L.r = p;
-    p += 3 * n;
-    if ((x <= 4 && y <= 4) || g.levels == kMgMaxLevels) break;
-    x = (x + 1) / 2;
-    y = (y + 1) / 2;
-  }
-  g.cinv = p;
-  p += 9 * (size_t)x * y * x * y;
-  g.lfac = line_dir ? reinterpret_cast<float*>(p) : nullptr;
-}
-
 void launch_mg_asm_mass_contacts(const float4* X, const uint8_t* cflags, const float2* lamc, Collide c, bool pd,
                                  double* A0, int V, cudaStream_t s) {
   if (V > 0) k_mg_mass_contacts<<<grid_for(V), kBlock, 0, s>>>(X, cflags, lamc, c, pd, A0, V);
@@ -1370,7 +1293,7 @@ constexpr int kMgWarpRows = 4096;
 
 void launch_mg_point_gs(const MgLevel& l, const double* b, double* x, int color, cudaStream_t s) {
   const int cx = color % 3, cy = color / 3;
-  const int n = ((l.nx - cx + 2) / 3) * ((l.ny - cy + 2) / 3);
+  const int n = mg_color_points(l.nx, l.ny, color);
   if (n <= 0) return;
   if (n <= kMgWarpRows)
     k_mg_point_gs<true><<<(n * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(l.A, l.dinv, b, x, l.nx, l.ny, cx, cy);
@@ -1380,8 +1303,7 @@ void launch_mg_point_gs(const MgLevel& l, const double* b, double* x, int color,
 
 void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, const double* x, double* r, int dir,
                           int color, cudaStream_t s) {
-  const int lines = (l.nx + l.ny - 1 - color + 4) / 5;
-  const int n = lines * std::min(l.nx, l.ny);
+  const int n = mg_line_items(l.nx, l.ny, color);
   if (n <= 0) return;
   if (n <= kMgWarpRows)
     k_mg_line_resid<true><<<(n * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(l.A, X, b, x, r, l.nx, l.ny, dir, color, n);
@@ -1391,7 +1313,7 @@ void launch_mg_line_resid(const MgLevel& l, const float4* X, const double* b, co
 
 void launch_mg_line_solve(const MgLevel& l, const float* lfac, double* r, double* x, int dir, int color,
                           cudaStream_t s) {
-  const int lines = (l.nx + l.ny - 1 - color + 4) / 5;
+  const int lines = mg_color_lines(l.nx, l.ny, color);
   if (lines > 0) k_mg_line_solve<<<lines, 256, 0, s>>>(lfac, r, x, l.nx, l.ny, dir, color);
 }
 

@@ -27,37 +27,9 @@
 #pragma once
 
 #include "xpbd_kernels.cuh"
+#include "xpbd_mg_index.h"
 
 namespace xpbd {
-
-constexpr int kMgSlots = 25;            // 5 x 5 stencil offsets
-constexpr int kMgBlock = kMgSlots * 9;  // float64 per vertex of a level matrix
-constexpr int kMgLineFactor = 27;       // float32 per vertex: two sub-diagonal blocks, an inverse pivot
-constexpr int kMgMaxLevels = 32;        // halving any int side reaches <= 4 within 31 levels
-constexpr int kMgCoarseMax = 16;        // vertices of the densely inverted level
-
-struct MgLevel {
-  int nx = 0, ny = 0;
-  double* A = nullptr;     // [n][25][9]
-  double* dinv = nullptr;  // [n][9] inverse diagonal blocks (zero where a row is empty or pinned)
-  double* x = nullptr;     // [n][3] correction (level 0: the caller's output)
-  double* b = nullptr;     // [n][3] right-hand side (level 0: the caller's input)
-  double* r = nullptr;     // [n][3] residual / line-solve scratch
-};
-
-struct MgPlan {
-  int levels = 0;
-  MgLevel lv[kMgMaxLevels];
-  double* cinv = nullptr;   // dense inverse of the coarsest level, (3 n_c)^2
-  float* lfac = nullptr;    // level-0 line factors [n0][27] float32, or null without line smoothing
-  int line_dir = 0;         // 0: point smoothing on level 0; +1: lines x - y = c; -1: lines x + y = c
-  int sweeps = 1;
-};
-
-// float64 count of the workspace for an nx x ny grid (levels, coarse inverse, line factors).
-size_t mg_workspace_doubles(int nx, int ny, bool lines);
-// Lays the plan's arrays out in `base` (mg_workspace_doubles of them).
-void mg_carve(MgPlan& g, double* base, int nx, int ny, int line_dir, int sweeps);
 
 // Level-0 assembly (A0 zeroed by the caller): mass and contact blocks, then the blocks of
 // one colour's records at a time (records of one colour share no vertex, so their rows
