@@ -1418,12 +1418,17 @@ struct VcycleGraph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t e = nullptr;
   cudaStream_t cs = nullptr;
+  mutable cudaStream_t replayed_on = nullptr;   // waited for before the graph is destroyed
+  mutable bool replayed = false;
   int64_t launches = 0, units = 0;
   double bytes = 0.0;
   VcycleGraph() = default;
   VcycleGraph(const VcycleGraph&) = delete;
   VcycleGraph& operator=(const VcycleGraph&) = delete;
   ~VcycleGraph() {
+    // Every step's CG loop ends with a stream synchronisation, so on the normal path no
+    // replay is in flight here; on an early error return one may be.
+    if (replayed) cudaStreamSynchronize(replayed_on);
     if (e) cudaGraphExecDestroy(e);
     if (g) cudaGraphDestroy(g);
     if (cs) cudaStreamDestroy(cs);
@@ -1462,6 +1467,8 @@ struct VcycleGraph {
     return ok;
   }
   cudaError_t run(xpbd_solver* h, cudaStream_t s) const {
+    replayed = true;
+    replayed_on = s;
     h->launches[XPBD_K_ADJ_OTHER] += launches;
     h->units[XPBD_K_ADJ_OTHER] += units;
     h->alg_bytes[XPBD_K_ADJ_OTHER] += bytes;
